@@ -1,0 +1,383 @@
+"""Plain FP64 CPU oracle for the shifted Grünwald–Letnikov fractional-diffusion
+solvers of Massei, Mazza, Robol, "Fast solvers for two-dimensional fractional
+diffusion equations using rank structured matrices" (arXiv:1804.05522).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+benchmark's CPU-baseline leg may import this module.  It shares no code with
+the CUDA path and never calls it.
+
+Every function is slow on purpose: it writes the definition out (dense
+matrices, dense LU, real-Schur Bartels–Stewart, Kronecker brute force), using
+numpy / scipy LAPACK routines only as single library steps.
+
+Parity status per function (what pins it, see tests/test_oracle_pins.py):
+  gl_weights                 pinned: closed Γ form, g_1=-α, ordering, partial
+                             sums, α∈{1,2} exact cases
+  gl_toeplitz / fd_operator  pinned: α=2 Laplacian, SDD, M-matrix signs,
+                             manufactured-solution first-order convergence
+  hodlr_tree                 pinned: brute-force enumeration of the split rule
+  norm2_power                pinned: vs dense SVD
+  aca_partial_pivot          pinned: exact recovery of exactly-low-rank inputs
+  truncate_lowrank           pinned: prescribed singular values
+  hodlr_reference            pinned: per-block SVD error bound, rank bounds
+  solve_dense                pinned: residual / library cross-check
+  sylvester_bartels_stewart  pinned: Kronecker brute force, α=2 DST closed form
+  apply_fd_operator_fft      pinned: dense product
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+from scipy.linalg import lapack
+
+
+# ---------------------------------------------------------------------------
+# §2.1, Eq. (Grun) and §3.4.2: Grünwald–Letnikov weights
+# ---------------------------------------------------------------------------
+def gl_weights(alpha: float, K: int) -> np.ndarray:
+    """g_0..g_K of g_k = (-1)^k binom(α, k), Eq. (Grun), §2.1.
+
+    Evaluated by the recurrence of §3.4.2 written as g_k = g_{k-1} (1 - (α+1)/k):
+    one correctly rounded division, subtraction and multiplication per step,
+    in that order (Python floats are IEEE doubles and are never contracted).
+    """
+    g = np.empty(K + 1, dtype=np.float64)
+    g[0] = 1.0
+    a1 = alpha + 1.0
+    prev = 1.0
+    for k in range(1, K + 1):
+        q = a1 / float(k)
+        f = 1.0 - q
+        prev = prev * f
+        g[k] = prev
+    return g
+
+
+def gl_toeplitz(alpha: float, N: int) -> np.ndarray:
+    """T_{α,N} = -[g_{i-j+1}]  (lower Hessenberg Toeplitz, Eq. (toeplitz_FD), §2.2.1)."""
+    g = gl_weights(alpha, N)
+    T = np.zeros((N, N))
+    for i in range(N):
+        for j in range(0, min(N, i + 2)):
+            T[i, j] = -g[i - j + 1]
+    return T
+
+
+def fd_scale(op) -> float:
+    """c = Δt / Δx^α, the factor in front of D_+T + D_-Tᵀ in Eq. (system_FD)."""
+    return op.dt * op.h ** (-op.alpha)
+
+
+def fd_operator(op) -> np.ndarray:
+    """Dense A = s I + (Δt/Δx^α)(D_+ T + D_- Tᵀ), Eq. (system_FD) §2.2.1.
+
+    s = 1 gives the 1D implicit-Euler matrix; s = 1/2 gives each factor of the
+    2D Kronecker form of §4.2 (I⊗(½I - ΔtM) + (½I - ΔtM)⊗I).
+    """
+    T = gl_toeplitz(op.alpha, op.N)
+    c = fd_scale(op)
+    return op.shift * np.eye(op.N) + c * (op.d_plus[:, None] * T + op.d_minus[:, None] * T.T)
+
+
+# ---------------------------------------------------------------------------
+# §3.4.1, Eq. (HODLRpart): HODLR partition
+# ---------------------------------------------------------------------------
+def hodlr_tree(N: int, leaf: int):
+    """Node ranges [lo, hi) per level; a node of size n splits into ⌊n/2⌋, ⌈n/2⌉
+    (Eq. (HODLRpart)).  Reading of 'until we reach a minimal dimension': every
+    node of a level splits while the largest node of that level exceeds `leaf`,
+    so all leaves sit on one level and have size <= leaf.
+    """
+    levels = [[(0, N)]]
+    while max(hi - lo for lo, hi in levels[-1]) > leaf:
+        nxt = []
+        for lo, hi in levels[-1]:
+            mid = lo + (hi - lo) // 2
+            nxt.append((lo, mid))
+            nxt.append((mid, hi))
+        levels.append(nxt)
+    return levels
+
+
+# ---------------------------------------------------------------------------
+# §3.4.1: truncation relative to ||A||_2
+# ---------------------------------------------------------------------------
+def norm2_power(A: np.ndarray, iters: int = 30) -> float:
+    """Estimate of ||A||_2 by `iters` power steps on AᵀA from the normalised
+    all-ones vector (the paper does not say how ||A||_2 is obtained)."""
+    n = A.shape[1]
+    v = np.full(n, 1.0 / math.sqrt(n))
+    s = 0.0
+    for _ in range(iters):
+        w = A.T @ (A @ v)
+        s = float(np.linalg.norm(w))
+        if s == 0.0:
+            return 0.0
+        v = w / s
+    return math.sqrt(s)
+
+
+def eps_rank(Y: np.ndarray, abstol: float) -> int:
+    """Number of singular values above `abstol` (ε-rank with ε||X|| = abstol, §3)."""
+    if Y.size == 0:
+        return 0
+    s = np.linalg.svd(Y, compute_uv=False)
+    return int(np.sum(s > abstol))
+
+
+def truncate_lowrank(U: np.ndarray, V: np.ndarray, abstol: float):
+    """Recompression of U Vᵀ: reduced QR of both factors, SVD of the small core,
+    drop singular values <= abstol (§4.1, the QR+SVD recompression cited there).
+    Returns (U', V') with U' = Q_U W Σ, V' = Q_V Z."""
+    if U.shape[1] == 0:
+        return U.copy(), V.copy()
+    Qu, Ru = np.linalg.qr(U)
+    Qv, Rv = np.linalg.qr(V)
+    W, s, Zt = np.linalg.svd(Ru @ Rv.T)
+    r = int(np.sum(s > abstol))
+    return (Qu @ W[:, :r]) * s[:r], Qv @ Zt[:r].T
+
+
+# ---------------------------------------------------------------------------
+# Adaptive cross approximation (replaces the two-sided Lanczos of §3.4.2)
+# ---------------------------------------------------------------------------
+def aca_partial_pivot(row_fn, col_fn, m: int, n: int, abstol: float, maxrank: int):
+    """Textbook ACA with partial pivoting on an m x n matrix given by its rows
+    and columns.
+
+    Operation order (fixed so that another FP64 implementation can reproduce the
+    pivots exactly):
+      * residual row:    r = a(i*,:) ; for l < k: r = r - u_l[i*] * v_l   (mul, then sub)
+      * column pivot:    j* = first argmax over unused columns of |r_j|
+      * v_k = r / r[j*]
+      * residual column: c = a(:,j*) ; for l < k: c = c - u_l * v_l[j*]
+      * u_k = c
+      * stop after term k when (Σ u_k²)(Σ v_k²) <= abstol², both sums taken
+        sequentially from index 0 (products rounded before the add)
+      * next row pivot:  first argmax over unused rows of |u_k|
+    A residual row that is exactly zero marks the row used and moves to the
+    lowest-index unused row.  Returns (U (m x k), V (n x k), rows, cols, converged).
+    """
+    U, V, rows, cols = [], [], [], []
+    used_r = np.zeros(m, dtype=bool)
+    used_c = np.zeros(n, dtype=bool)
+    i_star = 0
+    tol2 = abstol * abstol
+    converged = False
+    while len(U) < maxrank:
+        r = np.array(row_fn(i_star), dtype=np.float64)
+        for l in range(len(U)):
+            r = r - U[l][i_star] * V[l]
+        used_r[i_star] = True
+        absr = np.where(used_c, -1.0, np.abs(r))
+        j_star = int(np.argmax(absr))
+        if absr[j_star] <= 0.0:
+            free = np.flatnonzero(~used_r)
+            if free.size == 0:
+                converged = True
+                break
+            i_star = int(free[0])
+            continue
+        v = r / r[j_star]
+        c = np.array(col_fn(j_star), dtype=np.float64)
+        for l in range(len(U)):
+            c = c - U[l] * V[l][j_star]
+        u = c
+        used_c[j_star] = True
+        U.append(u)
+        V.append(v)
+        rows.append(i_star)
+        cols.append(j_star)
+        su = np.cumsum(u * u)[-1]
+        sv = np.cumsum(v * v)[-1]
+        if su * sv <= tol2:
+            converged = True
+            break
+        absu = np.where(used_r, -1.0, np.abs(u))
+        i_next = int(np.argmax(absu))
+        if absu[i_next] < 0.0:
+            converged = True
+            break
+        i_star = i_next
+    k = len(U)
+    Um = np.stack(U, 1) if k else np.zeros((m, 0))
+    Vm = np.stack(V, 1) if k else np.zeros((n, 0))
+    return Um, Vm, rows, cols, converged
+
+
+def toeplitz_lower_block_entries(g: np.ndarray, N: int):
+    """Row / column accessors of the top-level subdiagonal block T21 of
+    T_{α,N}: rows N1..N-1, columns 0..N1-1, entries -g_{N1+i-j+1}
+    (§3.4.2: T21 contains every lower off-diagonal block by restriction;
+    entries as in the proof of Lemma lem:fd-qsrank)."""
+    N1 = N // 2
+    N2 = N - N1
+
+    def row(i):
+        return -g[N1 + i - np.arange(N1) + 1]
+
+    def col(j):
+        return -g[N1 + np.arange(N2) - j + 1]
+
+    return N1, N2, row, col
+
+
+def hodlr_reference(A: np.ndarray, leaf: int, eps: float, normA: float | None = None):
+    """Definition of the HODLR approximation of §3.4.1: each off-diagonal block
+    of Eq. (HODLRpart), at every level, truncated at ε||A||_2 by its SVD.
+    Returns (tree, {(lo,hi): (rank12, rank21)}, abstol)."""
+    N = A.shape[0]
+    tree = hodlr_tree(N, leaf)
+    nrm = norm2_power(A) if normA is None else normA
+    abstol = eps * nrm
+    ranks = {}
+    for lvl in tree[:-1]:
+        for lo, hi in lvl:
+            mid = lo + (hi - lo) // 2
+            ranks[(lo, hi)] = (eps_rank(A[lo:mid, mid:hi], abstol), eps_rank(A[mid:hi, lo:mid], abstol))
+    return tree, ranks, abstol
+
+
+# ---------------------------------------------------------------------------
+# Lemma beckermann, Lemma lem:fd-qsrank, Corollary cor:fd-qsrank (§3.2)
+# ---------------------------------------------------------------------------
+def beckermann_bound(N: int, eps: float) -> int:
+    """𝔅(N, ε) = 2 + 2⌈(2/π²) log(4N/π) log(16/ε)⌉ (Lemma beckermann)."""
+    return 2 + 2 * math.ceil((2.0 / math.pi ** 2) * math.log(4.0 * N / math.pi) * math.log(16.0 / eps))
+
+
+def qsrank_bound_T(N: int, eps: float) -> int:
+    """qsrank_ε(T_{α,N}) <= 𝔅(N, ε/2) (Lemma lem:fd-qsrank)."""
+    return beckermann_bound(N, eps / 2.0)
+
+
+def qsrank_bound_M(N: int, eps: float, normM: float, normT: float, maxD: float) -> int:
+    """qsrank_ε(M) <= 1 + 𝔅(N, ε̂/2), ε̂ = ||M|| ε / (||T|| max||D±||) (Corollary cor:fd-qsrank)."""
+    eps_hat = normM * eps / (normT * maxD)
+    return 1 + beckermann_bound(N, eps_hat / 2.0)
+
+
+# ---------------------------------------------------------------------------
+# §3.5: 1D time stepping — dense LU oracle
+# ---------------------------------------------------------------------------
+def solve_dense(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """x = A^{-1} b by dense LU with partial pivoting (LAPACK getrf/getrs)."""
+    lu, piv = sla.lu_factor(A)
+    return sla.lu_solve((lu, piv), B)
+
+
+def fde1d_run(w, steps: int | None = None):
+    """Implicit Euler, Eq. (system_FD): A u^{(m)} = u^{(m-1)} + Δt f^{(m)}, m = 1..M,
+    f sampled at the new time level t_m = m Δt.  Returns u^{(M)}."""
+    op = w.ops[0]
+    A = fd_operator(op)
+    lu, piv = sla.lu_factor(A)
+    u = w.u0.copy()
+    M = w.steps if steps is None else steps
+    for m in range(1, M + 1):
+        b = u + w.dt * w.source(m * w.dt)
+        u = sla.lu_solve((lu, piv), b)
+    return u
+
+
+# ---------------------------------------------------------------------------
+# §4.2, Eq. (sylv-timestepping): 2D step as a Sylvester equation
+# ---------------------------------------------------------------------------
+def sylvester_bartels_stewart(A: np.ndarray, B: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """Solve A X + X Bᵀ = C by Bartels–Stewart: real Schur forms A = Q S Qᵀ,
+    B = Z R Zᵀ (LAPACK gees), quasi-triangular S Y + Y Rᵀ = Qᵀ C Z (LAPACK trsyl),
+    X = Q Y Zᵀ."""
+    S, Q = sla.schur(A, output="real")
+    R, Z = sla.schur(B, output="real")
+    Ct = Q.T @ C @ Z
+    Y, scale, info = lapack.dtrsyl(S, R, Ct, trana="N", tranb="T", isgn=1)
+    if info < 0:
+        raise RuntimeError(f"dtrsyl info={info}")
+    return Q @ (Y / scale) @ Z.T
+
+
+class SchurSylvester:
+    """Bartels–Stewart with the two real Schur forms computed once (the
+    coefficients of Eq. (sylv-timestepping) do not depend on time)."""
+
+    def __init__(self, A: np.ndarray, B: np.ndarray):
+        self.S, self.Q = sla.schur(A, output="real")
+        self.R, self.Z = sla.schur(B, output="real")
+
+    def solve(self, C: np.ndarray) -> np.ndarray:
+        Ct = self.Q.T @ C @ self.Z
+        Y, scale, info = lapack.dtrsyl(self.S, self.R, Ct, trana="N", tranb="T", isgn=1)
+        if info < 0:
+            raise RuntimeError(f"dtrsyl info={info}")
+        return self.Q @ (Y / scale) @ self.Z.T
+
+
+def sylvester_kron(A: np.ndarray, B: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """Kronecker brute force: (I ⊗ A + B ⊗ I) vec X = vec C with column-major
+    vec (vec(A X Bᵀ) = (B ⊗ A) vec X, §4.2)."""
+    n, m = C.shape
+    K = np.kron(np.eye(m), A) + np.kron(B, np.eye(n))
+    x = np.linalg.solve(K, C.reshape(-1, order="F"))
+    return x.reshape((n, m), order="F")
+
+
+def fde2d_rhs(w, U: np.ndarray, m: int) -> np.ndarray:
+    """C = U^{(m)} + Δt F^{(m+1)} (Eq. (sylv-timestepping) with the Δt of the
+    implicit Euler step written out; F sampled at t_{m+1} = (m+1) Δt)."""
+    return U + w.dt * w.source((m + 1) * w.dt)
+
+
+def fde2d_run(w, steps: int | None = None, return_all: bool = False):
+    """M implicit-Euler steps of the 2D problem, each one Sylvester equation
+    A_x U^{(m+1)} + U^{(m+1)} A_yᵀ = U^{(m)} + Δt F^{(m+1)} (Eq. (sylv-timestepping))."""
+    Ax = fd_operator(w.ops[0])
+    Ay = fd_operator(w.ops[1])
+    solver = SchurSylvester(Ax, Ay)
+    U = w.u0.copy()
+    M = w.steps if steps is None else steps
+    hist = []
+    for m in range(M):
+        U = solver.solve(fde2d_rhs(w, U, m))
+        if return_all:
+            hist.append(U.copy())
+    return (U, hist) if return_all else U
+
+
+# ---------------------------------------------------------------------------
+# Structured operator application for residual certificates at large N
+# ---------------------------------------------------------------------------
+def _fftconv(a: np.ndarray, b: np.ndarray, axis: int) -> np.ndarray:
+    """Linear convolution along `axis` by zero-padded FFT (numpy library FFT)."""
+    n = a.shape[0] + b.shape[axis] - 1
+    P = 1 << (n - 1).bit_length()
+    fa = np.fft.rfft(a, P)
+    fb = np.fft.rfft(b, P, axis=axis)
+    shape = [1] * b.ndim
+    shape[axis] = fa.shape[0]
+    return np.fft.irfft(fb * fa.reshape(shape), P, axis=axis)
+
+
+def apply_fd_operator_fft(op, X: np.ndarray, axis: int = 0) -> np.ndarray:
+    """A applied along `axis` of X (A X for axis 0, X Aᵀ for axis 1) with
+    A = s I + c (D_+ T + D_- Tᵀ), Eq. (system_FD).  (T x)_i = -Σ_m g_m x_{i+1-m}
+    and (Tᵀ x)_i = -Σ_m g_m x_{i-1+m}, both as FFT convolutions."""
+    N = op.N
+    g = gl_weights(op.alpha, N + 1)
+    c = fd_scale(op)
+    Xa = np.moveaxis(X, axis, 0)
+    conv = _fftconv(g, Xa, 0)
+    Tx = -conv[1:N + 1]
+    convr = _fftconv(g, Xa[::-1], 0)
+    Ttx = -convr[N - np.arange(N)]
+    dp = op.d_plus.reshape((-1,) + (1,) * (Xa.ndim - 1))
+    dm = op.d_minus.reshape((-1,) + (1,) * (Xa.ndim - 1))
+    Y = op.shift * Xa + c * (dp * Tx + dm * Ttx)
+    return np.moveaxis(Y, 0, axis)
+
+
+def sylvester_residual(opx, opy, X: np.ndarray, C: np.ndarray) -> float:
+    """||C - A_x X - X A_yᵀ||_F / ||C||_F with both products taken structurally."""
+    R = C - apply_fd_operator_fft(opx, X, 0) - apply_fd_operator_fft(opy, X, 1)
+    return float(np.linalg.norm(R) / np.linalg.norm(C))

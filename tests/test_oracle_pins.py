@@ -1,0 +1,344 @@
+"""Pins for the CPU oracle: each test checks the oracle against something the
+paper or plain mathematics fixes independently of the oracle's own formulas
+(closed forms, special cases that reduce to textbook routines, brute force,
+invariants).  A plausible slip in the oracle (dropped term, sign, index,
+transposed operand) fails at least one of these."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from scipy.special import gammaln, gamma
+
+from oracle import fde_oracle as O
+from paper_1804_05522_gb300 import inputs as I
+
+
+# ---------------------------------------------------------------- GL weights
+@pytest.mark.parametrize("alpha", [1.25, 1.5, 1.75])
+def test_gl_first_weights_exact(alpha):
+    # §2.1: g_0 = 1 and g_1 = -α (§2.2.1); exact for dyadic α
+    g = O.gl_weights(alpha, 4)
+    assert g[0] == 1.0 and g[1] == -alpha
+
+
+@pytest.mark.parametrize("alpha", [1.1, 1.3, 1.5, 1.7, 1.9])
+def test_gl_closed_gamma_form(alpha):
+    # Lemma lem:hadamard-product (proof): g_k = α(α-1)Γ(k-α)/(Γ(k+1)Γ(2-α)), k >= 2
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    K = 3000
+    g = O.gl_weights(alpha, K)
+    a = mp.mpf(alpha)
+    ks = list(range(2, K + 1, 7)) + [K]
+    ref = np.array([float(a * (a - 1) * mp.gamma(k - a) / (mp.gamma(k + 1) * mp.gamma(2 - a))) for k in ks])
+    # the recurrence accumulates at most ~k roundings
+    rel = np.abs(g[ks] / ref - 1.0)
+    assert np.all(rel <= 4e-16 * np.array(ks, dtype=float) + 1e-15), rel.max()
+
+
+@pytest.mark.parametrize("alpha", [1.05, 1.3, 1.5, 1.95])
+def test_gl_ordering_and_decay(alpha):
+    # §2.2.1: g_1 = -α, g_0 > g_2 > g_3 > ... > 0 and g_k = O(k^{-α-1})
+    g = O.gl_weights(alpha, 100000)
+    assert g[0] > g[2]
+    assert np.all(np.diff(g[2:]) < 0) and np.all(g[2:] > 0)
+    # asymptotics of (-1)^k binom(α,k) ~ k^{-α-1}/Γ(-α)
+    k = 100000
+    assert abs(g[k] * k ** (alpha + 1) * gamma(-alpha) - 1.0) < 1e-3 * (1 + alpha)
+
+
+@pytest.mark.parametrize("alpha", [1.2, 1.5, 1.8])
+def test_gl_partial_sums(alpha):
+    # Σ_{k<=K} g_k = (-1)^K binom(α-1,K) = Γ(K+1-α)/(Γ(K+1)Γ(1-α)) -> 0 from below
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    K = 3000
+    g = O.gl_weights(alpha, K)
+    S = np.cumsum(g)
+    a = mp.mpf(alpha)
+    ks = list(range(1, K + 1, 13)) + [K]
+    # Γ(1-α) < 0 for α in (1,2): the closed form is negative
+    ref = np.array([float(mp.gamma(k + 1 - a) / (mp.gamma(k + 1) * mp.gamma(1 - a))) for k in ks])
+    # cancellation: the sum of |g_k| is 2, so the absolute error is O(K u)
+    assert np.all(np.abs(S[ks] - ref) <= 4e-16 * np.array(ks, dtype=float) + 1e-15)
+    assert np.all(S[1:] < 0) and abs(S[-1]) < abs(S[10])
+
+
+def test_gl_integer_orders():
+    # α = 1, 2 give the first / second difference stencils exactly
+    np.testing.assert_array_equal(O.gl_weights(2.0, 6), [1, -2, 1, 0, 0, 0, 0])
+    np.testing.assert_array_equal(O.gl_weights(1.0, 5), [1, -1, 0, 0, 0, 0])
+
+
+# ----------------------------------------------------------- Toeplitz / A
+def test_toeplitz_alpha2_is_laplacian():
+    # Eq. (toeplitz_FD) at α = 2: -[g_{i-j+1}] = tridiag(-1, 2, -1)
+    N = 9
+    T = O.gl_toeplitz(2.0, N)
+    L = 2 * np.eye(N) - np.eye(N, k=1) - np.eye(N, k=-1)
+    np.testing.assert_array_equal(T, L)
+
+
+@pytest.mark.parametrize("alpha", [1.3, 1.7])
+def test_toeplitz_structure(alpha):
+    N = 40
+    T = O.gl_toeplitz(alpha, N)
+    g = O.gl_weights(alpha, N)
+    # lower Hessenberg: zero above the first superdiagonal; Toeplitz along diagonals
+    assert np.all(np.triu(T, 2) == 0)
+    for d in range(-1, N):
+        diag = np.diagonal(T, -d)
+        assert np.all(diag == diag[0])
+        assert diag[0] == -g[d + 1]
+    # Lemma lem:fd-qsrank proof: upper off-diagonal blocks have rank <= 1
+    for cut in range(1, N):
+        assert np.linalg.matrix_rank(T[:cut, cut:]) <= 1
+
+
+@pytest.mark.parametrize("alpha", [1.2, 1.5, 1.9])
+def test_hankel_psd(alpha):
+    # Lemma lem:hadamard-product: H = [g_{i+j}]_{i,j>=1} is positive semidefinite
+    n = 60
+    g = O.gl_weights(alpha, 2 * n + 2)
+    H = np.array([[g[i + j] for j in range(1, n + 1)] for i in range(1, n + 1)])
+    ev = np.linalg.eigvalsh(H)
+    assert ev.min() >= -1e-14 * ev.max()
+
+
+@pytest.mark.parametrize("shift", [1.0, 0.5])
+def test_fd_operator_sdd_and_signs(shift):
+    # §2.2.1: M^{FD} strictly diagonally dominant; diag = s + cα(d_+ + d_-);
+    # off-diagonals of D_+T + D_-Tᵀ are <= 0 (g_0 > 0, g_k > 0 for k >= 2)
+    w = I.fd1d(N=96, alpha=1.5, steps=10)
+    op = w.ops[0]
+    op.shift = shift
+    A = O.fd_operator(op)
+    c = O.fd_scale(op)
+    d = np.diag(A)
+    np.testing.assert_allclose(d, shift + c * op.alpha * (op.d_plus + op.d_minus), rtol=1e-14)
+    off = A - np.diag(d)
+    assert np.all(off <= 0)
+    assert np.all(np.abs(d) > np.abs(off).sum(1))
+
+
+def test_fd_operator_unshifted_rowsums():
+    # rows of T sum to -Σ_{k<=i+1} g_k (partial sums, positive): checks index of T
+    alpha, N = 1.4, 30
+    T = O.gl_toeplitz(alpha, N)
+    g = O.gl_weights(alpha, N + 1)
+    S = np.cumsum(g)
+    np.testing.assert_allclose(T.sum(1)[:-1], -S[1:N], rtol=1e-13)
+
+
+# --------------------------------------------------------- manufactured
+def _rl_power(p, alpha):
+    return math.gamma(p + 1) / math.gamma(p + 1 - alpha)
+
+
+def test_manufactured_solution_first_order():
+    """u = e^{-t} x²(1-x)²; f from the Riemann–Liouville power rule
+    (Eq. (frac-der); RL = GL for smooth u, §2.1).  Shifted GL + implicit Euler
+    is first order in Δx and Δt (§2.2.1), so halving both halves the error."""
+    alpha = 1.5
+    coeffs = {2: 1.0, 3: -2.0, 4: 1.0}  # x²(1-x)² = x² - 2x³ + x⁴
+
+    def Dplus(x):
+        return sum(cf * _rl_power(p, alpha) * x ** (p - alpha) for p, cf in coeffs.items())
+
+    errs = []
+    for N in (63, 127, 255):
+        x = I.grid(N)
+        h = 1.0 / (N + 1)
+        dt = 2.0 * h
+        M = int(round(0.5 / dt))
+        dp = math.gamma(3 - alpha) * x ** alpha
+        dm = math.gamma(3 - alpha) * (1 - x) ** alpha
+        op = I.OpSpec(N, alpha, h, dt, 1.0, dp, dm, 64, 1e-12)
+        A = O.fd_operator(op)
+        u = x ** 2 * (1 - x) ** 2
+        lu = sla.lu_factor(A)
+        U = u.copy()
+        for m in range(1, M + 1):
+            t = m * dt
+            # u_t - d_+ D_+^α u - d_- D_-^α u = f ; D_-^α u(x) = (D_+^α u)(1-x) by symmetry of u
+            f = -math.exp(-t) * u - math.exp(-t) * (dp * Dplus(x) + dm * Dplus(1 - x))
+            U = sla.lu_solve(lu, U + dt * f)
+        errs.append(np.max(np.abs(U - math.exp(-M * dt) * u)))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.6 < r1 < 2.6 and 1.6 < r2 < 2.6, errs
+
+
+# ---------------------------------------------------------------- tree
+@pytest.mark.parametrize("N,leaf", [(1024, 64), (1000, 64), (129, 64), (7, 2), (64, 64), (65, 64), (4096, 256), (300, 32)])
+def test_hodlr_tree(N, leaf):
+    tree = O.hodlr_tree(N, leaf)
+    # brute force: level l has 2^l contiguous nodes covering [0, N); children are ⌊n/2⌋, ⌈n/2⌉
+    for l, lvl in enumerate(tree):
+        assert len(lvl) == 2 ** l
+        assert lvl[0][0] == 0 and lvl[-1][1] == N
+        for (a, b), (c, d) in zip(lvl[:-1], lvl[1:]):
+            assert b == c
+        sizes = {b - a for a, b in lvl}
+        assert sizes <= {N // 2 ** l, -(-N // 2 ** l)}
+        if l > 0:
+            for p, (lo, hi) in enumerate(tree[l - 1]):
+                assert tree[l][2 * p] == (lo, lo + (hi - lo) // 2)
+                assert tree[l][2 * p + 1] == (lo + (hi - lo) // 2, hi)
+    L = len(tree) - 1
+    assert max(b - a for a, b in tree[-1]) <= leaf
+    assert L == 0 or max(b - a for a, b in tree[-2]) > leaf
+    assert L == next(l for l in range(40) if -(-N // 2 ** l) <= leaf)
+
+
+# ------------------------------------------------------------ norms / ranks
+def test_norm2_power():
+    w = I.fd1d(N=200, alpha=1.7, steps=8)
+    A = O.fd_operator(w.ops[0])
+    est = O.norm2_power(A)
+    ex = np.linalg.norm(A, 2)
+    assert est <= ex * (1 + 1e-12) and est > ex * (1 - 1e-3)
+
+
+def test_truncate_lowrank_prescribed_spectrum():
+    rng = I.SplitMix64(11)
+    m, n = 50, 40
+    Qa, _ = np.linalg.qr(rng.normal_array((m, 6)))
+    Qb, _ = np.linalg.qr(rng.normal_array((n, 6)))
+    s = np.array([1.0, 1e-3, 1e-6, 1e-9, 1e-12, 1e-15])
+    U = Qa * s
+    V = Qb
+    U2, V2 = O.truncate_lowrank(U, V, 1e-7)
+    assert U2.shape[1] == 3
+    err = np.linalg.norm(U @ V.T - U2 @ V2.T, 2)
+    assert abs(err - 1e-9) < 1e-11
+
+
+def test_aca_exact_low_rank():
+    rng = I.SplitMix64(5)
+    m, n, r = 70, 55, 5
+    M = rng.normal_array((m, r)) @ rng.normal_array((r, n))
+    U, V, rows, cols, conv = O.aca_partial_pivot(lambda i: M[i], lambda j: M[:, j], m, n, 1e-9, 30)
+    assert conv and U.shape[1] in (r, r + 1)
+    assert np.linalg.norm(M - U @ V.T) < 1e-10 * np.linalg.norm(M)
+    # pivots reproduce the cross exactly: u_k v_k interpolates the residual at (i*, j*)
+    assert len(set(rows)) == len(rows) and len(set(cols)) == len(cols)
+
+
+@pytest.mark.parametrize("alpha,N", [(1.5, 512), (1.2, 300), (1.8, 257)])
+def test_aca_toeplitz_block(alpha, N):
+    # §3.4.2: the top-level block T21 is numerically low rank; ACA reaches the tolerance
+    g = O.gl_weights(alpha, N + 1)
+    N1, N2, row, col = O.toeplitz_lower_block_entries(g, N)
+    T = O.gl_toeplitz(alpha, N)
+    T21 = T[N1:, :N1]
+    np.testing.assert_array_equal(row(3), T21[3])
+    np.testing.assert_array_equal(col(5), T21[:, 5])
+    tol = 1e-12 * np.linalg.norm(T, 2)
+    U, V, rows, cols, conv = O.aca_partial_pivot(row, col, N2, N1, tol, 200)
+    assert conv
+    err = np.linalg.norm(T21 - U @ V.T, 2)
+    assert err < 100 * tol
+    assert U.shape[1] <= O.qsrank_bound_T(N, 1e-12) + 10
+
+
+@pytest.mark.parametrize("alpha", [1.3, 1.7])
+def test_rank_bounds(alpha):
+    # Lemma lem:fd-qsrank and Corollary cor:fd-qsrank, checked by SVD
+    N, eps = 256, 1e-8
+    T = O.gl_toeplitz(alpha, N)
+    nT = np.linalg.norm(T, 2)
+    _, ranksT, _ = O.hodlr_reference(T, 16, eps, normA=nT)
+    assert max(max(r) for r in ranksT.values()) <= O.qsrank_bound_T(N, eps)
+    # the upper blocks of T are exactly rank 1 (only g_0 = 1 at the corner)
+    assert max(r[0] for r in ranksT.values()) <= 1
+    w = I.fd1d(N=N, alpha=alpha, steps=10)
+    op = w.ops[0]
+    A = O.fd_operator(op)
+    nA = np.linalg.norm(A, 2)
+    _, ranksA, _ = O.hodlr_reference(A, 16, eps, normA=nA)
+    bound = O.qsrank_bound_M(N, eps, nA, nT, max(op.d_plus.max(), op.d_minus.max()))
+    assert max(max(r) for r in ranksA.values()) <= bound
+
+
+# ---------------------------------------------------------------- solvers
+def _rand_stable(n, seed, shift):
+    rng = I.SplitMix64(seed)
+    return rng.normal_array((n, n)) + shift * np.eye(n)
+
+
+def test_bartels_stewart_vs_kronecker_random():
+    # random nonsymmetric A, B with complex eigenvalues (2x2 Schur blocks)
+    A = _rand_stable(13, 1, 6.0)
+    B = _rand_stable(11, 2, 6.0)
+    C = I.SplitMix64(3).normal_array((13, 11))
+    X1 = O.sylvester_bartels_stewart(A, B, C)
+    X2 = O.sylvester_kron(A, B, C)
+    np.testing.assert_allclose(X1, X2, rtol=0, atol=1e-13 * np.abs(X2).max())
+    assert np.linalg.norm(A @ X1 + X1 @ B.T - C) < 1e-12 * np.linalg.norm(C)
+
+
+def test_bartels_stewart_vs_kronecker_fd():
+    w = I.fd2d(N=16, alpha=(1.3, 1.7), steps=50)
+    Ax = O.fd_operator(w.ops[0])
+    Ay = O.fd_operator(w.ops[1])
+    C = O.fde2d_rhs(w, w.u0, 0)
+    X1 = O.sylvester_bartels_stewart(Ax, Ay, C)
+    X2 = O.sylvester_kron(Ax, Ay, C)
+    np.testing.assert_allclose(X1, X2, rtol=0, atol=1e-13 * np.abs(X2).max())
+
+
+def test_alpha2_dst_closed_form():
+    """α = 2, constant coefficients: A = s I + 2cd·tridiag(-1,2,-1), diagonalised by
+    the discrete sine transform; X = S((S C S) / (λ_i + λ_j)) S."""
+    N, s, dt, d = 24, 0.5, 0.01, 0.7
+    h = 1.0 / (N + 1)
+    op = I.OpSpec(N, 2.0, h, dt, s, np.full(N, d), np.full(N, d), 8, 1e-12)
+    A = O.fd_operator(op)
+    c = dt / h ** 2
+    j = np.arange(1, N + 1)
+    S = math.sqrt(2.0 / (N + 1)) * np.sin(np.pi * np.outer(j, j) / (N + 1))
+    lam = s + 2 * c * d * (2 - 2 * np.cos(j * np.pi / (N + 1)))
+    np.testing.assert_allclose(S @ np.diag(lam) @ S, A, atol=1e-10 * lam.max())
+    C = I.SplitMix64(9).normal_array((N, N))
+    X = S @ ((S @ C @ S) / (lam[:, None] + lam[None, :])) @ S
+    Xo = O.sylvester_bartels_stewart(A, A, C)
+    np.testing.assert_allclose(Xo, X, atol=1e-12 * np.abs(X).max())
+
+
+def test_symmetric_solution():
+    w = I.fd2d(N=40, alpha=(1.6, 1.6), steps=10)
+    A = O.fd_operator(w.ops[0])
+    C = I.SplitMix64(4).normal_array((40, 40))
+    C = C + C.T
+    X = O.sylvester_bartels_stewart(A, A, C)
+    assert np.abs(X - X.T).max() < 1e-12 * np.abs(X).max()
+
+
+def test_fft_operator_matches_dense():
+    w = I.fd2d(N=50, alpha=(1.3, 1.8), steps=10)
+    X = I.SplitMix64(8).normal_array((50, 50))
+    Ax = O.fd_operator(w.ops[0])
+    Ay = O.fd_operator(w.ops[1])
+    np.testing.assert_allclose(O.apply_fd_operator_fft(w.ops[0], X, 0), Ax @ X, atol=1e-12 * np.abs(Ax @ X).max())
+    np.testing.assert_allclose(O.apply_fd_operator_fft(w.ops[1], X, 1), X @ Ay.T, atol=1e-12 * np.abs(X @ Ay.T).max())
+
+
+def test_fde2d_run_matches_kronecker_steps():
+    w = I.fd2d(N=12, alpha=(1.3, 1.7), steps=5)
+    Ax = O.fd_operator(w.ops[0])
+    Ay = O.fd_operator(w.ops[1])
+    U = w.u0.copy()
+    for m in range(5):
+        U = O.sylvester_kron(Ax, Ay, U + w.dt * w.source((m + 1) * w.dt))
+    np.testing.assert_allclose(O.fde2d_run(w), U, atol=1e-13 * np.abs(U).max())
+
+
+def test_fde1d_run_residuals():
+    w = I.fd1d(N=128, alpha=1.5, steps=4)
+    A = O.fd_operator(w.ops[0])
+    u = w.u0.copy()
+    for m in range(1, 5):
+        b = u + w.dt * w.source(m * w.dt)
+        u = np.linalg.solve(A, b)
+    np.testing.assert_allclose(O.fde1d_run(w), u, rtol=1e-12, atol=1e-14)
