@@ -1,0 +1,210 @@
+/*
+ * fde_hodlr.h -- C ABI of the GB300 (sm_103a) HODLR solvers for the shifted
+ * Grünwald–Letnikov discretisation of space-fractional diffusion
+ * (Massei, Mazza, Robol, "Fast solvers for two-dimensional fractional
+ * diffusion equations using rank structured matrices", arXiv:1804.05522).
+ *
+ * What is computed
+ *   1D (§2.2.1, Eq. (system_FD)): one implicit-Euler step is the dense system
+ *        A u = b,   A = s I + (Δt/h^α) (D_+ T_α + D_- T_αᵀ),   s = 1,
+ *   with T_α = -[g_{i-j+1}] the lower Hessenberg Toeplitz matrix of
+ *   Eq. (toeplitz_FD) and g_k the Grünwald–Letnikov weights (Eq. (Grun)).
+ *   2D (§4.2, Eq. (sylv-timestepping)): one step is the Sylvester equation
+ *        A_x X + X A_yᵀ = C,   A_{x,y} as above with s = 1/2,
+ *   C = U^{(m)} + Δt F^{(m+1)}.
+ *
+ * How (all on one GPU, no CPU fallback)
+ *   hodlr_build  : g_k on the device; the top-level subdiagonal Toeplitz block
+ *                  compressed once by ACA and restricted to every level
+ *                  (§3.4.2), D_± scaling applied to the factors, per-block
+ *                  QR+SVD recompression at ε||A||_2 (§3.4.1).
+ *   hodlr_factor : HODLR factorisation (leaf LU + one small capacitance
+ *                  system per node), solves in O(k N log N) (§3.5).
+ *   sylv_step    : divide and conquer over the HODLR tree (Conclusions,
+ *                  D&C for HODLR right-hand sides) with leaf Bartels–Stewart
+ *                  and low-rank corrections solved by factored ADI, wrapped in
+ *                  FP64 iterative refinement against the exact structured
+ *                  residual.
+ *
+ * Conventions (every entry point)
+ *   - Matrices are column-major; X[i + j*ld] = u(x_i, y_j).
+ *   - Pointers named d_* are DEVICE pointers, h_* HOST pointers; where either
+ *     is accepted it says so.  Caller buffers are borrowed and must stay valid
+ *     until the work on `stream` that uses them has completed.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Handles own all of their device memory and free it in *_free.
+ *   - No call aborts, traps or spins without bound.  Argument errors are
+ *     detected on the host before any launch and return FDE_ERR_ARG; a failed
+ *     allocation returns FDE_ERR_NOMEM; an iteration that hits its cap returns
+ *     FDE_ERR_NOCONV; NaN/Inf in inputs or residuals returns FDE_ERR_NUMERIC;
+ *     any other CUDA error returns FDE_ERR_CUDA (fde_last_error() has text).
+ *   - Calls on one handle must not overlap (one stream per handle).
+ */
+#ifndef FDE_HODLR_H
+#define FDE_HODLR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FDE_OK = 0,
+  FDE_ERR_ARG = 1,
+  FDE_ERR_NOMEM = 2,
+  FDE_ERR_NOCONV = 3,
+  FDE_ERR_NUMERIC = 4,
+  FDE_ERR_CUDA = 5
+} fde_status;
+
+/* Precision of the inner HODLR/D&C solver.  Refinement residuals and the
+ * solution iterate are always FP64. */
+typedef enum {
+  FDE_FP64 = 0,         /* all inner kernels in FP64                    */
+  FDE_FP32_REFINE = 1   /* inner kernels in FP32, FP64 refinement        */
+} fde_prec;
+
+/* One 1D operator  A = shift*I + (dt/h^alpha) (D_+ T_alpha + D_- T_alphaᵀ)
+ * (§2.2.1, Eq. (system_FD)).  d_plus / d_minus are the diagonals of D_±
+ * sampled by the caller (host or device pointers, length N, finite, >= 0).
+ * Requirements: N >= 2, 1 < alpha <= 2, h > 0, dt > 0, shift > 0,
+ * 8 <= leaf <= 256, 0 < tol < 1 (truncation tolerance ε, relative to
+ * ||A||_2, §3.4.1). */
+typedef struct {
+  int N;
+  double alpha;
+  double h;
+  double dt;
+  double shift;
+  const double* d_plus;
+  const double* d_minus;
+  int leaf;
+  double tol;
+} fde_op_params;
+
+typedef struct hodlr_s* hodlr_t;
+typedef struct sylv_s* sylv_t;
+
+/* Summary of a built HODLR operator (read back for checks and reports). */
+typedef struct {
+  int N, leaf, levels, nleaves;
+  int kmax;              /* largest off-diagonal rank after recompression */
+  int aca_rank;          /* rank of the ACA of the top-level Toeplitz block */
+  int aca_converged;     /* 1 if ACA met its tolerance                     */
+  double norm2;          /* power-iteration estimate of ||A||_2            */
+  double c;              /* dt / h^alpha                                   */
+  double aca_tol;        /* absolute ACA tolerance used                    */
+} hodlr_info_t;
+
+/* Build the HODLR representation of the operator.  Owns its memory.
+ * Errors: FDE_ERR_ARG (bad parameters, NULL out), FDE_ERR_NOMEM,
+ * FDE_ERR_NUMERIC (non-finite d_±), FDE_ERR_NOCONV (ACA hit its rank cap). */
+fde_status hodlr_build(const fde_op_params* p, void* stream, hodlr_t* out);
+
+/* Factorise A + sigma*I for sigma = 0 (§3.5): leaf LU without pivoting
+ * (A is strictly diagonally dominant, §2.2.1) and one pivoted LU of the
+ * small capacitance matrix of every internal node.  Idempotent. */
+fde_status hodlr_factor(hodlr_t h, void* stream);
+
+/* x = A^{-1} b for nrhs right-hand sides (device pointers, leading dim ldb >= N;
+ * b and x may alias).  Requires hodlr_factor.  FP64. */
+fde_status hodlr_solve(hodlr_t h, const double* d_b, double* d_x, int nrhs, int ldb, void* stream);
+
+/* y = A x (HODLR matvec, FP64, device pointers), for checks. */
+fde_status hodlr_matvec(hodlr_t h, const double* d_x, double* d_y, int nrhs, int ldx, void* stream);
+
+fde_status hodlr_get_info(hodlr_t h, hodlr_info_t* info);
+
+/* Writes the dense N x N matrix represented by the HODLR (column-major,
+ * device pointer, ld >= N).  For checks at small N. */
+fde_status hodlr_to_dense(hodlr_t h, double* d_A, int ld, void* stream);
+
+/* Copies the GL weights g_0..g_{N+1} (host pointer, N+2 doubles). */
+fde_status hodlr_get_weights(hodlr_t h, double* h_g);
+
+/* Copies the ACA pivot sequence (host pointers, capacity cap each) and its
+ * length.  rows index the block rows N1..N-1 from 0, cols the columns 0..N1-1. */
+fde_status hodlr_get_aca_pivots(hodlr_t h, int* h_rows, int* h_cols, int cap, int* h_k);
+
+/* Copies the tree layout: node ranges [lo, hi) in level order, 2^(L+1)-1
+ * entries each (host pointers). */
+fde_status hodlr_get_tree(hodlr_t h, int* h_lo, int* h_hi, int cap);
+
+void hodlr_free(hodlr_t h);
+
+/* ------------------------------------------------------------------ 2D -- */
+/* Prepare the Sylvester solver for A_x X + X A_yᵀ = C (Eq. (sylv-timestepping)).
+ * Ax and Ay must have the same N and leaf and be built with shift 1/2.
+ * Computes the real Schur forms of every leaf block, the fADI shifts per level
+ * and the shifted factorisations.  The handle keeps references to Ax, Ay:
+ * free it before them. */
+fde_status sylv_create(hodlr_t Ax, hodlr_t Ay, int prec, void* stream, sylv_t* out);
+
+/* Refinement controls (defaults set by sylv_create). */
+typedef struct {
+  int max_sweeps;        /* cap on refinement sweeps (FDE_ERR_NOCONV beyond) */
+  double tol_update;     /* stop when ||δX||_F <= tol_update ||X||_F         */
+  double tol_relres;     /* or when ||R||_F <= tol_relres ||C||_F            */
+  int fixed_sweeps;      /* > 0: run exactly this many sweeps, no host sync   */
+} sylv_refine_t;
+fde_status sylv_get_refine(sylv_t s, sylv_refine_t* r);
+fde_status sylv_set_refine(sylv_t s, const sylv_refine_t* r);
+
+/* Solve A_x X + X A_yᵀ = C.  d_C, d_X: device FP64, column-major N x N,
+ * leading dimension ld >= N.  On entry X holds the initial guess (e.g. the
+ * previous time step; zeros are fine); on exit the refined solution.
+ * relres_out (host, may be NULL) receives ||C - A_x X - X A_yᵀ||_F / ||C||_F
+ * computed in FP64 from the structured operators; sweeps_out (host, may be
+ * NULL) the number of refinement sweeps. */
+fde_status sylv_step(sylv_t s, const double* d_C, double* d_X, int ld, void* stream,
+                     double* relres_out, int* sweeps_out);
+
+/* One application of the inner (unrefined) D&C solver: X = S(C).  For checks. */
+fde_status sylv_inner_solve(sylv_t s, const double* d_C, double* d_X, int ld, void* stream);
+
+/* R = C - A_x X - X A_yᵀ in FP64 (structured, FFT based).  For checks. */
+fde_status sylv_residual(sylv_t s, const double* d_C, const double* d_X, double* d_R, int ld, void* stream);
+
+void sylv_free(sylv_t s);
+
+/* ------------------------------------------------------------ time loop -- */
+/* Source f(x[,y],t) = Σ_l w_l(t) F_L[:,l] (⊗ F_R[:,l]),
+ * w_l(t) = amp_l + sin_amp_l * sin(omega_l * t), sampled at the new time level
+ * t_{m+1} = (m+1) dt (implicit Euler). */
+typedef struct {
+  int dim;                       /* 1 or 2                                       */
+  fde_op_params op_x;            /* shift must be 1 (1D) or 1/2 (2D)             */
+  fde_op_params op_y;            /* 2D only                                      */
+  int steps;                     /* number of implicit-Euler steps M             */
+  int rank;                      /* number of source terms r (0 allowed)         */
+  const double* h_src_left;      /* host, N x r column-major                     */
+  const double* h_src_right;     /* host, N x r column-major (2D only)           */
+  const double* h_amp;           /* host, r                                      */
+  const double* h_sin_amp;       /* host, r                                      */
+  const double* h_omega;         /* host, r                                      */
+  int prec;                      /* fde_prec                                     */
+  int use_graph;                 /* capture one step as a CUDA graph and replay  */
+} fde_run_params;
+
+typedef struct {
+  double setup_s;                /* build + factor + Schur + shift factors       */
+  double solve_s;                /* time-stepping loop                           */
+  double steps_per_s;
+  int sweeps_total;              /* refinement sweeps over all steps             */
+  int sweeps_max;
+  double relres_max;             /* worst final FP64 relative residual           */
+  int kmax_x, kmax_y;
+} fde_run_stats;
+
+/* Run M implicit-Euler steps from U0 (device, N (1D) or N x N (2D),
+ * column-major, ld = N) into U_out (device, same shape; may alias U0). */
+fde_status fde_run(const fde_run_params* p, const double* d_U0, double* d_U_out, void* stream,
+                   fde_run_stats* stats);
+
+const char* fde_strerror(fde_status s);
+/* Text of the last error on the calling thread (never NULL). */
+const char* fde_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDE_HODLR_H */

@@ -1,0 +1,230 @@
+"""Thin ctypes binding of the fde_hodlr C ABI (include/fde_hodlr.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+Device buffers are passed as integer addresses (e.g. torch.Tensor.data_ptr()),
+streams as integer cudaStream_t handles.  If the shared library has not been
+built, load() raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libfde_hodlr.so")
+
+FDE_OK, FDE_ERR_ARG, FDE_ERR_NOMEM, FDE_ERR_NOCONV, FDE_ERR_NUMERIC, FDE_ERR_CUDA = range(6)
+FDE_FP64, FDE_FP32_REFINE = 0, 1
+
+
+class OpParams(C.Structure):
+    _fields_ = [("N", C.c_int), ("alpha", C.c_double), ("h", C.c_double), ("dt", C.c_double),
+                ("shift", C.c_double), ("d_plus", C.c_void_p), ("d_minus", C.c_void_p),
+                ("leaf", C.c_int), ("tol", C.c_double)]
+
+
+class HodlrInfo(C.Structure):
+    _fields_ = [("N", C.c_int), ("leaf", C.c_int), ("levels", C.c_int), ("nleaves", C.c_int),
+                ("kmax", C.c_int), ("aca_rank", C.c_int), ("aca_converged", C.c_int),
+                ("norm2", C.c_double), ("c", C.c_double), ("aca_tol", C.c_double)]
+
+
+class RefineParams(C.Structure):
+    _fields_ = [("max_sweeps", C.c_int), ("tol_update", C.c_double), ("tol_relres", C.c_double),
+                ("fixed_sweeps", C.c_int)]
+
+
+class RunParams(C.Structure):
+    _fields_ = [("dim", C.c_int), ("op_x", OpParams), ("op_y", OpParams), ("steps", C.c_int),
+                ("rank", C.c_int), ("h_src_left", C.c_void_p), ("h_src_right", C.c_void_p),
+                ("h_amp", C.c_void_p), ("h_sin_amp", C.c_void_p), ("h_omega", C.c_void_p),
+                ("prec", C.c_int), ("use_graph", C.c_int)]
+
+
+class RunStats(C.Structure):
+    _fields_ = [("setup_s", C.c_double), ("solve_s", C.c_double), ("steps_per_s", C.c_double),
+                ("sweeps_total", C.c_int), ("sweeps_max", C.c_int), ("relres_max", C.c_double),
+                ("kmax_x", C.c_int), ("kmax_y", C.c_int)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "hodlr_build": ([C.POINTER(OpParams), _P, C.POINTER(_P)], C.c_int),
+    "hodlr_factor": ([_P, _P], C.c_int),
+    "hodlr_solve": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
+    "hodlr_matvec": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
+    "hodlr_get_info": ([_P, C.POINTER(HodlrInfo)], C.c_int),
+    "hodlr_to_dense": ([_P, _P, C.c_int, _P], C.c_int),
+    "hodlr_get_weights": ([_P, _P], C.c_int),
+    "hodlr_get_aca_pivots": ([_P, _P, _P, C.c_int, C.POINTER(C.c_int)], C.c_int),
+    "hodlr_get_tree": ([_P, _P, _P, C.c_int], C.c_int),
+    "hodlr_free": ([_P], None),
+    "sylv_create": ([_P, _P, C.c_int, _P, C.POINTER(_P)], C.c_int),
+    "sylv_get_refine": ([_P, C.POINTER(RefineParams)], C.c_int),
+    "sylv_set_refine": ([_P, C.POINTER(RefineParams)], C.c_int),
+    "sylv_step": ([_P, _P, _P, C.c_int, _P, C.POINTER(C.c_double), C.POINTER(C.c_int)], C.c_int),
+    "sylv_inner_solve": ([_P, _P, _P, C.c_int, _P], C.c_int),
+    "sylv_residual": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
+    "sylv_free": ([_P], None),
+    "fde_run": ([C.POINTER(RunParams), _P, _P, _P, C.POINTER(RunStats)], C.c_int),
+    "fde_strerror": ([C.c_int], C.c_char_p),
+    "fde_last_error": ([], C.c_char_p),
+}
+
+
+class FdeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fde status {status}: {msg}")
+        self.status = status
+
+
+class Lib:
+    """Loaded library with checked wrappers named after the C entry points."""
+
+    def __init__(self, path: str = LIB_PATH):
+        if not os.path.exists(path):
+            raise RuntimeError(f"fde_hodlr library not built ({path}); run __graft_entry__.build()")
+        self.dll = C.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(self.dll, name)
+            fn.argtypes = args
+            fn.restype = res
+        self._keep = []
+
+    # -- error handling
+    def check(self, status: int):
+        if status != FDE_OK:
+            raise FdeError(status, self.dll.fde_last_error().decode())
+        return status
+
+    def last_error(self) -> str:
+        return self.dll.fde_last_error().decode()
+
+    # -- parameter marshalling
+    def op_params(self, op, d_plus=None, d_minus=None) -> OpParams:
+        """fde_op_params from an inputs.OpSpec (coefficients passed as host arrays
+        unless device addresses are given)."""
+        dp = np.ascontiguousarray(op.d_plus, dtype=np.float64)
+        dm = np.ascontiguousarray(op.d_minus, dtype=np.float64)
+        self._keep += [dp, dm]
+        p = OpParams(op.N, op.alpha, op.h, op.dt, op.shift,
+                     d_plus if d_plus is not None else dp.ctypes.data,
+                     d_minus if d_minus is not None else dm.ctypes.data, op.leaf, op.tol)
+        p._arrays = (dp, dm)
+        return p
+
+    # -- HODLR
+    def hodlr_build(self, params: OpParams, stream: int = 0) -> int:
+        h = _P()
+        self.check(self.dll.hodlr_build(C.byref(params), stream, C.byref(h)))
+        return h.value
+
+    def hodlr_build_status(self, params: OpParams, stream: int = 0):
+        h = _P()
+        s = self.dll.hodlr_build(C.byref(params), stream, C.byref(h))
+        return s, h.value
+
+    def hodlr_factor(self, h: int, stream: int = 0):
+        self.check(self.dll.hodlr_factor(h, stream))
+
+    def hodlr_solve(self, h: int, b: int, x: int, nrhs: int, ldb: int, stream: int = 0):
+        self.check(self.dll.hodlr_solve(h, b, x, nrhs, ldb, stream))
+
+    def hodlr_matvec(self, h: int, x: int, y: int, nrhs: int, ldx: int, stream: int = 0):
+        self.check(self.dll.hodlr_matvec(h, x, y, nrhs, ldx, stream))
+
+    def hodlr_get_info(self, h: int) -> HodlrInfo:
+        info = HodlrInfo()
+        self.check(self.dll.hodlr_get_info(h, C.byref(info)))
+        return info
+
+    def hodlr_to_dense(self, h: int, A: int, ld: int, stream: int = 0):
+        self.check(self.dll.hodlr_to_dense(h, A, ld, stream))
+
+    def hodlr_get_weights(self, h: int, N: int) -> np.ndarray:
+        g = np.zeros(N + 2)
+        self.check(self.dll.hodlr_get_weights(h, g.ctypes.data))
+        return g
+
+    def hodlr_get_aca_pivots(self, h: int, cap: int = 512):
+        r = np.zeros(cap, dtype=np.int32)
+        c = np.zeros(cap, dtype=np.int32)
+        k = C.c_int()
+        self.check(self.dll.hodlr_get_aca_pivots(h, r.ctypes.data, c.ctypes.data, cap, C.byref(k)))
+        return r[:k.value].copy(), c[:k.value].copy()
+
+    def hodlr_get_tree(self, h: int, levels: int):
+        n = (1 << (levels + 1)) - 1
+        lo = np.zeros(n, dtype=np.int32)
+        hi = np.zeros(n, dtype=np.int32)
+        self.check(self.dll.hodlr_get_tree(h, lo.ctypes.data, hi.ctypes.data, n))
+        return lo, hi
+
+    def hodlr_free(self, h: int):
+        if h:
+            self.dll.hodlr_free(h)
+
+    # -- Sylvester
+    def sylv_create(self, ax: int, ay: int, prec: int, stream: int = 0) -> int:
+        s = _P()
+        self.check(self.dll.sylv_create(ax, ay, prec, stream, C.byref(s)))
+        return s.value
+
+    def sylv_get_refine(self, s: int) -> RefineParams:
+        r = RefineParams()
+        self.check(self.dll.sylv_get_refine(s, C.byref(r)))
+        return r
+
+    def sylv_set_refine(self, s: int, r: RefineParams):
+        self.check(self.dll.sylv_set_refine(s, C.byref(r)))
+
+    def sylv_step(self, s: int, Cp: int, Xp: int, ld: int, stream: int = 0):
+        rr = C.c_double()
+        sw = C.c_int()
+        self.check(self.dll.sylv_step(s, Cp, Xp, ld, stream, C.byref(rr), C.byref(sw)))
+        return rr.value, sw.value
+
+    def sylv_inner_solve(self, s: int, Cp: int, Xp: int, ld: int, stream: int = 0):
+        self.check(self.dll.sylv_inner_solve(s, Cp, Xp, ld, stream))
+
+    def sylv_residual(self, s: int, Cp: int, Xp: int, Rp: int, ld: int, stream: int = 0):
+        self.check(self.dll.sylv_residual(s, Cp, Xp, Rp, ld, stream))
+
+    def sylv_free(self, s: int):
+        if s:
+            self.dll.sylv_free(s)
+
+    # -- time loop
+    def run_params(self, w, prec: int = FDE_FP64, use_graph: int = 0) -> RunParams:
+        px = self.op_params(w.ops[0])
+        py = self.op_params(w.ops[1]) if w.dim == 2 else OpParams()
+        FL = np.asfortranarray(w.src_left, dtype=np.float64)
+        FR = np.asfortranarray(w.src_right if w.src_right is not None else np.zeros((1, 1)), dtype=np.float64)
+        amp = np.ascontiguousarray(w.src_amp, dtype=np.float64)
+        sa = np.ascontiguousarray(w.src_sin_amp, dtype=np.float64)
+        om = np.ascontiguousarray(w.src_omega, dtype=np.float64)
+        rp = RunParams(w.dim, px, py, w.steps, FL.shape[1], FL.ctypes.data, FR.ctypes.data,
+                       amp.ctypes.data, sa.ctypes.data, om.ctypes.data, prec, use_graph)
+        rp._arrays = (px, py, FL, FR, amp, sa, om)
+        return rp
+
+    def fde_run(self, params: RunParams, U0: int, Uout: int, stream: int = 0) -> RunStats:
+        st = RunStats()
+        self.check(self.dll.fde_run(C.byref(params), U0, Uout, stream, C.byref(st)))
+        return st
+
+
+_LIB = None
+
+
+def load(path: str = LIB_PATH) -> Lib:
+    global _LIB
+    if _LIB is None:
+        _LIB = Lib(path)
+    return _LIB
+
+
+def exported_symbols():
+    return list(_SIGS)

@@ -1,0 +1,54 @@
+// Batched dense building blocks (SIMT, FP64 and FP32).
+#pragma once
+#include "common.cuh"
+
+namespace fde {
+
+// One GEMM of a batch: C = alpha op(A) op(B) + beta C, column-major.
+// Optional two-level addressing along k (kblk > 0): the k-th column of a
+// non-transposed A (and of a transposed B) sits at (k / kblk) * kstr +
+// (k % kblk) * ld, i.e. k runs over kblk-wide panels that are kstr apart.
+template <typename T>
+struct GemmDesc {
+  const T* A;
+  const T* B;
+  T* C;
+  int m, n, k, lda, ldb, ldc;
+  int kblk = 0;
+  long long kstr = 0;
+};
+
+// A list of GEMMs with the same transposes / scalars, descriptors resident on
+// the device so that replays (and CUDA-graph capture) need no host work.
+template <typename T>
+struct GemmBatch {
+  GemmDesc<T>* d_desc = nullptr;
+  int batch = 0, max_m = 0, max_n = 0, max_k = 0;
+  bool ta = false, tb = false;
+  T alpha = T(1), beta = T(0);
+};
+
+template <typename T>
+fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, bool ta, bool tb, T alpha,
+                             T beta, GemmBatch<T>* out, cudaStream_t st);
+
+template <typename T>
+fde_status gemm_batch_run(const GemmBatch<T>& b, cudaStream_t st);
+
+// In-place inverse of `batch` square matrices (sizes n_i <= nmax, leading
+// dimension ld, matrix i at A + i*stride) by Gauss–Jordan elimination with
+// partial pivoting on the augmented matrix.  work: batch * nmax * 2*nmax.
+// *d_flag is set to 1 if a zero pivot is met (matrix left unchanged then).
+template <typename T>
+fde_status batched_inverse(T* A, int ld, size_t stride, const int* d_n, int batch, int nmax, T* work,
+                           int* d_flag, cudaStream_t st);
+
+// y[i] = (Tout) x[i]   (n elements)
+template <typename Tin, typename Tout>
+fde_status convert(const Tin* x, Tout* y, size_t n, cudaStream_t st);
+
+// 2D strided copy / convert: Y[i + j*ldy] = (Tout) X[i + j*ldx], m x n
+template <typename Tin, typename Tout>
+fde_status copy2d(const Tin* X, int ldx, Tout* Y, int ldy, int m, int n, cudaStream_t st);
+
+}  // namespace fde

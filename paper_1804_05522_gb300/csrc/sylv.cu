@@ -1,0 +1,953 @@
+// 2D step (§4.2, Eq. (sylv-timestepping)):  A_x X + X A_yᵀ = C.
+//
+// Inner solver S (FP64 or FP32): divide and conquer over the HODLR trees of
+// A_x and A_y (the D&C method the Conclusions name for HODLR right-hand
+// sides): the block-diagonal parts are solved recursively down to the leaf
+// pairs (Bartels–Stewart with precomputed real Schur forms), and on the way up
+// every level adds the low-rank correction δX of
+//     A δX + δX Bᵀ = -(A_off X0 + X0 B_offᵀ) = G Hᵀ        (rank <= 2k_x + 2k_y)
+// solved by factored ADI (the low-rank Sylvester form AX + XB = UVᵀ of §4.2)
+// with shifts from the Zolotarev problem on the spectral intervals of the
+// level's diagonal blocks.
+// Outer loop: iterative refinement in FP64 against the exact structured
+// residual R = C - A_x X - X A_yᵀ (Toeplitz products by FFT).
+#include <float.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "hodlr_internal.cuh"
+#include "schur.cuh"
+
+namespace fde {
+
+// =================================================== spectral bounds / shifts
+// Row sums and Gershgorin radii of the diagonal block A[lo:hi, lo:hi].
+// A is a nonsingular M-matrix (positive diagonal, non-positive off-diagonal
+// entries, strictly diagonally dominant; §2.2.1), so every eigenvalue of a
+// principal block has real part >= its smallest row sum, and <= max(a_ii + r_i).
+static void node_interval(const std::vector<double>& S, const std::vector<double>& dp, const std::vector<double>& dm,
+                          double c, double shift, double alpha, int lo, int hi, double* lam_lo, double* lam_hi) {
+  // S[k] = Σ_{m<=k} g_m ; S(-1) = 0
+  auto Sk = [&](int k) { return k < 0 ? 0.0 : S[k]; };
+  double mn = INFINITY, mx = 0.0;
+  for (int i = lo; i < hi; ++i) {
+    // Σ_{j=lo}^{hi-1} T[i][j] = -Σ_{k=max(i-hi+2,0)}^{i-lo+1} g_k
+    const int kmin = std::max(i - hi + 2, 0), kmax = i - lo + 1;
+    const double sT = -(Sk(kmax) - Sk(kmin - 1));
+    // Σ_{j=lo}^{hi-1} T[j][i] = -Σ_{k=max(lo-i+1,0)}^{hi-i} g_k
+    const int kmin2 = std::max(lo - i + 1, 0), kmax2 = hi - i;
+    const double sTt = -(Sk(kmax2) - Sk(kmin2 - 1));
+    const double rowsum = shift + c * (dp[i] * sT + dm[i] * sTt);
+    const double diag = shift + c * alpha * (dp[i] + dm[i]);
+    mn = std::min(mn, rowsum);
+    mx = std::max(mx, 2.0 * diag - rowsum);
+  }
+  *lam_lo = mn;
+  *lam_hi = mx;
+}
+
+// Jacobi elliptic functions by the arithmetic–geometric mean (descending
+// Landen transformation; Abramowitz & Stegun 16.4) and K(m) = π / (2 AGM).
+static void jacobi_dn_K(double u, double m, double* dn, double* K) {
+  double a[64], cc[64];
+  a[0] = 1.0;
+  double b = sqrt(1.0 - m);
+  cc[0] = sqrt(m);
+  int n = 0;
+  while (n < 60 && fabs(cc[n]) > 1e-17 * a[n]) {
+    a[n + 1] = 0.5 * (a[n] + b);
+    cc[n + 1] = 0.5 * (a[n] - b);
+    b = sqrt(a[n] * b);
+    ++n;
+  }
+  *K = M_PI / (2.0 * a[n]);
+  double phi = ldexp(1.0, n) * a[n] * u, phi_prev = phi;
+  for (int i = n; i > 0; --i) {
+    phi_prev = phi;
+    phi = 0.5 * (phi + asin(cc[i] * sin(phi) / a[i]));
+  }
+  *dn = (n == 0) ? 1.0 : cos(phi) / cos(phi_prev - phi);
+}
+
+// Shifts for A X + X Bᵀ = G Hᵀ with spec(A) ⊂ [a, b], spec(B) ⊂ [c, d]
+// (all > 0): the Zolotarev problem for E = [a, b] and F = [-d, -c] is mapped
+// by a Möbius transform onto [k, 1] ∪ [-1, -k], whose optimal zeros are
+// dn((2j-1)K'/(2J), k') (Wachspress); alpha_j -> zeros near E, beta_j -> poles near F.
+static void zolotarev_shifts(double a, double b, double c, double d, int J, std::vector<double>& al,
+                             std::vector<double>& be) {
+  const double m = (a + d) * (b + c) / ((a + c) * (b + d));
+  double k = 2.0 * m - 1.0 - 2.0 * sqrt(std::max(m * m - m, 0.0));
+  k = std::min(std::max(k, 1e-300), 1.0 - 1e-15);
+  const double mp = 1.0 - k * k;
+  double K, dn;
+  jacobi_dn_K(0.0, mp, &dn, &K);
+  // Möbius w -> z with k -> a, 1 -> b, -1 -> -d:  z = (A w + B)/(C w + 1)
+  // rows: A w + B - z C w = z
+  const double W[3] = {k, 1.0, -1.0}, Z[3] = {a, b, -d};
+  double M[3][4];
+  for (int i = 0; i < 3; ++i) {
+    M[i][0] = W[i];
+    M[i][1] = 1.0;
+    M[i][2] = -Z[i] * W[i];
+    M[i][3] = Z[i];
+  }
+  for (int col = 0; col < 3; ++col) {  // Gauss–Jordan with pivoting
+    int pv = col;
+    for (int i = col + 1; i < 3; ++i)
+      if (fabs(M[i][col]) > fabs(M[pv][col])) pv = i;
+    for (int j = 0; j < 4; ++j) std::swap(M[col][j], M[pv][j]);
+    for (int i = 0; i < 3; ++i)
+      if (i != col) {
+        const double f = M[i][col] / M[col][col];
+        for (int j = 0; j < 4; ++j) M[i][j] -= f * M[col][j];
+      }
+  }
+  const double A_ = M[0][3] / M[0][0], B_ = M[1][3] / M[1][1], C_ = M[2][3] / M[2][2];
+  auto inv = [&](double w) { return (A_ * w + B_) / (C_ * w + 1.0); };
+  al.resize(J);
+  be.resize(J);
+  for (int j = 0; j < J; ++j) {
+    double dnj, Kd;
+    jacobi_dn_K((2.0 * (j + 1) - 1.0) * K / (2.0 * J), mp, &dnj, &Kd);
+    al[j] = inv(dnj);
+    be[j] = inv(-dnj);
+  }
+}
+
+// max_E |r| / min_F |r| for r(z) = Π (z - alpha_j)/(z - beta_j), on log grids.
+static double zolotarev_bound(const std::vector<double>& al, const std::vector<double>& be, double a, double b,
+                              double c, double d) {
+  const int G = 400;
+  double num = 0.0, den = INFINITY;
+  for (int i = 0; i < G; ++i) {
+    const double z = a * pow(b / a, i / (double)(G - 1));
+    const double w = -c * pow(d / c, i / (double)(G - 1));
+    double rz = 1.0, rw = 1.0;
+    for (size_t j = 0; j < al.size(); ++j) {
+      rz *= fabs((z - al[j]) / (z - be[j]));
+      rw *= fabs((w - al[j]) / (w - be[j]));
+    }
+    num = std::max(num, rz);
+    den = std::min(den, rw);
+  }
+  return num / den;
+}
+
+// ================================================================ kernels
+template <typename T>
+__global__ void scale_sub_kernel(T* __restrict__ Z, T* __restrict__ G, size_t n, T cj) {
+  // Z <- cj Z ; G <- G - Z
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T z = cj * Z[i];
+    Z[i] = z;
+    G[i] -= z;
+  }
+}
+template <typename T>
+__global__ void axpy_kernel(T* __restrict__ Y, const T* __restrict__ X, size_t n, T a) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    Y[i] += a * X[i];
+}
+static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 32); }
+
+// X64 += (double) D ; partial sums of |D|^2 and |X64|^2 into acc[0], acc[1]
+template <typename T>
+__global__ void refine_update_kernel(double* __restrict__ X, const T* __restrict__ D, size_t n, double* acc) {
+  __shared__ double sh[32];
+  double sd = 0.0, sx = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double d = (double)D[i];
+    const double x = X[i] + d;
+    X[i] = x;
+    sd += d * d;
+    sx += x * x;
+  }
+  sd = block_sum(sd, sh);
+  sx = block_sum(sx, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(acc, sd);
+    atomicAdd(acc + 1, sx);
+  }
+}
+__global__ void sumsq_kernel(const double* __restrict__ X, size_t n, double* acc) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    s += X[i] * X[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) atomicAdd(acc, s);
+}
+__global__ void nonfinite_kernel(const double* __restrict__ X, size_t n, int* bad) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(X[i])) atomicExch(bad, 1);
+}
+
+// 32x32 tiled transpose of an N x N matrix (ld N):  Y = Xᵀ, or Y -= Xᵀ
+__global__ void transpose_kernel(const double* __restrict__ X, double* __restrict__ Y, int N, int subtract) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = bx + threadIdx.x, c = by + j;
+    if (r < N && c < N) tile[j][threadIdx.x] = X[r + (size_t)c * N];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = by + threadIdx.x, c = bx + j;
+    if (r < N && c < N) {
+      const double v = tile[threadIdx.x][j];
+      if (subtract)
+        Y[r + (size_t)c * N] -= v;
+      else
+        Y[r + (size_t)c * N] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------- FFT (FP64)
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// in-place radix-2 DIT on buf (input in bit-reversed order); tw[k] = e^{-2πik/P}
+__device__ void fft_dit(double2* buf, int P, int logP, const double2* __restrict__ tw, bool inverse) {
+  for (int s = 1; s <= logP; ++s) {
+    const int half = 1 << (s - 1), tstride = P >> s;
+    for (int bidx = threadIdx.x; bidx < (P >> 1); bidx += blockDim.x) {
+      const int grp = bidx >> (s - 1), j = bidx & (half - 1);
+      const int i0 = (grp << s) + j, i1 = i0 + half;
+      double2 w = tw[j * tstride];
+      if (inverse) w.y = -w.y;
+      const double2 u = buf[i0], v = cmul(buf[i1], w);
+      buf[i0] = make_double2(u.x + v.x, u.y + v.y);
+      buf[i1] = make_double2(u.x - v.x, u.y - v.y);
+    }
+    __syncthreads();
+  }
+}
+
+// Columns j0 = 2b, j1 = 2b+1 of X (N x ncols): Y = A X (mode 0) or
+// Y = C - A X (mode 1), A = s I + c (D_+ T + D_- Tᵀ) applied by FFT:
+//   (T x)_i  = -(g * x)[i+1]          (linear convolution, Eq. (toeplitz_FD))
+//   (Tᵀx)_i  = -(g ⋆ x)[i-1]          (correlation = conj(ĝ) in frequency)
+// Two real columns share one complex transform (x_0 + i x_1).
+__global__ void __launch_bounds__(1024) fd_fft_apply_kernel(const double* __restrict__ X, int ncols,
+                                                           const double* __restrict__ Cm, double* __restrict__ Y,
+                                                           const double2* __restrict__ Ghat,
+                                                           const double2* __restrict__ tw, int P, int logP,
+                                                           const double* __restrict__ dp,
+                                                           const double* __restrict__ dm, double c, double shift,
+                                                           int N, double2* __restrict__ scratch, int mode) {
+  extern __shared__ double2 buf[];
+  const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
+  const bool has1 = j1 < ncols;
+  const double* x0 = X + (size_t)j0 * N;
+  const double* x1 = X + (size_t)j1 * N;
+  double2* Xh = scratch + (size_t)blockIdx.x * P;
+  const unsigned sh = 32 - logP;
+  for (int n = threadIdx.x; n < P; n += blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    if (n < N) v = make_double2(x0[n], has1 ? x1[n] : 0.0);
+    buf[__brev(n) >> sh] = v;
+  }
+  __syncthreads();
+  fft_dit(buf, P, logP, tw, false);
+  for (int k = threadIdx.x; k < P; k += blockDim.x) Xh[k] = buf[k];
+  __syncthreads();
+  for (int k = threadIdx.x; k < P; k += blockDim.x) buf[__brev(k) >> sh] = cmul(Xh[k], Ghat[k]);
+  __syncthreads();
+  fft_dit(buf, P, logP, tw, true);
+  const double invP = 1.0 / P;
+  double* y0 = Y + (size_t)j0 * N;
+  double* y1 = Y + (size_t)j1 * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double2 tx = buf[i + 1];
+    y0[i] = shift * x0[i] - c * dp[i] * tx.x * invP;
+    if (has1) y1[i] = shift * x1[i] - c * dp[i] * tx.y * invP;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    const double2 gh = Ghat[k];
+    buf[__brev(k) >> sh] = cmul(Xh[k], make_double2(gh.x, -gh.y));
+  }
+  __syncthreads();
+  fft_dit(buf, P, logP, tw, true);
+  const double* c0 = Cm ? Cm + (size_t)j0 * N : nullptr;
+  const double* c1 = Cm ? Cm + (size_t)j1 * N : nullptr;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double2 ttx = buf[(i - 1 + P) & (P - 1)];
+    double v0 = y0[i] - c * dm[i] * ttx.x * invP;
+    if (mode == 1) v0 = c0[i] - v0;
+    y0[i] = v0;
+    if (has1) {
+      double v1 = y1[i] - c * dm[i] * ttx.y * invP;
+      if (mode == 1) v1 = c1[i] - v1;
+      y1[i] = v1;
+    }
+  }
+}
+
+// spectrum of the zero-padded weights g_0..g_N (one transform)
+__global__ void __launch_bounds__(1024) ghat_kernel(const double* __restrict__ g, int N, const double2* __restrict__ tw,
+                                                   int P, int logP, double2* Ghat) {
+  extern __shared__ double2 buf[];
+  const unsigned sh = 32 - logP;
+  for (int n = threadIdx.x; n < P; n += blockDim.x)
+    buf[__brev(n) >> sh] = make_double2(n <= N ? g[n] : 0.0, 0.0);
+  __syncthreads();
+  fft_dit(buf, P, logP, tw, false);
+  for (int k = threadIdx.x; k < P; k += blockDim.x) Ghat[k] = buf[k];
+}
+
+// Zero-padding masks for the constant parts of the fADI right-hand sides:
+// dst[rows of node, col0 + 0..K) = U masked to child-1 rows, [col0+K, col0+2K) masked to child-2 rows.
+template <typename T>
+struct MaskJob {
+  const T* U;   // level factor, ld N
+  T* dst;       // ld N
+  int lo, mid, hi, K;
+  T scale;
+};
+template <typename T>
+__global__ void mask_copy_kernel(const MaskJob<T>* __restrict__ jobs, int N) {
+  const MaskJob<T> jb = jobs[blockIdx.x];
+  const int len = jb.hi - jb.lo;
+  for (int e = threadIdx.x; e < len * 2 * jb.K; e += blockDim.x) {
+    const int r = jb.lo + e % len, cc = e / len;
+    const int half = cc / jb.K, kk = cc % jb.K;
+    const bool in = (half == 0) ? (r < jb.mid) : (r >= jb.mid);
+    jb.dst[r + (size_t)cc * N] = in ? jb.scale * jb.U[r + (size_t)kk * N] : T(0);
+  }
+}
+
+// =============================================================== solver
+template <typename T>
+struct LevelSolve {
+  int J = 0, Q = 0, ncols = 0;        // shifts, RHS width per pair, N x ncols blocks
+  std::vector<double> a, b;           // shifts: (B + a_j I), (A + b_j I)
+  T* Gt = nullptr;                    // constant part of G (N x ncols)
+  T* Ht = nullptr;                    // constant part of H
+  T* G = nullptr;                     // working G, H (N x ncols)
+  T* H = nullptr;
+  T* Zall = nullptr;                  // J panels of N x ncols
+  T* Wall = nullptr;
+  std::vector<Plan<T>> planA, planB;  // per shift
+  GemmBatch<T> g_rhs_x, g_rhs_y;      // HA (into H) and GB (into G) products with X0
+  GemmBatch<T> g_update;              // X += Σ_j Z_j W_jᵀ per pair
+};
+
+template <typename T>
+struct Inner {
+  T *Cin = nullptr, *W1 = nullptr, *W2 = nullptr, *X = nullptr;
+  T *Qx = nullptr, *Sx = nullptr, *Qy = nullptr, *Sy = nullptr;
+  GemmBatch<T> g_qxt, g_qy, g_qx, g_qyt;
+  std::vector<LevelSolve<T>> lv;
+  std::vector<Fact<T>> facts;         // keeps FP32 demoted factorisations alive
+};
+
+}  // namespace fde
+
+using namespace fde;
+
+struct sylv_s {
+  hodlr_s* ax = nullptr;
+  hodlr_s* ay = nullptr;
+  int prec = 0, N = 0, L = 0, lmax = 0;
+  DevPool pool;
+  double *Qx = nullptr, *Sx = nullptr, *Qy = nullptr, *Sy = nullptr;  // FP64 leaf Schur forms
+  int *d_lo = nullptr, *d_n = nullptr;
+  std::vector<Fact<double>> facts64;
+  Inner<double> in64;
+  Inner<float> in32;
+  // residual
+  int P = 0, logP = 0;
+  double2 *tw = nullptr, *GhX = nullptr, *GhY = nullptr, *fft_scratch = nullptr;
+  double *R = nullptr, *Xt = nullptr, *Yt = nullptr, *X64 = nullptr, *C64 = nullptr;
+  double* acc = nullptr;              // device accumulators
+  int* d_bad = nullptr;
+  sylv_refine_t refine{};
+  std::vector<int> J;
+};
+
+namespace fde {
+
+template <typename T>
+static std::vector<T*> level_V(hodlr_s* h);
+template <>
+std::vector<double*> level_V<double>(hodlr_s* h) {
+  return h->V;
+}
+template <>
+std::vector<float*> level_V<float>(hodlr_s* h) {
+  return h->V32;
+}
+template <typename T>
+static std::vector<T*> level_U(hodlr_s* h);
+template <>
+std::vector<double*> level_U<double>(hodlr_s* h) {
+  return h->U;
+}
+template <>
+std::vector<float*> level_U<float>(hodlr_s* h) {
+  return h->U32;
+}
+
+template <typename T>
+static fde_status convert_buf(const double* src, T** dst, size_t n, DevPool& pool, cudaStream_t st) {
+  FDE_TRY(pool.alloc(dst, n));
+  if (sizeof(T) == sizeof(double)) {
+    FDE_CUDA(cudaMemcpyAsync((void*)*dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    FDE_TRY((convert<double, float>(src, (float*)*dst, n, st)));
+  }
+  return FDE_OK;
+}
+
+// Build the inner solver of precision T: leaf transforms, fADI levels, plans.
+template <typename T>
+static fde_status build_inner(sylv_s* S, Inner<T>& in, const std::vector<Fact<T>*>& FA_all,
+                              const std::vector<Fact<T>*>& FB_all, cudaStream_t st) {
+  hodlr_s* ax = S->ax;
+  hodlr_s* ay = S->ay;
+  const Tree& tr = ax->tree;
+  const int N = S->N, L = S->L, lmax = S->lmax, nl = tr.nleaves();
+  DevPool& pool = S->pool;
+  const size_t NN = (size_t)N * N, nleaf_el = (size_t)nl * lmax * lmax;
+  FDE_TRY(pool.alloc(&in.Cin, NN));
+  FDE_TRY(pool.alloc(&in.W1, NN));
+  FDE_TRY(pool.alloc(&in.W2, NN));
+  FDE_TRY(pool.alloc(&in.X, NN));
+  FDE_TRY(convert_buf<T>(S->Qx, &in.Qx, nleaf_el, pool, st));
+  FDE_TRY(convert_buf<T>(S->Sx, &in.Sx, nleaf_el, pool, st));
+  FDE_TRY(convert_buf<T>(S->Qy, &in.Qy, nleaf_el, pool, st));
+  FDE_TRY(convert_buf<T>(S->Sy, &in.Sy, nleaf_el, pool, st));
+  // leaf transforms:  W1 = Qxᵀ C,  W2 = W1 Qy,  (trsyl on W2),  W1 = Qx W2,  X = W1 Qyᵀ
+  {
+    std::vector<GemmDesc<T>> a, b, c, d;
+    for (int p = 0; p < nl; ++p) {
+      const int lo = ax->leaf_lo[p], n = ax->leaf_n[p];
+      const T* Qp = in.Qx + (size_t)p * lmax * lmax;
+      a.push_back({Qp, in.Cin + lo, in.W1 + lo, n, N, n, lmax, N, N});
+      c.push_back({Qp, in.W2 + lo, in.W1 + lo, n, N, n, lmax, N, N});
+      const int loy = ay->leaf_lo[p], ny = ay->leaf_n[p];
+      const T* Qq = in.Qy + (size_t)p * lmax * lmax;
+      b.push_back({in.W1 + (size_t)loy * N, Qq, in.W2 + (size_t)loy * N, N, ny, ny, N, lmax, N});
+      d.push_back({in.W1 + (size_t)loy * N, Qq, in.X + (size_t)loy * N, N, ny, ny, N, lmax, N});
+    }
+    FDE_TRY(gemm_batch_upload(pool, a, true, false, T(1), T(0), &in.g_qxt, st));
+    FDE_TRY(gemm_batch_upload(pool, b, false, false, T(1), T(0), &in.g_qy, st));
+    FDE_TRY(gemm_batch_upload(pool, c, false, false, T(1), T(0), &in.g_qx, st));
+    FDE_TRY(gemm_batch_upload(pool, d, false, true, T(1), T(0), &in.g_qyt, st));
+  }
+  in.lv.resize(L);
+  std::vector<T*> Vx = level_V<T>(ax), Vy = level_V<T>(ay), Ux = level_U<T>(ax), Uy = level_U<T>(ay);
+  size_t fi = 0;
+  // scratch for plans (largest level)
+  for (int l = L - 1; l >= 0; --l) {
+    LevelSolve<T>& ls = in.lv[l];
+    const int Kx = ax->K[l], Ky = ay->K[l], Qw = 2 * Kx + 2 * Ky, nn = 1 << l;
+    ls.J = S->J[l];
+    ls.Q = Qw;
+    ls.ncols = nn * Qw;
+    const size_t blk = (size_t)N * ls.ncols;
+    FDE_TRY(pool.alloc(&ls.Gt, blk));
+    FDE_TRY(pool.alloc(&ls.Ht, blk));
+    FDE_TRY(pool.alloc(&ls.G, blk));
+    FDE_TRY(pool.alloc(&ls.H, blk));
+    FDE_TRY(pool.alloc(&ls.Zall, blk * ls.J));
+    FDE_TRY(pool.alloc(&ls.Wall, blk * ls.J));
+    FDE_CUDA(cudaMemsetAsync(ls.Gt, 0, blk * sizeof(T), st));
+    FDE_CUDA(cudaMemsetAsync(ls.Ht, 0, blk * sizeof(T), st));
+    // constant parts: G[:, qQ + 0..2Kx) = -[U^x|c1, U^x|c2] ; H[:, pQ + 2Kx..Q) = [U^y|c1', U^y|c2']
+    {
+      std::vector<MaskJob<T>> jobs;
+      for (int p = 0; p < nn; ++p) {
+        const int idx = tr.id(l, p);
+        const int lo = tr.lo[idx], hi = tr.hi[idx], mid = lo + (hi - lo) / 2;
+        const int loy = ay->tree.lo[idx], hiy = ay->tree.hi[idx], midy = loy + (hiy - loy) / 2;
+        for (int q = 0; q < nn; ++q) {
+          jobs.push_back({Ux[l], ls.Gt + (size_t)(q * Qw) * N, lo, mid, hi, Kx, T(-1)});
+          jobs.push_back({Uy[l], ls.Ht + (size_t)(q * Qw + 2 * Kx) * N, loy, midy, hiy, Ky, T(1)});
+        }
+      }
+      // note: for the H template, "q" above runs over the x-node index p' of the column block
+      MaskJob<T>* dj;
+      FDE_TRY(pool.alloc(&dj, jobs.size()));
+      FDE_CUDA(cudaMemcpy(dj, jobs.data(), jobs.size() * sizeof(MaskJob<T>), cudaMemcpyHostToDevice));
+      mask_copy_kernel<T><<<(int)jobs.size(), 256, 0, st>>>(dj, N);
+      FDE_LAUNCH("mask_copy_kernel");
+    }
+    // X0-dependent parts (GEMMs on the current X):
+    //   H[q rows, pQ + 0..Kx)   = X0[c2_p, q cols]ᵀ V^x[c2_p] ; [Kx, 2Kx) = X0[c1_p, q cols]ᵀ V^x[c1_p]
+    //   G[p rows, qQ+2Kx..+Ky)  = -X0[p rows, c2'_q] V^y[c2'_q] ; [.. + Ky, Q) = -X0[p rows, c1'_q] V^y[c1'_q]
+    {
+      std::vector<GemmDesc<T>> dh, dg, du;
+      for (int p = 0; p < nn; ++p) {
+        const int idx = tr.id(l, p);
+        const int lo = tr.lo[idx], hi = tr.hi[idx], mid = lo + (hi - lo) / 2;
+        for (int q = 0; q < nn; ++q) {
+          const int idy = ay->tree.id(l, q);
+          const int loy = ay->tree.lo[idy], hiy = ay->tree.hi[idy], midy = loy + (hiy - loy) / 2;
+          const int tq = hiy - loy, sp = hi - lo;
+          T* Hb = ls.H + loy + (size_t)(p * Qw) * N;
+          dh.push_back({in.X + mid + (size_t)loy * N, Vx[l] + mid, Hb, tq, Kx, hi - mid, N, N, N});
+          dh.push_back({in.X + lo + (size_t)loy * N, Vx[l] + lo, Hb + (size_t)Kx * N, tq, Kx, mid - lo, N, N, N});
+          T* Gb = ls.G + lo + (size_t)(q * Qw + 2 * Kx) * N;
+          dg.push_back({in.X + lo + (size_t)midy * N, Vy[l] + midy, Gb, sp, Ky, hiy - midy, N, N, N});
+          dg.push_back({in.X + lo + (size_t)loy * N, Vy[l] + loy, Gb + (size_t)Ky * N, sp, Ky, midy - loy, N, N, N});
+          GemmDesc<T> u{ls.Zall + lo + (size_t)(q * Qw) * N, ls.Wall + loy + (size_t)(p * Qw) * N,
+                        in.X + lo + (size_t)loy * N, sp, tq, ls.J * Qw, N, N, N};
+          u.kblk = Qw;
+          u.kstr = (long long)N * ls.ncols;
+          du.push_back(u);
+        }
+      }
+      FDE_TRY(gemm_batch_upload(pool, dh, true, false, T(1), T(0), &ls.g_rhs_x, st));
+      FDE_TRY(gemm_batch_upload(pool, dg, false, false, T(-1), T(0), &ls.g_rhs_y, st));
+      FDE_TRY(gemm_batch_upload(pool, du, false, true, T(1), T(1), &ls.g_update, st));
+    }
+    // solve plans per shift: Z_j = (A_p + b_j I)^{-1} G,  W_j = (B_q + a_j I)^{-1} H
+    const size_t zel = std::max(solve_scratch_elems(ax, ls.ncols, l), solve_scratch_elems(ay, ls.ncols, l));
+    T *zb, *wb;
+    FDE_TRY(pool.alloc(&zb, zel));
+    FDE_TRY(pool.alloc(&wb, zel));
+    ls.planA.resize(ls.J);
+    ls.planB.resize(ls.J);
+    for (int j = 0; j < ls.J; ++j) {
+      const Fact<T>& FA = *FA_all[fi + j];
+      const Fact<T>& FB = *FB_all[fi + j];
+      FDE_TRY(build_solve_plan<T>(ax, FA, Vx, ls.G, N, ls.Zall + (size_t)j * blk, N, ls.ncols, l, nullptr, zb, wb,
+                                  pool, &ls.planA[j], st));
+      FDE_TRY(build_solve_plan<T>(ay, FB, Vy, ls.H, N, ls.Wall + (size_t)j * blk, N, ls.ncols, l, nullptr, zb, wb,
+                                  pool, &ls.planB[j], st));
+    }
+    fi += ls.J;
+  }
+  FDE_CUDA(cudaStreamSynchronize(st));
+  return FDE_OK;
+}
+
+// X = S(C): in.Cin -> in.X
+template <typename T>
+static fde_status run_inner(sylv_s* S, Inner<T>& in, cudaStream_t st) {
+  hodlr_s* ax = S->ax;
+  hodlr_s* ay = S->ay;
+  const int N = S->N, nl = ax->tree.nleaves();
+  FDE_TRY(gemm_batch_run(in.g_qxt, st));
+  FDE_TRY(gemm_batch_run(in.g_qy, st));
+  FDE_TRY(leaf_trsyl<T>(in.Sx, in.Sy, S->lmax, S->d_lo, S->d_n, nl, S->d_lo + nl, S->d_n + nl, nl, in.W2, N, st));
+  FDE_TRY(gemm_batch_run(in.g_qx, st));
+  FDE_TRY(gemm_batch_run(in.g_qyt, st));
+  for (int l = S->L - 1; l >= 0; --l) {
+    LevelSolve<T>& ls = in.lv[l];
+    const size_t blk = (size_t)N * ls.ncols;
+    FDE_CUDA(cudaMemcpyAsync(ls.G, ls.Gt, blk * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    FDE_CUDA(cudaMemcpyAsync(ls.H, ls.Ht, blk * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    FDE_TRY(gemm_batch_run(ls.g_rhs_x, st));
+    FDE_TRY(gemm_batch_run(ls.g_rhs_y, st));
+    for (int j = 0; j < ls.J; ++j) {
+      FDE_TRY(plan_run(ls.planA[j], st));
+      FDE_TRY(plan_run(ls.planB[j], st));
+      const T cj = (T)(ls.a[j] + ls.b[j]);
+      T* Zj = ls.Zall + (size_t)j * blk;
+      T* Wj = ls.Wall + (size_t)j * blk;
+      scale_sub_kernel<T><<<grid_for(blk), 256, 0, st>>>(Zj, ls.G, blk, cj);
+      axpy_kernel<T><<<grid_for(blk), 256, 0, st>>>(ls.H, Wj, blk, -cj);
+      FDE_LAUNCH("fadi update");
+    }
+    FDE_TRY(gemm_batch_run(ls.g_update, st));
+  }
+  (void)ay;
+  return FDE_OK;
+}
+
+// R = C - A_x X - X A_yᵀ (FP64, structured)
+static fde_status residual(sylv_s* S, const double* C, const double* X, double* R, cudaStream_t st) {
+  hodlr_s* ax = S->ax;
+  hodlr_s* ay = S->ay;
+  const int N = S->N, P = S->P, lp = S->logP;
+  const int nb = (N + 1) / 2;
+  const size_t smem = (size_t)P * sizeof(double2);
+  fd_fft_apply_kernel<<<nb, 1024, smem, st>>>(X, N, C, R, S->GhX, S->tw, P, lp, ax->dp, ax->dm, ax->c,
+                                               ax->p.shift, N, S->fft_scratch, 1);
+  FDE_LAUNCH("fd_fft_apply_kernel x");
+  dim3 tg(ceil_div(N, 32), ceil_div(N, 32)), tb(32, 8);
+  transpose_kernel<<<tg, tb, 0, st>>>(X, S->Xt, N, 0);
+  fd_fft_apply_kernel<<<nb, 1024, smem, st>>>(S->Xt, N, nullptr, S->Yt, S->GhY, S->tw, P, lp, ay->dp, ay->dm, ay->c,
+                                               ay->p.shift, N, S->fft_scratch, 0);
+  FDE_LAUNCH("fd_fft_apply_kernel y");
+  transpose_kernel<<<tg, tb, 0, st>>>(S->Yt, R, N, 1);
+  FDE_LAUNCH("transpose_kernel");
+  return FDE_OK;
+}
+
+static fde_status read_acc(sylv_s* S, double* h, int n, cudaStream_t st) {
+  FDE_CUDA(cudaMemcpyAsync(h, S->acc, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FDE_CUDA(cudaStreamSynchronize(st));
+  return FDE_OK;
+}
+
+// One refinement sweep: Cin = (T) R ; inner solve ; X64 += X_T ; R = C - A(X64).
+// acc[0] = ||δ||², acc[1] = ||X||², acc[2] = ||R||² of this sweep.
+template <typename T>
+static fde_status sweep(sylv_s* S, Inner<T>& in, const double* C, double* X64, cudaStream_t st) {
+  const size_t NN = (size_t)S->N * S->N;
+  if (sizeof(T) == sizeof(double)) {
+    FDE_CUDA(cudaMemcpyAsync((void*)in.Cin, S->R, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    FDE_TRY((convert<double, float>(S->R, (float*)in.Cin, NN, st)));
+  }
+  FDE_TRY(run_inner<T>(S, in, st));
+  FDE_CUDA(cudaMemsetAsync(S->acc, 0, 3 * sizeof(double), st));
+  refine_update_kernel<T><<<grid_for(NN), 256, 0, st>>>(X64, in.X, NN, S->acc);
+  FDE_LAUNCH("refine_update_kernel");
+  FDE_TRY(residual(S, C, X64, S->R, st));
+  sumsq_kernel<<<grid_for(NN), 256, 0, st>>>(S->R, NN, S->acc + 2);
+  FDE_LAUNCH("sumsq_kernel");
+  return FDE_OK;
+}
+
+// Iterative refinement (FP64 residual, inner solve in the handle's precision).
+// Stops when ||δX||_F <= tol_update ||X||_F or ||R||_F <= tol_relres ||C||_F;
+// FDE_ERR_NOCONV if neither holds after max_sweeps.  With fixed_sweeps > 0 it
+// runs exactly that many sweeps and never synchronises with the host unless a
+// residual is requested.
+static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStream_t st, double* relres,
+                                 int* sweeps) {
+  const size_t NN = (size_t)S->N * S->N;
+  const sylv_refine_t& rf = S->refine;
+  const bool fixed = rf.fixed_sweeps > 0;
+  FDE_CUDA(cudaMemsetAsync(S->acc, 0, 8 * sizeof(double), st));
+  sumsq_kernel<<<grid_for(NN), 256, 0, st>>>(C, NN, S->acc + 4);
+  FDE_LAUNCH("sumsq_kernel");
+  if (!fixed) {
+    FDE_CUDA(cudaMemsetAsync(S->d_bad, 0, sizeof(int), st));
+    nonfinite_kernel<<<grid_for(NN), 256, 0, st>>>(C, NN, S->d_bad);
+    FDE_LAUNCH("nonfinite_kernel");
+    int bad = 0;
+    FDE_CUDA(cudaMemcpyAsync(&bad, S->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FDE_CUDA(cudaStreamSynchronize(st));
+    if (bad) {
+      set_error("sylv_step: non-finite right-hand side");
+      return FDE_ERR_NUMERIC;
+    }
+  }
+  FDE_TRY(residual(S, C, X, S->R, st));
+  const int nsw = fixed ? rf.fixed_sweeps : rf.max_sweeps;
+  int done = 0;
+  bool converged = fixed;
+  double a[8];
+  for (int sw = 0; sw < nsw; ++sw) {
+    if (S->prec == FDE_FP64)
+      FDE_TRY(sweep<double>(S, S->in64, C, X, st));
+    else
+      FDE_TRY(sweep<float>(S, S->in32, C, X, st));
+    ++done;
+    if (fixed) continue;
+    FDE_TRY(read_acc(S, a, 8, st));
+    if (!std::isfinite(a[0]) || !std::isfinite(a[1]) || !std::isfinite(a[2])) {
+      set_error("sylv_step: non-finite iterate after sweep %d", done);
+      return FDE_ERR_NUMERIC;
+    }
+    if (a[0] <= rf.tol_update * rf.tol_update * a[1] || a[2] <= rf.tol_relres * rf.tol_relres * a[4]) {
+      converged = true;
+      break;
+    }
+  }
+  if (sweeps) *sweeps = done;
+  if (relres) {
+    FDE_TRY(read_acc(S, a, 8, st));
+    *relres = (a[4] > 0.0) ? sqrt(a[2] / a[4]) : sqrt(a[2]);
+  }
+  if (!converged) {
+    set_error("sylv_step: no convergence after %d refinement sweeps", done);
+    return FDE_ERR_NOCONV;
+  }
+  return FDE_OK;
+}
+
+static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t st, sylv_s* S) {
+  S->ax = ax;
+  S->ay = ay;
+  S->prec = prec;
+  const int N = ax->tree.N, L = ax->tree.L;
+  S->N = N;
+  S->L = L;
+  S->lmax = ax->lmax;
+  DevPool& pool = S->pool;
+  const int nl = ax->tree.nleaves();
+  const size_t nleaf_el = (size_t)nl * S->lmax * S->lmax;
+  // ---- leaf Schur forms (K8)
+  FDE_TRY(pool.alloc(&S->Sx, nleaf_el));
+  FDE_TRY(pool.alloc(&S->Qx, nleaf_el));
+  FDE_TRY(pool.alloc(&S->Sy, nleaf_el));
+  FDE_TRY(pool.alloc(&S->Qy, nleaf_el));
+  FDE_CUDA(cudaMemcpyAsync(S->Sx, ax->D, nleaf_el * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  FDE_CUDA(cudaMemcpyAsync(S->Sy, ay->D, nleaf_el * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  FDE_TRY(pool.alloc(&S->d_lo, 2 * nl));
+  FDE_TRY(pool.alloc(&S->d_n, 2 * nl));
+  {
+    std::vector<int> lo(2 * nl), n(2 * nl);
+    for (int p = 0; p < nl; ++p) {
+      lo[p] = ax->leaf_lo[p];
+      n[p] = ax->leaf_n[p];
+      lo[nl + p] = ay->leaf_lo[p];
+      n[nl + p] = ay->leaf_n[p];
+    }
+    FDE_CUDA(cudaMemcpy(S->d_lo, lo.data(), 2 * nl * sizeof(int), cudaMemcpyHostToDevice));
+    FDE_CUDA(cudaMemcpy(S->d_n, n.data(), 2 * nl * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  int* d_fail;
+  FDE_TRY(pool.alloc(&d_fail, 2 * nl));
+  FDE_CUDA(cudaMemsetAsync(d_fail, 0, 2 * nl * sizeof(int), st));
+  FDE_TRY(leaf_schur(S->Sx, S->Qx, S->lmax, (size_t)S->lmax * S->lmax, S->d_n, nl, d_fail, st));
+  FDE_TRY(leaf_schur(S->Sy, S->Qy, S->lmax, (size_t)S->lmax * S->lmax, S->d_n + nl, nl, d_fail + nl, st));
+  {
+    std::vector<int> f(2 * nl);
+    FDE_CUDA(cudaMemcpyAsync(f.data(), d_fail, 2 * nl * sizeof(int), cudaMemcpyDeviceToHost, st));
+    FDE_CUDA(cudaStreamSynchronize(st));
+    for (int v : f)
+      if (v) {
+        set_error("sylv_create: leaf Schur iteration did not converge");
+        return FDE_ERR_NOCONV;
+      }
+  }
+  // ---- shifts per level (host: spectral intervals of the level's blocks)
+  std::vector<double> gx(N + 2), gy(N + 2), dpx(N), dmx(N), dpy(N), dmy(N);
+  FDE_CUDA(cudaMemcpy(gx.data(), ax->g, (N + 2) * sizeof(double), cudaMemcpyDeviceToHost));
+  FDE_CUDA(cudaMemcpy(gy.data(), ay->g, (N + 2) * sizeof(double), cudaMemcpyDeviceToHost));
+  FDE_CUDA(cudaMemcpy(dpx.data(), ax->dp, N * sizeof(double), cudaMemcpyDeviceToHost));
+  FDE_CUDA(cudaMemcpy(dmx.data(), ax->dm, N * sizeof(double), cudaMemcpyDeviceToHost));
+  FDE_CUDA(cudaMemcpy(dpy.data(), ay->dp, N * sizeof(double), cudaMemcpyDeviceToHost));
+  FDE_CUDA(cudaMemcpy(dmy.data(), ay->dm, N * sizeof(double), cudaMemcpyDeviceToHost));
+  std::vector<double> Sxs(N + 2), Sys(N + 2);
+  {
+    long double ax_ = 0, ay_ = 0;
+    for (int k = 0; k < N + 2; ++k) {
+      ax_ += gx[k];
+      ay_ += gy[k];
+      Sxs[k] = (double)ax_;
+      Sys[k] = (double)ay_;
+    }
+  }
+  const double target = (prec == FDE_FP64) ? 1e-13 : 1e-7;
+  S->J.assign(L, 0);
+  std::vector<std::vector<double>> A_(L), B_(L);
+  for (int l = 0; l < L; ++l) {
+    double a = INFINITY, b = 0.0, c = INFINITY, d = 0.0;
+    for (int p = 0; p < (1 << l); ++p) {
+      const int id = ax->tree.id(l, p);
+      double lo_, hi_;
+      node_interval(Sxs, dpx, dmx, ax->c, ax->p.shift, ax->p.alpha, ax->tree.lo[id], ax->tree.hi[id], &lo_, &hi_);
+      a = std::min(a, lo_);
+      b = std::max(b, hi_);
+      node_interval(Sys, dpy, dmy, ay->c, ay->p.shift, ay->p.alpha, ay->tree.lo[id], ay->tree.hi[id], &lo_, &hi_);
+      c = std::min(c, lo_);
+      d = std::max(d, hi_);
+    }
+    int J = 1;
+    std::vector<double> al, be;
+    for (J = 1; J <= 64; ++J) {
+      zolotarev_shifts(a, b, c, d, J, al, be);
+      if (zolotarev_bound(al, be, a, b, c, d) <= target) break;
+    }
+    if (J > 64) J = 64;
+    zolotarev_shifts(a, b, c, d, J, al, be);
+    S->J[l] = J;
+    A_[l] = al;
+    B_[l] = be;
+  }
+  // ---- shifted factorisations: A_x + b_j I and A_y + a_j I (b_j = -beta_j)
+  S->facts64.reserve(2 * 64 * L);
+  std::vector<Fact<double>*> FA64, FB64;
+  for (int l = L - 1; l >= 0; --l) {
+    for (int j = 0; j < S->J[l]; ++j) {
+      S->facts64.emplace_back();
+      FDE_TRY(hodlr_factorize(ax, -B_[l][j], l, &S->facts64.back(), st));
+    }
+    for (int j = 0; j < S->J[l]; ++j) {
+      S->facts64.emplace_back();
+      FDE_TRY(hodlr_factorize(ay, A_[l][j], l, &S->facts64.back(), st));
+    }
+  }
+  {
+    size_t idx = 0;
+    for (int l = L - 1; l >= 0; --l) {
+      for (int j = 0; j < S->J[l]; ++j) FA64.push_back(&S->facts64[idx++]);
+      for (int j = 0; j < S->J[l]; ++j) FB64.push_back(&S->facts64[idx++]);
+    }
+  }
+  // ---- inner solver(s)
+  auto set_shifts = [&](auto& in) {
+    for (int l = 0; l < L; ++l) {
+      in.lv[l].a = A_[l];
+      in.lv[l].b.resize(S->J[l]);
+      for (int j = 0; j < S->J[l]; ++j) in.lv[l].b[j] = -B_[l][j];
+    }
+  };
+  if (prec == FDE_FP64) {
+    FDE_TRY(build_inner<double>(S, S->in64, FA64, FB64, st));
+    set_shifts(S->in64);
+  } else {
+    FDE_TRY(hodlr_make_fp32(ax, st));
+    FDE_TRY(hodlr_make_fp32(ay, st));
+    S->in32.facts.resize(FA64.size() + FB64.size());
+    std::vector<Fact<float>*> FA32, FB32;
+    for (size_t i = 0; i < FA64.size(); ++i) {
+      FDE_TRY(fact_demote(ax, *FA64[i], &S->in32.facts[i], S->pool, st));
+      FA32.push_back(&S->in32.facts[i]);
+    }
+    for (size_t i = 0; i < FB64.size(); ++i) {
+      FDE_TRY(fact_demote(ay, *FB64[i], &S->in32.facts[FA64.size() + i], S->pool, st));
+      FB32.push_back(&S->in32.facts[FA64.size() + i]);
+    }
+    FDE_TRY(build_inner<float>(S, S->in32, FA32, FB32, st));
+    set_shifts(S->in32);
+  }
+  // ---- residual (FFT)
+  S->logP = 1;
+  while ((1 << S->logP) < 2 * N) ++S->logP;
+  S->P = 1 << S->logP;
+  if (S->P > 8192) {
+    set_error("argument error: N = %d exceeds the single-CTA FFT residual limit (N <= 4096)", N);
+    return FDE_ERR_ARG;
+  }
+  {
+    std::vector<double2> tw(S->P / 2);
+    for (int k = 0; k < S->P / 2; ++k) {
+      const double ang = -2.0 * M_PI * (double)k / (double)S->P;
+      tw[k] = make_double2(cos(ang), sin(ang));
+    }
+    FDE_TRY(pool.alloc(&S->tw, S->P / 2));
+    FDE_CUDA(cudaMemcpy(S->tw, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  }
+  FDE_TRY(pool.alloc(&S->GhX, S->P));
+  FDE_TRY(pool.alloc(&S->GhY, S->P));
+  const size_t smem = (size_t)S->P * sizeof(double2);
+  FDE_CUDA(cudaFuncSetAttribute(fd_fft_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FDE_CUDA(cudaFuncSetAttribute(ghat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ghat_kernel<<<1, 1024, smem, st>>>(ax->g, N, S->tw, S->P, S->logP, S->GhX);
+  ghat_kernel<<<1, 1024, smem, st>>>(ay->g, N, S->tw, S->P, S->logP, S->GhY);
+  FDE_LAUNCH("ghat_kernel");
+  const size_t NN = (size_t)N * N;
+  FDE_TRY(pool.alloc(&S->fft_scratch, (size_t)((N + 1) / 2) * S->P));
+  FDE_TRY(pool.alloc(&S->R, NN));
+  FDE_TRY(pool.alloc(&S->Xt, NN));
+  FDE_TRY(pool.alloc(&S->Yt, NN));
+  FDE_TRY(pool.alloc(&S->acc, 8));
+  FDE_TRY(pool.alloc(&S->d_bad, 1));
+  S->refine.max_sweeps = 12;
+  S->refine.tol_update = (prec == FDE_FP64) ? 1e-13 : 1e-11;
+  S->refine.tol_relres = 1e-14;
+  S->refine.fixed_sweeps = 0;
+  FDE_CUDA(cudaStreamSynchronize(st));
+  return FDE_OK;
+}
+
+}  // namespace fde
+
+// ===================================================================== ABI
+extern "C" fde_status sylv_create(hodlr_t Ax, hodlr_t Ay, int prec, void* stream, sylv_t* out) {
+  FDE_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  FDE_ARG(Ax != nullptr && Ay != nullptr, "NULL operator");
+  FDE_ARG(prec == FDE_FP64 || prec == FDE_FP32_REFINE, "unknown precision");
+  FDE_ARG(Ax->tree.N == Ay->tree.N && Ax->tree.leaf == Ay->tree.leaf, "A_x and A_y must share N and leaf");
+  FDE_ARG(Ax->tree.L >= 1, "N must exceed the leaf size");
+  sylv_s* S = new sylv_s();
+  fde_status s = create_impl(Ax, Ay, prec, (cudaStream_t)stream, S);
+  if (s != FDE_OK) {
+    delete S;
+    return s;
+  }
+  *out = S;
+  return FDE_OK;
+}
+
+extern "C" fde_status sylv_get_refine(sylv_t s, sylv_refine_t* r) {
+  FDE_ARG(s != nullptr && r != nullptr, "NULL argument");
+  *r = s->refine;
+  return FDE_OK;
+}
+extern "C" fde_status sylv_set_refine(sylv_t s, const sylv_refine_t* r) {
+  FDE_ARG(s != nullptr && r != nullptr, "NULL argument");
+  FDE_ARG(r->max_sweeps >= 1 && r->max_sweeps <= 100, "max_sweeps must be in [1, 100]");
+  FDE_ARG(r->fixed_sweeps >= 0 && r->fixed_sweeps <= 100, "fixed_sweeps must be in [0, 100]");
+  FDE_ARG(r->tol_update >= 0.0 && r->tol_relres >= 0.0, "tolerances must be >= 0");
+  s->refine = *r;
+  return FDE_OK;
+}
+
+static fde_status with_contig(sylv_t s, const double* C, double* X, int ld, cudaStream_t st,
+                              fde_status (*fn)(sylv_t, const double*, double*, cudaStream_t, void*), void* ctx) {
+  const int N = s->N;
+  if (ld == N) return fn(s, C, X, st, ctx);
+  if (!s->X64) {
+    FDE_TRY(s->pool.alloc(&s->X64, (size_t)N * N));
+    FDE_TRY(s->pool.alloc(&s->C64, (size_t)N * N));
+  }
+  FDE_TRY((copy2d<double, double>(C, ld, s->C64, N, N, N, st)));
+  FDE_TRY((copy2d<double, double>(X, ld, s->X64, N, N, N, st)));
+  FDE_TRY(fn(s, s->C64, s->X64, st, ctx));
+  FDE_TRY((copy2d<double, double>(s->X64, N, X, ld, N, N, st)));
+  return FDE_OK;
+}
+
+struct StepCtx {
+  double* relres;
+  int* sweeps;
+  fde_status status;
+};
+static fde_status step_fn(sylv_t s, const double* C, double* X, cudaStream_t st, void* ctx) {
+  StepCtx* c = (StepCtx*)ctx;
+  return sylv_step_impl(s, C, X, st, c->relres, c->sweeps);
+}
+
+extern "C" fde_status sylv_step(sylv_t s, const double* d_C, double* d_X, int ld, void* stream, double* relres_out,
+                                int* sweeps_out) {
+  FDE_ARG(s != nullptr, "handle is NULL");
+  FDE_ARG(d_C != nullptr && d_X != nullptr && d_C != d_X, "bad C / X");
+  FDE_ARG(ld >= s->N, "ld < N");
+  StepCtx ctx{relres_out, sweeps_out, FDE_OK};
+  return with_contig(s, d_C, d_X, ld, (cudaStream_t)stream, step_fn, &ctx);
+}
+
+static fde_status inner_fn(sylv_t s, const double* C, double* X, cudaStream_t st, void*) {
+  const size_t NN = (size_t)s->N * s->N;
+  if (s->prec == FDE_FP64) {
+    FDE_CUDA(cudaMemcpyAsync(s->in64.Cin, C, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    FDE_TRY(run_inner<double>(s, s->in64, st));
+    FDE_CUDA(cudaMemcpyAsync(X, s->in64.X, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    FDE_TRY((convert<double, float>(C, s->in32.Cin, NN, st)));
+    FDE_TRY(run_inner<float>(s, s->in32, st));
+    FDE_TRY((convert<float, double>(s->in32.X, X, NN, st)));
+  }
+  return FDE_OK;
+}
+
+extern "C" fde_status sylv_inner_solve(sylv_t s, const double* d_C, double* d_X, int ld, void* stream) {
+  FDE_ARG(s != nullptr, "handle is NULL");
+  FDE_ARG(d_C != nullptr && d_X != nullptr && d_C != d_X, "bad C / X");
+  FDE_ARG(ld >= s->N, "ld < N");
+  return with_contig(s, d_C, d_X, ld, (cudaStream_t)stream, inner_fn, nullptr);
+}
+
+extern "C" fde_status sylv_residual(sylv_t s, const double* d_C, const double* d_X, double* d_R, int ld,
+                                    void* stream) {
+  FDE_ARG(s != nullptr, "handle is NULL");
+  FDE_ARG(d_C != nullptr && d_X != nullptr && d_R != nullptr, "NULL buffer");
+  FDE_ARG(ld == s->N, "sylv_residual requires ld == N");
+  return residual(s, d_C, d_X, d_R, (cudaStream_t)stream);
+}
+
+extern "C" void sylv_free(sylv_t s) { delete s; }
+
+// Exposed for the time loop (fde_run.cu)
+namespace fde {
+fde_status sylv_step_internal(sylv_s* s, const double* C, double* X, cudaStream_t st, double* relres, int* sweeps) {
+  return sylv_step_impl(s, C, X, st, relres, sweeps);
+}
+int sylv_N(sylv_s* s) { return s->N; }
+}  // namespace fde

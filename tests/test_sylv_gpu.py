@@ -1,0 +1,132 @@
+"""GPU parity of the 2D Sylvester step (Eq. (sylv-timestepping)) and of the
+1D / 2D time loops against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import fde_oracle as O
+from paper_1804_05522_gb300 import binding as B
+from paper_1804_05522_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.float64).ravel(order="F").copy()).to("cuda")
+
+
+def _host(t, m, n):
+    return t.cpu().numpy().reshape((m, n), order="F")
+
+
+class Pair:
+    def __init__(self, lib, w, prec):
+        self.lib = lib
+        self.ax = lib.hodlr_build(lib.op_params(w.ops[0]))
+        self.ay = lib.hodlr_build(lib.op_params(w.ops[1]))
+        self.s = lib.sylv_create(self.ax, self.ay, prec)
+
+    def close(self):
+        self.lib.sylv_free(self.s)
+        self.lib.hodlr_free(self.ax)
+        self.lib.hodlr_free(self.ay)
+
+
+def _relerr(X, Y):
+    return np.linalg.norm(X - Y) / np.linalg.norm(Y)
+
+
+@pytest.mark.parametrize("N,leaf", [(64, 16), (100, 16), (256, 64)])
+def test_structured_residual(lib, N, leaf):
+    w = I.fd2d(N=N, alpha=(1.3, 1.7), steps=50, leaf=leaf)
+    P = Pair(lib, w, B.FDE_FP64)
+    try:
+        X = I.random_matrix_fast(N, N, seed=1)
+        C = I.random_matrix_fast(N, N, seed=2)
+        Rd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+        Cd, Xd = _dev(C), _dev(X)  # keep the device copies alive while the kernels run
+        lib.sylv_residual(P.s, Cd.data_ptr(), Xd.data_ptr(), Rd.data_ptr(), N)
+        torch.cuda.synchronize()
+        Ax = O.fd_operator(w.ops[0])
+        Ay = O.fd_operator(w.ops[1])
+        Ro = C - Ax @ X - X @ Ay.T
+        scale = np.linalg.norm(Ax @ X) + np.linalg.norm(X @ Ay.T)
+        assert np.linalg.norm(_host(Rd, N, N) - Ro) <= 1e-14 * scale
+    finally:
+        P.close()
+
+
+@pytest.mark.parametrize("prec", [B.FDE_FP64, B.FDE_FP32_REFINE])
+@pytest.mark.parametrize("N,leaf,alpha", [(16, 8, (1.3, 1.7)), (100, 16, (1.5, 1.2)), (256, 64, (1.3, 1.7)),
+                                          (129, 32, (1.9, 1.1))])
+def test_sylv_step_vs_oracle(lib, prec, N, leaf, alpha):
+    w = I.fd2d(N=N, alpha=alpha, steps=50, leaf=leaf)
+    P = Pair(lib, w, prec)
+    try:
+        C = O.fde2d_rhs(w, w.u0, 0) + I.random_matrix_fast(N, N, seed=3)
+        Ax = O.fd_operator(w.ops[0])
+        Ay = O.fd_operator(w.ops[1])
+        Xo = O.sylvester_kron(Ax, Ay, C) if N <= 16 else O.sylvester_bartels_stewart(Ax, Ay, C)
+        Xd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+        Cd = _dev(C)
+        # inner (unrefined) D&C solve: accuracy limited by truncation / fADI / precision
+        lib.sylv_inner_solve(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+        torch.cuda.synchronize()
+        e_inner = _relerr(_host(Xd, N, N), Xo)
+        assert e_inner < (1e-4 if prec == B.FDE_FP32_REFINE else 1e-6), e_inner
+        Xd.zero_()
+        relres, sweeps = lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+        X = _host(Xd, N, N)
+        e = _relerr(X, Xo)
+        # ≤1e-10 relative for the FP64 path, ≤1e-8 after refinement for FP32
+        assert e <= (1e-10 if prec == B.FDE_FP64 else 1e-8), (e, relres, sweeps)
+        assert relres < 1e-11 and 1 <= sweeps <= 12
+    finally:
+        P.close()
+
+
+def test_sylv_warm_start_and_symmetry(lib):
+    # A_x = A_y and symmetric C give a symmetric X (oracle pin); warm start from
+    # the exact solution needs a single sweep.
+    N = 128
+    w = I.fd2d(N=N, alpha=(1.6, 1.6), steps=20, leaf=32)
+    w.ops[1] = w.ops[0]
+    P = Pair(lib, w, B.FDE_FP32_REFINE)
+    try:
+        C = I.random_matrix_fast(N, N, seed=5)
+        C = C + C.T
+        Xd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+        Cd = _dev(C)
+        lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+        X = _host(Xd, N, N)
+        assert np.abs(X - X.T).max() <= 1e-9 * np.abs(X).max()
+        relres, sweeps = lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+        assert sweeps == 1 and relres < 1e-11
+    finally:
+        P.close()
+
+
+@pytest.mark.parametrize("prec", [B.FDE_FP64, B.FDE_FP32_REFINE])
+def test_fde_run_2d(lib, prec):
+    w = I.fd2d(N=96, alpha=(1.3, 1.7), steps=6, leaf=16)
+    rp = lib.run_params(w, prec=prec)
+    U0 = _dev(w.u0)
+    Uo = torch.zeros_like(U0)
+    st = lib.fde_run(rp, U0.data_ptr(), Uo.data_ptr())
+    U = _host(Uo, 96, 96)
+    Uref = O.fde2d_run(w)
+    assert _relerr(U, Uref) <= (1e-10 if prec == B.FDE_FP64 else 1e-8)
+    assert st.relres_max < 1e-11 and st.sweeps_max >= 1
+
+
+def test_fde_run_1d_workload(lib):
+    w = I.WORKLOADS["fd1d_n1024"]()
+    rp = lib.run_params(w, prec=B.FDE_FP64)
+    U0 = torch.from_numpy(w.u0.copy()).to("cuda")
+    Uo = torch.zeros_like(U0)
+    st = lib.fde_run(rp, U0.data_ptr(), Uo.data_ptr())
+    u = Uo.cpu().numpy()
+    uref = O.fde1d_run(w)
+    assert np.linalg.norm(u - uref) / np.linalg.norm(uref) <= 1e-10
+    assert st.sweeps_max <= 4
