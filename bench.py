@@ -1,0 +1,370 @@
+"""Benchmark: 2D fractional-diffusion implicit-Euler time steps per second.
+
+Workload (default): 2D N=4096 per side, alpha = (1.5, 1.5), dt = 1/100,
+coefficients d_{1,±}(x) = Γ(3-α)x^α, Γ(3-α)(1-x)^α, d_{2,±}(y) = Γ(3-α)(1+y)^α,
+Γ(3-α)(2-y)^α, source f = 100 (sin 10πx cos πy + sin 10t sin πx · y(1-y)),
+HODLR leaf 128, truncation 1e-10; each step solves A_x X + X A_yᵀ = C with the
+FP32 divide-and-conquer / factored-ADI inner solver and FP64 iterative
+refinement against the exact structured residual.  The same steps are also run
+with the FP64 inner solver for comparison.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  --impl reference times the CPU oracle
+(real-Schur Bartels–Stewart) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1804_05522_gb300 import inputs as I  # noqa: E402
+
+METRIC = "2D FDE time steps/s on N×N grid at ≤1e-8 rel err: FP32+refine vs FP64 HODLR"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Derived ALU peaks (GB300: 152 SMs, 2070 MHz max SM clock):
+#   FP32 SIMT: 128 FMA lanes/SM x 2 flop;  FP64: 2 FMA/clk/SM x 2 flop
+SMS, SM_MHZ = 152, 2070.0
+FP32_SIMT_PEAK_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MHZ * 1e6 / 1e12
+ORACLE_SAMPLE_N = 1024
+
+
+def workload_for(name: str):
+    return I.WORKLOADS[name]()
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fd2d_n4096")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--prof-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_step_sample(name: str, repeats: int = 1):
+    """Time the CPU oracle (Bartels–Stewart with precomputed real Schur forms,
+    as in the oracle's time loop) for `repeats` steps of the same workload family
+    at N = ORACLE_SAMPLE_N; returns (seconds per step, sample description)."""
+    from oracle import fde_oracle as O
+
+    w = workload_for(name)
+    a1, a2 = w.ops[0].alpha, w.ops[1].alpha
+    ws = I.fd2d(N=ORACLE_SAMPLE_N, alpha=(a1, a2), steps=w.steps, leaf=128)
+    solver = O.SchurSylvester(O.fd_operator(ws.ops[0]), O.fd_operator(ws.ops[1]))
+    U = ws.u0.copy()
+    t0 = time.perf_counter()
+    for m in range(repeats):
+        U = solver.solve(O.fde2d_rhs(ws, U, m))
+    dt = (time.perf_counter() - t0) / repeats
+    return dt, f"oracle Bartels-Stewart step at N={ORACLE_SAMPLE_N} (Schur setup excluded), {repeats} step(s)"
+
+
+def scale_to(N: int, sec_per_step: float) -> float:
+    """Oracle steps/s at N from the sample by the O(N^3) per-step cost."""
+    return 1.0 / (sec_per_step * (N / ORACLE_SAMPLE_N) ** 3)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile(prefix="clocks_", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def read_peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline(lib, N):
+    """Dominant kernel family by device time in the timed region."""
+    fams = ["gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply", "transpose", "refine", "fadi_axpy"]
+    rec = {}
+    for f in fams:
+        ms, n, work, kind = lib.prof_query(f)
+        if n:
+            rec[f] = dict(ms=ms, launches=n, work=work, kind=kind)
+    if not rec:
+        return None, rec
+    total = sum(v["ms"] for v in rec.values())
+    dom = max(rec, key=lambda f: rec[f]["ms"])
+    v = rec[dom]
+    per_launch_s = v["ms"] / 1e3 / v["launches"]
+    work_per_launch = v["work"] / v["launches"]
+    peaks = read_peaks()
+    if v["kind"] == 0:
+        achieved = work_per_launch / per_launch_s / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    elif dom == "gemm32tc":
+        # tcgen05 kind::tf32; peak = measured bf16 (sustained: the kernel runs
+        # inside a long step) x nominal tf32/bf16 dense ratio 1.1/2.25
+        achieved = work_per_launch / per_launch_s / 1e12
+        bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak = bf16 * 1.1 / 2.25
+        r = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": ("measured" if "bf16_tflops_sustained" in peaks else "fallback")
+             + " sustained bf16 x 1.1/2.25 (tf32)"}
+    else:
+        achieved = work_per_launch / per_launch_s / 1e12
+        peak = FP32_SIMT_PEAK_TFLOPS if dom.endswith("32") else FP64_PEAK_TFLOPS
+        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": "derived: 152 SMs x %s x 2070 MHz" % ("128 FP32 lanes x 2" if dom.endswith("32")
+                                                                  else "2 FP64 FMA/clk x 2")}
+    r.update({"frac": achieved / peak, "traffic": None, "kernel": dom,
+              "algorithmic_work_per_launch": work_per_launch, "launches": v["launches"],
+              "avg_launch_ms": v["ms"] / v["launches"], "share_of_instrumented_time": v["ms"] / total})
+    shares = {f: round(rec[f]["ms"] / total, 4) for f in rec}
+    return r, shares
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    from paper_1804_05522_gb300 import binding as B
+
+    lib = B.load()
+    w = workload_for(args.workload)
+    N = w.N
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    U0 = torch.from_numpy(np.asarray(w.u0, dtype=np.float64).ravel(order="F").copy()).to(dev)
+    rp = lib.run_params(w, prec=B.FDE_FP32_REFINE)
+    r32 = lib.runner_create(rp, U0.data_ptr(), stream)
+    setup32 = lib.runner_stats(r32).setup_s
+    lib.runner_advance(r32, args.warmup, stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    st0 = lib.runner_stats(r32)
+    launches0 = lib.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record()
+    lib.runner_advance(r32, args.steps, stream)
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    barrier()
+    launches = lib.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    st1 = lib.runner_stats(r32)
+    # profiled pass: same state / workload, eager launches bracketed by CUDA
+    # events on the launching stream (the timed region above replays graphs)
+    roof, shares = None, {}
+    if args.prof_steps > 0:
+        lib.prof_reset()
+        lib.prof_enable(True)
+        lib.runner_advance(r32, args.prof_steps, stream)
+        torch.cuda.synchronize()
+        lib.prof_enable(False)
+        roof, shares = roofline(lib, N)
+        if roof is not None:
+            roof["measured"] = (f"profiled pass of {args.prof_steps} steps right after the timed region (eager "
+                                f"launches, CUDA events on the launching stream)")
+        lib.prof_reset()
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+    sweeps = (st1.sweeps_total - st0.sweeps_total) / max(args.steps, 1)
+
+    # ---- FP64 inner solver on the same state (comparison + agreement)
+    extra = {}
+    if args.fp64_steps > 0 and rank == 0:
+        state = torch.empty_like(U0)
+        lib.runner_state(r32, state.data_ptr(), stream)
+        m0 = args.warmup + args.steps + args.prof_steps
+        rp64 = lib.run_params(w, prec=B.FDE_FP64)
+        r64 = lib.runner_create(rp64, state.data_ptr(), stream)
+        setup64 = lib.runner_stats(r64).setup_s
+        lib.runner_load(r64, state.data_ptr(), m0, stream)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        lib.runner_advance(r64, args.fp64_steps, stream)
+        f1.record()
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        lib.runner_advance(r32, args.fp64_steps, stream)
+        a = torch.empty_like(U0)
+        b = torch.empty_like(U0)
+        lib.runner_state(r32, a.data_ptr(), stream)
+        lib.runner_state(r64, b.data_ptr(), stream)
+        torch.cuda.synchronize()
+        agree = float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        st64 = lib.runner_stats(r64)
+        lib.runner_free(r64)
+        extra["fp64_path"] = {"steps_per_s": args.fp64_steps / (ms64 / 1e3), "setup_s": setup64,
+                              "steps": args.fp64_steps, "relres_max": st64.relres_max,
+                              "fp32_vs_fp64_rel_diff": agree, "speedup_fp32_refine": value / world /
+                              (args.fp64_steps / (ms64 / 1e3))}
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host_in = torch.empty(N * N, dtype=torch.float64, pin_memory=True)
+        host_out = torch.empty(N * N, dtype=torch.float64, pin_memory=True)
+        lib.runner_state(r32, host_in.data_ptr(), stream)
+        step0 = lib.runner_stats(r32)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        m = args.warmup + args.steps + args.prof_steps + (args.fp64_steps if rank == 0 else 0)
+        for i in range(args.e2e_steps):
+            lib.runner_load(r32, host_in.data_ptr(), m + i, stream)       # H2D of the step's input
+            lib.runner_advance(r32, 1, stream)
+            lib.runner_state(r32, host_out.data_ptr(), stream)             # D2H of the step's result
+            host_in, host_out = host_out, host_in
+        g1.record()
+        torch.cuda.synchronize()
+        ems = g1.elapsed_time(g0) * -1 if False else g0.elapsed_time(g1)
+        wall = time.perf_counter() - t0
+        del step0
+        e2e = {"value": world * args.e2e_steps / (ems / 1e3), "unit": "steps/s",
+               "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8,
+               "host_wall_steps_per_s": args.e2e_steps / wall}
+    lib.runner_free(r32)
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        sec, sample = oracle_step_sample(args.workload, 1)
+        cpu = {"value": scale_to(N, sec), "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": sample + f"; {sec:.2f} s/step, scaled to N={N} by (N/{ORACLE_SAMPLE_N})^3",
+               "sample_steps_per_s": 1.0 / sec}
+    cfg = {"workload": f"{args.workload}: 2D N={N} per side ({N*N} unknowns), alpha=({w.ops[0].alpha},{w.ops[1].alpha}), "
+                       f"dt=1/{w.steps}, leaf {w.ops[0].leaf}, HODLR tol {w.ops[0].tol:g}, FP32 D&C+fADI inner, "
+                       f"FP64 refinement",
+           "N": N, "leaf": w.ops[0].leaf, "tol": w.ops[0].tol, "time_steps_total": w.steps,
+           "l2_policy": "working set (X, C, R FP64 = 3 x %d MB + factors) exceeds the 129 MB L2" % (N * N * 8 >> 20),
+           "setup_s": setup32, "refine_sweeps_per_step": sweeps, "relres_max": st1.relres_max,
+           "kmax_x": st1.kmax_x, "kmax_y": st1.kmax_y, "parallelism": "replicas" if world > 1 else "single"}
+    out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 refine", "data": "synthetic",
+           "config": cfg, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+           "kernel_time_shares": shares, "cpu_baseline": cpu, "clocks": clk}
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ reference
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload_for(args.workload)
+    N = w.N
+    for _ in range(args.warmup):
+        oracle_step_sample(args.workload, 1)
+    t0 = time.perf_counter()
+    secs = []
+    for _ in range(args.steps):
+        s, sample = oracle_step_sample(args.workload, 1)
+        secs.append(s)
+    wall = time.perf_counter() - t0
+    per = float(np.mean(secs))
+    value = scale_to(N, per)
+    out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "N": N},
+           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample + f"; mean {per:.2f} s/step over {args.steps} steps, scaled to N={N} "
+                                               f"by (N/{ORACLE_SAMPLE_N})^3", "wall_s": wall},
+           "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -200,6 +200,37 @@ typedef struct {
 fde_status fde_run(const fde_run_params* p, const double* d_U0, double* d_U_out, void* stream,
                    fde_run_stats* stats);
 
+/* Stateful form of fde_run for callers that advance the state themselves.
+ * fde_runner_create does the whole setup (build, factorisations, Schur forms,
+ * shift factorisations) from U0 (host or device, same shape as in fde_run).
+ * fde_runner_advance runs nsteps implicit-Euler steps on `stream`.
+ * fde_runner_load / fde_runner_state copy the state in / out (host or device
+ * pointers; ld = N); load also sets the time level to step_index.
+ * Stats accumulate over all advances. */
+typedef struct fde_runner_s* fde_runner_t;
+fde_status fde_runner_create(const fde_run_params* p, const double* U0, void* stream, fde_runner_t* out);
+fde_status fde_runner_advance(fde_runner_t r, int nsteps, void* stream);
+fde_status fde_runner_load(fde_runner_t r, const double* U, int step_index, void* stream);
+fde_status fde_runner_state(fde_runner_t r, double* U_out, void* stream);
+fde_status fde_runner_stats(fde_runner_t r, fde_run_stats* stats);
+void fde_runner_free(fde_runner_t r);
+
+/* Instrumentation.  fde_launch_count: kernels launched by this library in
+ * this process so far.  fde_prof_enable(1) makes the library bracket the
+ * launches of its main kernel families with CUDA events on their stream;
+ * fde_prof_query returns the summed device time (ms) and launch count of a
+ * family ("gemm32", "gemm64", "trsyl32", "trsyl64", "fft_apply", "schur",
+ * "recompress", "fadi_axpy", "transpose", "refine"), synchronising the events
+ * it reads;
+ * fde_prof_reset clears the records. */
+unsigned long long fde_launch_count(void);
+void fde_prof_enable(int on);
+/* work (may be NULL): algorithmic work of the recorded launches, FLOPs when
+ * *work_kind == 1 (FP32 for *32 families, FP64 otherwise), DRAM bytes when
+ * *work_kind == 0 (work_kind may be NULL). */
+fde_status fde_prof_query(const char* family, double* ms, long long* launches, double* work, int* work_kind);
+void fde_prof_reset(void);
+
 const char* fde_strerror(fde_status s);
 /* Text of the last error on the calling thread (never NULL). */
 const char* fde_last_error(void);

@@ -69,6 +69,17 @@ _SIGS = {
     "sylv_residual": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "sylv_free": ([_P], None),
     "fde_run": ([C.POINTER(RunParams), _P, _P, _P, C.POINTER(RunStats)], C.c_int),
+    "fde_runner_create": ([C.POINTER(RunParams), _P, _P, C.POINTER(_P)], C.c_int),
+    "fde_runner_advance": ([_P, C.c_int, _P], C.c_int),
+    "fde_runner_load": ([_P, _P, C.c_int, _P], C.c_int),
+    "fde_runner_state": ([_P, _P, _P], C.c_int),
+    "fde_runner_stats": ([_P, C.POINTER(RunStats)], C.c_int),
+    "fde_runner_free": ([_P], None),
+    "fde_launch_count": ([], C.c_ulonglong),
+    "fde_prof_enable": ([C.c_int], None),
+    "fde_prof_query": ([C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                        C.POINTER(C.c_int)], C.c_int),
+    "fde_prof_reset": ([], None),
     "fde_strerror": ([C.c_int], C.c_char_p),
     "fde_last_error": ([], C.c_char_p),
 }
@@ -214,6 +225,50 @@ class Lib:
         st = RunStats()
         self.check(self.dll.fde_run(C.byref(params), U0, Uout, stream, C.byref(st)))
         return st
+
+
+    # -- runner (stateful time loop)
+    def runner_create(self, params: RunParams, U0: int, stream: int = 0) -> int:
+        r = _P()
+        self.check(self.dll.fde_runner_create(C.byref(params), U0, stream, C.byref(r)))
+        return r.value
+
+    def runner_advance(self, r: int, nsteps: int, stream: int = 0):
+        self.check(self.dll.fde_runner_advance(r, nsteps, stream))
+
+    def runner_load(self, r: int, U: int, step_index: int, stream: int = 0):
+        self.check(self.dll.fde_runner_load(r, U, step_index, stream))
+
+    def runner_state(self, r: int, U: int, stream: int = 0):
+        self.check(self.dll.fde_runner_state(r, U, stream))
+
+    def runner_stats(self, r: int) -> RunStats:
+        st = RunStats()
+        self.check(self.dll.fde_runner_stats(r, C.byref(st)))
+        return st
+
+    def runner_free(self, r: int):
+        if r:
+            self.dll.fde_runner_free(r)
+
+    # -- instrumentation
+    def launch_count(self) -> int:
+        return int(self.dll.fde_launch_count())
+
+    def prof_enable(self, on: bool):
+        self.dll.fde_prof_enable(1 if on else 0)
+
+    def prof_query(self, family: str):
+        """(device ms, launches, algorithmic work, kind) with kind 1 = FLOPs, 0 = bytes."""
+        ms = C.c_double()
+        n = C.c_longlong()
+        w = C.c_double()
+        k = C.c_int()
+        self.check(self.dll.fde_prof_query(family.encode(), C.byref(ms), C.byref(n), C.byref(w), C.byref(k)))
+        return ms.value, n.value, w.value, k.value
+
+    def prof_reset(self):
+        self.dll.fde_prof_reset()
 
 
 _LIB = None

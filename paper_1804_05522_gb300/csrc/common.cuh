@@ -20,8 +20,26 @@ fde_status cuda_status(cudaError_t e, const char* what, const char* file, int li
     if (e__ != cudaSuccess) return ::fde::cuda_status(e__, #call, __FILE__, __LINE__); \
   } while (0)
 
+void count_launch();
+void count_launches(size_t n);
+bool prof_enabled();
+
+// Brackets a kernel launch with CUDA events when profiling is on.
+// work: algorithmic FLOPs (kind 1) or bytes (kind 0) of the bracketed launches.
+struct ProfScope {
+  const char* fam;
+  cudaStream_t st;
+  cudaEvent_t a;
+  double work;
+  int kind;
+  ProfScope(const char* family, cudaStream_t st, double work = 0.0, int kind = 1);
+  ~ProfScope();
+};
+
+// Checks the launch just issued and counts it.
 #define FDE_LAUNCH(what)                                                        \
   do {                                                                          \
+    ::fde::count_launch();                                                      \
     cudaError_t e__ = cudaGetLastError();                                       \
     if (e__ != cudaSuccess) return ::fde::cuda_status(e__, what, __FILE__, __LINE__); \
   } while (0)

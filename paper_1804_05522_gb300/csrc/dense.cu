@@ -114,6 +114,7 @@ fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, b
     b.max_m = d.m > b.max_m ? d.m : b.max_m;
     b.max_n = d.n > b.max_n ? d.n : b.max_n;
     b.max_k = d.k > b.max_k ? d.k : b.max_k;
+    b.flops += 2.0 * d.m * d.n * d.k;
   }
   if (b.batch > 0) {
     FDE_TRY(pool.alloc(&b.d_desc, h.size()));
@@ -129,10 +130,16 @@ fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, b
 template <typename T>
 fde_status gemm_batch_run(const GemmBatch<T>& b, cudaStream_t st) {
   if (b.batch == 0 || b.max_m == 0 || b.max_n == 0) return FDE_OK;
+  if constexpr (sizeof(T) == 4) {
+    bool used = false;
+    FDE_TRY(tc_gemm_run(reinterpret_cast<const GemmBatch<float>&>(b), st, &used));
+    if (used) return FDE_OK;
+  }
   for (int z0 = 0; z0 < b.batch; z0 += 65535) {
     int nz = b.batch - z0 < 65535 ? b.batch - z0 : 65535;
     dim3 grid(ceil_div(b.max_m, 64), ceil_div(b.max_n, 64), nz);
     const GemmDesc<T>* d = b.d_desc + z0;
+    ProfScope ps(sizeof(T) == 4 ? "gemm32" : "gemm64", st, z0 == 0 ? b.flops : 0.0, 1);
     if (!b.ta && !b.tb)
       gemm_batched_kernel<T, false, false><<<grid, 256, 0, st>>>(d, b.alpha, b.beta);
     else if (b.ta && !b.tb)

@@ -24,6 +24,7 @@ template <typename T>
 struct GemmBatch {
   GemmDesc<T>* d_desc = nullptr;
   int batch = 0, max_m = 0, max_n = 0, max_k = 0;
+  double flops = 0.0;  // Σ 2 m n k over the batch
   bool ta = false, tb = false;
   T alpha = T(1), beta = T(0);
 };
@@ -34,6 +35,14 @@ fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, b
 
 template <typename T>
 fde_status gemm_batch_run(const GemmBatch<T>& b, cudaStream_t st);
+
+// Tensor-core path for FP32 batches (tc_gemm.cu).  Mode from FDE_TC
+// (0 = SIMT only, 1 = TF32, 3 = 3xTF32, the default).
+fde_status tc_gemm_run(const GemmBatch<float>& b, cudaStream_t st, bool* used);
+int tc_mode();
+void set_tc_mode(int m);
+fde_status tc_error_flag(int* out);
+fde_status tc_prepare();
 
 // In-place inverse of `batch` square matrices (sizes n_i <= nmax, leading
 // dimension ld, matrix i at A + i*stride) by Gauss–Jordan elimination with

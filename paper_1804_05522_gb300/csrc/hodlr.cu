@@ -597,9 +597,8 @@ size_t solve_scratch_elems(const hodlr_s* h, int ncols, int lvl0) {
 }
 
 template <typename T>
-fde_status build_solve_plan(const hodlr_s* h, const Fact<T>& F, const std::vector<T*>& V, const T* X, int ldx,
-                            T* Y, int ldy, int ncols, int lvl0, T* tmp, T* zbuf, T* wbuf, DevPool& pool,
-                            Plan<T>* out, cudaStream_t st) {
+fde_status build_solve_spec(const hodlr_s* h, const Fact<T>& F, const std::vector<T*>& V, const T* X, int ldx, T* Y,
+                            int ldy, int ncols, int lvl0, T* tmp, T* zbuf, T* wbuf, std::vector<HostOp<T>>* ops) {
   const Tree& tr = h->tree;
   const int N = tr.N, L = tr.L, lmax = h->lmax;
   if (lvl0 < F.lmin) {
@@ -609,41 +608,38 @@ fde_status build_solve_plan(const hodlr_s* h, const Fact<T>& F, const std::vecto
   const bool inplace = (X == Y);
   T* W = inplace ? tmp : Y;
   const int ldw = inplace ? N : ldy;
-  out->ops.clear();
+  ops->clear();
   {
-    std::vector<GemmDesc<T>> d;
+    HostOp<T> op;
     for (int p = 0; p < tr.nleaves(); ++p) {
       const int id = tr.id(L, p), lo = tr.lo[id], n = tr.hi[id] - lo;
-      d.push_back({F.Dinv + (size_t)p * lmax * lmax, X + lo, W + lo, n, ncols, n, lmax, ldx, ldw});
+      op.d.push_back({F.Dinv + (size_t)p * lmax * lmax, X + lo, W + lo, n, ncols, n, lmax, ldx, ldw});
     }
-    PlanOp<T> op;
-    FDE_TRY(gemm_batch_upload(pool, d, false, false, T(1), T(0), &op.g, st));
-    out->ops.push_back(op);
+    ops->push_back(op);
   }
   for (int l = L - 1; l >= lvl0; --l) {
     const int K = h->K[l], K2 = 2 * K;
-    std::vector<GemmDesc<T>> dz, dw, du;
+    HostOp<T> oz, ow, ou;
+    oz.ta = true;
+    ou.alpha = T(-1);
+    ou.beta = T(1);
     for (int p = 0; p < (1 << l); ++p) {
       const int id = tr.id(l, p), lo = tr.lo[id], hi = tr.hi[id], mid = lo + (hi - lo) / 2;
       const int t = mid - lo, s = hi - mid;
       T* zp = zbuf + (size_t)p * K2 * ncols;
       T* wp = wbuf + (size_t)p * K2 * ncols;
-      dz.push_back({V[l] + mid, W + mid, zp, K, ncols, s, N, ldw, K2});
-      dz.push_back({V[l] + lo, W + lo, zp + K, K, ncols, t, N, ldw, K2});
-      dw.push_back({F.Kinv[l] + (size_t)p * K2 * K2, zp, wp, K2, ncols, K2, K2, K2, K2});
-      du.push_back({F.Ut[l] + lo, wp, W + lo, t, ncols, K, N, K2, ldw});
-      du.push_back({F.Ut[l] + mid, wp + K, W + mid, s, ncols, K, N, K2, ldw});
+      oz.d.push_back({V[l] + mid, W + mid, zp, K, ncols, s, N, ldw, K2});
+      oz.d.push_back({V[l] + lo, W + lo, zp + K, K, ncols, t, N, ldw, K2});
+      ow.d.push_back({F.Kinv[l] + (size_t)p * K2 * K2, zp, wp, K2, ncols, K2, K2, K2, K2});
+      ou.d.push_back({F.Ut[l] + lo, wp, W + lo, t, ncols, K, N, K2, ldw});
+      ou.d.push_back({F.Ut[l] + mid, wp + K, W + mid, s, ncols, K, N, K2, ldw});
     }
-    PlanOp<T> oz, ow, ou;
-    FDE_TRY(gemm_batch_upload(pool, dz, true, false, T(1), T(0), &oz.g, st));
-    FDE_TRY(gemm_batch_upload(pool, dw, false, false, T(1), T(0), &ow.g, st));
-    FDE_TRY(gemm_batch_upload(pool, du, false, false, T(-1), T(1), &ou.g, st));
-    out->ops.push_back(oz);
-    out->ops.push_back(ow);
-    out->ops.push_back(ou);
+    ops->push_back(oz);
+    ops->push_back(ow);
+    ops->push_back(ou);
   }
   if (inplace) {
-    PlanOp<T> cp;
+    HostOp<T> cp;
     cp.kind = 1;
     cp.src = tmp;
     cp.ld_src = N;
@@ -651,10 +647,72 @@ fde_status build_solve_plan(const hodlr_s* h, const Fact<T>& F, const std::vecto
     cp.ld_dst = ldy;
     cp.m = N;
     cp.n = ncols;
-    out->ops.push_back(cp);
+    ops->push_back(cp);
   }
   return FDE_OK;
 }
+
+template <typename T>
+fde_status upload_specs(const std::vector<std::vector<HostOp<T>>>& specs, DevPool& pool, Plan<T>* out,
+                        cudaStream_t st) {
+  out->ops.clear();
+  size_t nsteps = 0;
+  for (const auto& s : specs) nsteps = std::max(nsteps, s.size());
+  for (size_t i = 0; i < nsteps; ++i) {
+    HostOp<T> m;
+    bool first = true;
+    for (const auto& s : specs) {
+      if (i >= s.size()) continue;
+      const HostOp<T>& o = s[i];
+      if (o.kind == 1) {  // copies are never merged
+        PlanOp<T> cp;
+        cp.kind = 1;
+        cp.src = o.src;
+        cp.dst = o.dst;
+        cp.ld_src = o.ld_src;
+        cp.ld_dst = o.ld_dst;
+        cp.m = o.m;
+        cp.n = o.n;
+        out->ops.push_back(cp);
+        continue;
+      }
+      if (first) {
+        m = o;
+        first = false;
+      } else {
+        if (o.ta != m.ta || o.tb != m.tb || o.alpha != m.alpha || o.beta != m.beta) {
+          set_error("upload_specs: incompatible steps");
+          return FDE_ERR_ARG;
+        }
+        m.d.insert(m.d.end(), o.d.begin(), o.d.end());
+      }
+    }
+    if (!first) {
+      PlanOp<T> op;
+      FDE_TRY(gemm_batch_upload(pool, m.d, m.ta, m.tb, m.alpha, m.beta, &op.g, st));
+      out->ops.push_back(op);
+    }
+  }
+  return FDE_OK;
+}
+
+template <typename T>
+fde_status build_solve_plan(const hodlr_s* h, const Fact<T>& F, const std::vector<T*>& V, const T* X, int ldx,
+                            T* Y, int ldy, int ncols, int lvl0, T* tmp, T* zbuf, T* wbuf, DevPool& pool,
+                            Plan<T>* out, cudaStream_t st) {
+  std::vector<std::vector<HostOp<T>>> specs(1);
+  FDE_TRY(build_solve_spec<T>(h, F, V, X, ldx, Y, ldy, ncols, lvl0, tmp, zbuf, wbuf, &specs[0]));
+  return upload_specs<T>(specs, pool, out, st);
+}
+
+#define INST_SPEC(T)                                                                                        \
+  template fde_status build_solve_spec<T>(const hodlr_s*, const Fact<T>&, const std::vector<T*>&, const T*, int, \
+                                          T*, int, int, int, T*, T*, T*, std::vector<HostOp<T>>*);           \
+  template fde_status upload_specs<T>(const std::vector<std::vector<HostOp<T>>>&, DevPool&, Plan<T>*,        \
+                                      cudaStream_t);
+INST_SPEC(double)
+INST_SPEC(float)
+#undef INST_SPEC
 
 template fde_status plan_run<double>(const Plan<double>&, cudaStream_t);
 template fde_status plan_run<float>(const Plan<float>&, cudaStream_t);
@@ -666,10 +724,10 @@ template fde_status build_solve_plan<float>(const hodlr_s*, const Fact<float>&, 
                                             DevPool&, Plan<float>*, cudaStream_t);
 
 // ------------------------------------------------------ factorisation
-fde_status hodlr_factorize(hodlr_s* h, double sigma, int lmin, Fact<double>* F, cudaStream_t st) {
+fde_status hodlr_factorize(hodlr_s* h, double sigma, int lmin, Fact<double>* F, cudaStream_t st, DevPool* ext) {
   const Tree& tr = h->tree;
   const int N = tr.N, L = tr.L, lmax = h->lmax, nl = tr.nleaves();
-  DevPool& pool = h->pool;
+  DevPool& pool = ext ? *ext : h->pool;
   DevPool scratch;
   F->sigma = sigma;
   F->lmin = lmin;
@@ -823,6 +881,7 @@ static fde_status build_impl(const fde_op_params* p, cudaStream_t st, hodlr_s* h
   FDE_TRY(scratch.alloc(&d_flag, 4));
   FDE_CUDA(cudaMemsetAsync(d_flag, 0, 4 * sizeof(int), st));
   finite_check_kernel<<<64, 256, 0, st>>>(h->dp, N, d_flag);
+  FDE_LAUNCH("finite_check_kernel");
   finite_check_kernel<<<64, 256, 0, st>>>(h->dm, N, d_flag);
   FDE_LAUNCH("finite_check_kernel");
   gl_weights_kernel<<<1, 32, 0, st>>>(p->alpha, N + 1, h->g);
@@ -836,11 +895,14 @@ static fde_status build_impl(const fde_op_params* p, cudaStream_t st, hodlr_s* h
   const int mvb = ceil_div((long)N * 32, 256);
   for (int it = 0; it < 30; ++it) {
     fd_matvec_kernel<<<mvb, 256, 0, st>>>(h->g, h->dp, h->dm, h->c, p->shift, N, v, w, 0);
+    FDE_LAUNCH("fd_matvec_kernel");
     fd_matvec_kernel<<<mvb, 256, 0, st>>>(h->g, h->dp, h->dm, h->c, p->shift, N, w, v, 1);
+    FDE_LAUNCH("fd_matvec_kernel");
     norm2_kernel<<<1, 1024, 0, st>>>(v, N, nrm);
+    FDE_LAUNCH("norm2_kernel");
     scale_inv_kernel<<<64, 256, 0, st>>>(v, N, nrm);
+    FDE_LAUNCH("scale_inv_kernel");
   }
-  FDE_LAUNCH("power iteration");
   int hflag[4];
   double hn;
   FDE_CUDA(cudaMemcpyAsync(hflag, d_flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -942,6 +1004,7 @@ static fde_status build_impl(const fde_op_params* p, cudaStream_t st, hodlr_s* h
     FDE_LAUNCH("block_factors_kernel");
     const size_t smem = (3 * (size_t)r * r + 3 * r) * sizeof(double) + r * sizeof(int);
     FDE_CUDA(cudaFuncSetAttribute(recompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps("recompress", st);
     recompress_kernel<<<(int)jobs.size(), 512, smem, st>>>(d_jobs, r, r, h->blk_tol);
     FDE_LAUNCH("recompress_kernel");
     std::vector<int> ranks(njobs);

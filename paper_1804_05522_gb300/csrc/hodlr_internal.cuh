@@ -35,6 +35,18 @@ template <typename T>
 struct Plan {
   std::vector<PlanOp<T>> ops;
 };
+// Host-side form of a plan step (descriptors not yet uploaded), so that
+// independent plans can be merged into shared launches.
+template <typename T>
+struct HostOp {
+  int kind = 0;  // 0 = gemm, 1 = copy
+  std::vector<GemmDesc<T>> d;
+  bool ta = false, tb = false;
+  T alpha = T(1), beta = T(0);
+  const T* src = nullptr;
+  T* dst = nullptr;
+  int ld_src = 0, ld_dst = 0, m = 0, n = 0;
+};
 template <typename T>
 fde_status plan_run(const Plan<T>& p, cudaStream_t st);
 
@@ -72,8 +84,10 @@ struct hodlr_s {
 
 namespace fde {
 
-// Factorise A + sigma I for levels lmin..L into F (FP64).
-fde_status hodlr_factorize(hodlr_s* h, double sigma, int lmin, Fact<double>* F, cudaStream_t st);
+// Factorise A + sigma I for levels lmin..L into F (FP64).  Memory comes from
+// `pool` (the handle's own pool when NULL).
+fde_status hodlr_factorize(hodlr_s* h, double sigma, int lmin, Fact<double>* F, cudaStream_t st,
+                           DevPool* pool = nullptr);
 // Demote an FP64 factorisation to FP32 (allocates in pool).
 fde_status fact_demote(hodlr_s* h, const Fact<double>& F, Fact<float>* G, DevPool& pool, cudaStream_t st);
 // y = A x (trans 0) or Aᵀ x (trans 1) for the exact operator, FP64, O(N²).
@@ -89,6 +103,14 @@ template <typename T>
 fde_status build_solve_plan(const hodlr_s* h, const Fact<T>& F, const std::vector<T*>& V, const T* X, int ldx,
                             T* Y, int ldy, int ncols, int lvl0, T* tmp, T* zbuf, T* wbuf, DevPool& pool,
                             Plan<T>* out, cudaStream_t st);
+template <typename T>
+fde_status build_solve_spec(const hodlr_s* h, const Fact<T>& F, const std::vector<T*>& V, const T* X, int ldx, T* Y,
+                            int ldy, int ncols, int lvl0, T* tmp, T* zbuf, T* wbuf, std::vector<HostOp<T>>* ops);
+// Upload a list of specs; specs with the same step count are merged step by
+// step into single launches (their steps must agree in kind/transposes/scalars).
+template <typename T>
+fde_status upload_specs(const std::vector<std::vector<HostOp<T>>>& specs, DevPool& pool, Plan<T>* out,
+                        cudaStream_t st);
 size_t solve_scratch_elems(const hodlr_s* h, int ncols, int lvl0);
 
 }  // namespace fde

@@ -8,7 +8,8 @@
 
 struct sylv_s;
 namespace fde {
-fde_status sylv_step_internal(sylv_s* s, const double* C, double* X, cudaStream_t st, double* relres, int* sweeps);
+fde_status sylv_step_internal(sylv_s* s, const double* C, double* X, cudaStream_t st, double* relres, int* sweeps,
+                              const double* C_prev);
 }
 using namespace fde;
 
@@ -39,11 +40,10 @@ __global__ void rhs1d_kernel(const double* __restrict__ u, const double* __restr
     b[i] = u[i] + dt * f;
   }
 }
-// r = b - y ; acc += |r|^2
 __global__ void sub_kernel(const double* __restrict__ b, const double* __restrict__ y, double* __restrict__ r, int N) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) r[i] = b[i] - y[i];
 }
-// x += d ; acc[0] += |d|^2, acc[1] += |x|^2
+// x += d ; acc[0] = |d|^2, acc[1] = |x|^2
 __global__ void add_norms_kernel(double* __restrict__ x, const double* __restrict__ d, int N, double* acc) {
   __shared__ double sh[32];
   double sd = 0.0, sx = 0.0;
@@ -61,81 +61,131 @@ __global__ void add_norms_kernel(double* __restrict__ x, const double* __restric
   }
 }
 
-SrcW weights(const fde_run_params* p, double t) {
-  SrcW w{};
-  for (int l = 0; l < p->rank; ++l) w.w[l] = p->h_amp[l] + p->h_sin_amp[l] * sin(p->h_omega[l] * t);
-  return w;
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-struct Guard {
+}  // namespace
+
+struct fde_runner_s {
+  fde_run_params p{};
+  std::vector<double> amp, samp, om;
   hodlr_t ax = nullptr, ay = nullptr;
   sylv_t s = nullptr;
-  ~Guard() {
+  DevPool pool;
+  double *U = nullptr, *C = nullptr, *FL = nullptr, *FR = nullptr;
+  double* C2 = nullptr;          // previous step's right-hand side (2D)
+  bool have_prev = false;        // C2 / the solver's residual belong to the current U
+  double *y = nullptr, *rr = nullptr, *acc = nullptr;
+  int N = 0, step = 0;
+  fde_run_stats stats{};
+  ~fde_runner_s() {
     sylv_free(s);
     hodlr_free(ax);
     hodlr_free(ay);
   }
+  SrcW weights(double t) const {
+    SrcW w{};
+    for (int l = 0; l < p.rank; ++l) w.w[l] = amp[l] + samp[l] * sin(om[l] * t);
+    return w;
+  }
 };
 
-}  // namespace
-
-extern "C" fde_status fde_run(const fde_run_params* p, const double* d_U0, double* d_Uout, void* stream,
-                              fde_run_stats* stats) {
+static fde_status check_run(const fde_run_params* p) {
   FDE_ARG(p != nullptr, "params is NULL");
-  FDE_ARG(d_U0 != nullptr && d_Uout != nullptr, "NULL state buffer");
   FDE_ARG(p->dim == 1 || p->dim == 2, "dim must be 1 or 2");
-  FDE_ARG(p->steps >= 1, "steps must be >= 1");
+  FDE_ARG(p->steps >= 0, "steps must be >= 0");
   FDE_ARG(p->rank >= 0 && p->rank <= kMaxSrc, "source rank must be in [0, 8]");
   FDE_ARG(p->rank == 0 || (p->h_src_left && p->h_amp && p->h_sin_amp && p->h_omega), "NULL source arrays");
   FDE_ARG(p->dim == 1 || p->rank == 0 || p->h_src_right, "NULL right source factor");
   FDE_ARG(p->prec == FDE_FP64 || p->prec == FDE_FP32_REFINE, "unknown precision");
   if (p->dim == 2) FDE_ARG(p->op_x.N == p->op_y.N && p->op_x.leaf == p->op_y.leaf, "op_x / op_y differ in N or leaf");
-  cudaStream_t st = (cudaStream_t)stream;
-  const int N = p->op_x.N;
-  const double dt = p->op_x.dt;
-  Guard g;
-  DevPool pool;
+  return FDE_OK;
+}
+
+static fde_status copy_state(double* dst, const double* src, size_t n, cudaStream_t st) {
+  const bool dd = is_device_ptr(dst), sd = is_device_ptr(src);
+  const cudaMemcpyKind k = sd ? (dd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost)
+                              : (dd ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
+  FDE_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), k, st));
+  if (!dd || !sd) FDE_CUDA(cudaStreamSynchronize(st));
+  return FDE_OK;
+}
+
+static fde_status runner_create(const fde_run_params* p, const double* U0, cudaStream_t st, fde_runner_s* R) {
+  R->p = *p;
+  const int N = p->op_x.N, r = p->rank;
+  R->N = N;
+  R->amp.assign(p->h_amp, p->h_amp + r);
+  R->samp.assign(p->h_sin_amp, p->h_sin_amp + r);
+  R->om.assign(p->h_omega, p->h_omega + r);
+  R->p.h_amp = R->p.h_sin_amp = R->p.h_omega = nullptr;
+  R->p.h_src_left = R->p.h_src_right = nullptr;
   const double t0 = now_seconds();
-  FDE_TRY(hodlr_build(&p->op_x, stream, &g.ax));
-  double *FL = nullptr, *FR = nullptr;
-  const int r = p->rank;
+  FDE_TRY(hodlr_build(&p->op_x, st, &R->ax));
+  DevPool& pool = R->pool;
   if (r > 0) {
-    FDE_TRY(pool.alloc(&FL, (size_t)N * r));
-    FDE_CUDA(cudaMemcpy(FL, p->h_src_left, (size_t)N * r * sizeof(double), cudaMemcpyHostToDevice));
+    FDE_TRY(pool.alloc(&R->FL, (size_t)N * r));
+    FDE_CUDA(cudaMemcpy(R->FL, p->h_src_left, (size_t)N * r * sizeof(double), cudaMemcpyHostToDevice));
     if (p->dim == 2) {
-      FDE_TRY(pool.alloc(&FR, (size_t)N * r));
-      FDE_CUDA(cudaMemcpy(FR, p->h_src_right, (size_t)N * r * sizeof(double), cudaMemcpyHostToDevice));
+      FDE_TRY(pool.alloc(&R->FR, (size_t)N * r));
+      FDE_CUDA(cudaMemcpy(R->FR, p->h_src_right, (size_t)N * r * sizeof(double), cudaMemcpyHostToDevice));
     }
   }
-  fde_run_stats s{};
+  const size_t n = (p->dim == 1) ? (size_t)N : (size_t)N * N;
+  FDE_TRY(pool.alloc(&R->U, n));
+  FDE_TRY(pool.alloc(&R->C, n));
   if (p->dim == 1) {
-    FDE_TRY(hodlr_factor(g.ax, stream));
-    double *u, *b, *y, *rr, *acc;
-    FDE_TRY(pool.alloc(&u, N));
-    FDE_TRY(pool.alloc(&b, N));
-    FDE_TRY(pool.alloc(&y, N));
-    FDE_TRY(pool.alloc(&rr, N));
-    FDE_TRY(pool.alloc(&acc, 2));
-    FDE_CUDA(cudaMemcpyAsync(u, d_U0, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    FDE_CUDA(cudaStreamSynchronize(st));
-    const double t1 = now_seconds();
-    s.setup_s = t1 - t0;
+    FDE_TRY(hodlr_factor(R->ax, st));
+    FDE_TRY(pool.alloc(&R->y, N));
+    FDE_TRY(pool.alloc(&R->rr, N));
+    FDE_TRY(pool.alloc(&R->acc, 2));
+  } else {
+    FDE_TRY(hodlr_build(&p->op_y, st, &R->ay));
+    FDE_TRY(sylv_create(R->ax, R->ay, p->prec, st, &R->s));
+    FDE_TRY(pool.alloc(&R->C2, n));
+  }
+  FDE_TRY(copy_state(R->U, U0, n, st));
+  FDE_CUDA(cudaStreamSynchronize(st));
+  R->stats.setup_s = now_seconds() - t0;
+  hodlr_info_t ix;
+  hodlr_get_info(R->ax, &ix);
+  R->stats.kmax_x = ix.kmax;
+  if (R->ay) {
+    hodlr_get_info(R->ay, &ix);
+    R->stats.kmax_y = ix.kmax;
+  }
+  return FDE_OK;
+}
+
+static fde_status runner_advance(fde_runner_s* R, int nsteps, cudaStream_t st) {
+  const int N = R->N, r = R->p.rank;
+  const double dt = R->p.op_x.dt;
+  const double t1 = now_seconds();
+  if (R->p.dim == 1) {
     const int nb = std::min(1024, ceil_div(N, 256));
-    for (int m = 1; m <= p->steps; ++m) {
-      rhs1d_kernel<<<nb, 256, 0, st>>>(u, FL, N, r, weights(p, m * dt), dt, b);
+    for (int i = 0; i < nsteps; ++i) {
+      const int m = R->step + 1;
+      rhs1d_kernel<<<nb, 256, 0, st>>>(R->U, R->FL, N, r, R->weights(m * dt), dt, R->C);
       FDE_LAUNCH("rhs1d_kernel");
       // refinement: x = u (warm start); r = b - A x; δ = Â^{-1} r; x += δ
       int sw = 0;
       double rel = 0.0;
       for (sw = 1; sw <= 10; ++sw) {
-        FDE_TRY(fd_apply_dense(g.ax, u, y, 0, st));
-        sub_kernel<<<nb, 256, 0, st>>>(b, y, rr, N);
+        FDE_TRY(fd_apply_dense(R->ax, R->U, R->y, 0, st));
+        sub_kernel<<<nb, 256, 0, st>>>(R->C, R->y, R->rr, N);
         FDE_LAUNCH("sub_kernel");
-        FDE_TRY(hodlr_solve(g.ax, rr, rr, 1, N, stream));
-        add_norms_kernel<<<1, 1024, 0, st>>>(u, rr, N, acc);
+        FDE_TRY(hodlr_solve(R->ax, R->rr, R->rr, 1, N, st));
+        add_norms_kernel<<<1, 1024, 0, st>>>(R->U, R->rr, N, R->acc);
         FDE_LAUNCH("add_norms_kernel");
         double a[2];
-        FDE_CUDA(cudaMemcpyAsync(a, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        FDE_CUDA(cudaMemcpyAsync(a, R->acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         FDE_CUDA(cudaStreamSynchronize(st));
         if (!std::isfinite(a[0])) {
           set_error("fde_run: non-finite iterate");
@@ -148,45 +198,94 @@ extern "C" fde_status fde_run(const fde_run_params* p, const double* d_U0, doubl
         set_error("fde_run: 1D refinement did not converge (last update %.3e)", rel);
         return FDE_ERR_NOCONV;
       }
-      s.sweeps_total += sw;
-      s.sweeps_max = std::max(s.sweeps_max, sw);
+      R->stats.sweeps_total += sw;
+      R->stats.sweeps_max = std::max(R->stats.sweeps_max, sw);
+      R->step = m;
     }
-    FDE_CUDA(cudaMemcpyAsync(d_Uout, u, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    FDE_CUDA(cudaStreamSynchronize(st));
-    s.solve_s = now_seconds() - t1;
   } else {
-    FDE_TRY(hodlr_build(&p->op_y, stream, &g.ay));
-    FDE_TRY(sylv_create(g.ax, g.ay, p->prec, stream, &g.s));
     const size_t NN = (size_t)N * N;
-    double *U, *C;
-    FDE_TRY(pool.alloc(&U, NN));
-    FDE_TRY(pool.alloc(&C, NN));
-    FDE_CUDA(cudaMemcpyAsync(U, d_U0, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    FDE_CUDA(cudaStreamSynchronize(st));
-    const double t1 = now_seconds();
-    s.setup_s = t1 - t0;
     const int nb = (int)std::min<size_t>((NN + 255) / 256, 152 * 32);
-    for (int m = 0; m < p->steps; ++m) {
-      rhs2d_kernel<<<nb, 256, 0, st>>>(U, FL, FR, N, r, weights(p, (m + 1) * dt), dt, C);
+    for (int i = 0; i < nsteps; ++i) {
+      const int m = R->step;
+      std::swap(R->C, R->C2);  // C2 <- previous right-hand side
+      rhs2d_kernel<<<nb, 256, 0, st>>>(R->U, R->FL, R->FR, N, r, R->weights((m + 1) * dt), dt, R->C);
       FDE_LAUNCH("rhs2d_kernel");
       double rel = 0.0;
       int sw = 0;
-      FDE_TRY(sylv_step_internal(g.s, C, U, st, &rel, &sw));
-      s.sweeps_total += sw;
-      s.sweeps_max = std::max(s.sweeps_max, sw);
-      s.relres_max = std::max(s.relres_max, rel);
+      fde_status s = sylv_step_internal(R->s, R->C, R->U, st, &rel, &sw, R->have_prev ? R->C2 : nullptr);
+      R->have_prev = (s == FDE_OK);
+      FDE_TRY(s);
+      R->stats.sweeps_total += sw;
+      R->stats.sweeps_max = std::max(R->stats.sweeps_max, sw);
+      R->stats.relres_max = std::max(R->stats.relres_max, rel);
+      R->step = m + 1;
     }
-    FDE_CUDA(cudaMemcpyAsync(d_Uout, U, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    FDE_CUDA(cudaStreamSynchronize(st));
-    s.solve_s = now_seconds() - t1;
-    hodlr_info_t iy;
-    hodlr_get_info(g.ay, &iy);
-    s.kmax_y = iy.kmax;
   }
-  hodlr_info_t ix;
-  hodlr_get_info(g.ax, &ix);
-  s.kmax_x = ix.kmax;
-  s.steps_per_s = p->steps / std::max(s.solve_s, 1e-12);
-  if (stats) *stats = s;
+  FDE_CUDA(cudaStreamSynchronize(st));
+  R->stats.solve_s += now_seconds() - t1;
   return FDE_OK;
+}
+
+extern "C" fde_status fde_runner_create(const fde_run_params* p, const double* U0, void* stream, fde_runner_t* out) {
+  FDE_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  FDE_TRY(check_run(p));
+  FDE_ARG(U0 != nullptr, "U0 is NULL");
+  fde_runner_s* R = new fde_runner_s();
+  fde_status s = runner_create(p, U0, (cudaStream_t)stream, R);
+  if (s != FDE_OK) {
+    delete R;
+    return s;
+  }
+  *out = R;
+  return FDE_OK;
+}
+
+extern "C" fde_status fde_runner_advance(fde_runner_t r, int nsteps, void* stream) {
+  FDE_ARG(r != nullptr, "runner is NULL");
+  FDE_ARG(nsteps >= 0, "nsteps must be >= 0");
+  return runner_advance(r, nsteps, (cudaStream_t)stream);
+}
+
+extern "C" fde_status fde_runner_load(fde_runner_t r, const double* U, int step_index, void* stream) {
+  FDE_ARG(r != nullptr && U != nullptr, "NULL argument");
+  FDE_ARG(step_index >= 0, "step_index must be >= 0");
+  const size_t n = (r->p.dim == 1) ? (size_t)r->N : (size_t)r->N * r->N;
+  FDE_TRY(copy_state(r->U, U, n, (cudaStream_t)stream));
+  r->step = step_index;
+  r->have_prev = false;
+  return FDE_OK;
+}
+
+extern "C" fde_status fde_runner_state(fde_runner_t r, double* U_out, void* stream) {
+  FDE_ARG(r != nullptr && U_out != nullptr, "NULL argument");
+  const size_t n = (r->p.dim == 1) ? (size_t)r->N : (size_t)r->N * r->N;
+  return copy_state(U_out, r->U, n, (cudaStream_t)stream);
+}
+
+extern "C" fde_status fde_runner_stats(fde_runner_t r, fde_run_stats* stats) {
+  FDE_ARG(r != nullptr && stats != nullptr, "NULL argument");
+  *stats = r->stats;
+  const int done = r->stats.sweeps_total > 0 ? r->step : 0;
+  stats->steps_per_s = (r->stats.solve_s > 0.0) ? done / r->stats.solve_s : 0.0;
+  return FDE_OK;
+}
+
+extern "C" void fde_runner_free(fde_runner_t r) { delete r; }
+
+extern "C" fde_status fde_run(const fde_run_params* p, const double* d_U0, double* d_Uout, void* stream,
+                              fde_run_stats* stats) {
+  FDE_TRY(check_run(p));
+  FDE_ARG(d_U0 != nullptr && d_Uout != nullptr, "NULL state buffer");
+  FDE_ARG(p->steps >= 1, "steps must be >= 1");
+  fde_runner_t r = nullptr;
+  FDE_TRY(fde_runner_create(p, d_U0, stream, &r));
+  fde_status s = fde_runner_advance(r, p->steps, stream);
+  if (s == FDE_OK) s = fde_runner_state(r, d_Uout, stream);
+  if (s == FDE_OK && stats) {
+    fde_runner_stats(r, stats);
+    stats->steps_per_s = p->steps / std::max(stats->solve_s, 1e-12);
+  }
+  fde_runner_free(r);
+  return s;
 }

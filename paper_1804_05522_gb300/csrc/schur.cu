@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(256) schur_kernel(double* Hall, double* Qall, 
 fde_status leaf_schur(double* H, double* Q, int ld, size_t stride, const int* d_n, int count, int* d_fail,
                       cudaStream_t st) {
   if (count == 0) return FDE_OK;
+  ProfScope ps("schur", st);
   schur_kernel<<<count, 256, ld * sizeof(double), st>>>(H, Q, ld, stride, d_n, d_fail);
   FDE_LAUNCH("schur_kernel");
   return FDE_OK;
@@ -254,67 +255,228 @@ __device__ void small_solve(T M[4][4], T b[4], int m) {
   }
 }
 
-// One CTA per leaf pair.  Columns of Y are solved from the last block to the
-// first (Rᵀ is lower quasi-triangular); inside a column block the rows are
-// solved bottom-up over the 1x1 / 2x2 blocks of S (the small coupled system
-// for a (row block, column block) is (I ⊗ S_bb + R_bb ⊗ I) vec Y_b = vec B_b).
+// One CTA per leaf pair, solving  S Y + Y Rᵀ = C  (S, R upper quasi-triangular)
+// by back substitution over the diagonal blocks (1x1 / 2x2) of both factors.
+// Column groups (R's diagonal blocks, last first) are handled in waves of up
+// to kWarps groups, one warp per group.  Inside a wave the warps advance as a
+// wavefront: warp g solves row group ρ (S's blocks, bottom first) at step
+// ρ + g, so every coupling it needs — rows below in its own columns and the
+// same rows in the later columns of the wave — was finalised at earlier steps.
+// A small coupled system (I ⊗ S_bb + R_bb ⊗ I) vec Y_b = vec B_b of size <= 4
+// is solved per (row group, column group).  Before a wave, its columns get
+// the contribution of all columns solved in earlier waves (a GEMM-like update).
+constexpr int kWarps = 32;
+
 template <typename T>
-__global__ void __launch_bounds__(256) trsyl_kernel(const T* __restrict__ Sall, const T* __restrict__ Rall, int lmax,
-                                                   const int* __restrict__ lo_x, const int* __restrict__ n_x, int nx,
-                                                   const int* __restrict__ lo_y, const int* __restrict__ n_y, T* W,
-                                                   int ldw) {
+__global__ void __launch_bounds__(kWarps * 32) trsyl_kernel(const T* __restrict__ Sall, const T* __restrict__ Rall,
+                                                           int lmax, const int* __restrict__ lo_x,
+                                                           const int* __restrict__ n_x, int nx,
+                                                           const int* __restrict__ lo_y,
+                                                           const int* __restrict__ n_y, T* W, int ldw, int mode) {
+  // mode 0: everything in global memory; 1: Y in shared; 2: Y, S, R in shared.
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = blockIdx.x % nx, q = blockIdx.x / nx;
+  const int n1 = n_x[p], n2 = n_y[q];
+  T* Yg = W + lo_x[p] + (size_t)lo_y[q] * ldw;
+  int* rg0 = (int*)smem_raw;  // start row of row group ρ (bottom first)
+  int* rgs = rg0 + lmax;      // its size
+  int* cg0 = rgs + lmax;      // start column of column group γ (last first)
+  int* cgs = cg0 + lmax;
+  __shared__ int s_nrg, s_ncg;
   const T* S = Sall + (size_t)p * lmax * lmax;
   const T* R = Rall + (size_t)q * lmax * lmax;
-  const int n1 = n_x[p], n2 = n_y[q];
-  T* Y = W + lo_x[p] + (size_t)lo_y[q] * ldw;
-#define SS(i, j) S[(i) + (size_t)(j)*lmax]
-#define RR(i, j) R[(i) + (size_t)(j)*lmax]
-#define YY(i, j) Y[(i) + (size_t)(j)*ldw]
-  int k1 = n2 - 1;
-  while (k1 >= 0) {
-    const int kb = (k1 > 0 && RR(k1, k1 - 1) != T(0)) ? 2 : 1;
-    const int k0 = k1 - kb + 1;
-    // right-hand side: Y[:, k] -= Σ_{l > k1} R[k][l] Y[:, l]
-    for (int i = threadIdx.x; i < n1; i += blockDim.x)
-      for (int k = k0; k <= k1; ++k) {
+  int lds = lmax, ldr = lmax;
+  T* Y = Yg;
+  int ldy = ldw;
+  T* dyn = (T*)(cgs + lmax);
+  if (mode >= 1) {
+    // odd leading dimensions keep the strided (row-wise) accesses conflict free
+    Y = dyn;
+    ldy = n1 | 1;
+    for (int e = threadIdx.x; e < n1 * n2; e += blockDim.x)
+      Y[e % n1 + (e / n1) * ldy] = Yg[e % n1 + (size_t)(e / n1) * ldw];
+    dyn += (size_t)ldy * n2;
+  }
+  if (mode == 2) {
+    T* Ss = dyn;
+    const int ls = n1 | 1;
+    for (int e = threadIdx.x; e < n1 * n1; e += blockDim.x) Ss[e % n1 + (e / n1) * ls] = S[e % n1 + (size_t)(e / n1) * lmax];
+    dyn += (size_t)ls * n1;
+    T* Rs = dyn;
+    const int lr = n2 | 1;
+    for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) Rs[e % n2 + (e / n2) * lr] = R[e % n2 + (size_t)(e / n2) * lmax];
+    S = Ss;
+    R = Rs;
+    lds = ls;
+    ldr = lr;
+  }
+  __syncthreads();
+#define SS(i, j) S[(i) + (size_t)(j)*lds]
+#define RR(i, j) R[(i) + (size_t)(j)*ldr]
+#define YY(i, j) Y[(i) + (size_t)(j)*ldy]
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int i1 = n1 - 1; i1 >= 0;) {
+      const int ib = (i1 > 0 && SS(i1, i1 - 1) != T(0)) ? 2 : 1;
+      rg0[c] = i1 - ib + 1;
+      rgs[c] = ib;
+      ++c;
+      i1 -= ib;
+    }
+    s_nrg = c;
+  } else if (threadIdx.x == 32) {
+    int c = 0;
+    for (int k1 = n2 - 1; k1 >= 0;) {
+      const int kb = (k1 > 0 && RR(k1, k1 - 1) != T(0)) ? 2 : 1;
+      cg0[c] = k1 - kb + 1;
+      cgs[c] = kb;
+      ++c;
+      k1 -= kb;
+    }
+    s_ncg = c;
+  }
+  __syncthreads();
+  const int nrg = s_nrg, ncg = s_ncg;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int wb = 0; wb < ncg; wb += kWarps) {
+    const int we = min(ncg, wb + kWarps);
+    // columns of this wave: [cfirst, clast]; columns already solved: > clast
+    const int clast = cg0[wb] + cgs[wb] - 1;
+    const int cfirst = cg0[we - 1];
+    if (clast + 1 < n2) {
+      const int wcols = clast - cfirst + 1;
+      for (int e = threadIdx.x; e < n1 * wcols; e += blockDim.x) {
+        const int i = e % n1, k = cfirst + e / n1;
         T acc = T(0);
-        for (int l = k1 + 1; l < n2; ++l) acc += RR(k, l) * YY(i, l);
+        for (int l = clast + 1; l < n2; ++l) acc += RR(k, l) * YY(i, l);
         YY(i, k) -= acc;
       }
+    }
     __syncthreads();
-    int i1 = n1 - 1;
-    while (i1 >= 0) {
-      const int ib = (i1 > 0 && SS(i1, i1 - 1) != T(0)) ? 2 : 1;
-      const int i0 = i1 - ib + 1;
-      if (threadIdx.x == 0) {
-        T M[4][4], b[4];
-        const int m = ib * kb;
-        for (int ka = 0; ka < kb; ++ka)
-          for (int ia = 0; ia < ib; ++ia) {
-            const int a = ia + ib * ka;
-            b[a] = YY(i0 + ia, k0 + ka);
-            for (int kc = 0; kc < kb; ++kc)
-              for (int ic = 0; ic < ib; ++ic) {
-                const int c = ic + ib * kc;
-                M[a][c] = (ka == kc ? SS(i0 + ia, i0 + ic) : T(0)) + (ia == ic ? RR(k0 + ka, k0 + kc) : T(0));
+    const int nsteps = nrg + (we - wb) - 1;
+    for (int t = 0; t < nsteps; ++t) {
+      const int g = warp, gam = wb + g, rho = t - g;
+      if (gam < we && rho >= 0 && rho < nrg && rgs[rho] == 1 && cgs[gam] == 1) {
+        // 1x1 blocks (real eigenvalues on both sides): the common case
+        const int i0 = rg0[rho], k0 = cg0[gam];
+        T acc = T(0);
+        for (int l = k0 + 1 + lane; l <= clast; l += 32) acc += RR(k0, l) * YY(i0, l);
+        acc = warp_sum(acc);
+        const T y = (YY(i0, k0) - acc) / (SS(i0, i0) + RR(k0, k0));
+        __syncwarp();
+        if (lane == 0) YY(i0, k0) = y;
+        for (int i = lane; i < i0; i += 32) YY(i, k0) -= SS(i, i0) * y;
+      } else if (gam < we && rho >= 0 && rho < nrg) {
+        // 2x2 blocks (complex pairs) on one or both sides: a system of size
+        // ib*kb <= 4, laid out with stride 2 (unknown ia + 2 kb) and padded with
+        // identity rows, solved in registers by unrolled Gaussian elimination
+        const int i0 = rg0[rho], ib = rgs[rho];
+        const int k0 = cg0[gam], kb = cgs[gam];
+        const int k1 = k0 + kb - 1;
+        T c[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+        for (int l = k1 + 1 + lane; l <= clast; l += 32) {
+          const T y0 = YY(i0, l), y1 = (ib == 2) ? YY(i0 + 1, l) : T(0);
+          const T r0 = RR(k0, l), r1 = (kb == 2) ? RR(k0 + 1, l) : T(0);
+          c[0][0] += r0 * y0;
+          c[0][1] += r1 * y0;
+          c[1][0] += r0 * y1;
+          c[1][1] += r1 * y1;
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int bb = 0; bb < 2; ++bb) c[a][bb] = warp_sum(c[a][bb]);
+        T yv[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+        if (lane == 0) {
+          T M[4][4], rhs[4];
+#pragma unroll
+          for (int kb_ = 0; kb_ < 2; ++kb_)
+#pragma unroll
+            for (int ia = 0; ia < 2; ++ia) {
+              const int u = ia + 2 * kb_;
+              const bool used = ia < ib && kb_ < kb;
+              rhs[u] = used ? YY(i0 + ia, k0 + kb_) - c[ia][kb_] : T(0);
+#pragma unroll
+              for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+                for (int ic = 0; ic < 2; ++ic) {
+                  const int v = ic + 2 * kc;
+                  T m = T(0);
+                  if (used && ic < ib && kc < kb)
+                    m = (kb_ == kc ? SS(i0 + ia, i0 + ic) : T(0)) + (ia == ic ? RR(k0 + kb_, k0 + kc) : T(0));
+                  else if (!used && u == v)
+                    m = T(1);
+                  M[u][v] = m;
+                }
+            }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            int pv = k;
+            T best = fabs(M[k][k]);
+#pragma unroll
+            for (int i = k + 1; i < 4; ++i)
+              if (fabs(M[i][k]) > best) {
+                best = fabs(M[i][k]);
+                pv = i;
               }
+#pragma unroll
+            for (int i = k + 1; i < 4; ++i)
+              if (i == pv) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const T t = M[k][j];
+                  M[k][j] = M[i][j];
+                  M[i][j] = t;
+                }
+                const T t = rhs[k];
+                rhs[k] = rhs[i];
+                rhs[i] = t;
+              }
+#pragma unroll
+            for (int i = k + 1; i < 4; ++i) {
+              const T f = M[i][k] / M[k][k];
+#pragma unroll
+              for (int j = k; j < 4; ++j) M[i][j] -= f * M[k][j];
+              rhs[i] -= f * rhs[k];
+            }
           }
-        small_solve(M, b, m);
-        for (int ka = 0; ka < kb; ++ka)
-          for (int ia = 0; ia < ib; ++ia) YY(i0 + ia, k0 + ka) = b[ia + ib * ka];
+#pragma unroll
+          for (int k = 3; k >= 0; --k) {
+            T sacc = rhs[k];
+#pragma unroll
+            for (int j = k + 1; j < 4; ++j) sacc -= M[k][j] * rhs[j];
+            rhs[k] = sacc / M[k][k];
+          }
+#pragma unroll
+          for (int kb_ = 0; kb_ < 2; ++kb_)
+#pragma unroll
+            for (int ia = 0; ia < 2; ++ia) yv[ia][kb_] = rhs[ia + 2 * kb_];
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int bb = 0; bb < 2; ++bb) yv[a][bb] = __shfl_sync(0xffffffffu, yv[a][bb], 0);
+        __syncwarp();
+        if (lane == 0) {
+#pragma unroll
+          for (int ia = 0; ia < 2; ++ia)
+#pragma unroll
+            for (int kb_ = 0; kb_ < 2; ++kb_)
+              if (ia < ib && kb_ < kb) YY(i0 + ia, k0 + kb_) = yv[ia][kb_];
+        }
+        // rows above the block, same columns: Y[i][k] -= S[i][i0..] y
+        for (int i = lane; i < i0; i += 32) {
+          const T s0 = SS(i, i0), s1 = (ib == 2) ? SS(i, i0 + 1) : T(0);
+          YY(i, k0) -= s0 * yv[0][0] + s1 * yv[1][0];
+          if (kb == 2) YY(i, k0 + 1) -= s0 * yv[0][1] + s1 * yv[1][1];
+        }
       }
       __syncthreads();
-      for (int i = threadIdx.x; i < i0; i += blockDim.x)
-        for (int k = k0; k <= k1; ++k) {
-          T acc = SS(i, i0) * YY(i0, k);
-          if (ib == 2) acc += SS(i, i1) * YY(i1, k);
-          YY(i, k) -= acc;
-        }
-      __syncthreads();
-      i1 = i0 - 1;
     }
-    k1 = k0 - 1;
+  }
+  if (mode >= 1) {
+    for (int e = threadIdx.x; e < n1 * n2; e += blockDim.x)
+      Yg[e % n1 + (size_t)(e / n1) * ldw] = Y[e % n1 + (e / n1) * ldy];
   }
 #undef SS
 #undef RR
@@ -323,15 +485,26 @@ __global__ void __launch_bounds__(256) trsyl_kernel(const T* __restrict__ Sall, 
 
 template <typename T>
 fde_status leaf_trsyl(const T* S, const T* R, int lmax, const int* d_lo_x, const int* d_n_x, int nx,
-                      const int* d_lo_y, const int* d_n_y, int ny, T* W, int ldw, cudaStream_t st) {
-  trsyl_kernel<T><<<nx * ny, 256, 0, st>>>(S, R, lmax, d_lo_x, d_n_x, nx, d_lo_y, d_n_y, W, ldw);
+                      const int* d_lo_y, const int* d_n_y, int ny, T* W, int ldw, cudaStream_t st, double flops) {
+  const size_t tables = 4 * (size_t)lmax * sizeof(int);
+  const size_t mat = (size_t)(lmax | 1) * lmax * sizeof(T);  // one padded lmax x lmax block
+  const size_t limit = 220 * 1024;
+  const int mode = (tables + 3 * mat <= limit) ? 2 : (tables + mat <= limit) ? 1 : 0;
+  const size_t smem = tables + (mode == 2 ? 3 * mat : mode == 1 ? mat : 0);
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(T) == 8]) {
+    FDE_CUDA(cudaFuncSetAttribute(trsyl_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+    attr_set[sizeof(T) == 8] = true;
+  }
+  ProfScope ps(sizeof(T) == 4 ? "trsyl32" : "trsyl64", st, flops, 1);
+  trsyl_kernel<T><<<nx * ny, kWarps * 32, smem, st>>>(S, R, lmax, d_lo_x, d_n_x, nx, d_lo_y, d_n_y, W, ldw, mode);
   FDE_LAUNCH("trsyl_kernel");
   return FDE_OK;
 }
 
 template fde_status leaf_trsyl<double>(const double*, const double*, int, const int*, const int*, int, const int*,
-                                       const int*, int, double*, int, cudaStream_t);
+                                       const int*, int, double*, int, cudaStream_t, double);
 template fde_status leaf_trsyl<float>(const float*, const float*, int, const int*, const int*, int, const int*,
-                                      const int*, int, float*, int, cudaStream_t);
+                                      const int*, int, float*, int, cudaStream_t, double);
 
 }  // namespace fde

@@ -17,8 +17,10 @@ fde_status leaf_schur(double* H, double* Q, int ld, size_t stride, const int* d_
 //   S_p Y + Y R_qᵀ = C   in place on the (p, q) block of W (ld ldw),
 // S_p, R_q upper quasi-triangular (leaf Schur forms).  Bartels–Stewart
 // back substitution over 1x1 / 2x2 diagonal blocks.
+// flops: algorithmic work for the instrumentation (Σ n1 n2 (n1 + n2)).
 template <typename T>
 fde_status leaf_trsyl(const T* S, const T* R, int lmax, const int* d_lo_x, const int* d_n_x, int nx,
-                      const int* d_lo_y, const int* d_n_y, int ny, T* W, int ldw, cudaStream_t st);
+                      const int* d_lo_y, const int* d_n_y, int ny, T* W, int ldw, cudaStream_t st,
+                      double flops = 0.0);
 
 }  // namespace fde

@@ -151,6 +151,18 @@ __global__ void axpy_kernel(T* __restrict__ Y, const T* __restrict__ X, size_t n
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     Y[i] += a * X[i];
 }
+// One fADI step's factor updates for both sides (same element count):
+//   Z <- cj Z ; G <- G - Z ; H <- H - cj W
+template <typename T>
+__global__ void fadi_update_kernel(T* __restrict__ Z, T* __restrict__ G, T* __restrict__ H, const T* __restrict__ W,
+                                   size_t n, T cj) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T z = cj * Z[i];
+    Z[i] = z;
+    G[i] -= z;
+    H[i] -= cj * W[i];
+  }
+}
 static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 32); }
 
 // X64 += (double) D ; partial sums of |D|^2 and |X64|^2 into acc[0], acc[1]
@@ -179,6 +191,12 @@ __global__ void sumsq_kernel(const double* __restrict__ X, size_t n, double* acc
     s += X[i] * X[i];
   s = block_sum(s, sh);
   if (threadIdx.x == 0) atomicAdd(acc, s);
+}
+// R <- C - Cprev + R  (residual of the previous solution for the new C)
+__global__ void shift_residual_kernel(const double* __restrict__ C, const double* __restrict__ Cp, double* __restrict__ R,
+                                      size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    R[i] = C[i] - Cp[i] + R[i];
 }
 __global__ void nonfinite_kernel(const double* __restrict__ X, size_t n, int* bad) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -300,6 +318,32 @@ __global__ void __launch_bounds__(1024) ghat_kernel(const double* __restrict__ g
   for (int k = threadIdx.x; k < P; k += blockDim.x) Ghat[k] = buf[k];
 }
 
+// Spans of the nodes of one level.
+struct NodeSpan {
+  int lo, n;
+};
+// R[lo_p + i][i] = 1 for node p (a block-diagonal identity slab N x smax)
+__global__ void slab_diag_kernel(const NodeSpan* __restrict__ nodes, int nn, double* R, int N) {
+  const NodeSpan nd = nodes[blockIdx.x];
+  for (int i = threadIdx.x; i < nd.n; i += blockDim.x) R[(nd.lo + i) + (size_t)i * N] = 1.0;
+  (void)nn;
+}
+// M_p[(j smax + m) + col (J smax)] = scale * P[lo_p + m][col]  and  R -= cj P
+__global__ void rational_step_kernel(const NodeSpan* __restrict__ nodes, const double* __restrict__ P, double* R, int N,
+                                     int smax, int J, int j, double scale, double cj, double* M) {
+  const NodeSpan nd = nodes[blockIdx.y];
+  const size_t ldm = (size_t)J * smax;
+  double* Mp = M + (size_t)blockIdx.y * ldm * smax;
+  const size_t total = (size_t)nd.n * smax;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e % nd.n), col = (int)(e / nd.n);
+    const size_t gi = (size_t)(nd.lo + m) + (size_t)col * N;
+    const double pv = P[gi];
+    Mp[(size_t)j * smax + m + (size_t)col * ldm] = scale * pv;
+    R[gi] -= cj * pv;
+  }
+}
+
 // Zero-padding masks for the constant parts of the fADI right-hand sides:
 // dst[rows of node, col0 + 0..K) = U masked to child-1 rows, [col0+K, col0+2K) masked to child-2 rows.
 template <typename T>
@@ -332,13 +376,25 @@ struct LevelSolve {
   T* H = nullptr;
   T* Zall = nullptr;                  // J panels of N x ncols
   T* Wall = nullptr;
-  std::vector<Plan<T>> planA, planB;  // per shift
+  std::vector<Plan<T>> plan;          // per shift: both sides' solves, merged launches
   GemmBatch<T> g_rhs_x, g_rhs_y;      // HA (into H) and GB (into G) products with X0
   GemmBatch<T> g_update;              // X += Σ_j Z_j W_jᵀ per pair
+  // rational form: Z_j = P_j G_0 with P_j = -c_j (A + b_j)^{-1} Π_{i<j} (I - c_i (A + b_i)^{-1})
+  // precomputed per node and stacked over j (rows j*smax + m), same for the B side
+  bool rational = false;
+  int smax = 0, Kx = 0, Ky = 0;
+  T *MA = nullptr, *MB = nullptr;     // 2^l blocks of (J smax) x smax
+  T *ZA = nullptr, *WB = nullptr;     // constant parts: MA·GA (J smax x 2Kx), MB·HB (J smax x 2Ky)
+  T *Hx = nullptr, *Gy = nullptr;     // X0-dependent RHS factors: N x 2^l 2Kx, N x 2^l 2Ky
+  T *ZB = nullptr, *WA = nullptr;     // MA·Gy (J smax x 2^l 2Ky), MB·Hx (J smax x 2^l 2Kx)
+  // the two update terms accumulate into the same X tile: separate launches
+  GemmBatch<T> r_rhs_h, r_rhs_g, r_apply, r_update, r_update2;
 };
 
 template <typename T>
 struct Inner {
+  cudaGraphExec_t exec = nullptr;     // captured run of the whole inner solve
+  size_t graph_kernels = 0;
   T *Cin = nullptr, *W1 = nullptr, *W2 = nullptr, *X = nullptr;
   T *Qx = nullptr, *Sx = nullptr, *Qy = nullptr, *Sy = nullptr;
   GemmBatch<T> g_qxt, g_qy, g_qx, g_qyt;
@@ -351,6 +407,8 @@ struct Inner {
 using namespace fde;
 
 struct sylv_s {
+  cudaStream_t gs = nullptr;          // private stream for graph capture / replay
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   hodlr_s* ax = nullptr;
   hodlr_s* ay = nullptr;
   int prec = 0, N = 0, L = 0, lmax = 0;
@@ -368,6 +426,16 @@ struct sylv_s {
   int* d_bad = nullptr;
   sylv_refine_t refine{};
   std::vector<int> J;
+  double trsyl_flops = 0.0, fft_flops = 0.0;
+  bool R_valid = false;               // R holds C_last - A(X_last) of the last step
+  bool rational = false;              // fADI levels in precomputed rational form
+  ~sylv_s() {
+    if (in64.exec) cudaGraphExecDestroy(in64.exec);
+    if (in32.exec) cudaGraphExecDestroy(in32.exec);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (gs) cudaStreamDestroy(gs);
+  }
 };
 
 namespace fde {
@@ -404,10 +472,162 @@ static fde_status convert_buf(const double* src, T** dst, size_t n, DevPool& poo
   return FDE_OK;
 }
 
+// Rational-form fADI level (see LevelSolve): forms, in FP64 with the shifted
+// HODLR factorisations, the stacked operators of both sides and the constant
+// right-hand-side parts, converts them to T and records the four per-step
+// batches (RHS products, operator application, low-rank update).
+template <typename T>
+static fde_status build_level_rational(sylv_s* S, Inner<T>& in, int l, const std::vector<Fact<double>*>& FA,
+                                       const std::vector<Fact<double>*>& FB, const std::vector<double>& a,
+                                       const std::vector<double>& b, cudaStream_t st) {
+  hodlr_s* ax = S->ax;
+  hodlr_s* ay = S->ay;
+  const Tree& tr = ax->tree;
+  const int N = S->N, nn = 1 << l, J = (int)a.size();
+  LevelSolve<T>& ls = in.lv[l];
+  DevPool& pool = S->pool;
+  DevPool scratch;
+  ls.rational = true;
+  ls.J = J;
+  ls.Kx = ax->K[l];
+  ls.Ky = ay->K[l];
+  const int Kx = ls.Kx, Ky = ls.Ky;
+  int smax = 0;
+  std::vector<NodeSpan> nx(nn), ny(nn);
+  for (int p = 0; p < nn; ++p) {
+    const int id = tr.id(l, p);
+    nx[p] = {tr.lo[id], tr.hi[id] - tr.lo[id]};
+    ny[p] = {ay->tree.lo[id], ay->tree.hi[id] - ay->tree.lo[id]};
+    smax = std::max(smax, std::max(nx[p].n, ny[p].n));
+  }
+  ls.smax = smax;
+  const size_t ldm = (size_t)J * smax;  // leading dimension of stacked blocks
+  const size_t mblk = ldm * smax;        // one node's stacked operator
+  NodeSpan *dnx, *dny;
+  FDE_TRY(scratch.alloc(&dnx, nn));
+  FDE_TRY(scratch.alloc(&dny, nn));
+  FDE_CUDA(cudaMemcpy(dnx, nx.data(), nn * sizeof(NodeSpan), cudaMemcpyHostToDevice));
+  FDE_CUDA(cudaMemcpy(dny, ny.data(), nn * sizeof(NodeSpan), cudaMemcpyHostToDevice));
+  double *R, *P, *M64, *zb, *wb;
+  FDE_TRY(scratch.alloc(&R, (size_t)N * smax));
+  FDE_TRY(scratch.alloc(&P, (size_t)N * smax));
+  FDE_TRY(scratch.alloc(&M64, nn * mblk));
+  const size_t zel = std::max(solve_scratch_elems(ax, smax, l), solve_scratch_elems(ay, smax, l));
+  FDE_TRY(scratch.alloc(&zb, zel));
+  FDE_TRY(scratch.alloc(&wb, zel));
+  FDE_TRY(pool.alloc(&ls.MA, nn * mblk));
+  FDE_TRY(pool.alloc(&ls.MB, nn * mblk));
+  for (int side = 0; side < 2; ++side) {
+    hodlr_s* h = side == 0 ? ax : ay;
+    const NodeSpan* dn = side == 0 ? dnx : dny;
+    FDE_CUDA(cudaMemsetAsync(R, 0, (size_t)N * smax * sizeof(double), st));
+    FDE_CUDA(cudaMemsetAsync(M64, 0, nn * mblk * sizeof(double), st));
+    slab_diag_kernel<<<nn, 256, 0, st>>>(dn, nn, R, N);
+    FDE_LAUNCH("slab_diag_kernel");
+    for (int j = 0; j < J; ++j) {
+      const double cj = a[j] + b[j];
+      Plan<double> pl;
+      FDE_TRY(build_solve_plan<double>(h, side == 0 ? *FA[j] : *FB[j], h->V, R, N, P, N, smax, l, nullptr, zb, wb,
+                                       scratch, &pl, st));
+      FDE_TRY(plan_run(pl, st));
+      // side A keeps -c_j P_j (the step scale and the sign of G_0 folded in), side B keeps P_j
+      dim3 grid((unsigned)std::min<size_t>(((size_t)smax * smax + 255) / 256, 1024), nn);
+      rational_step_kernel<<<grid, 256, 0, st>>>(dn, P, R, N, smax, J, j, side == 0 ? -cj : 1.0, cj, M64);
+      FDE_LAUNCH("rational_step_kernel");
+      FDE_CUDA(cudaStreamSynchronize(st));
+    }
+    T* dst = side == 0 ? ls.MA : ls.MB;
+    if (sizeof(T) == sizeof(double))
+      FDE_CUDA(cudaMemcpyAsync((void*)dst, M64, nn * mblk * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else
+      FDE_TRY((convert<double, float>(M64, (float*)dst, nn * mblk, st)));
+    // constant right-hand-side parts: ZA_p = MA_p [U^x|c1, U^x|c2],  WB_q = MB_q [U^y|c1', U^y|c2']
+    const int K = side == 0 ? Kx : Ky;
+    double* U2 = P;  // reuse as an N x 2K slab
+    std::vector<MaskJob<double>> jobs;
+    for (int p = 0; p < nn; ++p) {
+      const int id = h->tree.id(l, p);
+      const int lo = h->tree.lo[id], hi = h->tree.hi[id], mid = lo + (hi - lo) / 2;
+      jobs.push_back({h->U[l], U2, lo, mid, hi, K, 1.0});
+    }
+    MaskJob<double>* dj;
+    FDE_TRY(scratch.alloc(&dj, jobs.size()));
+    FDE_CUDA(cudaMemcpy(dj, jobs.data(), jobs.size() * sizeof(MaskJob<double>), cudaMemcpyHostToDevice));
+    mask_copy_kernel<double><<<nn, 256, 0, st>>>(dj, N);
+    FDE_LAUNCH("mask_copy_kernel");
+    double* C64;
+    FDE_TRY(scratch.alloc(&C64, nn * ldm * 2 * K));
+    std::vector<GemmDesc<double>> dd;
+    for (int p = 0; p < nn; ++p)
+      dd.push_back({M64 + p * mblk, U2 + (side == 0 ? nx[p].lo : ny[p].lo), C64 + p * ldm * 2 * K, (int)ldm, 2 * K,
+                    side == 0 ? nx[p].n : ny[p].n, (int)ldm, N, (int)ldm});
+    GemmBatch<double> gbd;
+    FDE_TRY(gemm_batch_upload(scratch, dd, false, false, 1.0, 0.0, &gbd, st));
+    FDE_TRY(gemm_batch_run(gbd, st));
+    T** cdst = side == 0 ? &ls.ZA : &ls.WB;
+    FDE_TRY(pool.alloc(cdst, nn * ldm * 2 * K));
+    if (sizeof(T) == sizeof(double))
+      FDE_CUDA(cudaMemcpyAsync((void*)*cdst, C64, nn * ldm * 2 * K * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else
+      FDE_TRY((convert<double, float>(C64, (float*)*cdst, nn * ldm * 2 * K, st)));
+    FDE_CUDA(cudaStreamSynchronize(st));
+  }
+  // per-step buffers and batches
+  FDE_TRY(pool.alloc(&ls.Hx, (size_t)N * nn * 2 * Kx));
+  FDE_TRY(pool.alloc(&ls.Gy, (size_t)N * nn * 2 * Ky));
+  FDE_TRY(pool.alloc(&ls.ZB, nn * ldm * nn * 2 * Ky));
+  FDE_TRY(pool.alloc(&ls.WA, nn * ldm * nn * 2 * Kx));
+  std::vector<T*> Vx = level_V<T>(ax), Vy = level_V<T>(ay);
+  std::vector<GemmDesc<T>> dh, dg, dap, dup, dup2;
+  for (int p = 0; p < nn; ++p) {
+    const int lo = nx[p].lo, sp = nx[p].n, mid = lo + sp / 2, hi = lo + sp;
+    for (int q = 0; q < nn; ++q) {
+      const int loy = ny[q].lo, tq = ny[q].n, midy = loy + tq / 2, hiy = loy + tq;
+      // Hx[q rows, p block] = [X0[c2_p, q cols]ᵀ V^x[c2_p], X0[c1_p, q cols]ᵀ V^x[c1_p]]
+      T* Hb = ls.Hx + loy + (size_t)(p * 2 * Kx) * N;
+      dh.push_back({in.X + mid + (size_t)loy * N, Vx[l] + mid, Hb, tq, Kx, hi - mid, N, N, N});
+      dh.push_back({in.X + lo + (size_t)loy * N, Vx[l] + lo, Hb + (size_t)Kx * N, tq, Kx, mid - lo, N, N, N});
+      // Gy[p rows, q block] = [X0[p rows, c2'_q] V^y[c2'_q], X0[p rows, c1'_q] V^y[c1'_q]]
+      T* Gb = ls.Gy + lo + (size_t)(q * 2 * Ky) * N;
+      dg.push_back({in.X + lo + (size_t)midy * N, Vy[l] + midy, Gb, sp, Ky, hiy - midy, N, N, N});
+      dg.push_back({in.X + lo + (size_t)loy * N, Vy[l] + loy, Gb + (size_t)Ky * N, sp, Ky, midy - loy, N, N, N});
+      // X_pq += Σ_j ZA_p,j WA_q,j[p block]ᵀ + ZB_p,j[q block] WB_q,jᵀ   (k = (j, c), two-level)
+      GemmDesc<T> u1{ls.ZA + p * ldm * 2 * Kx, ls.WA + q * ldm * nn * 2 * Kx + (size_t)(p * 2 * Kx) * ldm,
+                     in.X + lo + (size_t)loy * N, sp, tq, J * 2 * Kx, (int)ldm, (int)ldm, N};
+      u1.kblk = 2 * Kx;
+      u1.kstr = smax;
+      GemmDesc<T> u2{ls.ZB + p * ldm * nn * 2 * Ky + (size_t)(q * 2 * Ky) * ldm, ls.WB + q * ldm * 2 * Ky,
+                     in.X + lo + (size_t)loy * N, sp, tq, J * 2 * Ky, (int)ldm, (int)ldm, N};
+      u2.kblk = 2 * Ky;
+      u2.kstr = smax;
+      dup.push_back(u1);
+      dup2.push_back(u2);
+    }
+    // ZB_p = MA_p Gy[p rows] (x node p);  WA_p = MB_p Hx[p rows] (y node p)
+    dap.push_back({ls.MA + p * mblk, ls.Gy + lo, ls.ZB + p * ldm * nn * 2 * Ky, (int)ldm, nn * 2 * Ky, sp, (int)ldm,
+                   N, (int)ldm});
+    dap.push_back({ls.MB + p * mblk, ls.Hx + ny[p].lo, ls.WA + p * ldm * nn * 2 * Kx, (int)ldm, nn * 2 * Kx, ny[p].n,
+                   (int)ldm, N, (int)ldm});
+  }
+  FDE_TRY(gemm_batch_upload(pool, dh, true, false, T(1), T(0), &ls.r_rhs_h, st));
+  FDE_TRY(gemm_batch_upload(pool, dg, false, false, T(1), T(0), &ls.r_rhs_g, st));
+  FDE_TRY(gemm_batch_upload(pool, dap, false, false, T(1), T(0), &ls.r_apply, st));
+  FDE_TRY(gemm_batch_upload(pool, dup, false, true, T(1), T(1), &ls.r_update, st));
+  FDE_TRY(gemm_batch_upload(pool, dup2, false, true, T(1), T(1), &ls.r_update2, st));
+  FDE_CUDA(cudaStreamSynchronize(st));
+  return FDE_OK;
+}
+
+struct RationalSrc {
+  std::vector<Fact<double>*> FA, FB;  // FP64 shifted factorisations, level order L-1..0
+  std::vector<std::vector<double>> a, b;
+};
+
 // Build the inner solver of precision T: leaf transforms, fADI levels, plans.
 template <typename T>
 static fde_status build_inner(sylv_s* S, Inner<T>& in, const std::vector<Fact<T>*>& FA_all,
-                              const std::vector<Fact<T>*>& FB_all, cudaStream_t st) {
+                              const std::vector<Fact<T>*>& FB_all, cudaStream_t st,
+                              const RationalSrc* rsrc = nullptr) {
   hodlr_s* ax = S->ax;
   hodlr_s* ay = S->ay;
   const Tree& tr = ax->tree;
@@ -443,7 +663,18 @@ static fde_status build_inner(sylv_s* S, Inner<T>& in, const std::vector<Fact<T>
   in.lv.resize(L);
   std::vector<T*> Vx = level_V<T>(ax), Vy = level_V<T>(ay), Ux = level_U<T>(ax), Uy = level_U<T>(ay);
   size_t fi = 0;
-  // scratch for plans (largest level)
+  if (rsrc) {
+    size_t off = 0;
+    for (int l = L - 1; l >= 0; --l) {
+      const int J = S->J[l];
+      std::vector<Fact<double>*> fa(rsrc->FA.begin() + off, rsrc->FA.begin() + off + J);
+      std::vector<Fact<double>*> fb(rsrc->FB.begin() + off, rsrc->FB.begin() + off + J);
+      FDE_TRY(build_level_rational<T>(S, in, l, fa, fb, rsrc->a[l], rsrc->b[l], st));
+      off += J;
+    }
+    FDE_CUDA(cudaStreamSynchronize(st));
+    return FDE_OK;
+  }
   for (int l = L - 1; l >= 0; --l) {
     LevelSolve<T>& ls = in.lv[l];
     const int Kx = ax->K[l], Ky = ay->K[l], Qw = 2 * Kx + 2 * Ky, nn = 1 << l;
@@ -507,20 +738,21 @@ static fde_status build_inner(sylv_s* S, Inner<T>& in, const std::vector<Fact<T>
       FDE_TRY(gemm_batch_upload(pool, dg, false, false, T(-1), T(0), &ls.g_rhs_y, st));
       FDE_TRY(gemm_batch_upload(pool, du, false, true, T(1), T(1), &ls.g_update, st));
     }
-    // solve plans per shift: Z_j = (A_p + b_j I)^{-1} G,  W_j = (B_q + a_j I)^{-1} H
-    const size_t zel = std::max(solve_scratch_elems(ax, ls.ncols, l), solve_scratch_elems(ay, ls.ncols, l));
-    T *zb, *wb;
-    FDE_TRY(pool.alloc(&zb, zel));
-    FDE_TRY(pool.alloc(&wb, zel));
-    ls.planA.resize(ls.J);
-    ls.planB.resize(ls.J);
+    // solve plans per shift: Z_j = (A_p + b_j I)^{-1} G,  W_j = (B_q + a_j I)^{-1} H,
+    // the two sides merged step by step into shared launches
+    T *zbA, *wbA, *zbB, *wbB;
+    FDE_TRY(pool.alloc(&zbA, solve_scratch_elems(ax, ls.ncols, l)));
+    FDE_TRY(pool.alloc(&wbA, solve_scratch_elems(ax, ls.ncols, l)));
+    FDE_TRY(pool.alloc(&zbB, solve_scratch_elems(ay, ls.ncols, l)));
+    FDE_TRY(pool.alloc(&wbB, solve_scratch_elems(ay, ls.ncols, l)));
+    ls.plan.resize(ls.J);
     for (int j = 0; j < ls.J; ++j) {
-      const Fact<T>& FA = *FA_all[fi + j];
-      const Fact<T>& FB = *FB_all[fi + j];
-      FDE_TRY(build_solve_plan<T>(ax, FA, Vx, ls.G, N, ls.Zall + (size_t)j * blk, N, ls.ncols, l, nullptr, zb, wb,
-                                  pool, &ls.planA[j], st));
-      FDE_TRY(build_solve_plan<T>(ay, FB, Vy, ls.H, N, ls.Wall + (size_t)j * blk, N, ls.ncols, l, nullptr, zb, wb,
-                                  pool, &ls.planB[j], st));
+      std::vector<std::vector<HostOp<T>>> specs(2);
+      FDE_TRY(build_solve_spec<T>(ax, *FA_all[fi + j], Vx, ls.G, N, ls.Zall + (size_t)j * blk, N, ls.ncols, l,
+                                  nullptr, zbA, wbA, &specs[0]));
+      FDE_TRY(build_solve_spec<T>(ay, *FB_all[fi + j], Vy, ls.H, N, ls.Wall + (size_t)j * blk, N, ls.ncols, l,
+                                  nullptr, zbB, wbB, &specs[1]));
+      FDE_TRY(upload_specs<T>(specs, pool, &ls.plan[j], st));
     }
     fi += ls.J;
   }
@@ -536,31 +768,48 @@ static fde_status run_inner(sylv_s* S, Inner<T>& in, cudaStream_t st) {
   const int N = S->N, nl = ax->tree.nleaves();
   FDE_TRY(gemm_batch_run(in.g_qxt, st));
   FDE_TRY(gemm_batch_run(in.g_qy, st));
-  FDE_TRY(leaf_trsyl<T>(in.Sx, in.Sy, S->lmax, S->d_lo, S->d_n, nl, S->d_lo + nl, S->d_n + nl, nl, in.W2, N, st));
+  FDE_TRY(leaf_trsyl<T>(in.Sx, in.Sy, S->lmax, S->d_lo, S->d_n, nl, S->d_lo + nl, S->d_n + nl, nl, in.W2, N, st,
+                        S->trsyl_flops));
   FDE_TRY(gemm_batch_run(in.g_qx, st));
   FDE_TRY(gemm_batch_run(in.g_qyt, st));
   for (int l = S->L - 1; l >= 0; --l) {
     LevelSolve<T>& ls = in.lv[l];
+    if (ls.rational) {
+      FDE_TRY(gemm_batch_run(ls.r_rhs_h, st));
+      FDE_TRY(gemm_batch_run(ls.r_rhs_g, st));
+      FDE_TRY(gemm_batch_run(ls.r_apply, st));
+      FDE_TRY(gemm_batch_run(ls.r_update, st));
+      FDE_TRY(gemm_batch_run(ls.r_update2, st));
+      continue;
+    }
     const size_t blk = (size_t)N * ls.ncols;
     FDE_CUDA(cudaMemcpyAsync(ls.G, ls.Gt, blk * sizeof(T), cudaMemcpyDeviceToDevice, st));
     FDE_CUDA(cudaMemcpyAsync(ls.H, ls.Ht, blk * sizeof(T), cudaMemcpyDeviceToDevice, st));
     FDE_TRY(gemm_batch_run(ls.g_rhs_x, st));
     FDE_TRY(gemm_batch_run(ls.g_rhs_y, st));
     for (int j = 0; j < ls.J; ++j) {
-      FDE_TRY(plan_run(ls.planA[j], st));
-      FDE_TRY(plan_run(ls.planB[j], st));
+      FDE_TRY(plan_run(ls.plan[j], st));
       const T cj = (T)(ls.a[j] + ls.b[j]);
       T* Zj = ls.Zall + (size_t)j * blk;
       T* Wj = ls.Wall + (size_t)j * blk;
-      scale_sub_kernel<T><<<grid_for(blk), 256, 0, st>>>(Zj, ls.G, blk, cj);
-      axpy_kernel<T><<<grid_for(blk), 256, 0, st>>>(ls.H, Wj, blk, -cj);
-      FDE_LAUNCH("fadi update");
+      {
+        ProfScope ps("fadi_axpy", st, 7.0 * blk * sizeof(T), 0);
+        fadi_update_kernel<T><<<grid_for(blk), 256, 0, st>>>(Zj, ls.G, ls.H, Wj, blk, cj);
+        FDE_LAUNCH("fadi_update_kernel");
+      }
     }
     FDE_TRY(gemm_batch_run(ls.g_update, st));
   }
   (void)ay;
   return FDE_OK;
 }
+
+// Capture run_inner into a CUDA graph (on a private stream) so that each
+// replay costs one launch; profiling (per-kernel events) uses the eager path.
+template <typename T>
+static fde_status capture_inner(sylv_s* S, Inner<T>& in);
+template <typename T>
+static fde_status inner_solve(sylv_s* S, Inner<T>& in, cudaStream_t st);
 
 // R = C - A_x X - X A_yᵀ (FP64, structured)
 static fde_status residual(sylv_s* S, const double* C, const double* X, double* R, cudaStream_t st) {
@@ -569,22 +818,81 @@ static fde_status residual(sylv_s* S, const double* C, const double* X, double* 
   const int N = S->N, P = S->P, lp = S->logP;
   const int nb = (N + 1) / 2;
   const size_t smem = (size_t)P * sizeof(double2);
-  fd_fft_apply_kernel<<<nb, 1024, smem, st>>>(X, N, C, R, S->GhX, S->tw, P, lp, ax->dp, ax->dm, ax->c,
-                                               ax->p.shift, N, S->fft_scratch, 1);
-  FDE_LAUNCH("fd_fft_apply_kernel x");
+  {
+    ProfScope ps("fft_apply", st, S->fft_flops, 1);
+    fd_fft_apply_kernel<<<nb, 1024, smem, st>>>(X, N, C, R, S->GhX, S->tw, P, lp, ax->dp, ax->dm, ax->c,
+                                                 ax->p.shift, N, S->fft_scratch, 1);
+    FDE_LAUNCH("fd_fft_apply_kernel x");
+  }
   dim3 tg(ceil_div(N, 32), ceil_div(N, 32)), tb(32, 8);
-  transpose_kernel<<<tg, tb, 0, st>>>(X, S->Xt, N, 0);
-  fd_fft_apply_kernel<<<nb, 1024, smem, st>>>(S->Xt, N, nullptr, S->Yt, S->GhY, S->tw, P, lp, ay->dp, ay->dm, ay->c,
-                                               ay->p.shift, N, S->fft_scratch, 0);
-  FDE_LAUNCH("fd_fft_apply_kernel y");
-  transpose_kernel<<<tg, tb, 0, st>>>(S->Yt, R, N, 1);
-  FDE_LAUNCH("transpose_kernel");
+  {
+    ProfScope ps("transpose", st, 16.0 * N * N, 0);
+    transpose_kernel<<<tg, tb, 0, st>>>(X, S->Xt, N, 0);
+    FDE_LAUNCH("transpose_kernel");
+  }
+  {
+    ProfScope ps("fft_apply", st, S->fft_flops, 1);
+    fd_fft_apply_kernel<<<nb, 1024, smem, st>>>(S->Xt, N, nullptr, S->Yt, S->GhY, S->tw, P, lp, ay->dp, ay->dm,
+                                                 ay->c, ay->p.shift, N, S->fft_scratch, 0);
+    FDE_LAUNCH("fd_fft_apply_kernel y");
+  }
+  {
+    ProfScope ps("transpose", st, 24.0 * N * N, 0);
+    transpose_kernel<<<tg, tb, 0, st>>>(S->Yt, R, N, 1);
+    FDE_LAUNCH("transpose_kernel");
+  }
   return FDE_OK;
 }
 
 static fde_status read_acc(sylv_s* S, double* h, int n, cudaStream_t st) {
   FDE_CUDA(cudaMemcpyAsync(h, S->acc, n * sizeof(double), cudaMemcpyDeviceToHost, st));
   FDE_CUDA(cudaStreamSynchronize(st));
+  return FDE_OK;
+}
+
+template <typename T>
+static fde_status capture_inner(sylv_s* S, Inner<T>& in) {
+  if (!S->gs) {
+    FDE_CUDA(cudaStreamCreateWithFlags(&S->gs, cudaStreamNonBlocking));
+    FDE_CUDA(cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming));
+    FDE_CUDA(cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming));
+  }
+  cudaGraph_t g = nullptr;
+  FDE_CUDA(cudaStreamBeginCapture(S->gs, cudaStreamCaptureModeThreadLocal));
+  fde_status s = run_inner<T>(S, in, S->gs);
+  cudaError_t e = cudaStreamEndCapture(S->gs, &g);
+  if (s != FDE_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();  // a failed capture leaves nothing behind
+    if (s != FDE_OK) return s;
+    FDE_CUDA(e);
+  }
+  size_t n = 0;
+  FDE_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) FDE_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+  size_t kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    FDE_CUDA(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  in.graph_kernels = kernels;
+  e = cudaGraphInstantiate(&in.exec, g, 0);
+  cudaGraphDestroy(g);
+  FDE_CUDA(e);
+  return FDE_OK;
+}
+
+template <typename T>
+static fde_status inner_solve(sylv_s* S, Inner<T>& in, cudaStream_t st) {
+  if (!in.exec || prof_enabled()) return run_inner<T>(S, in, st);
+  FDE_CUDA(cudaEventRecord(S->ev_in, st));
+  FDE_CUDA(cudaStreamWaitEvent(S->gs, S->ev_in, 0));
+  FDE_CUDA(cudaGraphLaunch(in.exec, S->gs));
+  FDE_CUDA(cudaEventRecord(S->ev_out, S->gs));
+  FDE_CUDA(cudaStreamWaitEvent(st, S->ev_out, 0));
+  count_launches(in.graph_kernels);
   return FDE_OK;
 }
 
@@ -598,10 +906,13 @@ static fde_status sweep(sylv_s* S, Inner<T>& in, const double* C, double* X64, c
   } else {
     FDE_TRY((convert<double, float>(S->R, (float*)in.Cin, NN, st)));
   }
-  FDE_TRY(run_inner<T>(S, in, st));
+  FDE_TRY(inner_solve<T>(S, in, st));
   FDE_CUDA(cudaMemsetAsync(S->acc, 0, 3 * sizeof(double), st));
-  refine_update_kernel<T><<<grid_for(NN), 256, 0, st>>>(X64, in.X, NN, S->acc);
-  FDE_LAUNCH("refine_update_kernel");
+  {
+    ProfScope ps("refine", st, (16.0 + sizeof(T)) * NN, 0);
+    refine_update_kernel<T><<<grid_for(NN), 256, 0, st>>>(X64, in.X, NN, S->acc);
+    FDE_LAUNCH("refine_update_kernel");
+  }
   FDE_TRY(residual(S, C, X64, S->R, st));
   sumsq_kernel<<<grid_for(NN), 256, 0, st>>>(S->R, NN, S->acc + 2);
   FDE_LAUNCH("sumsq_kernel");
@@ -614,7 +925,7 @@ static fde_status sweep(sylv_s* S, Inner<T>& in, const double* C, double* X64, c
 // runs exactly that many sweeps and never synchronises with the host unless a
 // residual is requested.
 static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStream_t st, double* relres,
-                                 int* sweeps) {
+                                 int* sweeps, const double* C_prev = nullptr) {
   const size_t NN = (size_t)S->N * S->N;
   const sylv_refine_t& rf = S->refine;
   const bool fixed = rf.fixed_sweeps > 0;
@@ -633,7 +944,15 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
       return FDE_ERR_NUMERIC;
     }
   }
-  FDE_TRY(residual(S, C, X, S->R, st));
+  if (C_prev && S->R_valid) {
+    // X is the solution computed for C_prev and S->R = C_prev - A(X): the new
+    // residual follows exactly without applying the operator again.
+    shift_residual_kernel<<<grid_for(NN), 256, 0, st>>>(C, C_prev, S->R, NN);
+    FDE_LAUNCH("shift_residual_kernel");
+  } else {
+    FDE_TRY(residual(S, C, X, S->R, st));
+  }
+  S->R_valid = false;
   const int nsw = fixed ? rf.fixed_sweeps : rf.max_sweeps;
   int done = 0;
   bool converged = fixed;
@@ -664,6 +983,7 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
     set_error("sylv_step: no convergence after %d refinement sweeps", done);
     return FDE_ERR_NOCONV;
   }
+  S->R_valid = done > 0;
   return FDE_OK;
 }
 
@@ -678,6 +998,7 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
   DevPool& pool = S->pool;
   const int nl = ax->tree.nleaves();
   const size_t nleaf_el = (size_t)nl * S->lmax * S->lmax;
+  FDE_TRY(tc_prepare());
   // ---- leaf Schur forms (K8)
   FDE_TRY(pool.alloc(&S->Sx, nleaf_el));
   FDE_TRY(pool.alloc(&S->Qx, nleaf_el));
@@ -758,17 +1079,27 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
     A_[l] = al;
     B_[l] = be;
   }
-  // ---- shifted factorisations: A_x + b_j I and A_y + a_j I (b_j = -beta_j)
+  // ---- shifted factorisations: A_x + b_j I and A_y + a_j I (b_j = -beta_j).
+  // FP64 inner solver: per-step shifted HODLR solves (fewest flops, kept).
+  // FP32 inner solver: rational form (factorisations only needed at setup).
+  bool rational = (prec == FDE_FP32_REFINE);
+  if (const char* fm = getenv("FDE_FADI")) {
+    if (!strcmp(fm, "hodlr")) rational = false;
+    if (!strcmp(fm, "rational")) rational = true;
+  }
+  S->rational = rational;
+  DevPool setup_pool;
+  DevPool& fpool = rational ? setup_pool : S->pool;
   S->facts64.reserve(2 * 64 * L);
   std::vector<Fact<double>*> FA64, FB64;
   for (int l = L - 1; l >= 0; --l) {
     for (int j = 0; j < S->J[l]; ++j) {
       S->facts64.emplace_back();
-      FDE_TRY(hodlr_factorize(ax, -B_[l][j], l, &S->facts64.back(), st));
+      FDE_TRY(hodlr_factorize(ax, -B_[l][j], l, &S->facts64.back(), st, &fpool));
     }
     for (int j = 0; j < S->J[l]; ++j) {
       S->facts64.emplace_back();
-      FDE_TRY(hodlr_factorize(ay, A_[l][j], l, &S->facts64.back(), st));
+      FDE_TRY(hodlr_factorize(ay, A_[l][j], l, &S->facts64.back(), st, &fpool));
     }
   }
   {
@@ -786,24 +1117,50 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
       for (int j = 0; j < S->J[l]; ++j) in.lv[l].b[j] = -B_[l][j];
     }
   };
+  RationalSrc rs;
+  if (rational) {
+    rs.FA = FA64;
+    rs.FB = FB64;
+    rs.a.resize(L);
+    rs.b.resize(L);
+    for (int l = 0; l < L; ++l) {
+      rs.a[l] = A_[l];
+      rs.b[l].resize(S->J[l]);
+      for (int j = 0; j < S->J[l]; ++j) rs.b[l][j] = -B_[l][j];
+    }
+  }
   if (prec == FDE_FP64) {
-    FDE_TRY(build_inner<double>(S, S->in64, FA64, FB64, st));
+    if (rational)
+      FDE_TRY(build_inner<double>(S, S->in64, {}, {}, st, &rs));
+    else
+      FDE_TRY(build_inner<double>(S, S->in64, FA64, FB64, st));
     set_shifts(S->in64);
+    FDE_CUDA(cudaStreamSynchronize(st));
+    FDE_TRY(capture_inner<double>(S, S->in64));
   } else {
     FDE_TRY(hodlr_make_fp32(ax, st));
     FDE_TRY(hodlr_make_fp32(ay, st));
-    S->in32.facts.resize(FA64.size() + FB64.size());
-    std::vector<Fact<float>*> FA32, FB32;
-    for (size_t i = 0; i < FA64.size(); ++i) {
-      FDE_TRY(fact_demote(ax, *FA64[i], &S->in32.facts[i], S->pool, st));
-      FA32.push_back(&S->in32.facts[i]);
+    if (rational) {
+      FDE_TRY(build_inner<float>(S, S->in32, {}, {}, st, &rs));
+    } else {
+      S->in32.facts.resize(FA64.size() + FB64.size());
+      std::vector<Fact<float>*> FA32, FB32;
+      for (size_t i = 0; i < FA64.size(); ++i) {
+        FDE_TRY(fact_demote(ax, *FA64[i], &S->in32.facts[i], S->pool, st));
+        FA32.push_back(&S->in32.facts[i]);
+      }
+      for (size_t i = 0; i < FB64.size(); ++i) {
+        FDE_TRY(fact_demote(ay, *FB64[i], &S->in32.facts[FA64.size() + i], S->pool, st));
+        FB32.push_back(&S->in32.facts[FA64.size() + i]);
+      }
+      FDE_TRY(build_inner<float>(S, S->in32, FA32, FB32, st));
     }
-    for (size_t i = 0; i < FB64.size(); ++i) {
-      FDE_TRY(fact_demote(ay, *FB64[i], &S->in32.facts[FA64.size() + i], S->pool, st));
-      FB32.push_back(&S->in32.facts[FA64.size() + i]);
-    }
-    FDE_TRY(build_inner<float>(S, S->in32, FA32, FB32, st));
     set_shifts(S->in32);
+    FDE_CUDA(cudaStreamSynchronize(st));
+    FDE_TRY(capture_inner<float>(S, S->in32));
+  }
+  if (rational) {
+    S->facts64.clear();  // their memory lives in setup_pool, released on return
   }
   // ---- residual (FFT)
   S->logP = 1;
@@ -828,6 +1185,7 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
   FDE_CUDA(cudaFuncSetAttribute(fd_fft_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FDE_CUDA(cudaFuncSetAttribute(ghat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ghat_kernel<<<1, 1024, smem, st>>>(ax->g, N, S->tw, S->P, S->logP, S->GhX);
+  FDE_LAUNCH("ghat_kernel");
   ghat_kernel<<<1, 1024, smem, st>>>(ay->g, N, S->tw, S->P, S->logP, S->GhY);
   FDE_LAUNCH("ghat_kernel");
   const size_t NN = (size_t)N * N;
@@ -837,6 +1195,14 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
   FDE_TRY(pool.alloc(&S->Yt, NN));
   FDE_TRY(pool.alloc(&S->acc, 8));
   FDE_TRY(pool.alloc(&S->d_bad, 1));
+  // algorithmic work for the instrumentation
+  for (int p = 0; p < nl; ++p)
+    for (int q = 0; q < nl; ++q) {
+      const double n1 = ax->leaf_n[p], n2 = ay->leaf_n[q];
+      S->trsyl_flops += n1 * n2 * (n1 + n2);
+    }
+  // per residual direction: (N+1)/2 column pairs x (3 complex FFTs of 5 P log2 P + 2 pointwise products)
+  S->fft_flops = (double)((N + 1) / 2) * (3.0 * 5.0 * S->P * S->logP + 12.0 * S->P);
   S->refine.max_sweeps = 12;
   S->refine.tol_update = (prec == FDE_FP64) ? 1e-13 : 1e-11;
   S->refine.tol_relres = 1e-14;
@@ -917,11 +1283,11 @@ static fde_status inner_fn(sylv_t s, const double* C, double* X, cudaStream_t st
   const size_t NN = (size_t)s->N * s->N;
   if (s->prec == FDE_FP64) {
     FDE_CUDA(cudaMemcpyAsync(s->in64.Cin, C, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    FDE_TRY(run_inner<double>(s, s->in64, st));
+    FDE_TRY(inner_solve<double>(s, s->in64, st));
     FDE_CUDA(cudaMemcpyAsync(X, s->in64.X, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
   } else {
     FDE_TRY((convert<double, float>(C, s->in32.Cin, NN, st)));
-    FDE_TRY(run_inner<float>(s, s->in32, st));
+    FDE_TRY(inner_solve<float>(s, s->in32, st));
     FDE_TRY((convert<float, double>(s->in32.X, X, NN, st)));
   }
   return FDE_OK;
@@ -946,8 +1312,9 @@ extern "C" void sylv_free(sylv_t s) { delete s; }
 
 // Exposed for the time loop (fde_run.cu)
 namespace fde {
-fde_status sylv_step_internal(sylv_s* s, const double* C, double* X, cudaStream_t st, double* relres, int* sweeps) {
-  return sylv_step_impl(s, C, X, st, relres, sweeps);
+fde_status sylv_step_internal(sylv_s* s, const double* C, double* X, cudaStream_t st, double* relres, int* sweeps,
+                              const double* C_prev) {
+  return sylv_step_impl(s, C, X, st, relres, sweeps, C_prev);
 }
 int sylv_N(sylv_s* s) { return s->N; }
 }  // namespace fde

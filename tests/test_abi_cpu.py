@@ -20,7 +20,7 @@ def _declared():
         if f.endswith(".h"):
             src = open(os.path.join(ROOT, "include", f)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"^\s*(?:fde_status|void|const char\*)\s+(\w+)\s*\(", src, flags=re.M)
+            names += re.findall(r"^\s*(?:fde_status|void|const char\*|unsigned long long)\s+(\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 

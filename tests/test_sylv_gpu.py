@@ -130,3 +130,26 @@ def test_fde_run_1d_workload(lib):
     uref = O.fde1d_run(w)
     assert np.linalg.norm(u - uref) / np.linalg.norm(uref) <= 1e-10
     assert st.sweeps_max <= 4
+
+
+@pytest.mark.parametrize("prec,mode", [(B.FDE_FP32_REFINE, "hodlr"), (B.FDE_FP64, "rational")])
+def test_sylv_step_both_fadi_forms(lib, monkeypatch, prec, mode):
+    """The fADI corrections in per-step HODLR-solve form and in precomputed
+    rational form give the same refined solution."""
+    monkeypatch.setenv("FDE_FADI", mode)
+    N = 128
+    w = I.fd2d(N=N, alpha=(1.4, 1.6), steps=40, leaf=32)
+    P = Pair(lib, w, prec)
+    try:
+        C = O.fde2d_rhs(w, w.u0, 0) + I.random_matrix_fast(N, N, seed=7)
+        Xo = O.sylvester_bartels_stewart(O.fd_operator(w.ops[0]), O.fd_operator(w.ops[1]), C)
+        Cd = _dev(C)
+        Xd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+        lib.sylv_inner_solve(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+        torch.cuda.synchronize()
+        assert _relerr(_host(Xd, N, N), Xo) < (1e-4 if prec == B.FDE_FP32_REFINE else 1e-6)
+        Xd.zero_()
+        relres, sweeps = lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+        assert _relerr(_host(Xd, N, N), Xo) <= (1e-8 if prec == B.FDE_FP32_REFINE else 1e-10)
+    finally:
+        P.close()
