@@ -112,6 +112,23 @@ fde_status hodlr_solve(hodlr_t h, const double* d_b, double* d_x, int nrhs, int 
 /* y = A x (HODLR matvec, FP64, device pointers), for checks. */
 fde_status hodlr_matvec(hodlr_t h, const double* d_x, double* d_y, int nrhs, int ldx, void* stream);
 
+/* y = A x like hodlr_matvec, without allocating device memory.  The paper has
+ * no counterpart: this entry point is for callers that must not allocate on
+ * the call path (a loop with a fixed memory budget, or a process whose device
+ * memory another allocator already owns), since hodlr_matvec allocates its
+ * coupling products and descriptor arrays per call and synchronises `stream`
+ * to free them.  This call only enqueues kernels on `stream` and returns.
+ *
+ * x, y: device pointers, column-major N x nrhs, leading dimension ldx >= N,
+ * x != y; the caller owns both.  Scratch is one static device array of
+ * 2^19 doubles (4 MiB) per device; a call needs max_l 2^(l+1) K_l nrhs doubles
+ * (K_l the padded level rank, hodlr_get_info) and larger requests return
+ * FDE_ERR_ARG before anything is launched.  Nothing has to be zeroed first.
+ * The first call on a device looks up the array's address; make that first
+ * call before any stream capture.  Calls that overlap in time on one device
+ * (two streams, two host threads) race on the shared scratch: order them. */
+fde_status hodlr_matvec_noalloc(hodlr_t h, const double* d_x, double* d_y, int nrhs, int ldx, void* stream);
+
 fde_status hodlr_get_info(hodlr_t h, hodlr_info_t* info);
 
 /* Writes the dense N x N matrix represented by the HODLR (column-major,

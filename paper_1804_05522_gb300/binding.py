@@ -55,6 +55,7 @@ _SIGS = {
     "hodlr_factor": ([_P, _P], C.c_int),
     "hodlr_solve": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "hodlr_matvec": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
+    "hodlr_matvec_noalloc": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "hodlr_get_info": ([_P, C.POINTER(HodlrInfo)], C.c_int),
     "hodlr_to_dense": ([_P, _P, C.c_int, _P], C.c_int),
     "hodlr_get_weights": ([_P, _P], C.c_int),
@@ -145,6 +146,9 @@ class Lib:
 
     def hodlr_matvec(self, h: int, x: int, y: int, nrhs: int, ldx: int, stream: int = 0):
         self.check(self.dll.hodlr_matvec(h, x, y, nrhs, ldx, stream))
+
+    def hodlr_matvec_noalloc(self, h: int, x: int, y: int, nrhs: int, ldx: int, stream: int = 0):
+        self.check(self.dll.hodlr_matvec_noalloc(h, x, y, nrhs, ldx, stream))
 
     def hodlr_get_info(self, h: int) -> HodlrInfo:
         info = HodlrInfo()
