@@ -18,8 +18,10 @@
  *                  compressed once by ACA and restricted to every level
  *                  (§3.4.2), D_± scaling applied to the factors, per-block
  *                  QR+SVD recompression at ε||A||_2 (§3.4.1).
- *   hodlr_factor : HODLR factorisation (leaf LU + one small capacitance
- *                  system per node), solves in O(k N log N) (§3.5).
+ *   hodlr_factor : HODLR factorisation (§3.5) in telescoping form: explicit
+ *                  leaf inverses and one small capacitance inverse per
+ *                  internal node, so that solves are batched GEMMs,
+ *                  O(k N log N) per right-hand side.
  *   sylv_step    : divide and conquer over the HODLR tree (Conclusions,
  *                  D&C for HODLR right-hand sides) with leaf Bartels–Stewart
  *                  and low-rank corrections solved by factored ADI, wrapped in
@@ -100,9 +102,12 @@ typedef struct {
  * FDE_ERR_NUMERIC (non-finite d_±), FDE_ERR_NOCONV (ACA hit its rank cap). */
 fde_status hodlr_build(const fde_op_params* p, void* stream, hodlr_t* out);
 
-/* Factorise A + sigma*I for sigma = 0 (§3.5): leaf LU without pivoting
- * (A is strictly diagonally dominant, §2.2.1) and one pivoted LU of the
- * small capacitance matrix of every internal node.  Idempotent. */
+/* Factorise A (§3.5), level by level from the leaves up: A_l = A_{l+1} +
+ * [U12 V21ᵀ; U21 V12ᵀ] (the level-l couplings) is inverted by the
+ * Sherman–Morrison–Woodbury identity, which needs A_{l+1}^{-1} U (computed
+ * with the levels below) and the inverse of a 2k x 2k capacitance matrix per
+ * node; leaves are inverted explicitly.  All inverses by Gauss–Jordan with
+ * partial pivoting.  Idempotent. */
 fde_status hodlr_factor(hodlr_t h, void* stream);
 
 /* x = A^{-1} b for nrhs right-hand sides (device pointers, leading dim ldb >= N;
@@ -232,11 +237,26 @@ fde_status fde_runner_state(fde_runner_t r, double* U_out, void* stream);
 fde_status fde_runner_stats(fde_runner_t r, fde_run_stats* stats);
 void fde_runner_free(fde_runner_t r);
 
+/* Batched FP32 GEMM of the FP32 inner solver (the dense products of the
+ * Sylvester divide-and-conquer, §3.3-§3.4), exposed for checks:
+ *   C_i = alpha op(A_i) op(B_i) + beta C_i,  i < batch,
+ * column-major device matrices, X_i = X + i * strideX.  op(A) is m x k,
+ * op(B) k x n.  kblk > 0 selects two-level addressing along k for a
+ * non-transposed A and a transposed B: column k sits at
+ * (k / kblk) * kstr + (k % kblk) * ld.  mode: 0 SIMT FP32 FMA, 1 tcgen05 TF32,
+ * 3 tcgen05 3xTF32 (hi/lo split, FP32-level accuracy), -1 the library's
+ * current setting; batches too small for the tensor cores (m < 64, n < 32 or
+ * k < 32) always take the SIMT kernel.  Allocates the descriptor array and
+ * synchronises `stream`.  FDE_ERR_CUDA if a tensor-core wait expired. */
+fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const float* A, int lda,
+                        long long strideA, const float* B, int ldb, long long strideB, float beta, float* C,
+                        int ldc, long long strideC, int batch, int kblk, long long kstr, int mode, void* stream);
+
 /* Instrumentation.  fde_launch_count: kernels launched by this library in
  * this process so far.  fde_prof_enable(1) makes the library bracket the
  * launches of its main kernel families with CUDA events on their stream;
  * fde_prof_query returns the summed device time (ms) and launch count of a
- * family ("gemm32", "gemm64", "trsyl32", "trsyl64", "fft_apply", "schur",
+ * family ("gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply", "schur",
  * "recompress", "fadi_axpy", "transpose", "refine"), synchronising the events
  * it reads;
  * fde_prof_reset clears the records. */

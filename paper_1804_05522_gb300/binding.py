@@ -56,6 +56,9 @@ _SIGS = {
     "hodlr_solve": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "hodlr_matvec": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "hodlr_matvec_noalloc": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
+    "fde_gemm_f32": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, _P, C.c_int, C.c_longlong, _P, C.c_int,
+                      C.c_longlong, C.c_float, _P, C.c_int, C.c_longlong, C.c_int, C.c_int, C.c_longlong, C.c_int, _P],
+                     C.c_int),
     "hodlr_get_info": ([_P, C.POINTER(HodlrInfo)], C.c_int),
     "hodlr_to_dense": ([_P, _P, C.c_int, _P], C.c_int),
     "hodlr_get_weights": ([_P, _P], C.c_int),
@@ -146,6 +149,11 @@ class Lib:
 
     def hodlr_matvec(self, h: int, x: int, y: int, nrhs: int, ldx: int, stream: int = 0):
         self.check(self.dll.hodlr_matvec(h, x, y, nrhs, ldx, stream))
+
+    def gemm_f32(self, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, Cm, ldc, sC, batch=1, kblk=0, kstr=0,
+                 mode=-1, stream: int = 0):
+        self.check(self.dll.fde_gemm_f32(int(ta), int(tb), m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, Cm, ldc, sC,
+                                         batch, kblk, kstr, mode, stream))
 
     def hodlr_matvec_noalloc(self, h: int, x: int, y: int, nrhs: int, ldx: int, stream: int = 0):
         self.check(self.dll.hodlr_matvec_noalloc(h, x, y, nrhs, ldx, stream))

@@ -1,5 +1,7 @@
 // Batched dense kernels: SIMT GEMM with per-batch descriptors, batched
 // Gauss–Jordan inversion, conversions.
+#include <cstdint>
+
 #include "dense.cuh"
 
 namespace fde {
@@ -110,7 +112,13 @@ fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, b
   b.alpha = alpha;
   b.beta = beta;
   b.batch = (int)h.size();
+  auto vec_ok = [](const T* p, int ld, int kblk, long long kstr) {
+    return ((uintptr_t)p % 16) == 0 && ld % 4 == 0 && (kblk == 0 || kstr % 4 == 0);
+  };
+  b.vec_a = b.vec_b = b.batch > 0;
   for (const auto& d : h) {
+    b.vec_a = b.vec_a && vec_ok(d.A, d.lda, ta ? 0 : d.kblk, d.kstr);
+    b.vec_b = b.vec_b && vec_ok(d.B, d.ldb, tb ? d.kblk : 0, d.kstr);
     b.max_m = d.m > b.max_m ? d.m : b.max_m;
     b.max_n = d.n > b.max_n ? d.n : b.max_n;
     b.max_k = d.k > b.max_k ? d.k : b.max_k;

@@ -26,6 +26,9 @@ struct GemmBatch {
   int batch = 0, max_m = 0, max_n = 0, max_k = 0;
   double flops = 0.0;  // Σ 2 m n k over the batch
   bool ta = false, tb = false;
+  // every descriptor's A (resp. B) base is 16-byte aligned and its ld (and
+  // kstr) a multiple of 4 elements: 4-wide vector loads are allowed
+  bool vec_a = false, vec_b = false;
   T alpha = T(1), beta = T(0);
 };
 

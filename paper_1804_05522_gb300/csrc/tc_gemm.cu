@@ -2,13 +2,13 @@
 //
 //   C = alpha op(A) op(B) + beta C      (column-major, per-batch descriptors)
 //
-// Tile 128 x 128 x 32.  Operand tiles are staged in shared memory in the
-// canonical K-major layout with 128-byte swizzle (8-row x 128-byte atoms,
-// 1024 bytes apart), double buffered; one elected thread issues
-// tcgen05.mma.kind::tf32 (M=128, N=128, K=8 per instruction) accumulating in
-// tensor memory; completion of each stage is signalled by tcgen05.commit on an
-// mbarrier.  The epilogue reads the accumulator with tcgen05.ld (one warp per
-// 32-lane quarter) and writes C with coalesced stores.
+// Tile 128 x BN x 32 (BN = 64 or 128).  Operand tiles are staged in shared
+// memory in the canonical K-major layout with 128-byte swizzle (8-row x
+// 128-byte atoms, 1024 bytes apart) in a ring of slots filled by eight loader
+// warps; one elected thread issues tcgen05.mma.kind::tf32 (M = 128, N = BN,
+// K = 8 per instruction) accumulating in tensor memory, and tcgen05.commit on
+// per-slot mbarriers hands each slot back to the loaders.  The epilogue reads
+// the accumulator with tcgen05.ld and writes C with coalesced stores.
 // Precision: mode 1 = TF32 inputs (inputs rounded to TF32), mode 3 = 3xTF32
 // split (a = a_hi + a_lo, products hi*hi + hi*lo + lo*hi) which keeps FP32-level
 // accuracy.  Accumulation is FP32.
@@ -23,8 +23,7 @@ namespace tc {
 // Raised by a kernel whose bounded mbarrier wait ran out (read by the host).
 __device__ int g_wait_timeout;
 
-constexpr int BM = 128, BN = 128, BK = 32;
-constexpr int TILE_BYTES = BM * BK * 4;  // 16 KB (A or B tile, TF32)
+constexpr int BM = 128, BK = 32;
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -99,11 +98,6 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2u << 61;             // SWIZZLE_128B
   return d;
 }
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 128.
-__host__ __device__ constexpr uint32_t idesc_tf32() {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
 // round to TF32 (nearest, ties away) and the remainder
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
@@ -111,77 +105,174 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// Byte offset of element (row r, k c) inside a 128 x 32 K-major SW128 tile.
+// Byte offset of element (row r, k c) inside a K-major SW128 tile (rows in
+// 8-row groups of 1024 bytes, 32 FP32 k per 128-byte row, 16-byte chunks
+// XOR-swizzled by the row within the group).
 __device__ __forceinline__ uint32_t sw_off(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((c >> 2) ^ (r & 7)) & 7) << 4) + ((c & 3) << 2));
 }
 
-// Load a 128 (rows) x 32 (k) tile of op(X) into hi (and lo) tiles.
-// kcontig: element (row, k) sits at X[k_off(k) + row*ld] (k contiguous);
-// else at X[row + k_off(k)] with k_off(k) = column address of k (two-level).
-template <bool KCONTIG>
-__device__ __forceinline__ void load_tile(const float* __restrict__ X, int ld, int kblk, long long kstr, int row0,
-                                          int nrows, int k0, int K, uint8_t* hi, uint8_t* lo, bool split) {
-  const int tid = threadIdx.x;  // 128 threads: one row each
-  const int r = tid;
-  const int grow = row0 + r;
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+constexpr int kLoaders = 256;              // 8 warps: global -> shared, then the epilogue
+constexpr int kThreads = kLoaders + 32;    // + 1 warp that issues the MMAs
+constexpr int kMaxStages = 8;
+
+// One loader thread's share of an R x 32 operand tile: 4 rows x 4 k blocks
+// (R / 128 of them; R = 64 leaves the upper half of the threads idle).
+// Block b of thread t: kq = (t + 256 b) & 7, row group (t + 256 b) >> 3, so a
+// quarter warp covers one 4-row group across all eight 16-byte chunks (no
+// bank conflicts on the swizzled stores) and reads either 128 contiguous
+// bytes of a k-contiguous row or 64 contiguous bytes of a row-contiguous column.
+template <int R>
+struct OpRegs {
+  static constexpr int NB = R >= 128 ? R / 128 : 1;
+  float v[NB][16];  // v[b][r * 4 + c]: row 4 rg + r, k 4 kq + c
+};
+
+// element (row, k) of the operand tile: KCONTIG -> X[k + row * ld];
+// otherwise X[row + col(k)], col(k) = k * ld or the two-level panel address.
+template <int R, bool KCONTIG>
+__device__ __forceinline__ void tile_load(OpRegs<R>& o, const float* __restrict__ X, int ld, int kblk,
+                                          long long kstr, int row0, int nrows, int k0, int K, bool vec) {
+  const int t = threadIdx.x;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    float v[4];
+  for (int b = 0; b < OpRegs<R>::NB; ++b) {
+    const int blk = t + kLoaders * b;
+    float* v = o.v[b];
+    if (blk >= 2 * R) break;
+    const int kq = blk & 7, rg = blk >> 3;
+    const int row = row0 + 4 * rg, k = k0 + 4 * kq;
+    if (KCONTIG) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = k0 + 4 * j + q;
-      float x = 0.f;
-      if (grow < nrows && k < K) {
-        if (KCONTIG) {
-          x = X[(size_t)k + (size_t)grow * ld];
+      for (int r = 0; r < 4; ++r) {
+        const float* p = X + (size_t)(row + r) * ld + k;
+        if (row + r < nrows) {
+          if (vec && k + 3 < K) {
+            const float4 q = ldg4(p);
+            v[r * 4 + 0] = q.x;
+            v[r * 4 + 1] = q.y;
+            v[r * 4 + 2] = q.z;
+            v[r * 4 + 3] = q.w;
+          } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[r * 4 + c] = (k + c < K) ? __ldg(p + c) : 0.f;
+          }
         } else {
-          const long long col = kblk ? (long long)(k / kblk) * kstr + (long long)(k % kblk) * ld : (long long)k * ld;
-          x = X[(long long)grow + col];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) v[r * 4 + c] = 0.f;
         }
       }
-      v[q] = x;
-    }
-    float4 h, l;
-    h.x = to_tf32(v[0]);
-    h.y = to_tf32(v[1]);
-    h.z = to_tf32(v[2]);
-    h.w = to_tf32(v[3]);
-    const uint32_t off = sw_off(r, 4 * j);
-    *reinterpret_cast<float4*>(hi + off) = h;
-    if (split) {
-      l.x = to_tf32(v[0] - h.x);
-      l.y = to_tf32(v[1] - h.y);
-      l.z = to_tf32(v[2] - h.z);
-      l.w = to_tf32(v[3] - h.w);
-      *reinterpret_cast<float4*>(lo + off) = l;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int kk = k + c;
+        if (kk < K) {
+          const long long col = kblk ? (long long)(kk / kblk) * kstr + (long long)(kk % kblk) * ld : (long long)kk * ld;
+          const float* p = X + col + row;
+          if (vec && row + 3 < nrows) {
+            const float4 q = ldg4(p);
+            v[0 * 4 + c] = q.x;
+            v[1 * 4 + c] = q.y;
+            v[2 * 4 + c] = q.z;
+            v[3 * 4 + c] = q.w;
+          } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) v[r * 4 + c] = (row + r < nrows) ? __ldg(p + r) : 0.f;
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) v[r * 4 + c] = 0.f;
+        }
+      }
     }
   }
 }
 
-// 128 threads per CTA; grid (ceil(m/128), ceil(n/128), batch).
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc<float>* __restrict__ descs, float alpha, float beta,
-                                                      int split) {
+// Round to TF32 and store (hi, and the TF32-rounded remainder lo in split mode).
+template <int R>
+__device__ __forceinline__ void tile_store(const OpRegs<R>& o, uint8_t* hi, uint8_t* lo, bool split) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int b = 0; b < OpRegs<R>::NB; ++b) {
+    const int blk = t + kLoaders * b;
+    if (blk >= 2 * R) break;
+    const int kq = blk & 7, rg = blk >> 3;
+    const float* v = o.v[b];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t off = sw_off(4 * rg + r, 4 * kq);
+      float4 h;
+      h.x = to_tf32(v[r * 4 + 0]);
+      h.y = to_tf32(v[r * 4 + 1]);
+      h.z = to_tf32(v[r * 4 + 2]);
+      h.w = to_tf32(v[r * 4 + 3]);
+      *reinterpret_cast<float4*>(hi + off) = h;
+      if (split) {
+        float4 l;
+        l.x = to_tf32(v[r * 4 + 0] - h.x);
+        l.y = to_tf32(v[r * 4 + 1] - h.y);
+        l.z = to_tf32(v[r * 4 + 2] - h.z);
+        l.w = to_tf32(v[r * 4 + 3] - h.w);
+        *reinterpret_cast<float4*>(lo + off) = l;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = BN.
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc_tf32_n() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+// Warp-specialised batched GEMM.  Warps 0-7 load op(A) (128 x 32) and op(B)
+// (BN x 32) tiles with coalesced vector loads, two tiles in flight per thread,
+// round them to TF32 (hi / lo) into a ring of `stages` shared-memory slots and
+// arrive on that slot's `full` barrier; warp 8 waits on `full`, issues the
+// tcgen05 MMAs of the slot and commits them to the slot's `empty` barrier,
+// which the loaders wait on before refilling it.  The accumulator lives in
+// TMEM (BN columns); warps 0-7 read it back (lane quarter = warp % 4, column
+// half = warp / 4) and write C.  Every wait is bounded: on expiry the kernel
+// raises g_wait_timeout, skips the epilogue and still frees its TMEM.
+// grid (ceil(m / 128), ceil(n / BN), batch), kThreads threads.
+template <int BN, bool TA, bool TB>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const GemmDesc<float>* __restrict__ descs, float alpha, float beta, int split, int stages,
+                   int vec_a, int vec_b) {
   const GemmDesc<float> d = descs[blockIdx.z];
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   if (m0 >= d.m || n0 >= d.n) return;
+  constexpr int A_BYTES = BM * BK * 4, B_BYTES = BN * BK * 4;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base_u32 = smem_u32(smem_raw);
   const uint32_t pad = ((base_u32 + 1023u) & ~1023u) - base_u32;
   uint8_t* sm = smem_raw + pad;  // 1024-byte aligned
-  const int ntile = split ? 4 : 2;  // A_hi, B_hi (, A_lo, B_lo) per stage
-  uint8_t* stage[2] = {sm, sm + ntile * TILE_BYTES};
-  __shared__ __align__(8) uint64_t bars[2];
+  // slot layout: A_hi | B_hi | A_lo | B_lo (lo only in split mode)
+  const int slot_bytes = (A_BYTES + B_BYTES) * (split ? 2 : 1);
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
   __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(smem_u32(&bars[0]), 1);
-    mbar_init(smem_u32(&bars[1]), 1);
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), kLoaders);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    s_fail = 0;
     fence_barrier_init();
   }
-  if (warp == 0) {
-    tmem_alloc(smem_u32(&tmem_base), BN);
+  // split mode keeps the hi*lo + lo*hi corrections in a second accumulator
+  // (columns BN..2BN-1): summed into the hi*hi one they would lose their low
+  // bits to its alignment
+  const uint32_t tcols = split ? 2 * BN : BN;
+  if (warp == kLoaders / 32) {
+    tmem_alloc(smem_u32(&tmem_base), tcols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -189,45 +280,94 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc<float>* __r
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   const int nk = (d.k + BK - 1) / BK;
-  bool ok = true;
-  for (int kt = 0; kt < nk; ++kt) {
-    const int b = kt & 1;
-    if (kt >= 2) ok = ok && mbar_wait(smem_u32(&bars[b]), (uint32_t)(((kt - 2) >> 1) & 1));
-    uint8_t* st = stage[b];
-    const int k0 = kt * BK;
-    // A: rows = m (op(A) is m x k); B: rows = n (op(B)ᵀ is n x k)
-    load_tile<TA>(d.A, d.lda, TA ? 0 : d.kblk, d.kstr, m0, d.m, k0, d.k, st, st + 2 * TILE_BYTES, split);
-    load_tile<!TB>(d.B, d.ldb, TB ? d.kblk : 0, d.kstr, n0, d.n, k0, d.k, st + TILE_BYTES, st + 3 * TILE_BYTES, split);
-    fence_proxy_async();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+
+  if (warp < kLoaders / 32) {
+    // ---------------- loaders
+    OpRegs<BM> ra[2];
+    OpRegs<BN> rb[2];
+    const int a_kblk = TA ? 0 : d.kblk, b_kblk = TB ? d.kblk : 0;
+    auto load = [&](int kt, int i) {
+      tile_load<BM, TA>(ra[i], d.A, d.lda, a_kblk, d.kstr, m0, d.m, kt * BK, d.k, vec_a != 0);
+      tile_load<BN, !TB>(rb[i], d.B, d.ldb, b_kblk, d.kstr, n0, d.n, kt * BK, d.k, vec_b != 0);
+    };
+    auto put = [&](int kt, int i) -> bool {
+      const int s = kt % stages;
+      if (kt >= stages && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)((kt / stages - 1) & 1))) return false;
+      uint8_t* slot = sm + (size_t)s * slot_bytes;
+      tile_store<BM>(ra[i], slot, slot + A_BYTES + B_BYTES, split != 0);
+      tile_store<BN>(rb[i], slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
+      fence_proxy_async();
+      mbar_arrive(smem_u32(&full_bar[s]));
+      return true;
+    };
+    bool ok = true;
+    if (nk > 0) load(0, 0);
+    if (nk > 1) load(1, 1);
+    for (int kt = 0; kt < nk && ok; kt += 2) {
+      ok = put(kt, 0);
+      if (ok && kt + 2 < nk) load(kt + 2, 0);
+      if (ok && kt + 1 < nk) {
+        ok = put(kt + 1, 1);
+        if (ok && kt + 3 < nk) load(kt + 3, 1);
+      }
+    }
+    if (!ok) s_fail = 1;
+  } else if (lane == 0) {
+    // ---------------- MMA issuer
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % stages;
+      if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((kt / stages) & 1))) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
-      const uint32_t a_hi = smem_u32(st), b_hi = smem_u32(st + TILE_BYTES);
-      const uint32_t a_lo = smem_u32(st + 2 * TILE_BYTES), b_lo = smem_u32(st + 3 * TILE_BYTES);
+      uint8_t* slot = sm + (size_t)s * slot_bytes;
+      const uint32_t a_hi = smem_u32(slot), b_hi = smem_u32(slot + A_BYTES);
+      const uint32_t a_lo = smem_u32(slot + A_BYTES + B_BYTES), b_lo = smem_u32(slot + 2 * A_BYTES + B_BYTES);
 #pragma unroll
       for (int kk = 0; kk < BK / 8; ++kk) {
         const uint32_t off = kk * 32;  // 8 TF32 = 32 bytes along k inside the swizzle atom
         const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
-        mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_tf32(), acc0);
+        mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_tf32_n<BN>(), acc0);
         if (split) {
-          mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc_tf32(), 1u);
-          mma_tf32(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc_tf32(), 1u);
+          mma_tf32(tmem + BN, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc_tf32_n<BN>(), acc0);
+          mma_tf32(tmem + BN, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc_tf32_n<BN>(), 1u);
         }
       }
-      mma_commit(smem_u32(&bars[b]));
+      mma_commit(smem_u32(&empty_bar[s]));
     }
+    if (!ok) s_fail = 1;
+    // completes once every MMA issued above has finished
+    mma_commit(smem_u32(&done_bar));
   }
-  // wait for the last stage (its commit covers all earlier MMAs)
-  if (nk > 0) ok = ok && mbar_wait(smem_u32(&bars[(nk - 1) & 1]), (uint32_t)(((nk - 1) >> 1) & 1));
-  tc_fence_after();
-  const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
-  if (all_ok && nk > 0) {
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+  // epilogue (the MMA warp only waits at the final barrier)
+  bool ok = true;
+  if (warp < kLoaders / 32) {
+    ok = mbar_wait(smem_u32(&done_bar), 0u);
+    tc_fence_after();
+  }
+  const bool all_ok = __syncthreads_and(ok && s_fail == 0 ? 1 : 0) != 0;
+  if (all_ok && warp < kLoaders / 32) {
+    __syncwarp();
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = m0 + quarter * 32 + lane;
+    const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
       float v[32];
-      tmem_ld32(tw + c0, v);
+      if (nk > 0) {
+        tmem_ld32(tw + c0, v);
+        if (split) {
+          float w[32];
+          tmem_ld32(tw + BN + c0, w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+      }
       if (row < d.m) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -242,7 +382,24 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc<float>* __r
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, BN);
+  if (warp == kLoaders / 32) {
+    __syncwarp();
+    tmem_dealloc(tmem, tcols);
+  }
+}
+
+template <int BN>
+constexpr size_t slot_bytes(int split) {
+  return (size_t)(BM * BK * 4 + BN * BK * 4) * (split ? 2 : 1);
+}
+// dynamic bytes after the 1 KB alignment pad; 1 KB more stays free for the
+// kernel's static shared memory (227 KB per block in all)
+constexpr size_t kSmemBudget = 227 * 1024 - 2048;
+
+template <int BN>
+int stages_for(int split) {
+  int s = (int)(kSmemBudget / slot_bytes<BN>(split));
+  return s > kMaxStages ? kMaxStages : s;
 }
 
 }  // namespace tc
@@ -265,16 +422,46 @@ fde_status tc_error_flag(int* out) {
   return FDE_OK;
 }
 
+template <int BN, bool TA, bool TB>
+static fde_status set_attr() {
+  FDE_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<BN, TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(1024 + tc::kSmemBudget)));
+  return FDE_OK;
+}
+
 // Kernel attributes are set once, before any stream capture.
 fde_status tc_prepare() {
   static bool done = false;
   if (done) return FDE_OK;
-  const int smax = 1024 + 8 * tc::TILE_BYTES;
-  FDE_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-  FDE_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-  FDE_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-  FDE_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+  FDE_TRY((set_attr<64, false, false>()));
+  FDE_TRY((set_attr<64, false, true>()));
+  FDE_TRY((set_attr<64, true, false>()));
+  FDE_TRY((set_attr<64, true, true>()));
+  FDE_TRY((set_attr<128, false, false>()));
+  FDE_TRY((set_attr<128, false, true>()));
+  FDE_TRY((set_attr<128, true, false>()));
+  FDE_TRY((set_attr<128, true, true>()));
   done = true;
+  return FDE_OK;
+}
+
+template <int BN>
+static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t st) {
+  const int stages = tc::stages_for<BN>(split);
+  const size_t smem = 1024 + (size_t)stages * tc::slot_bytes<BN>(split);
+  const int which = (b.ta ? 2 : 0) + (b.tb ? 1 : 0);
+  auto kern = (which == 0) ? tc::tc_gemm_kernel<BN, false, false>
+              : (which == 1) ? tc::tc_gemm_kernel<BN, false, true>
+              : (which == 2) ? tc::tc_gemm_kernel<BN, true, false>
+                             : tc::tc_gemm_kernel<BN, true, true>;
+  for (int z0 = 0; z0 < b.batch; z0 += 65535) {
+    const int nz = b.batch - z0 < 65535 ? b.batch - z0 : 65535;
+    dim3 grid(ceil_div(b.max_m, tc::BM), ceil_div(b.max_n, BN), nz);
+    ProfScope ps("gemm32tc", st, z0 == 0 ? b.flops : 0.0, 1);
+    kern<<<grid, tc::kThreads, smem, st>>>(b.d_desc + z0, b.alpha, b.beta, split, stages, b.vec_a ? 1 : 0,
+                                           b.vec_b ? 1 : 0);
+    FDE_LAUNCH("tc_gemm_kernel");
+  }
   return FDE_OK;
 }
 
@@ -286,21 +473,51 @@ fde_status tc_gemm_run(const GemmBatch<float>& b, cudaStream_t st, bool* used) {
   if (mode == 0 || b.max_m < 64 || b.max_n < 32 || b.max_k < 32) return FDE_OK;
   FDE_TRY(tc_prepare());
   const int split = (mode == 3) ? 1 : 0;
-  const size_t smem = 1024 + 2 * (size_t)(split ? 4 : 2) * tc::TILE_BYTES;
-  const int which = (b.ta ? 2 : 0) + (b.tb ? 1 : 0);
-  auto kern = (which == 0) ? tc::tc_gemm_kernel<false, false>
-              : (which == 1) ? tc::tc_gemm_kernel<false, true>
-              : (which == 2) ? tc::tc_gemm_kernel<true, false>
-                             : tc::tc_gemm_kernel<true, true>;
-  for (int z0 = 0; z0 < b.batch; z0 += 65535) {
-    const int nz = b.batch - z0 < 65535 ? b.batch - z0 : 65535;
-    dim3 grid(ceil_div(b.max_m, tc::BM), ceil_div(b.max_n, tc::BN), nz);
-    ProfScope ps("gemm32tc", st, z0 == 0 ? b.flops : 0.0, 1);
-    kern<<<grid, 128, smem, st>>>(b.d_desc + z0, b.alpha, b.beta, split);
-    FDE_LAUNCH("tc_gemm_kernel");
-  }
+  if (b.max_n <= 64)
+    FDE_TRY(launch_bn<64>(b, split, st));
+  else
+    FDE_TRY(launch_bn<128>(b, split, st));
   *used = true;
   return FDE_OK;
 }
 
 }  // namespace fde
+
+extern "C" fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const float* A, int lda,
+                                   long long strideA, const float* B, int ldb, long long strideB, float beta,
+                                   float* C, int ldc, long long strideC, int batch, int kblk, long long kstr,
+                                   int mode, void* stream) {
+  using namespace fde;
+  FDE_ARG(m >= 0 && n >= 0 && k >= 0 && batch >= 0, "negative size");
+  FDE_ARG(A != nullptr && B != nullptr && C != nullptr, "NULL matrix");
+  FDE_ARG(mode == -1 || mode == 0 || mode == 1 || mode == 3, "mode must be -1, 0, 1 or 3");
+  FDE_ARG(kblk >= 0 && (kblk == 0 || kstr >= 0), "bad kblk / kstr");
+  FDE_ARG(ldc >= (m > 1 ? m : 1), "ldc < m");
+  FDE_ARG(lda >= 1 && ldb >= 1, "bad lda / ldb");
+  if (batch == 0 || m == 0 || n == 0) return FDE_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<GemmDesc<float>> h;
+  for (int i = 0; i < batch; ++i) {
+    GemmDesc<float> d{A + (size_t)i * strideA, B + (size_t)i * strideB, C + (size_t)i * strideC, m, n, k, lda, ldb,
+                      ldc};
+    d.kblk = kblk;
+    d.kstr = kstr;
+    h.push_back(d);
+  }
+  DevPool scratch;
+  GemmBatch<float> gb;
+  FDE_TRY(gemm_batch_upload(scratch, h, ta != 0, tb != 0, alpha, beta, &gb, st));
+  const int saved = tc_mode();
+  if (mode >= 0) set_tc_mode(mode);
+  const fde_status s = gemm_batch_run(gb, st);
+  set_tc_mode(saved);
+  FDE_TRY(s);
+  FDE_CUDA(cudaStreamSynchronize(st));
+  int flag = 0;
+  FDE_TRY(tc_error_flag(&flag));
+  if (flag) {
+    set_error("tensor-core GEMM: a bounded wait expired");
+    return FDE_ERR_CUDA;
+  }
+  return FDE_OK;
+}

@@ -1,0 +1,133 @@
+"""The batched FP32 GEMM of the FP32 inner solver (SIMT, tcgen05 TF32 and
+3xTF32) against an FP64 matrix product of the same FP32 inputs, through the C
+ABI.  Shapes span several 128-row tiles with ragged edges, both tile widths
+(BN = 64 / 128), all transpose combinations, unaligned leading dimensions
+(scalar load path) and two-level k addressing."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# elementwise error bounds relative to (|A| |B|)_ij:
+#  SIMT / 3xTF32: FP32 accumulation over k terms plus the 2^-21 split residue
+#  TF32: operands rounded to 11 significant bits (2 * 2^-11) plus accumulation
+def _bound(mode, k):
+    u = 2.0 ** -24
+    if mode == 1:
+        return 2 * 2.0 ** -11 + 2 * k * u
+    return 2.0 ** -20 + 2 * k * u
+
+
+def _opnd(rng, rows, cols, ld, batch):
+    """batch column-major rows x cols FP32 matrices (leading dim ld), packed."""
+    buf = np.zeros((batch, cols, ld), dtype=np.float32)
+    buf[:, :, :rows] = rng.standard_normal((batch, cols, rows)).astype(np.float32)
+    return buf
+
+
+def _mat(buf, i, rows, cols):
+    return buf[i, :, :rows].T.astype(np.float64)  # rows x cols
+
+
+SHAPES = [
+    # m, n, k, pad (ld = rows + pad), batch
+    (300, 200, 150, 0, 2),
+    (256, 40, 96, 4, 3),      # BN = 64, aligned ld
+    (130, 130, 33, 1, 1),     # odd ld: scalar loads; k tail
+    (512, 384, 320, 0, 1),
+]
+
+
+@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_gemm_f32(lib, mode, ta, tb, shape):
+    m, n, k, pad, batch = shape
+    rng = np.random.default_rng(m * 7 + n * 3 + k + 100 * ta + 10 * tb + mode)
+    ar, ac = (k, m) if ta else (m, k)
+    br, bc = (n, k) if tb else (k, n)
+    lda, ldb, ldc = ar + pad, br + pad, m + pad
+    A = _opnd(rng, ar, ac, lda, batch)
+    B = _opnd(rng, br, bc, ldb, batch)
+    C0 = _opnd(rng, m, n, ldc, batch)
+    alpha, beta = 0.75, -0.5
+    dA, dB, dC = (torch.from_numpy(x.ravel().copy()).cuda() for x in (A, B, C0))
+    lib.prof_reset()
+    lib.prof_enable(True)
+    lib.gemm_f32(ta, tb, m, n, k, alpha, dA.data_ptr(), lda, lda * ac, dB.data_ptr(), ldb, ldb * bc, beta,
+                 dC.data_ptr(), ldc, ldc * n, batch=batch, mode=mode)
+    lib.prof_enable(False)
+    tc_launches = lib.prof_query("gemm32tc")[1]
+    simt_launches = lib.prof_query("gemm32")[1]
+    lib.prof_reset()
+    assert (tc_launches > 0) == (mode != 0) and (simt_launches > 0) == (mode == 0)
+    Cg = dC.cpu().numpy().reshape(batch, n, ldc)
+    for i in range(batch):
+        a = _mat(A, i, ar, ac)
+        b = _mat(B, i, br, bc)
+        opa, opb = (a.T if ta else a), (b.T if tb else b)
+        ref = alpha * opa @ opb + beta * _mat(C0, i, m, n)
+        scale = abs(alpha) * np.abs(opa) @ np.abs(opb) + abs(beta) * np.abs(_mat(C0, i, m, n))
+        got = Cg[i, :, :m].T.astype(np.float64)
+        err = np.abs(got - ref)
+        assert np.all(err <= _bound(mode, k) * scale + 1e-30), (np.max(err / scale), _bound(mode, k))
+        # padding rows of C untouched
+        if pad:
+            assert np.array_equal(Cg[i, :, m:], C0[i, :, m:])
+
+
+@pytest.mark.parametrize("mode", [1, 3])
+def test_gemm_two_level_k(lib, mode):
+    """k runs over panels of kblk columns that sit kstr apart (non-transposed A,
+    transposed B), as in the stacked low-rank update of the Sylvester solver."""
+    rng = np.random.default_rng(5 + mode)
+    m, n, J, kblk = 260, 200, 5, 34
+    k = J * kblk
+    lda = m + 4
+    kstr = lda * (kblk + 3)  # panels with gaps between them
+    ldb = n
+    kstr_b = kstr  # both operands use the same panel stride
+    Abuf = rng.standard_normal(kstr * J).astype(np.float32)
+    Bbuf = np.zeros(kstr_b * J + ldb * kblk, dtype=np.float32)
+    Bbuf[:] = rng.standard_normal(Bbuf.size).astype(np.float32)
+
+    def col(kk):
+        return (kk // kblk) * kstr + (kk % kblk) * lda
+
+    def colb(kk):
+        return (kk // kblk) * kstr_b + (kk % kblk) * ldb
+
+    opa = np.stack([Abuf[col(kk):col(kk) + m] for kk in range(k)], axis=1).astype(np.float64)     # m x k
+    opb = np.stack([Bbuf[colb(kk):colb(kk) + n] for kk in range(k)], axis=1).astype(np.float64).T  # k x n
+    ldc = m
+    C0 = np.zeros(ldc * n, dtype=np.float32)
+    dA, dB, dC = (torch.from_numpy(x.copy()).cuda() for x in (Abuf, Bbuf, C0))
+    # A and B share kblk / kstr in one call: use the B panel stride = A's
+    assert kstr_b == kstr
+    lib.gemm_f32(0, 1, m, n, k, 1.0, dA.data_ptr(), lda, 0, dB.data_ptr(), ldb, 0, 0.0, dC.data_ptr(), ldc, 0,
+                 batch=1, kblk=kblk, kstr=kstr, mode=mode)
+    got = dC.cpu().numpy().reshape(n, ldc).T.astype(np.float64)
+    ref = opa @ opb
+    scale = np.abs(opa) @ np.abs(opb)
+    assert np.all(np.abs(got - ref) <= _bound(mode, k) * scale)
+
+
+def test_gemm_split_beats_tf32(lib):
+    """3xTF32 must be markedly more accurate than plain TF32 on the same data."""
+    rng = np.random.default_rng(11)
+    m = n = 256
+    k = 512
+    A = rng.standard_normal((k, m)).astype(np.float32)  # column-major m x k as (k, m) row-major
+    B = rng.standard_normal((n, k)).astype(np.float32)
+    ref = A.T.astype(np.float64) @ B.T.astype(np.float64)
+    errs = {}
+    for mode in (1, 3):
+        dA, dB = torch.from_numpy(A.ravel().copy()).cuda(), torch.from_numpy(B.ravel().copy()).cuda()
+        dC = torch.zeros(m * n, dtype=torch.float32, device="cuda")
+        lib.gemm_f32(0, 0, m, n, k, 1.0, dA.data_ptr(), m, 0, dB.data_ptr(), k, 0, 0.0, dC.data_ptr(), m, 0,
+                     mode=mode)
+        got = dC.cpu().numpy().reshape(n, m).T
+        errs[mode] = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert errs[3] < 2e-6 and errs[1] > 100 * errs[3], errs
