@@ -128,28 +128,16 @@ def read_peaks():
         return {}
 
 
-def roofline(lib, N):
-    """Dominant kernel family by device time in the timed region."""
-    fams = ["gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply", "transpose", "refine", "fadi_axpy"]
-    rec = {}
-    for f in fams:
-        ms, n, work, kind = lib.prof_query(f)
-        if n:
-            rec[f] = dict(ms=ms, launches=n, work=work, kind=kind)
-    if not rec:
-        return None, rec
-    total = sum(v["ms"] for v in rec.values())
-    dom = max(rec, key=lambda f: rec[f]["ms"])
-    v = rec[dom]
-    per_launch_s = v["ms"] / 1e3 / v["launches"]
-    work_per_launch = v["work"] / v["launches"]
-    peaks = read_peaks()
-    if v["kind"] == 0:
+def family_roofline(fam, ms, launches, work, kind, peaks):
+    """Achieved rate of one kernel family against its roofline."""
+    per_launch_s = ms / 1e3 / launches
+    work_per_launch = work / launches
+    if kind == 0:
         achieved = work_per_launch / per_launch_s / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
              "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-    elif dom == "gemm32tc":
+    elif fam == "gemm32tc":
         # tcgen05 kind::tf32; peak = measured bf16 (sustained: the kernel runs
         # inside a long step) x nominal tf32/bf16 dense ratio 1.1/2.25
         achieved = work_per_launch / per_launch_s / 1e12
@@ -160,15 +148,41 @@ def roofline(lib, N):
              + " sustained bf16 x 1.1/2.25 (tf32)"}
     else:
         achieved = work_per_launch / per_launch_s / 1e12
-        peak = FP32_SIMT_PEAK_TFLOPS if dom.endswith("32") else FP64_PEAK_TFLOPS
+        fp32 = fam.endswith("32")
+        peak = FP32_SIMT_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
         r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-             "peak_source": "derived: 152 SMs x %s x 2070 MHz" % ("128 FP32 lanes x 2" if dom.endswith("32")
+             "peak_source": "derived: 152 SMs x %s x 2070 MHz" % ("128 FP32 lanes x 2" if fp32
                                                                   else "2 FP64 FMA/clk x 2")}
-    r.update({"frac": achieved / peak, "traffic": None, "kernel": dom,
-              "algorithmic_work_per_launch": work_per_launch, "launches": v["launches"],
-              "avg_launch_ms": v["ms"] / v["launches"], "share_of_instrumented_time": v["ms"] / total})
-    shares = {f: round(rec[f]["ms"] / total, 4) for f in rec}
-    return r, shares
+    r.update({"frac": achieved / peak, "kernel": fam, "algorithmic_work_per_launch": work_per_launch,
+              "launches": launches, "avg_launch_ms": ms / launches})
+    return r
+
+
+FAMILIES = ["gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply", "transpose", "refine", "fadi_axpy"]
+
+
+def roofline(lib, N):
+    """Every instrumented kernel family against its roofline; the dominant one
+    (largest device time) is the headline."""
+    rec = {}
+    for f in FAMILIES:
+        ms, n, work, kind = lib.prof_query(f)
+        if n:
+            rec[f] = (ms, n, work, kind)
+    if not rec:
+        return None, {}
+    peaks = read_peaks()
+    total = sum(v[0] for v in rec.values())
+    fams = {f: family_roofline(f, *rec[f], peaks) for f in rec}
+    for f in fams:
+        fams[f]["share_of_instrumented_time"] = rec[f][0] / total
+    dom = max(rec, key=lambda f: rec[f][0])
+    r = dict(fams[dom])
+    r["traffic"] = None
+    detail = {f: {"share": round(v["share_of_instrumented_time"], 4), "avg_launch_ms": round(v["avg_launch_ms"], 4),
+                  "launches": v["launches"], "achieved": round(v["achieved"], 3), "unit": v["unit"],
+                  "frac": round(v["frac"], 4), "bound": v["bound"]} for f, v in fams.items()}
+    return r, detail
 
 
 # ------------------------------------------------------------------ ours
@@ -313,7 +327,7 @@ def run_ours(args, rank, world, local_rank):
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 refine", "data": "synthetic",
            "config": cfg, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-           "kernel_time_shares": shares, "cpu_baseline": cpu, "clocks": clk}
+           "kernels": shares, "cpu_baseline": cpu, "clocks": clk}
     out.update(extra)
     print(json.dumps(out), flush=True)
 

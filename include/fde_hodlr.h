@@ -164,7 +164,11 @@ fde_status sylv_create(hodlr_t Ax, hodlr_t Ay, int prec, void* stream, sylv_t* o
 /* Refinement controls (defaults set by sylv_create). */
 typedef struct {
   int max_sweeps;        /* cap on refinement sweeps (FDE_ERR_NOCONV beyond) */
-  double tol_update;     /* stop when ||δX||_F <= tol_update ||X||_F         */
+  double tol_update;     /* stop when the error left after the last update,
+                            estimated as ||δX_k||_F or, once the sweeps
+                            contract (rho = ||δX_k|| / ||δX_{k-1}|| < 1/2),
+                            as rho ||δX_k||_F / (1 - rho), is
+                            <= tol_update ||X||_F                          */
   double tol_relres;     /* or when ||R||_F <= tol_relres ||C||_F            */
   int fixed_sweeps;      /* > 0: run exactly this many sweeps, no host sync   */
 } sylv_refine_t;

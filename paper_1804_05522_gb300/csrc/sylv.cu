@@ -920,7 +920,10 @@ static fde_status sweep(sylv_s* S, Inner<T>& in, const double* C, double* X64, c
 }
 
 // Iterative refinement (FP64 residual, inner solve in the handle's precision).
-// Stops when ||δX||_F <= tol_update ||X||_F or ||R||_F <= tol_relres ||C||_F;
+// Stops when the error left after the last update is estimated below
+// tol_update ||X||_F — ||δX_k||_F itself, or rho ||δX_k||_F / (1 - rho) with
+// the observed contraction rho = ||δX_k|| / ||δX_{k-1}|| once rho < 1/2 — or
+// when ||R||_F <= tol_relres ||C||_F;
 // FDE_ERR_NOCONV if neither holds after max_sweeps.  With fixed_sweeps > 0 it
 // runs exactly that many sweeps and never synchronises with the host unless a
 // residual is requested.
@@ -957,6 +960,7 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
   int done = 0;
   bool converged = fixed;
   double a[8];
+  double prev_d2 = -1.0;
   for (int sw = 0; sw < nsw; ++sw) {
     if (S->prec == FDE_FP64)
       FDE_TRY(sweep<double>(S, S->in64, C, X, st));
@@ -969,7 +973,17 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
       set_error("sylv_step: non-finite iterate after sweep %d", done);
       return FDE_ERR_NUMERIC;
     }
-    if (a[0] <= rf.tol_update * rf.tol_update * a[1] || a[2] <= rf.tol_relres * rf.tol_relres * a[4]) {
+    const double tol2 = rf.tol_update * rf.tol_update * a[1];
+    bool stop = a[0] <= tol2 || a[2] <= rf.tol_relres * rf.tol_relres * a[4];
+    if (!stop && prev_d2 > 0.0 && a[0] < 0.25 * prev_d2) {
+      // the sweeps contract the error by rho ~ ||δ_k|| / ||δ_{k-1}|| < 1/2:
+      // what the next sweeps would still add is about rho ||δ_k|| / (1 - rho)
+      const double rho = sqrt(a[0] / prev_d2);
+      const double rest = rho / (1.0 - rho);
+      stop = a[0] * rest * rest <= tol2;
+    }
+    prev_d2 = a[0];
+    if (stop) {
       converged = true;
       break;
     }
