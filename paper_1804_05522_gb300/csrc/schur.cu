@@ -224,280 +224,361 @@ fde_status leaf_schur(double* H, double* Q, int ld, size_t stride, const int* d_
 }
 
 // ------------------------------------------------ quasi-triangular Sylvester
-// Small dense solve M y = b (size m <= 4) by Gaussian elimination with
-// partial pivoting.
-template <typename T>
-__device__ void small_solve(T M[4][4], T b[4], int m) {
-  for (int k = 0; k < m; ++k) {
-    int pv = k;
-    for (int i = k + 1; i < m; ++i)
-      if (fabs((double)M[i][k]) > fabs((double)M[pv][k])) pv = i;
-    if (pv != k) {
-      for (int j = 0; j < m; ++j) {
-        T t = M[k][j];
-        M[k][j] = M[pv][j];
-        M[pv][j] = t;
-      }
-      T t = b[k];
-      b[k] = b[pv];
-      b[pv] = t;
-    }
-    for (int i = k + 1; i < m; ++i) {
-      const T f = M[i][k] / M[k][k];
-      for (int j = k; j < m; ++j) M[i][j] -= f * M[k][j];
-      b[i] -= f * b[k];
-    }
-  }
-  for (int k = m - 1; k >= 0; --k) {
-    T s = b[k];
-    for (int j = k + 1; j < m; ++j) s -= M[k][j] * b[j];
-    b[k] = s / M[k][k];
-  }
-}
-
-// One CTA per leaf pair, solving  S Y + Y Rᵀ = C  (S, R upper quasi-triangular)
-// by back substitution over the diagonal blocks (1x1 / 2x2) of both factors.
-// Column groups (R's diagonal blocks, last first) are handled in waves of up
-// to kWarps groups, one warp per group.  Inside a wave the warps advance as a
-// wavefront: warp g solves row group ρ (S's blocks, bottom first) at step
-// ρ + g, so every coupling it needs — rows below in its own columns and the
-// same rows in the later columns of the wave — was finalised at earlier steps.
-// A small coupled system (I ⊗ S_bb + R_bb ⊗ I) vec Y_b = vec B_b of size <= 4
-// is solved per (row group, column group).  Before a wave, its columns get
-// the contribution of all columns solved in earlier waves (a GEMM-like update).
-constexpr int kWarps = 32;
+//
+// For every leaf pair (p, q):  S Y + Y Rᵀ = F  in place of F, S = S_p (n1 x n1)
+// and R = R_q (n2 x n2) upper quasi-triangular (real Schur forms: 2 x 2
+// diagonal blocks for complex-conjugate pairs).  Bartels–Stewart order:
+// columns of Y from the last to the first (Rᵀ is lower quasi-triangular),
+// rows of each column from the last to the first (S upper quasi-triangular).
+//
+// One CTA per pair.  The rows are cut, from the bottom, into blocks of at most
+// 32 rows that never split a 2 x 2 block of S; warp w owns block w (lane =
+// row).  The columns are taken in groups of one, or two for a 2 x 2 block of
+// R, from the right.  Warp w solves group g at barrier step g + w (a wavefront
+// over the row blocks), so the rows below its block are final for that group
+// when it starts: their values come from a ring of shared-memory columns, and
+// the S coupling with them is a dot product per lane.  Inside the block the
+// back substitution runs over the row groups bottom-up with shuffles only:
+// the owner lane of a row group solves its small system (1, 2 or 4 unknowns,
+// closed form from inverses each lane prepared before the chain) and
+// broadcasts the solution, every lane removes its coupling.
+//
+// Each lane keeps, for its row, the right-hand sides of a window of 32
+// consecutive columns in registers (yb[31] = the current group's last
+// column).  Columns are further cut, from the right, into blocks of at most
+// 32 that never split a 2 x 2 block of R: at the start of a block the window
+// is reloaded from F minus the coupling with all columns solved before the
+// block (read back from Y, written by this lane); after each group its
+// coupling is subtracted from the rest of the window, which then shifts.
+constexpr int kMaxRowWarps = 9;   // leaves up to 256 rows: blocks of >= 31 rows
 
 template <typename T>
-__global__ void __launch_bounds__(kWarps * 32) trsyl_kernel(const T* __restrict__ Sall, const T* __restrict__ Rall,
-                                                           int lmax, const int* __restrict__ lo_x,
-                                                           const int* __restrict__ n_x, int nx,
-                                                           const int* __restrict__ lo_y,
-                                                           const int* __restrict__ n_y, T* W, int ldw, int mode) {
-  // mode 0: everything in global memory; 1: Y in shared; 2: Y, S, R in shared.
+__global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 ? 128 : 168)
+    trsyl_kernel(const T* __restrict__ Sall, const T* __restrict__ Rall, int lmax, const int* __restrict__ lo_x,
+                 const int* __restrict__ n_x, int nx, const int* __restrict__ lo_y, const int* __restrict__ n_y,
+                 T* __restrict__ W, int ldw, int use_panel, int panel_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = blockIdx.x % nx, q = blockIdx.x / nx;
   const int n1 = n_x[p], n2 = n_y[q];
-  T* Yg = W + lo_x[p] + (size_t)lo_y[q] * ldw;
-  int* rg0 = (int*)smem_raw;  // start row of row group ρ (bottom first)
-  int* rgs = rg0 + lmax;      // its size
-  int* cg0 = rgs + lmax;      // start column of column group γ (last first)
-  int* cgs = cg0 + lmax;
-  __shared__ int s_nrg, s_ncg;
+  if (n1 <= 0 || n2 <= 0) return;
+  T* Y = W + lo_x[p] + (size_t)lo_y[q] * ldw;
   const T* S = Sall + (size_t)p * lmax * lmax;
   const T* R = Rall + (size_t)q * lmax * lmax;
-  int lds = lmax, ldr = lmax;
-  T* Y = Yg;
-  int ldy = ldw;
-  T* dyn = (T*)(cgs + lmax);
-  if (mode >= 1) {
-    // odd leading dimensions keep the strided (row-wise) accesses conflict free
-    Y = dyn;
-    ldy = n1 | 1;
-    for (int e = threadIdx.x; e < n1 * n2; e += blockDim.x)
-      Y[e % n1 + (e / n1) * ldy] = Yg[e % n1 + (size_t)(e / n1) * ldw];
-    dyn += (size_t)ldy * n2;
-  }
-  if (mode == 2) {
-    T* Ss = dyn;
-    const int ls = n1 | 1;
-    for (int e = threadIdx.x; e < n1 * n1; e += blockDim.x) Ss[e % n1 + (e / n1) * ls] = S[e % n1 + (size_t)(e / n1) * lmax];
-    dyn += (size_t)ls * n1;
-    T* Rs = dyn;
-    const int lr = n2 | 1;
-    for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) Rs[e % n2 + (e / n2) * lr] = R[e % n2 + (size_t)(e / n2) * lmax];
-    S = Ss;
-    R = Rs;
-    lds = ls;
-    ldr = lr;
-  }
-  __syncthreads();
-#define SS(i, j) S[(i) + (size_t)(j)*lds]
-#define RR(i, j) R[(i) + (size_t)(j)*ldr]
-#define YY(i, j) Y[(i) + (size_t)(j)*ldy]
+  // ring of solved columns: one slot per launched warp + 1 (a slot is reread
+  // by the warps above for nwarps - 1 steps after it is written)
+  const int ring = (int)(blockDim.x >> 5) + 1;
+  T* ycol = reinterpret_cast<T*>(smem_raw);                  // ring x [col k | col k-1] x lmax
+  T* sdiag = ycol + (size_t)ring * 2 * lmax;                 // per warp: its diagonal S block, 32 x 33
+  T* panel = sdiag + (size_t)(blockDim.x >> 5) * 32 * 33;    // S panels (use_panel), see below
+  int* cg_top = reinterpret_cast<int*>(panel + (use_panel ? panel_elems : 0));
+  int* cg_info = cg_top + lmax;                              // bit 0: two columns; bit 1: block start
+  int* cg_cblo = cg_info + lmax;                             // first column of the group's column block
+  __shared__ int rb_lo[kMaxRowWarps], rb_n[kMaxRowWarps], poff[kMaxRowWarps];
+  __shared__ int s_ncg, s_nrb;
+#define SS(i, j) S[(i) + (size_t)(j)*lmax]
+#define RR(i, j) R[(i) + (size_t)(j)*lmax]
   if (threadIdx.x == 0) {
-    int c = 0;
-    for (int i1 = n1 - 1; i1 >= 0;) {
-      const int ib = (i1 > 0 && SS(i1, i1 - 1) != T(0)) ? 2 : 1;
-      rg0[c] = i1 - ib + 1;
-      rgs[c] = ib;
-      ++c;
-      i1 -= ib;
+    int w = 0;
+    for (int hi = n1; hi > 0 && w < kMaxRowWarps; ++w) {
+      int lo = hi - 32 > 0 ? hi - 32 : 0;
+      if (lo > 0 && SS(lo, lo - 1) != T(0)) ++lo;  // keep the 2 x 2 block (lo-1, lo) together
+      rb_lo[w] = lo;
+      rb_n[w] = hi - lo;
+      hi = lo;
     }
-    s_nrg = c;
-  } else if (threadIdx.x == 32) {
-    int c = 0;
-    for (int k1 = n2 - 1; k1 >= 0;) {
-      const int kb = (k1 > 0 && RR(k1, k1 - 1) != T(0)) ? 2 : 1;
-      cg0[c] = k1 - kb + 1;
-      cgs[c] = kb;
-      ++c;
-      k1 -= kb;
+    s_nrb = w;
+    // panel of warp w: S(block rows, columns rhi..n1-1), column-major, ld 33
+    int off = 0;
+    for (int v = 0; v < w; ++v) {
+      poff[v] = off;
+      off += 33 * (n1 - (rb_lo[v] + rb_n[v]));
     }
-    s_ncg = c;
+  }
+  // the column tables come from the second warp's first thread, or from
+  // thread 0 as well when the CTA is a single warp (leaves of <= 31 rows)
+  if (threadIdx.x == (blockDim.x > 32 ? 32u : 0u)) {
+    int g = 0, cb_lo = n2;
+    for (int k = n2 - 1; k >= 0;) {
+      int info = 0;
+      if (k < cb_lo) {  // a new column block [cb_lo, k + 1)
+        int lo = k + 1 - 32 > 0 ? k + 1 - 32 : 0;
+        if (lo > 0 && RR(lo, lo - 1) != T(0)) ++lo;
+        cb_lo = lo;
+        info |= 2;
+      }
+      const int gs = (k > 0 && RR(k, k - 1) != T(0)) ? 2 : 1;
+      cg_top[g] = k;
+      cg_info[g] = info | (gs == 2 ? 1 : 0);
+      cg_cblo[g] = cb_lo;
+      ++g;
+      k -= gs;
+    }
+    s_ncg = g;
   }
   __syncthreads();
-  const int nrg = s_nrg, ncg = s_ncg;
+  const int ncg = s_ncg, nrb = s_nrb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int wb = 0; wb < ncg; wb += kWarps) {
-    const int we = min(ncg, wb + kWarps);
-    // columns of this wave: [cfirst, clast]; columns already solved: > clast
-    const int clast = cg0[wb] + cgs[wb] - 1;
-    const int cfirst = cg0[we - 1];
-    if (clast + 1 < n2) {
-      const int wcols = clast - cfirst + 1;
-      for (int e = threadIdx.x; e < n1 * wcols; e += blockDim.x) {
-        const int i = e % n1, k = cfirst + e / n1;
-        T acc = T(0);
-        for (int l = clast + 1; l < n2; ++l) acc += RR(k, l) * YY(i, l);
-        YY(i, k) -= acc;
+  {
+    // every warp's diagonal block (the back-substitution chain reads a column per row)
+    const int w_ = threadIdx.x >> 5, l_ = threadIdx.x & 31;
+    const int vlo = w_ < s_nrb ? rb_lo[w_] : 0, vn = w_ < s_nrb ? rb_n[w_] : 0;
+    T* sv = sdiag + (size_t)w_ * 32 * 33 + l_;
+    for (int t = 0; t < 32; ++t) sv[t * 33] = (l_ < vn && t < vn) ? SS(vlo + l_, vlo + t) : T(0);
+  }
+  if (use_panel) {
+    // the S coupling of every column group rereads these entries: stage them
+    for (int v = 0; v < nrb; ++v) {
+      const int vlo = rb_lo[v], vn = rb_n[v], vhi = vlo + vn, cols = n1 - vhi;
+      T* pv = panel + poff[v];
+      for (int e = threadIdx.x; e < 32 * cols; e += blockDim.x) {
+        const int r = e & 31, c = e >> 5;
+        pv[c * 33 + r] = r < vn ? SS(vlo + r, vhi + c) : T(0);
+      }
+    }
+  }
+  __syncthreads();
+  const bool wact = warp < nrb;
+  const int rlo = wact ? rb_lo[warp] : 0, nr = wact ? rb_n[warp] : 0, rhi = rlo + nr;
+  const bool active = lane < nr;
+  const int i = rlo + lane;
+  // this lane's row of the diagonal block of S (sd[t * 33] = S(i, rlo + t),
+  // filled before the first barrier below), and its 2 x 2 block if any
+  T* sd = sdiag + (size_t)warp * 32 * 33 + lane;
+  const T sii = active ? SS(i, i) : T(1);
+  const bool bottom = active && lane > 0 && SS(i, i - 1) != T(0);
+  const unsigned pair_mask = __ballot_sync(0xffffffffu, bottom);  // bit r: rows (r-1, r) form a 2 x 2 block
+  T s00 = T(0), s01 = T(0), s10 = T(0), s11 = T(0);  // the 2 x 2 block of S (bottom lanes)
+  if (bottom) {
+    s00 = SS(i - 1, i - 1);
+    s01 = SS(i - 1, i);
+    s10 = SS(i, i - 1);
+    s11 = sii;
+  }
+  T yb[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) yb[t] = T(0);
+  const int nsteps = ncg + (int)(blockDim.x >> 5) - 1;
+  for (int m = 0; m < nsteps; ++m) {
+    const int g = m - warp;
+    if (wact && g >= 0 && g < ncg) {
+      const int k = cg_top[g], info = cg_info[g], cb_lo = cg_cblo[g];
+      const bool two = (info & 1) != 0;
+      if (info & 2) {
+        // block start: window columns k-31..k = F minus the coupling with the
+        // columns l > k solved before (Y(i, l), written by this lane)
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const int col = k - 31 + t;
+          yb[t] = (active && col >= cb_lo) ? Y[i + (size_t)col * ldw] : T(0);
+        }
+#pragma unroll 4
+        for (int l = k + 1; l < n2; ++l) {
+          const T yl = active ? Y[i + (size_t)l * ldw] : T(0);
+          const T* Rl = R + (size_t)l * lmax;
+#pragma unroll
+          for (int t = 0; t < 32; ++t) {
+            const int col = k - 31 + t;
+            if (col >= cb_lo) yb[t] -= __ldg(Rl + col) * yl;
+          }
+        }
+      }
+      const int slot = g % ring;
+      T* yk = ycol + (size_t)slot * 2 * lmax;  // column k, then column k-1
+      T fb = yb[31], fa = two ? yb[30] : T(0);  // fb: column k, fa: column k-1
+      // coupling with the rows below this block (final, from the ring)
+      if (active) {
+        if (use_panel) {
+          const T* pw = panel + poff[warp] + lane;
+          T b0 = T(0), b1 = T(0), a0 = T(0), a1 = T(0);
+          int j = rhi;
+          for (; j + 1 < n1; j += 2) {
+            const T s0 = pw[(j - rhi) * 33], s1 = pw[(j + 1 - rhi) * 33];
+            b0 += s0 * yk[j];
+            b1 += s1 * yk[j + 1];
+            if (two) {
+              a0 += s0 * yk[lmax + j];
+              a1 += s1 * yk[lmax + j + 1];
+            }
+          }
+          if (j < n1) {
+            const T s0 = pw[(j - rhi) * 33];
+            b0 += s0 * yk[j];
+            if (two) a0 += s0 * yk[lmax + j];
+          }
+          fb -= b0 + b1;
+          fa -= a0 + a1;
+        } else {
+          for (int j = rhi; j < n1; ++j) {
+            const T sij = __ldg(S + i + (size_t)j * lmax);
+            fb -= sij * yk[j];
+            if (two) fa -= sij * yk[lmax + j];
+          }
+        }
+      }
+      T ya_fin = T(0), yb_fin = T(0);
+      if (!two) {
+        const T mu = __ldg(R + k + (size_t)k * lmax);
+        T inv = T(1) / (sii + mu), p00 = T(0), p01 = T(0), p10 = T(0), p11 = T(0);
+        if (bottom) {  // inverse of (S_2x2 + mu I)
+          const T d = (s00 + mu) * (s11 + mu) - s01 * s10;
+          p00 = (s11 + mu) / d;
+          p01 = -s01 / d;
+          p10 = -s10 / d;
+          p11 = (s00 + mu) / d;
+        }
+        for (int rr = nr - 1; rr >= 0;) {
+          if (rr > 0 && ((pair_mask >> rr) & 1u)) {
+            const T st = sd[(rr - 1) * 33], sb = sd[rr * 33];
+            const T ftop = __shfl_sync(0xffffffffu, fb, rr - 1);
+            T y0 = T(0), y1 = T(0);
+            if (lane == rr) {
+              y0 = p00 * ftop + p01 * fb;
+              y1 = p10 * ftop + p11 * fb;
+            }
+            y0 = __shfl_sync(0xffffffffu, y0, rr);
+            y1 = __shfl_sync(0xffffffffu, y1, rr);
+            if (lane == rr - 1) yb_fin = y0;
+            if (lane == rr) yb_fin = y1;
+            fb -= st * y0 + sb * y1;
+            rr -= 2;
+          } else {
+            const T sb = sd[rr * 33];
+            T y = (lane == rr) ? fb * inv : T(0);
+            y = __shfl_sync(0xffffffffu, y, rr);
+            if (lane == rr) yb_fin = y;
+            fb -= sb * y;
+            rr -= 1;
+          }
+        }
+      } else {
+        // R block [[a, b], [c, d]] couples columns k-1 (unknown 1) and k (unknown 2)
+        const T a = __ldg(R + (k - 1) + (size_t)(k - 1) * lmax), b = __ldg(R + (k - 1) + (size_t)k * lmax);
+        const T c = __ldg(R + k + (size_t)(k - 1) * lmax), d = __ldg(R + k + (size_t)k * lmax);
+        // 1 x 1 row: [[s+a, b], [c, s+d]]^{-1}
+        const T det1 = (sii + a) * (sii + d) - b * c;
+        const T e00 = (sii + d) / det1, e01 = -b / det1, e10 = -c / det1, e11 = (sii + a) / det1;
+        // 2 x 2 row block S2: the blocks of I(x)S2 + R(x)I commute, so the
+        // inverse needs only Δ = (S2 + aI)(S2 + dI) - bc I
+        T q00 = T(0), q01 = T(0), q10 = T(0), q11 = T(0);
+        if (bottom) {
+          const T tr = s00 + s11 + a + d, cst = a * d - b * c;
+          const T D00 = s00 * s00 + s01 * s10 + (a + d) * s00 + cst, D01 = s01 * tr;
+          const T D10 = s10 * tr, D11 = s10 * s01 + s11 * s11 + (a + d) * s11 + cst;
+          const T dd = D00 * D11 - D01 * D10;
+          q00 = D11 / dd;
+          q01 = -D01 / dd;
+          q10 = -D10 / dd;
+          q11 = D00 / dd;
+        }
+        for (int rr = nr - 1; rr >= 0;) {
+          if (rr > 0 && ((pair_mask >> rr) & 1u)) {
+            const T st = sd[(rr - 1) * 33], sb = sd[rr * 33];
+            const T fat = __shfl_sync(0xffffffffu, fa, rr - 1), fbt = __shfl_sync(0xffffffffu, fb, rr - 1);
+            T u0 = T(0), u1 = T(0), v0 = T(0), v1 = T(0);  // column k-1 (top, bottom), column k
+            if (lane == rr) {
+              const T g1t = (s00 + d) * fat + s01 * fa - b * fbt, g1b = s10 * fat + (s11 + d) * fa - b * fb;
+              const T g2t = (s00 + a) * fbt + s01 * fb - c * fat, g2b = s10 * fbt + (s11 + a) * fb - c * fa;
+              u0 = q00 * g1t + q01 * g1b;
+              u1 = q10 * g1t + q11 * g1b;
+              v0 = q00 * g2t + q01 * g2b;
+              v1 = q10 * g2t + q11 * g2b;
+            }
+            u0 = __shfl_sync(0xffffffffu, u0, rr);
+            u1 = __shfl_sync(0xffffffffu, u1, rr);
+            v0 = __shfl_sync(0xffffffffu, v0, rr);
+            v1 = __shfl_sync(0xffffffffu, v1, rr);
+            if (lane == rr - 1) {
+              ya_fin = u0;
+              yb_fin = v0;
+            }
+            if (lane == rr) {
+              ya_fin = u1;
+              yb_fin = v1;
+            }
+            fa -= st * u0 + sb * u1;
+            fb -= st * v0 + sb * v1;
+            rr -= 2;
+          } else {
+            const T sb = sd[rr * 33];
+            T u = T(0), v = T(0);
+            if (lane == rr) {
+              u = e00 * fa + e01 * fb;
+              v = e10 * fa + e11 * fb;
+            }
+            u = __shfl_sync(0xffffffffu, u, rr);
+            v = __shfl_sync(0xffffffffu, v, rr);
+            if (lane == rr) {
+              ya_fin = u;
+              yb_fin = v;
+            }
+            fa -= sb * u;
+            fb -= sb * v;
+            rr -= 1;
+          }
+        }
+      }
+      if (active) {
+        Y[i + (size_t)k * ldw] = yb_fin;
+        yk[i] = yb_fin;
+        if (two) {
+          Y[i + (size_t)(k - 1) * ldw] = ya_fin;
+          yk[lmax + i] = ya_fin;
+        }
+      }
+      // remove the group's coupling from the rest of the window, then shift it
+      const T* Rk = R + (size_t)k * lmax;
+      const T* Rk1 = R + (size_t)(k - 1) * lmax;
+#pragma unroll
+      for (int t = 0; t < 31; ++t) {
+        const int col = k - 31 + t;
+        if (col >= cb_lo && (t < 30 || !two)) {
+          T v = __ldg(Rk + col) * yb_fin;
+          if (two) v += __ldg(Rk1 + col) * ya_fin;
+          yb[t] -= v;
+        }
+      }
+      if (two) {
+#pragma unroll
+        for (int t = 31; t >= 2; --t) yb[t] = yb[t - 2];
+        yb[1] = T(0);
+        yb[0] = T(0);
+      } else {
+#pragma unroll
+        for (int t = 31; t >= 1; --t) yb[t] = yb[t - 1];
+        yb[0] = T(0);
       }
     }
     __syncthreads();
-    const int nsteps = nrg + (we - wb) - 1;
-    for (int t = 0; t < nsteps; ++t) {
-      const int g = warp, gam = wb + g, rho = t - g;
-      if (gam < we && rho >= 0 && rho < nrg && rgs[rho] == 1 && cgs[gam] == 1) {
-        // 1x1 blocks (real eigenvalues on both sides): the common case
-        const int i0 = rg0[rho], k0 = cg0[gam];
-        T acc = T(0);
-        for (int l = k0 + 1 + lane; l <= clast; l += 32) acc += RR(k0, l) * YY(i0, l);
-        acc = warp_sum(acc);
-        const T y = (YY(i0, k0) - acc) / (SS(i0, i0) + RR(k0, k0));
-        __syncwarp();
-        if (lane == 0) YY(i0, k0) = y;
-        for (int i = lane; i < i0; i += 32) YY(i, k0) -= SS(i, i0) * y;
-      } else if (gam < we && rho >= 0 && rho < nrg) {
-        // 2x2 blocks (complex pairs) on one or both sides: a system of size
-        // ib*kb <= 4, laid out with stride 2 (unknown ia + 2 kb) and padded with
-        // identity rows, solved in registers by unrolled Gaussian elimination
-        const int i0 = rg0[rho], ib = rgs[rho];
-        const int k0 = cg0[gam], kb = cgs[gam];
-        const int k1 = k0 + kb - 1;
-        T c[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
-        for (int l = k1 + 1 + lane; l <= clast; l += 32) {
-          const T y0 = YY(i0, l), y1 = (ib == 2) ? YY(i0 + 1, l) : T(0);
-          const T r0 = RR(k0, l), r1 = (kb == 2) ? RR(k0 + 1, l) : T(0);
-          c[0][0] += r0 * y0;
-          c[0][1] += r1 * y0;
-          c[1][0] += r0 * y1;
-          c[1][1] += r1 * y1;
-        }
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-          for (int bb = 0; bb < 2; ++bb) c[a][bb] = warp_sum(c[a][bb]);
-        T yv[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
-        if (lane == 0) {
-          T M[4][4], rhs[4];
-#pragma unroll
-          for (int kb_ = 0; kb_ < 2; ++kb_)
-#pragma unroll
-            for (int ia = 0; ia < 2; ++ia) {
-              const int u = ia + 2 * kb_;
-              const bool used = ia < ib && kb_ < kb;
-              rhs[u] = used ? YY(i0 + ia, k0 + kb_) - c[ia][kb_] : T(0);
-#pragma unroll
-              for (int kc = 0; kc < 2; ++kc)
-#pragma unroll
-                for (int ic = 0; ic < 2; ++ic) {
-                  const int v = ic + 2 * kc;
-                  T m = T(0);
-                  if (used && ic < ib && kc < kb)
-                    m = (kb_ == kc ? SS(i0 + ia, i0 + ic) : T(0)) + (ia == ic ? RR(k0 + kb_, k0 + kc) : T(0));
-                  else if (!used && u == v)
-                    m = T(1);
-                  M[u][v] = m;
-                }
-            }
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            int pv = k;
-            T best = fabs(M[k][k]);
-#pragma unroll
-            for (int i = k + 1; i < 4; ++i)
-              if (fabs(M[i][k]) > best) {
-                best = fabs(M[i][k]);
-                pv = i;
-              }
-#pragma unroll
-            for (int i = k + 1; i < 4; ++i)
-              if (i == pv) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  const T t = M[k][j];
-                  M[k][j] = M[i][j];
-                  M[i][j] = t;
-                }
-                const T t = rhs[k];
-                rhs[k] = rhs[i];
-                rhs[i] = t;
-              }
-#pragma unroll
-            for (int i = k + 1; i < 4; ++i) {
-              const T f = M[i][k] / M[k][k];
-#pragma unroll
-              for (int j = k; j < 4; ++j) M[i][j] -= f * M[k][j];
-              rhs[i] -= f * rhs[k];
-            }
-          }
-#pragma unroll
-          for (int k = 3; k >= 0; --k) {
-            T sacc = rhs[k];
-#pragma unroll
-            for (int j = k + 1; j < 4; ++j) sacc -= M[k][j] * rhs[j];
-            rhs[k] = sacc / M[k][k];
-          }
-#pragma unroll
-          for (int kb_ = 0; kb_ < 2; ++kb_)
-#pragma unroll
-            for (int ia = 0; ia < 2; ++ia) yv[ia][kb_] = rhs[ia + 2 * kb_];
-        }
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-          for (int bb = 0; bb < 2; ++bb) yv[a][bb] = __shfl_sync(0xffffffffu, yv[a][bb], 0);
-        __syncwarp();
-        if (lane == 0) {
-#pragma unroll
-          for (int ia = 0; ia < 2; ++ia)
-#pragma unroll
-            for (int kb_ = 0; kb_ < 2; ++kb_)
-              if (ia < ib && kb_ < kb) YY(i0 + ia, k0 + kb_) = yv[ia][kb_];
-        }
-        // rows above the block, same columns: Y[i][k] -= S[i][i0..] y
-        for (int i = lane; i < i0; i += 32) {
-          const T s0 = SS(i, i0), s1 = (ib == 2) ? SS(i, i0 + 1) : T(0);
-          YY(i, k0) -= s0 * yv[0][0] + s1 * yv[1][0];
-          if (kb == 2) YY(i, k0 + 1) -= s0 * yv[0][1] + s1 * yv[1][1];
-        }
-      }
-      __syncthreads();
-    }
-  }
-  if (mode >= 1) {
-    for (int e = threadIdx.x; e < n1 * n2; e += blockDim.x)
-      Yg[e % n1 + (size_t)(e / n1) * ldw] = Y[e % n1 + (e / n1) * ldy];
   }
 #undef SS
 #undef RR
-#undef YY
 }
 
 template <typename T>
 fde_status leaf_trsyl(const T* S, const T* R, int lmax, const int* d_lo_x, const int* d_n_x, int nx,
                       const int* d_lo_y, const int* d_n_y, int ny, T* W, int ldw, cudaStream_t st, double flops) {
-  const size_t tables = 4 * (size_t)lmax * sizeof(int);
-  const size_t mat = (size_t)(lmax | 1) * lmax * sizeof(T);  // one padded lmax x lmax block
-  const size_t limit = 220 * 1024;
-  const int mode = (tables + 3 * mat <= limit) ? 2 : (tables + mat <= limit) ? 1 : 0;
-  const size_t smem = tables + (mode == 2 ? 3 * mat : mode == 1 ? mat : 0);
+  if (lmax > 32 * kMaxRowWarps - kMaxRowWarps) {
+    set_error("leaf_trsyl: leaf size %d above %d", lmax, 32 * kMaxRowWarps - kMaxRowWarps);
+    return FDE_ERR_ARG;
+  }
+  const int warps = (lmax + 30) / 31 < kMaxRowWarps ? (lmax + 30) / 31 : kMaxRowWarps;
+  // largest panel total: warp w has at most 32 w rows below its block
+  int panel_elems = 0;
+  for (int w = 0; w < warps; ++w) panel_elems += 33 * (32 * w < lmax ? 32 * w : lmax);
+  const size_t base = ((size_t)(warps + 1) * 2 * lmax + (size_t)warps * 32 * 33) * sizeof(T) +
+                      3 * (size_t)lmax * sizeof(int);
+  const size_t with_panel = base + (size_t)panel_elems * sizeof(T);
+  const size_t limit = 224 * 1024;
+  const int use_panel = with_panel <= limit ? 1 : 0;
+  const size_t smem = use_panel ? with_panel : base;
   static bool attr_set[2] = {false, false};
   if (!attr_set[sizeof(T) == 8]) {
     FDE_CUDA(cudaFuncSetAttribute(trsyl_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
     attr_set[sizeof(T) == 8] = true;
   }
   ProfScope ps(sizeof(T) == 4 ? "trsyl32" : "trsyl64", st, flops, 1);
-  trsyl_kernel<T><<<nx * ny, kWarps * 32, smem, st>>>(S, R, lmax, d_lo_x, d_n_x, nx, d_lo_y, d_n_y, W, ldw, mode);
+  trsyl_kernel<T><<<nx * ny, warps * 32, smem, st>>>(S, R, lmax, d_lo_x, d_n_x, nx, d_lo_y, d_n_y, W, ldw, use_panel,
+                                                     panel_elems);
   FDE_LAUNCH("trsyl_kernel");
   return FDE_OK;
 }

@@ -112,116 +112,98 @@ __device__ __forceinline__ uint32_t sw_off(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((c >> 2) ^ (r & 7)) & 7) << 4) + ((c & 3) << 2));
 }
 
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 
 constexpr int kLoaders = 256;              // 8 warps: global -> shared, then the epilogue
 constexpr int kThreads = kLoaders + 32;    // + 1 warp that issues the MMAs
-constexpr int kMaxStages = 8;
+constexpr int kMaxSlots = 8;               // MMA slots (TF32 hi / lo tiles)
+constexpr int kRaw = 3;                    // raw FP32 stages filled by cp.async
 
-// One loader thread's share of an R x 32 operand tile: 4 rows x 4 k blocks
-// (R / 128 of them; R = 64 leaves the upper half of the threads idle).
-// Block b of thread t: kq = (t + 256 b) & 7, row group (t + 256 b) >> 3, so a
-// quarter warp covers one 4-row group across all eight 16-byte chunks (no
-// bank conflicts on the swizzled stores) and reads either 128 contiguous
-// bytes of a k-contiguous row or 64 contiguous bytes of a row-contiguous column.
-template <int R>
-struct OpRegs {
-  static constexpr int NB = R >= 128 ? R / 128 : 1;
-  float v[NB][16];  // v[b][r * 4 + c]: row 4 rg + r, k 4 kq + c
-};
-
-// element (row, k) of the operand tile: KCONTIG -> X[k + row * ld];
-// otherwise X[row + col(k)], col(k) = k * ld or the two-level panel address.
-template <int R, bool KCONTIG>
-__device__ __forceinline__ void tile_load(OpRegs<R>& o, const float* __restrict__ X, int ld, int kblk,
-                                          long long kstr, int row0, int nrows, int k0, int K, bool vec) {
-  const int t = threadIdx.x;
-#pragma unroll
-  for (int b = 0; b < OpRegs<R>::NB; ++b) {
-    const int blk = t + kLoaders * b;
-    float* v = o.v[b];
-    if (blk >= 2 * R) break;
-    const int kq = blk & 7, rg = blk >> 3;
-    const int row = row0 + 4 * rg, k = k0 + 4 * kq;
-    if (KCONTIG) {
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const float* p = X + (size_t)(row + r) * ld + k;
-        if (row + r < nrows) {
-          if (vec && k + 3 < K) {
-            const float4 q = ldg4(p);
-            v[r * 4 + 0] = q.x;
-            v[r * 4 + 1] = q.y;
-            v[r * 4 + 2] = q.z;
-            v[r * 4 + 3] = q.w;
-          } else {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) v[r * 4 + c] = (k + c < K) ? __ldg(p + c) : 0.f;
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) v[r * 4 + c] = 0.f;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int kk = k + c;
-        if (kk < K) {
-          const long long col = kblk ? (long long)(kk / kblk) * kstr + (long long)(kk % kblk) * ld : (long long)kk * ld;
-          const float* p = X + col + row;
-          if (vec && row + 3 < nrows) {
-            const float4 q = ldg4(p);
-            v[0 * 4 + c] = q.x;
-            v[1 * 4 + c] = q.y;
-            v[2 * 4 + c] = q.z;
-            v[3 * 4 + c] = q.w;
-          } else {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) v[r * 4 + c] = (row + r < nrows) ? __ldg(p + r) : 0.f;
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < 4; ++r) v[r * 4 + c] = 0.f;
-        }
-      }
-    }
-  }
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0) : "memory");
 }
-
-// Round to TF32 and store (hi, and the TF32-rounded remainder lo in split mode).
-template <int R>
-__device__ __forceinline__ void tile_store(const OpRegs<R>& o, uint8_t* hi, uint8_t* lo, bool split) {
-  const int t = threadIdx.x;
-#pragma unroll
-  for (int b = 0; b < OpRegs<R>::NB; ++b) {
-    const int blk = t + kLoaders * b;
-    if (blk >= 2 * R) break;
-    const int kq = blk & 7, rg = blk >> 3;
-    const float* v = o.v[b];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const uint32_t off = sw_off(4 * rg + r, 4 * kq);
-      float4 h;
-      h.x = to_tf32(v[r * 4 + 0]);
-      h.y = to_tf32(v[r * 4 + 1]);
-      h.z = to_tf32(v[r * 4 + 2]);
-      h.w = to_tf32(v[r * 4 + 3]);
-      *reinterpret_cast<float4*>(hi + off) = h;
-      if (split) {
-        float4 l;
-        l.x = to_tf32(v[r * 4 + 0] - h.x);
-        l.y = to_tf32(v[r * 4 + 1] - h.y);
-        l.z = to_tf32(v[r * 4 + 2] - h.z);
-        l.w = to_tf32(v[r * 4 + 3] - h.w);
-        *reinterpret_cast<float4*>(lo + off) = l;
-      }
-    }
-  }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
-
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// barrier of the loader warps only (named barrier 1)
+__device__ __forceinline__ void loader_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kLoaders) : "memory"); }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Asynchronous copy of an R x 32 tile of op(X) (element (row, k): X[k + row*ld]
+// when KCONTIG, else X[row + col(k)], col(k) = k*ld or the two-level panel
+// address) into the swizzled K-major layout at dst; out-of-range elements are
+// zero-filled.
+//  - row-contiguous X: warp w owns k = 4w + (lane >> 3); lanes (lane & 7) take 8
+//    consecutive rows, so one instruction reads 4 columns x 32 contiguous bytes
+//    and writes 32 distinct banks; the column address is computed once.
+//  - k-contiguous X: 8 lanes read one row's 128 bytes as 16-byte copies.
+template <int R, bool KCONTIG>
+__device__ __forceinline__ void tile_copy(uint32_t dst, const float* __restrict__ X, int ld, int kblk, long long kstr,
+                                          int row0, int nrows, int k0, int K, bool vec) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!KCONTIG) {
+    const int c = 4 * w + (lane >> 3), kk = k0 + c, rr = lane & 7;
+    const bool kin = kk < K;
+    const long long col =
+        !kin ? 0 : kblk ? (long long)(kk / kblk) * kstr + (long long)(kk % kblk) * ld : (long long)kk * ld;
+    const float* base = X + col + row0;
+#pragma unroll
+    for (int j = 0; j < R / 8; ++j) {
+      const int r = 8 * j + rr;
+      const bool ok = kin && row0 + r < nrows;
+      cp_async4(dst + sw_off(r, c), ok ? base + r : X, ok);
+    }
+  } else {
+    const int kq = lane & 7, kk = k0 + 4 * kq;
+#pragma unroll
+    for (int j = 0; j < R / 32; ++j) {
+      const int r = (R / 8) * w + 4 * j + (lane >> 3);
+      const int grow = row0 + r;
+      const float* p = X + (size_t)grow * ld + kk;
+      const uint32_t o = dst + sw_off(r, 4 * kq);
+      if (vec && grow < nrows && kk + 3 < K) {
+        cp_async16(o, p);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const bool ok = grow < nrows && kk + c < K;
+          cp_async4(o + 4 * c, ok ? p + c : X, ok);
+        }
+      }
+    }
+  }
+}
+
+// Raw FP32 tile -> TF32 hi (and the TF32-rounded remainder lo in split mode),
+// same swizzled offsets; thread t converts 16-byte chunks t, t + 256, ...
+template <int R>
+__device__ __forceinline__ void tile_convert(const uint8_t* raw, uint8_t* hi, uint8_t* lo, bool split) {
+#pragma unroll
+  for (int i = 0; i < R / 32; ++i) {
+    const int ch = threadIdx.x + kLoaders * i, r = ch >> 3, kq = ch & 7;
+    const uint32_t off = sw_off(r, 4 * kq);
+    const float4 v = *reinterpret_cast<const float4*>(raw + off);
+    float4 h;
+    h.x = to_tf32(v.x);
+    h.y = to_tf32(v.y);
+    h.z = to_tf32(v.z);
+    h.w = to_tf32(v.w);
+    *reinterpret_cast<float4*>(hi + off) = h;
+    if (split) {
+      float4 l;
+      l.x = to_tf32(v.x - h.x);
+      l.y = to_tf32(v.y - h.y);
+      l.z = to_tf32(v.z - h.z);
+      l.w = to_tf32(v.w - h.w);
+      *reinterpret_cast<float4*>(lo + off) = l;
+    }
+  }
 }
 
 // Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = BN.
@@ -230,19 +212,29 @@ __host__ __device__ constexpr uint32_t idesc_tf32_n() {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-// Warp-specialised batched GEMM.  Warps 0-7 load op(A) (128 x 32) and op(B)
-// (BN x 32) tiles with coalesced vector loads, two tiles in flight per thread,
-// round them to TF32 (hi / lo) into a ring of `stages` shared-memory slots and
-// arrive on that slot's `full` barrier; warp 8 waits on `full`, issues the
-// tcgen05 MMAs of the slot and commits them to the slot's `empty` barrier,
-// which the loaders wait on before refilling it.  The accumulator lives in
-// TMEM (BN columns); warps 0-7 read it back (lane quarter = warp % 4, column
-// half = warp / 4) and write C.  Every wait is bounded: on expiry the kernel
-// raises g_wait_timeout, skips the epilogue and still frees its TMEM.
+template <int BN>
+__host__ __device__ constexpr int raw_bytes() {
+  return (BM + BN) * BK * 4;
+}
+
+// Warp-specialised batched GEMM.
+//  - Warps 0-7 (loaders) copy the op(A) (128 x 32) and op(B) (BN x 32) tiles of
+//    k-tile kt + 2 with cp.async into a ring of kRaw raw FP32 stages, wait for
+//    tile kt (cp.async.wait_group + a barrier of the loader warps), round it to
+//    TF32 (hi, and lo = remainder in split mode) into MMA slot kt % mslots
+//    once the `empty` barrier of that slot says its MMAs are done, and arrive
+//    on the slot's `full` barrier.
+//  - Warp 8 waits on `full`, issues the tcgen05 MMAs of the slot (one elected
+//    thread) and commits them to `empty`.
+//  - The accumulator lives in TMEM; warps 0-7 read it back (lane quarter =
+//    warp % 4, column half = warp / 4) and write C.
+// Every mbarrier wait is bounded: on expiry the kernel raises g_wait_timeout,
+// keeps the loop structure (so no barrier is left waiting), skips the
+// epilogue and still frees its TMEM.
 // grid (ceil(m / 128), ceil(n / BN), batch), kThreads threads.
 template <int BN, bool TA, bool TB>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_gemm_kernel(const GemmDesc<float>* __restrict__ descs, float alpha, float beta, int split, int stages,
+    tc_gemm_kernel(const GemmDesc<float>* __restrict__ descs, float alpha, float beta, int split, int mslots,
                    int vec_a, int vec_b) {
   const GemmDesc<float> d = descs[blockIdx.z];
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -252,15 +244,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t base_u32 = smem_u32(smem_raw);
   const uint32_t pad = ((base_u32 + 1023u) & ~1023u) - base_u32;
   uint8_t* sm = smem_raw + pad;  // 1024-byte aligned
-  // slot layout: A_hi | B_hi | A_lo | B_lo (lo only in split mode)
+  // MMA slot: A_hi | B_hi | A_lo | B_lo (lo only in split mode); raw stages after the slots
   const int slot_bytes = (A_BYTES + B_BYTES) * (split ? 2 : 1);
-  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
+  uint8_t* raw = sm + (size_t)mslots * slot_bytes;
+  __shared__ __align__(8) uint64_t full_bar[kMaxSlots], empty_bar[kMaxSlots], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < stages; ++s) {
-      mbar_init(smem_u32(&full_bar[s]), kLoaders);
+    for (int s = 0; s < mslots; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), kLoaders / 32);  // one arrival per loader warp
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     mbar_init(smem_u32(&done_bar), 1);
@@ -283,41 +276,48 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp < kLoaders / 32) {
     // ---------------- loaders
-    OpRegs<BM> ra[2];
-    OpRegs<BN> rb[2];
     const int a_kblk = TA ? 0 : d.kblk, b_kblk = TB ? d.kblk : 0;
-    auto load = [&](int kt, int i) {
-      tile_load<BM, TA>(ra[i], d.A, d.lda, a_kblk, d.kstr, m0, d.m, kt * BK, d.k, vec_a != 0);
-      tile_load<BN, !TB>(rb[i], d.B, d.ldb, b_kblk, d.kstr, n0, d.n, kt * BK, d.k, vec_b != 0);
+    auto issue = [&](int kt) {
+      const uint32_t dst = smem_u32(raw + (size_t)(kt % kRaw) * raw_bytes<BN>());
+      tile_copy<BM, TA>(dst, d.A, d.lda, a_kblk, d.kstr, m0, d.m, kt * BK, d.k, vec_a != 0);
+      tile_copy<BN, !TB>(dst + A_BYTES, d.B, d.ldb, b_kblk, d.kstr, n0, d.n, kt * BK, d.k, vec_b != 0);
     };
-    auto put = [&](int kt, int i) -> bool {
-      const int s = kt % stages;
-      if (kt >= stages && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)((kt / stages - 1) & 1))) return false;
-      uint8_t* slot = sm + (size_t)s * slot_bytes;
-      tile_store<BM>(ra[i], slot, slot + A_BYTES + B_BYTES, split != 0);
-      tile_store<BN>(rb[i], slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
-      fence_proxy_async();
-      mbar_arrive(smem_u32(&full_bar[s]));
-      return true;
-    };
-    bool ok = true;
-    if (nk > 0) load(0, 0);
-    if (nk > 1) load(1, 1);
-    for (int kt = 0; kt < nk && ok; kt += 2) {
-      ok = put(kt, 0);
-      if (ok && kt + 2 < nk) load(kt + 2, 0);
-      if (ok && kt + 1 < nk) {
-        ok = put(kt + 1, 1);
-        if (ok && kt + 3 < nk) load(kt + 3, 1);
-      }
+#pragma unroll
+    for (int kt = 0; kt < kRaw - 1; ++kt) {
+      if (kt < nk) issue(kt);
+      cp_async_commit();
     }
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+      cp_async_wait<kRaw - 2>();  // this thread's copies of tile kt have landed
+      loader_sync();              // everyone's have; raw stage of tile kt-1 is free
+      if (kt + kRaw - 1 < nk) issue(kt + kRaw - 1);
+      cp_async_commit();
+      const int ms = kt % mslots;
+      if (kt >= mslots) {
+        // one lane per warp polls the slot's `empty` barrier
+        int got = 1;
+        if (lane == 0 && ok) got = mbar_wait(smem_u32(&empty_bar[ms]), (uint32_t)((kt / mslots - 1) & 1)) ? 1 : 0;
+        ok = ok && __shfl_sync(0xffffffffu, got, 0) != 0;
+      }
+      if (ok) {
+        const uint8_t* rs = raw + (size_t)(kt % kRaw) * raw_bytes<BN>();
+        uint8_t* slot = sm + (size_t)ms * slot_bytes;
+        tile_convert<BM>(rs, slot, slot + A_BYTES + B_BYTES, split != 0);
+        tile_convert<BN>(rs + A_BYTES, slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
+        fence_proxy_async();  // this thread's tiles -> visible to the tensor core
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&full_bar[ms]));
+    }
+    cp_async_wait<0>();
     if (!ok) s_fail = 1;
   } else if (lane == 0) {
     // ---------------- MMA issuer
     bool ok = true;
     for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % stages;
-      if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((kt / stages) & 1))) {
+      const int s = kt % mslots;
+      if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((kt / mslots) & 1))) {
         ok = false;
         break;
       }
@@ -397,9 +397,9 @@ constexpr size_t slot_bytes(int split) {
 constexpr size_t kSmemBudget = 227 * 1024 - 2048;
 
 template <int BN>
-int stages_for(int split) {
-  int s = (int)(kSmemBudget / slot_bytes<BN>(split));
-  return s > kMaxStages ? kMaxStages : s;
+int mslots_for(int split) {
+  int s = (int)((kSmemBudget - (size_t)kRaw * raw_bytes<BN>()) / slot_bytes<BN>(split));
+  return s > kMaxSlots ? kMaxSlots : s;
 }
 
 }  // namespace tc
@@ -447,8 +447,8 @@ fde_status tc_prepare() {
 
 template <int BN>
 static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t st) {
-  const int stages = tc::stages_for<BN>(split);
-  const size_t smem = 1024 + (size_t)stages * tc::slot_bytes<BN>(split);
+  const int mslots = tc::mslots_for<BN>(split);
+  const size_t smem = 1024 + (size_t)mslots * tc::slot_bytes<BN>(split) + (size_t)tc::kRaw * tc::raw_bytes<BN>();
   const int which = (b.ta ? 2 : 0) + (b.tb ? 1 : 0);
   auto kern = (which == 0) ? tc::tc_gemm_kernel<BN, false, false>
               : (which == 1) ? tc::tc_gemm_kernel<BN, false, true>
@@ -458,7 +458,7 @@ static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t s
     const int nz = b.batch - z0 < 65535 ? b.batch - z0 : 65535;
     dim3 grid(ceil_div(b.max_m, tc::BM), ceil_div(b.max_n, BN), nz);
     ProfScope ps("gemm32tc", st, z0 == 0 ? b.flops : 0.0, 1);
-    kern<<<grid, tc::kThreads, smem, st>>>(b.d_desc + z0, b.alpha, b.beta, split, stages, b.vec_a ? 1 : 0,
+    kern<<<grid, tc::kThreads, smem, st>>>(b.d_desc + z0, b.alpha, b.beta, split, mslots, b.vec_a ? 1 : 0,
                                            b.vec_b ? 1 : 0);
     FDE_LAUNCH("tc_gemm_kernel");
   }

@@ -59,7 +59,10 @@ def test_structured_residual(lib, N, leaf):
 
 @pytest.mark.parametrize("prec", [B.FDE_FP64, B.FDE_FP32_REFINE])
 @pytest.mark.parametrize("N,leaf,alpha", [(16, 8, (1.3, 1.7)), (100, 16, (1.5, 1.2)), (256, 64, (1.3, 1.7)),
-                                          (129, 32, (1.9, 1.1))])
+                                          (129, 32, (1.9, 1.1)),
+                                          # leaves of 128 and 256 rows: several row and column blocks
+                                          # in the leaf Sylvester solve, complex Schur pairs on both sides
+                                          (512, 128, (1.5, 1.5)), (512, 256, (1.2, 1.8))])
 def test_sylv_step_vs_oracle(lib, prec, N, leaf, alpha):
     w = I.fd2d(N=N, alpha=alpha, steps=50, leaf=leaf)
     P = Pair(lib, w, prec)
