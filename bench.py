@@ -146,6 +146,12 @@ def family_roofline(fam, ms, launches, work, kind, peaks):
         r = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
              "peak_source": ("measured" if "bf16_tflops_sustained" in peaks else "fallback")
              + " sustained bf16 x 1.1/2.25 (tf32)"}
+    elif fam == "fft_df":
+        achieved = work_per_launch / per_launch_s / 1e12
+        peak = FP32_SIMT_PEAK_TFLOPS / DF_OPS_PER_FLOP
+        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": "derived: FP32 SIMT peak (152 SMs x 128 lanes x 2 x 2070 MHz) / %.1f FP32 ops per "
+                            "double-float FFT flop" % DF_OPS_PER_FLOP}
     else:
         achieved = work_per_launch / per_launch_s / 1e12
         fp32 = fam.endswith("32")
@@ -158,7 +164,10 @@ def family_roofline(fam, ms, launches, work, kind, peaks):
     return r
 
 
-FAMILIES = ["gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply", "transpose", "refine", "fadi_axpy"]
+FAMILIES = ["gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply", "fft_df", "transpose", "refine",
+            "fadi_axpy"]
+# double-float FFT: a radix-2 butterfly (10 real flops) costs ~148 FP32 operations
+DF_OPS_PER_FLOP = 14.8
 
 
 def roofline(lib, N):

@@ -1,0 +1,178 @@
+// Double-float FFT for the incremental FP64-grade residual.
+//
+// A double-float number is an unevaluated sum hi + lo of two FP32 values with
+// |lo| <= ulp(hi) / 2.  The error-free transformations are the classical ones:
+// the two-sum of Knuth (TAOCP vol. 2, §4.2.2), the fast two-sum of Dekker
+// ("A floating-point technique for extending the available precision", 1971)
+// for |a| >= |b|, and the two-product through a fused multiply-add.  Addition
+// uses the accurate variant (both components two-summed), multiplication
+// folds the cross terms into the FMA error term.
+#include "fft_df.cuh"
+
+namespace fde {
+
+namespace {
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return make_float2(s, e);
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+  const float s = a + b;
+  const float e = b - (s - a);
+  return make_float2(s, e);
+}
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+  float2 s = two_sum(x.x, y.x);
+  const float2 t = two_sum(x.y, y.y);
+  s.y += t.x;
+  s = fast_two_sum(s.x, s.y);
+  s.y += t.y;
+  return fast_two_sum(s.x, s.y);
+}
+__device__ __forceinline__ float2 df_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
+  const float p = x.x * y.x;
+  float e = fmaf(x.x, y.x, -p);
+  e = fmaf(x.x, y.y, e);
+  e = fmaf(x.y, y.x, e);
+  return fast_two_sum(p, e);
+}
+// complex double-float: x = re.hi, y = re.lo, z = im.hi, w = im.lo
+__device__ __forceinline__ float4 c_mul(float4 a, float4 b) {
+  const float2 ar = make_float2(a.x, a.y), ai = make_float2(a.z, a.w);
+  const float2 br = make_float2(b.x, b.y), bi = make_float2(b.z, b.w);
+  const float2 re = df_add(df_mul(ar, br), df_neg(df_mul(ai, bi)));
+  const float2 im = df_add(df_mul(ar, bi), df_mul(ai, br));
+  return make_float4(re.x, re.y, im.x, im.y);
+}
+__device__ __forceinline__ float4 c_add(float4 a, float4 b) {
+  const float2 re = df_add(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  const float2 im = df_add(make_float2(a.z, a.w), make_float2(b.z, b.w));
+  return make_float4(re.x, re.y, im.x, im.y);
+}
+__device__ __forceinline__ float4 c_sub(float4 a, float4 b) {
+  const float2 re = df_add(make_float2(a.x, a.y), make_float2(-b.x, -b.y));
+  const float2 im = df_add(make_float2(a.z, a.w), make_float2(-b.z, -b.w));
+  return make_float4(re.x, re.y, im.x, im.y);
+}
+__device__ __forceinline__ float4 c_conj(float4 a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+__device__ __forceinline__ float2 split_double(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+// in-place radix-2 decimation-in-time FFT on buf (input in bit-reversed
+// order), twiddles tw[k] = e^{-2πik/P} (conjugated for the inverse)
+__device__ void fft_dit_df(float4* buf, int P, int logP, const float4* __restrict__ tw, bool inverse) {
+  for (int s = 1; s <= logP; ++s) {
+    const int half = 1 << (s - 1), tstride = P >> s;
+    for (int b = threadIdx.x; b < (P >> 1); b += blockDim.x) {
+      const int grp = b >> (s - 1), j = b & (half - 1);
+      const int i0 = (grp << s) + j, i1 = i0 + half;
+      float4 w = tw[j * tstride];
+      if (inverse) w = c_conj(w);
+      const float4 u = buf[i0];
+      const float4 v = (s == 1) ? buf[i1] : c_mul(buf[i1], w);
+      buf[i0] = c_add(u, v);
+      buf[i1] = c_sub(u, v);
+    }
+    __syncthreads();
+  }
+}
+
+// Columns j0 = 2b, j1 = 2b + 1 share one complex transform (x_0 + i x_1):
+//   (T x)_i  = -(g * x)[i+1],   (Tᵀx)_i = -(g ⋆ x)[i-1]   (correlation: conj(ĝ))
+__global__ void __launch_bounds__(1024) fd_fft_sub_df_kernel(const float* __restrict__ X, long long xs, long long xc,
+                                                            int ncols, double* R, long long rs, long long rc,
+                                                            const float4* __restrict__ Ghat,
+                                                            const float4* __restrict__ tw, int P, int logP,
+                                                            const double* __restrict__ dp,
+                                                            const double* __restrict__ dm, double c, double shift,
+                                                            int N, float4* __restrict__ scratch) {
+  extern __shared__ float4 buf[];
+  const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
+  const bool has1 = j1 < ncols;
+  const unsigned sh = 32 - logP;
+  for (int n = threadIdx.x; n < P; n += blockDim.x) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n < N) {
+      v.x = X[n * xs + j0 * xc];
+      if (has1) v.z = X[n * xs + j1 * xc];
+    }
+    buf[__brev(n) >> sh] = v;
+  }
+  __syncthreads();
+  fft_dit_df(buf, P, logP, tw, false);
+  float4* Xh = scratch + (size_t)blockIdx.x * P;
+  for (int k = threadIdx.x; k < P; k += blockDim.x) Xh[k] = buf[k];
+  __syncthreads();
+  for (int k = threadIdx.x; k < P; k += blockDim.x) buf[__brev(k) >> sh] = c_mul(Xh[k], Ghat[k]);
+  __syncthreads();
+  fft_dit_df(buf, P, logP, tw, true);
+  const double invP = 1.0 / P;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float4 t = buf[i + 1];
+    const double conv0 = (double)t.x + (double)t.y, conv1 = (double)t.z + (double)t.w;
+    const double x0 = X[i * xs + j0 * xc];
+    R[i * rs + j0 * rc] -= shift * x0 - c * dp[i] * conv0 * invP;
+    if (has1) {
+      const double x1 = X[i * xs + j1 * xc];
+      R[i * rs + j1 * rc] -= shift * x1 - c * dp[i] * conv1 * invP;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < P; k += blockDim.x) buf[__brev(k) >> sh] = c_mul(Xh[k], c_conj(Ghat[k]));
+  __syncthreads();
+  fft_dit_df(buf, P, logP, tw, true);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float4 t = buf[(i - 1 + P) & (P - 1)];
+    const double conv0 = (double)t.x + (double)t.y, conv1 = (double)t.z + (double)t.w;
+    R[i * rs + j0 * rc] += c * dm[i] * conv0 * invP;
+    if (has1) R[i * rs + j1 * rc] += c * dm[i] * conv1 * invP;
+  }
+}
+
+__global__ void complex_to_df_kernel(const double2* __restrict__ in, float4* __restrict__ out, int n) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const double2 v = in[k];
+    const float2 re = split_double(v.x), im = split_double(v.y);
+    out[k] = make_float4(re.x, re.y, im.x, im.y);
+  }
+}
+
+}  // namespace
+
+fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols, double* R, long long rs,
+                           long long rc, const float4* Ghat, const float4* tw, int P, int logP, const double* dp,
+                           const double* dm, double c, double shift, int N, float4* scratch, cudaStream_t st,
+                           double flops) {
+  if (ncols <= 0 || N <= 0) return FDE_OK;
+  if (P > 8192 || P < 2 * N) {
+    set_error("fd_apply_sub_df: transform length %d outside [2N, 8192]", P);
+    return FDE_ERR_ARG;
+  }
+  const size_t smem = (size_t)P * sizeof(float4);
+  static bool attr = false;
+  if (!attr) {
+    FDE_CUDA(cudaFuncSetAttribute(fd_fft_sub_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(8192 * sizeof(float4))));
+    attr = true;
+  }
+  ProfScope ps("fft_df", st, flops, 1);
+  fd_fft_sub_df_kernel<<<(ncols + 1) / 2, 1024, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, dp, dm,
+                                                            c, shift, N, scratch);
+  FDE_LAUNCH("fd_fft_sub_df_kernel");
+  return FDE_OK;
+}
+
+fde_status complex_to_df(const double2* in, float4* out, int n, cudaStream_t st) {
+  if (n <= 0) return FDE_OK;
+  complex_to_df_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+  FDE_LAUNCH("complex_to_df_kernel");
+  return FDE_OK;
+}
+
+}  // namespace fde

@@ -1,0 +1,25 @@
+// Incremental structured residual in double-float arithmetic.
+#pragma once
+#include "common.cuh"
+
+namespace fde {
+
+// R(i, j) -= (A x_j)(i), i < N, j < ncols, for the columns x_j of a float
+// matrix (x_j(i) = X[i * xs + j * xc]; R(i, j) = R[i * rs + j * rc]), with
+//   A = shift I + c (D_+ T + D_- Tᵀ),   T = -[g_{i-j+1}]   (§2.2.1, Eq. (toeplitz_FD)).
+// The Toeplitz products are evaluated by FFT of length P = 2^logP >= 2N in
+// double-float arithmetic (pairs of FP32 numbers, ~48 significant bits) on
+// the FP32 pipe; the result is accumulated into R in FP64.  Meant for small
+// updates x = δX of an iterative refinement, whose error budget scales with
+// ||δX||.  Ghat / tw: spectrum of g_0..g_N and twiddles e^{-2πik/P}, k < P/2,
+// as double-float complex (x = re.hi, y = re.lo, z = im.hi, w = im.lo).
+// scratch: ceil(ncols/2) * P float4.
+fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols, double* R, long long rs,
+                           long long rc, const float4* Ghat, const float4* tw, int P, int logP, const double* dp,
+                           const double* dm, double c, double shift, int N, float4* scratch, cudaStream_t st,
+                           double flops = 0.0);
+
+// out[k] = double-float split of the complex value in[k]
+fde_status complex_to_df(const double2* in, float4* out, int n, cudaStream_t st);
+
+}  // namespace fde

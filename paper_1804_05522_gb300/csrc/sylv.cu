@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "fft_df.cuh"
 #include "hodlr_internal.cuh"
 #include "schur.cuh"
 
@@ -421,6 +422,8 @@ struct sylv_s {
   // residual
   int P = 0, logP = 0;
   double2 *tw = nullptr, *GhX = nullptr, *GhY = nullptr, *fft_scratch = nullptr;
+  float4 *tw_df = nullptr, *GhX_df = nullptr, *GhY_df = nullptr;  // double-float copies
+  bool resid_df = false;              // later sweeps update R in double-float (FP32 inner solver)
   double *R = nullptr, *Xt = nullptr, *Yt = nullptr, *X64 = nullptr, *C64 = nullptr;
   double* acc = nullptr;              // device accumulators
   int* d_bad = nullptr;
@@ -896,10 +899,28 @@ static fde_status inner_solve(sylv_s* S, Inner<T>& in, cudaStream_t st) {
   return FDE_OK;
 }
 
-// One refinement sweep: Cin = (T) R ; inner solve ; X64 += X_T ; R = C - A(X64).
+// R -= A_x δ + δ A_yᵀ for the FP32 update δ (the inner solution), both
+// directions read δ in place through strides (double-float FFT).
+static fde_status residual_update_df(sylv_s* S, const float* d, cudaStream_t st) {
+  hodlr_s* ax = S->ax;
+  hodlr_s* ay = S->ay;
+  const int N = S->N;
+  float4* scr = reinterpret_cast<float4*>(S->fft_scratch);
+  FDE_TRY(fd_apply_sub_df(d, 1, N, N, S->R, 1, N, S->GhX_df, S->tw_df, S->P, S->logP, ax->dp, ax->dm, ax->c,
+                          ax->p.shift, N, scr, st, S->fft_flops));
+  FDE_TRY(fd_apply_sub_df(d, N, 1, N, S->R, N, 1, S->GhY_df, S->tw_df, S->P, S->logP, ay->dp, ay->dm, ay->c,
+                          ay->p.shift, N, scr, st, S->fft_flops));
+  return FDE_OK;
+}
+
+// One refinement sweep: Cin = (T) R ; inner solve ; X64 += X_T ; then either
+// R = C - A(X64) exactly in FP64, or (incremental, FP32 inner solver only)
+// R -= A(δ) in double-float: the error of that update scales with ||δ||, which
+// after the first sweep of a step is ~1e-3 of ||X|| or less.
 // acc[0] = ||δ||², acc[1] = ||X||², acc[2] = ||R||² of this sweep.
 template <typename T>
-static fde_status sweep(sylv_s* S, Inner<T>& in, const double* C, double* X64, cudaStream_t st) {
+static fde_status sweep(sylv_s* S, Inner<T>& in, const double* C, double* X64, cudaStream_t st,
+                        bool incremental = false) {
   const size_t NN = (size_t)S->N * S->N;
   if (sizeof(T) == sizeof(double)) {
     FDE_CUDA(cudaMemcpyAsync((void*)in.Cin, S->R, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -913,7 +934,10 @@ static fde_status sweep(sylv_s* S, Inner<T>& in, const double* C, double* X64, c
     refine_update_kernel<T><<<grid_for(NN), 256, 0, st>>>(X64, in.X, NN, S->acc);
     FDE_LAUNCH("refine_update_kernel");
   }
-  FDE_TRY(residual(S, C, X64, S->R, st));
+  if (incremental && sizeof(T) == sizeof(float))
+    FDE_TRY(residual_update_df(S, reinterpret_cast<const float*>(in.X), st));
+  else
+    FDE_TRY(residual(S, C, X64, S->R, st));
   sumsq_kernel<<<grid_for(NN), 256, 0, st>>>(S->R, NN, S->acc + 2);
   FDE_LAUNCH("sumsq_kernel");
   return FDE_OK;
@@ -961,11 +985,12 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
   bool converged = fixed;
   double a[8];
   double prev_d2 = -1.0;
+  bool incr_ok = S->resid_df;  // the first sweep of a step always recomputes R exactly
   for (int sw = 0; sw < nsw; ++sw) {
     if (S->prec == FDE_FP64)
       FDE_TRY(sweep<double>(S, S->in64, C, X, st));
     else
-      FDE_TRY(sweep<float>(S, S->in32, C, X, st));
+      FDE_TRY(sweep<float>(S, S->in32, C, X, st, incr_ok && sw > 0));
     ++done;
     if (fixed) continue;
     FDE_TRY(read_acc(S, a, 8, st));
@@ -982,6 +1007,8 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
       const double rest = rho / (1.0 - rho);
       stop = a[0] * rest * rest <= tol2;
     }
+    // incremental residuals only while the sweeps contract well (rho < 0.1)
+    if (prev_d2 > 0.0 && a[0] > 0.01 * prev_d2) incr_ok = false;
     prev_d2 = a[0];
     if (stop) {
       converged = true;
@@ -1209,6 +1236,16 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
   FDE_LAUNCH("ghat_kernel");
   ghat_kernel<<<1, 1024, smem, st>>>(ay->g, N, S->tw, S->P, S->logP, S->GhY);
   FDE_LAUNCH("ghat_kernel");
+  if (prec != FDE_FP64) {
+    const char* rm = getenv("FDE_RESID");
+    S->resid_df = !(rm && strcmp(rm, "fp64") == 0);
+    FDE_TRY(pool.alloc(&S->tw_df, S->P / 2));
+    FDE_TRY(pool.alloc(&S->GhX_df, S->P));
+    FDE_TRY(pool.alloc(&S->GhY_df, S->P));
+    FDE_TRY(complex_to_df(S->tw, S->tw_df, S->P / 2, st));
+    FDE_TRY(complex_to_df(S->GhX, S->GhX_df, S->P, st));
+    FDE_TRY(complex_to_df(S->GhY, S->GhY_df, S->P, st));
+  }
   const size_t NN = (size_t)N * N;
   FDE_TRY(pool.alloc(&S->fft_scratch, (size_t)((N + 1) / 2) * S->P));
   FDE_TRY(pool.alloc(&S->R, NN));

@@ -158,3 +158,41 @@ def test_sylv_step_both_fadi_forms(lib, monkeypatch, prec, mode):
         assert _relerr(_host(Xd, N, N), Xo) <= (1e-8 if prec == B.FDE_FP32_REFINE else 1e-10)
     finally:
         P.close()
+
+
+@pytest.mark.parametrize("N,leaf,alpha", [(256, 64, (1.3, 1.7)), (1000, 128, (1.5, 1.5))])
+def test_incremental_df_residual_matches_fp64(lib, monkeypatch, N, leaf, alpha):
+    """FP32 inner solver: refinement with the double-float incremental residual
+    (later sweeps) and with exact FP64 residuals (every sweep) reach the same
+    solution, both within 1e-8 of the oracle; the warm-started steps of a time
+    loop (residual reuse across steps) agree as well."""
+    w = I.fd2d(N=N, alpha=alpha, steps=50, leaf=leaf)
+    C = O.fde2d_rhs(w, w.u0, 0) + I.random_matrix_fast(N, N, seed=11)
+    Xo = O.sylvester_bartels_stewart(O.fd_operator(w.ops[0]), O.fd_operator(w.ops[1]), C)
+    sols = {}
+    for mode in ("df", "fp64"):
+        monkeypatch.setenv("FDE_RESID", mode)
+        P = Pair(lib, w, B.FDE_FP32_REFINE)
+        try:
+            Cd = _dev(C)
+            Xd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+            relres, sweeps = lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+            sols[mode] = _host(Xd, N, N)
+            assert _relerr(sols[mode], Xo) <= 1e-8, (mode, relres, sweeps)
+        finally:
+            P.close()
+    assert _relerr(sols["df"], sols["fp64"]) <= 1e-9
+    # time loop: residual reuse + incremental updates over several steps
+    runs = {}
+    for mode in ("df", "fp64"):
+        monkeypatch.setenv("FDE_RESID", mode)
+        w6 = I.fd2d(N=min(N, 256), alpha=alpha, steps=50, leaf=leaf)
+        rp = lib.run_params(w6, prec=B.FDE_FP32_REFINE)
+        rp.steps = 6
+        U0 = _dev(w6.u0)
+        Uo = torch.zeros_like(U0)
+        lib.fde_run(rp, U0.data_ptr(), Uo.data_ptr())
+        runs[mode] = _host(Uo, w6.N, w6.N)
+    Uref = O.fde2d_run(w6, steps=6)
+    for mode in runs:
+        assert _relerr(runs[mode], Uref) <= 1e-8, mode
