@@ -116,7 +116,25 @@ fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, b
     return ((uintptr_t)p % 16) == 0 && ld % 4 == 0 && (kblk == 0 || kstr % 4 == 0);
   };
   b.vec_a = b.vec_b = b.batch > 0;
-  for (const auto& d : h) {
+  std::vector<GemmDesc<T>> hd(h);
+  for (auto& d : hd) {
+    if (d.kblk > 0) {
+      // division by the invariant kblk as a multiply-shift (Granlund and
+      // Montgomery, "Division by invariant integers using multiplication", 1994):
+      // l = ceil(log2 kblk), m = ceil(2^(32+l) / kblk) is exact for numerators < 2^32
+      int l = 0;
+      while ((1ll << l) < d.kblk) ++l;
+      const unsigned long long two = 1ull << (32 + l);
+      d.kmagic = (two + (unsigned long long)d.kblk - 1ull) / (unsigned long long)d.kblk;
+      d.kshift = 32 + l;
+      for (int k = 0; k < d.k + 64; ++k)
+        if ((int)(((unsigned long long)k * d.kmagic) >> d.kshift) != k / d.kblk) {
+          set_error("gemm_batch_upload: multiply-shift division by %d failed at %d", d.kblk, k);
+          return FDE_ERR_ARG;
+        }
+    }
+  }
+  for (const auto& d : hd) {
     b.vec_a = b.vec_a && vec_ok(d.A, d.lda, ta ? 0 : d.kblk, d.kstr);
     b.vec_b = b.vec_b && vec_ok(d.B, d.ldb, tb ? d.kblk : 0, d.kstr);
     b.max_m = d.m > b.max_m ? d.m : b.max_m;
@@ -126,7 +144,7 @@ fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, b
   }
   if (b.batch > 0) {
     FDE_TRY(pool.alloc(&b.d_desc, h.size()));
-    FDE_CUDA(cudaMemcpyAsync(b.d_desc, h.data(), h.size() * sizeof(GemmDesc<T>), cudaMemcpyHostToDevice, st));
+    FDE_CUDA(cudaMemcpyAsync(b.d_desc, hd.data(), hd.size() * sizeof(GemmDesc<T>), cudaMemcpyHostToDevice, st));
     // descriptors live in pageable host memory owned by the caller's vector:
     // make sure the copy has consumed them before returning.
     FDE_CUDA(cudaStreamSynchronize(st));

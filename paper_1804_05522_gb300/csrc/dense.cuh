@@ -16,6 +16,9 @@ struct GemmDesc {
   int m, n, k, lda, ldb, ldc;
   int kblk = 0;
   long long kstr = 0;
+  // k / kblk = (k * kmagic) >> kshift for 0 <= k < 2^31 (set by gemm_batch_upload)
+  unsigned long long kmagic = 0;
+  int kshift = 0;
 };
 
 // A list of GEMMs with the same transposes / scalars, descriptors resident on

@@ -2,7 +2,7 @@
 //
 //   C = alpha op(A) op(B) + beta C      (column-major, per-batch descriptors)
 //
-// Tile 128 x BN x 32 (BN = 64 or 128).  Operand tiles are staged in shared
+// Tile 128 x BN x 32 (BN = 32, 64 or 128), persistent CTAs (one per SM).  Operand tiles are staged in shared
 // memory in the canonical K-major layout with 128-byte swizzle (8-row x
 // 128-byte atoms, 1024 bytes apart) in a ring of slots filled by eight loader
 // warps; one elected thread issues tcgen05.mma.kind::tf32 (M = 128, N = BN,
@@ -71,22 +71,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-// 32 consecutive accumulator columns of this thread's lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,"
-      "%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -114,7 +98,6 @@ __device__ __forceinline__ uint32_t sw_off(int r, int c) {
 
 
 constexpr int kLoaders = 256;              // 8 warps: global -> shared, then the epilogue
-constexpr int kThreads = kLoaders + 32;    // + 1 warp that issues the MMAs
 constexpr int kMaxSlots = 8;               // MMA slots (TF32 hi / lo tiles)
 constexpr int kRaw = 3;                    // raw FP32 stages filled by cp.async
 
@@ -135,29 +118,49 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const float* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
 // Asynchronous copy of an R x 32 tile of op(X) (element (row, k): X[k + row*ld]
 // when KCONTIG, else X[row + col(k)], col(k) = k*ld or the two-level panel
-// address) into the swizzled K-major layout at dst; out-of-range elements are
-// zero-filled.
-//  - row-contiguous X: warp w owns k = 4w + (lane >> 3); lanes (lane & 7) take 8
-//    consecutive rows, so one instruction reads 4 columns x 32 contiguous bytes
-//    and writes 32 distinct banks; the column address is computed once.
-//  - k-contiguous X: 8 lanes read one row's 128 bytes as 16-byte copies.
+// address) into a raw stage at dst; out-of-range elements are zero-filled.
+//  - row-contiguous X: the raw stage is row-contiguous too (raw[k * R + row]);
+//    each 16-byte copy takes 4 consecutive rows of one k, so a warp moves 512
+//    contiguous bytes per instruction; tile_convert_mn transposes.
+//  - k-contiguous X: the raw stage already has the swizzled K-major layout of
+//    the MMA operand; 8 lanes copy one row's 128 bytes.
 template <int R, bool KCONTIG>
 __device__ __forceinline__ void tile_copy(uint32_t dst, const float* __restrict__ X, int ld, int kblk, long long kstr,
-                                          int row0, int nrows, int k0, int K, bool vec) {
+                                          unsigned long long kmagic, int kshift, int row0, int nrows, int k0, int K,
+                                          bool vec) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!KCONTIG) {
-    const int c = 4 * w + (lane >> 3), kk = k0 + c, rr = lane & 7;
-    const bool kin = kk < K;
-    const long long col =
-        !kin ? 0 : kblk ? (long long)(kk / kblk) * kstr + (long long)(kk % kblk) * ld : (long long)kk * ld;
-    const float* base = X + col + row0;
+    constexpr int C4 = R / 4;                    // 16-byte chunks per k row
+    constexpr int PER = (32 * C4) / kLoaders;    // chunks per thread
 #pragma unroll
-    for (int j = 0; j < R / 8; ++j) {
-      const int r = 8 * j + rr;
-      const bool ok = kin && row0 + r < nrows;
-      cp_async4(dst + sw_off(r, c), ok ? base + r : X, ok);
+    for (int i = 0; i < PER; ++i) {
+      const int ch = threadIdx.x + kLoaders * i, kl = ch / C4, r = 4 * (ch % C4);
+      const int kk = k0 + kl, grow = row0 + r;
+      const uint32_t o = dst + (uint32_t)(kl * R + r) * 4u;
+      int nvalid = nrows - grow;
+      nvalid = kk < K ? (nvalid < 0 ? 0 : nvalid > 4 ? 4 : nvalid) : 0;
+      long long col = 0;
+      if (nvalid > 0) {
+        if (kblk) {
+          const int q = (int)(((unsigned long long)kk * kmagic) >> kshift);
+          col = (long long)q * kstr + (long long)(kk - q * kblk) * ld;
+        } else {
+          col = (long long)kk * ld;
+        }
+      }
+      const float* p = X + col + grow;
+      if (vec) {
+        cp_async16_zfill(o, nvalid > 0 ? p : X, 4 * nvalid);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cp_async4(o + 4 * c, c < nvalid ? p + c : X, c < nvalid);
+      }
     }
   } else {
     const int kq = lane & 7, kk = k0 + 4 * kq;
@@ -206,6 +209,59 @@ __device__ __forceinline__ void tile_convert(const uint8_t* raw, uint8_t* hi, ui
   }
 }
 
+__device__ __forceinline__ float pick4(const float (&v)[4], int j) {
+  return j == 0 ? v[0] : j == 1 ? v[1] : j == 2 ? v[2] : v[3];
+}
+
+// Row-contiguous raw stage (raw[k * R + row]) -> swizzled K-major TF32 hi
+// (and lo).  Thread block (mg, kg): rows 4mg..4mg+3 x k 4kg..4kg+3, read as
+// four 16-byte row segments and transposed in registers; the four stores
+// visit the rows in an order rotated by (mg >> 1) & 3, so the 8 lanes of a
+// quarter warp always hit 8 different 16-byte bank groups.
+template <int R>
+__device__ __forceinline__ void tile_convert_mn(const uint8_t* raw, uint8_t* hi, uint8_t* lo, bool split) {
+  constexpr int NB = (R / 4) * 8;
+#pragma unroll
+  for (int i = 0; i < (NB + kLoaders - 1) / kLoaders; ++i) {
+    const int b = threadIdx.x + kLoaders * i;
+    if (b >= NB) break;
+    const int mg = b % (R / 4), kg = b / (R / 4);
+    float v[4][4];  // v[kk][rr]
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const float4 q = *reinterpret_cast<const float4*>(raw + (size_t)((4 * kg + kk) * R + 4 * mg) * 4);
+      v[kk][0] = q.x;
+      v[kk][1] = q.y;
+      v[kk][2] = q.z;
+      v[kk][3] = q.w;
+    }
+    const int rot = (mg >> 1) & 3;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const int rr = (st + rot) & 3;
+      const uint32_t off = sw_off(4 * mg + rr, 4 * kg);
+      float4 x, h;
+      x.x = pick4(v[0], rr);
+      x.y = pick4(v[1], rr);
+      x.z = pick4(v[2], rr);
+      x.w = pick4(v[3], rr);
+      h.x = to_tf32(x.x);
+      h.y = to_tf32(x.y);
+      h.z = to_tf32(x.z);
+      h.w = to_tf32(x.w);
+      *reinterpret_cast<float4*>(hi + off) = h;
+      if (split) {
+        float4 l;
+        l.x = to_tf32(x.x - h.x);
+        l.y = to_tf32(x.y - h.y);
+        l.z = to_tf32(x.z - h.z);
+        l.w = to_tf32(x.w - h.w);
+        *reinterpret_cast<float4*>(lo + off) = l;
+      }
+    }
+  }
+}
+
 // Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = BN.
 template <int BN>
 __host__ __device__ constexpr uint32_t idesc_tf32_n() {
@@ -217,28 +273,58 @@ __host__ __device__ constexpr int raw_bytes() {
   return (BM + BN) * BK * 4;
 }
 
-// Warp-specialised batched GEMM.
-//  - Warps 0-7 (loaders) copy the op(A) (128 x 32) and op(B) (BN x 32) tiles of
-//    k-tile kt + 2 with cp.async into a ring of kRaw raw FP32 stages, wait for
-//    tile kt (cp.async.wait_group + a barrier of the loader warps), round it to
-//    TF32 (hi, and lo = remainder in split mode) into MMA slot kt % mslots
-//    once the `empty` barrier of that slot says its MMAs are done, and arrive
-//    on the slot's `full` barrier.
-//  - Warp 8 waits on `full`, issues the tcgen05 MMAs of the slot (one elected
-//    thread) and commits them to `empty`.
-//  - The accumulator lives in TMEM; warps 0-7 read it back (lane quarter =
-//    warp % 4, column half = warp / 4) and write C.
-// Every mbarrier wait is bounded: on expiry the kernel raises g_wait_timeout,
-// keeps the loop structure (so no barrier is left waiting), skips the
-// epilogue and still frees its TMEM.
-// grid (ceil(m / 128), ceil(n / BN), batch), kThreads threads.
+// 32 consecutive accumulator columns of this thread's lane, without waiting
+// (tcgen05.wait::ld before the registers are used)
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,"
+      "%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// bounded wait that gives up at once when another role has already failed
+__device__ __forceinline__ bool mbar_wait_f(uint32_t bar, uint32_t parity, volatile int* fail) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && *fail) return false;
+  }
+  atomicExch(&g_wait_timeout, 1);
+  *fail = 1;
+  return false;
+}
+
+constexpr int kEpiWarps = 4;                                   // one per TMEM lane quarter
+constexpr int kPThreads = kLoaders + 32 * kEpiWarps + 32;      // loaders, epilogue, MMA
+constexpr int kEpiWarp0 = kLoaders / 32;                       // warps 8..11
+constexpr int kMmaWarp = kEpiWarp0 + kEpiWarps;                // warp 12
+
+// Persistent warp-specialised batched GEMM: one CTA per SM walks the tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... of the flattened
+// (batch, n tile, m tile) space (m fastest, so neighbouring CTAs share B).
+//  - Warps 0-7 (loaders) copy the op(A) (128 x 32) and op(B) (BN x 32) tiles
+//    of k-tile kt + 2 with cp.async into a ring of kRaw raw FP32 stages, wait
+//    for k-tile kt (cp.async.wait_group + a barrier of the loader warps), round
+//    it to TF32 (hi, and lo = remainder in split mode) into MMA slot
+//    g % mslots (g counts k-tiles over all tiles of the CTA) once the slot's
+//    `empty` barrier says its MMAs are done, and arrive on its `full` barrier.
+//  - Warp 12 waits on `full`, issues the tcgen05 MMAs of the slot (one
+//    elected thread) into accumulator buffer b = (tile count) & 1 in TMEM and
+//    commits them to `empty`; after the last k-tile it commits to tfull[b].
+//  - Warps 8-11 (epilogue) wait on tfull[b], read buffer b (warp = lane
+//    quarter), release it on tempty[b] and write C; meanwhile the MMAs of the
+//    next tile fill the other buffer.
+// Every mbarrier wait is bounded; after a failure the roles skip their work
+// but keep the loop structure (no barrier is left waiting), raise
+// g_wait_timeout and free the TMEM.
 template <int BN, bool TA, bool TB>
-__global__ void __launch_bounds__(kThreads, 1)
-    tc_gemm_kernel(const GemmDesc<float>* __restrict__ descs, float alpha, float beta, int split, int mslots,
-                   int vec_a, int vec_b) {
-  const GemmDesc<float> d = descs[blockIdx.z];
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  if (m0 >= d.m || n0 >= d.n) return;
+__global__ void __launch_bounds__(kPThreads, 1)
+    tc_gemm_kernel(const GemmDesc<float>* __restrict__ descs, int batch, int mt, int nt, float alpha, float beta,
+                   int split, int mslots, int vec_a, int vec_b) {
   constexpr int A_BYTES = BM * BK * 4, B_BYTES = BN * BK * 4;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base_u32 = smem_u32(smem_raw);
@@ -247,144 +333,189 @@ __global__ void __launch_bounds__(kThreads, 1)
   // MMA slot: A_hi | B_hi | A_lo | B_lo (lo only in split mode); raw stages after the slots
   const int slot_bytes = (A_BYTES + B_BYTES) * (split ? 2 : 1);
   uint8_t* raw = sm + (size_t)mslots * slot_bytes;
-  __shared__ __align__(8) uint64_t full_bar[kMaxSlots], empty_bar[kMaxSlots], done_bar;
+  __shared__ __align__(8) uint64_t full_bar[kMaxSlots], empty_bar[kMaxSlots], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
+  volatile int* fail = &s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < mslots; ++s) {
       mbar_init(smem_u32(&full_bar[s]), kLoaders / 32);  // one arrival per loader warp
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    mbar_init(smem_u32(&done_bar), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+    }
     s_fail = 0;
     fence_barrier_init();
   }
-  // split mode keeps the hi*lo + lo*hi corrections in a second accumulator
-  // (columns BN..2BN-1): summed into the hi*hi one they would lose their low
-  // bits to its alignment
+  // per buffer: columns [0, BN) hi*hi; in split mode [BN, 2BN) the hi*lo +
+  // lo*hi corrections (summed into the hi*hi accumulator they would lose
+  // their low bits to its alignment)
   const uint32_t tcols = split ? 2 * BN : BN;
-  if (warp == kLoaders / 32) {
-    tmem_alloc(smem_u32(&tmem_base), tcols);
+  if (warp == kMmaWarp) {
+    tmem_alloc(smem_u32(&tmem_base), 2 * tcols);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const int nk = (d.k + BK - 1) / BK;
+  const int tiles = batch * mt * nt;
 
   if (warp < kLoaders / 32) {
     // ---------------- loaders
-    const int a_kblk = TA ? 0 : d.kblk, b_kblk = TB ? d.kblk : 0;
-    auto issue = [&](int kt) {
-      const uint32_t dst = smem_u32(raw + (size_t)(kt % kRaw) * raw_bytes<BN>());
-      tile_copy<BM, TA>(dst, d.A, d.lda, a_kblk, d.kstr, m0, d.m, kt * BK, d.k, vec_a != 0);
-      tile_copy<BN, !TB>(dst + A_BYTES, d.B, d.ldb, b_kblk, d.kstr, n0, d.n, kt * BK, d.k, vec_b != 0);
-    };
-#pragma unroll
-    for (int kt = 0; kt < kRaw - 1; ++kt) {
-      if (kt < nk) issue(kt);
-      cp_async_commit();
-    }
+    int g = 0;  // k-tiles done by this CTA (ring position)
     bool ok = true;
-    for (int kt = 0; kt < nk; ++kt) {
-      cp_async_wait<kRaw - 2>();  // this thread's copies of tile kt have landed
-      loader_sync();              // everyone's have; raw stage of tile kt-1 is free
-      if (kt + kRaw - 1 < nk) issue(kt + kRaw - 1);
-      cp_async_commit();
-      const int ms = kt % mslots;
-      if (kt >= mslots) {
-        // one lane per warp polls the slot's `empty` barrier
-        int got = 1;
-        if (lane == 0 && ok) got = mbar_wait(smem_u32(&empty_bar[ms]), (uint32_t)((kt / mslots - 1) & 1)) ? 1 : 0;
-        ok = ok && __shfl_sync(0xffffffffu, got, 0) != 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const int z = t / (mt * nt), rem = t - z * (mt * nt), ni = rem / mt, mi = rem - ni * mt;
+      const GemmDesc<float> d = descs[z];
+      const int m0 = mi * BM, n0 = ni * BN;
+      if (m0 >= d.m || n0 >= d.n) continue;
+      const int nk = (d.k + BK - 1) / BK;
+      const int a_kblk = TA ? 0 : d.kblk, b_kblk = TB ? d.kblk : 0;
+      auto issue = [&](int kt) {
+        const uint32_t dst = smem_u32(raw + (size_t)((g + kt) % kRaw) * raw_bytes<BN>());
+        tile_copy<BM, TA>(dst, d.A, d.lda, a_kblk, d.kstr, d.kmagic, d.kshift, m0, d.m, kt * BK, d.k, vec_a != 0);
+        tile_copy<BN, !TB>(dst + A_BYTES, d.B, d.ldb, b_kblk, d.kstr, d.kmagic, d.kshift, n0, d.n, kt * BK, d.k,
+                           vec_b != 0);
+      };
+#pragma unroll
+      for (int kt = 0; kt < kRaw - 1; ++kt) {
+        if (kt < nk) issue(kt);
+        cp_async_commit();
       }
-      if (ok) {
-        const uint8_t* rs = raw + (size_t)(kt % kRaw) * raw_bytes<BN>();
-        uint8_t* slot = sm + (size_t)ms * slot_bytes;
-        tile_convert<BM>(rs, slot, slot + A_BYTES + B_BYTES, split != 0);
-        tile_convert<BN>(rs + A_BYTES, slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
-        fence_proxy_async();  // this thread's tiles -> visible to the tensor core
+      for (int kt = 0; kt < nk; ++kt) {
+        cp_async_wait<kRaw - 2>();  // this thread's copies of k-tile kt have landed
+        loader_sync();              // everyone's have; the raw stage of k-tile kt-1 is free
+        if (kt + kRaw - 1 < nk) issue(kt + kRaw - 1);
+        cp_async_commit();
+        const int gg = g + kt, ms = gg % mslots;
+        if (gg >= mslots) {
+          // one lane per warp polls the slot's `empty` barrier
+          int got = 1;
+          if (lane == 0 && ok) got = mbar_wait_f(smem_u32(&empty_bar[ms]), (uint32_t)((gg / mslots - 1) & 1), fail);
+          ok = ok && __shfl_sync(0xffffffffu, got, 0) != 0;
+        }
+        if (ok) {
+          const uint8_t* rs = raw + (size_t)(gg % kRaw) * raw_bytes<BN>();
+          uint8_t* slot = sm + (size_t)ms * slot_bytes;
+          if (TA)
+            tile_convert<BM>(rs, slot, slot + A_BYTES + B_BYTES, split != 0);
+          else
+            tile_convert_mn<BM>(rs, slot, slot + A_BYTES + B_BYTES, split != 0);
+          if (!TB)
+            tile_convert<BN>(rs + A_BYTES, slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
+          else
+            tile_convert_mn<BN>(rs + A_BYTES, slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
+          fence_proxy_async();  // this thread's tiles -> visible to the tensor core
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&full_bar[ms]));
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&full_bar[ms]));
+      g += nk;
     }
     cp_async_wait<0>();
-    if (!ok) s_fail = 1;
-  } else if (lane == 0) {
+  } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer
-    bool ok = true;
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % mslots;
-      if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((kt / mslots) & 1))) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      uint8_t* slot = sm + (size_t)s * slot_bytes;
-      const uint32_t a_hi = smem_u32(slot), b_hi = smem_u32(slot + A_BYTES);
-      const uint32_t a_lo = smem_u32(slot + A_BYTES + B_BYTES), b_lo = smem_u32(slot + 2 * A_BYTES + B_BYTES);
+    if (lane == 0) {
+      int g = 0, lt = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int z = t / (mt * nt), rem = t - z * (mt * nt), ni = rem / mt, mi = rem - ni * mt;
+        const GemmDesc<float> d = descs[z];
+        if (mi * BM >= d.m || ni * BN >= d.n) continue;
+        const int nk = (d.k + BK - 1) / BK;
+        const int b = lt & 1, u = lt >> 1;
+        const uint32_t acc = tmem + (uint32_t)b * tcols;
+        // the epilogue has drained this buffer (its previous use)
+        if (ok && u > 0) ok = mbar_wait_f(smem_u32(&tempty[b]), (uint32_t)((u - 1) & 1), fail);
+        tc_fence_after();
+        for (int kt = 0; kt < nk; ++kt) {
+          const int gg = g + kt, s = gg % mslots;
+          if (ok) ok = mbar_wait_f(smem_u32(&full_bar[s]), (uint32_t)((gg / mslots) & 1), fail);
+          if (!ok) break;
+          tc_fence_after();
+          uint8_t* slot = sm + (size_t)s * slot_bytes;
+          const uint32_t a_hi = smem_u32(slot), b_hi = smem_u32(slot + A_BYTES);
+          const uint32_t a_lo = smem_u32(slot + A_BYTES + B_BYTES), b_lo = smem_u32(slot + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < BK / 8; ++kk) {
-        const uint32_t off = kk * 32;  // 8 TF32 = 32 bytes along k inside the swizzle atom
-        const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
-        mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_tf32_n<BN>(), acc0);
-        if (split) {
-          mma_tf32(tmem + BN, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc_tf32_n<BN>(), acc0);
-          mma_tf32(tmem + BN, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc_tf32_n<BN>(), 1u);
+          for (int kk = 0; kk < BK / 8; ++kk) {
+            const uint32_t off = kk * 32;  // 8 TF32 = 32 bytes along k inside the swizzle atom
+            const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
+            mma_tf32(acc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_tf32_n<BN>(), acc0);
+            if (split) {
+              mma_tf32(acc + BN, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc_tf32_n<BN>(), acc0);
+              mma_tf32(acc + BN, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc_tf32_n<BN>(), 1u);
+            }
+          }
+          mma_commit(smem_u32(&empty_bar[s]));
         }
+        // completes once every MMA issued so far has finished
+        mma_commit(smem_u32(&tfull[b]));
+        g += nk;
+        ++lt;
       }
-      mma_commit(smem_u32(&empty_bar[s]));
     }
-    if (!ok) s_fail = 1;
-    // completes once every MMA issued above has finished
-    mma_commit(smem_u32(&done_bar));
-  }
-  // epilogue (the MMA warp only waits at the final barrier)
-  bool ok = true;
-  if (warp < kLoaders / 32) {
-    ok = mbar_wait(smem_u32(&done_bar), 0u);
-    tc_fence_after();
-  }
-  const bool all_ok = __syncthreads_and(ok && s_fail == 0 ? 1 : 0) != 0;
-  if (all_ok && warp < kLoaders / 32) {
     __syncwarp();
-    const int quarter = warp & 3, half = warp >> 2;
-    const int row = m0 + quarter * 32 + lane;
-    const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16);
+  } else {
+    // ---------------- epilogue (warp = TMEM lane quarter)
+    const int quarter = warp - kEpiWarp0;  // == warp % 4
+    int lt = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const int z = t / (mt * nt), rem = t - z * (mt * nt), ni = rem / mt, mi = rem - ni * mt;
+      const GemmDesc<float> d = descs[z];
+      const int m0 = mi * BM, n0 = ni * BN;
+      if (m0 >= d.m || n0 >= d.n) continue;
+      const int nk = (d.k + BK - 1) / BK;
+      const int b = lt & 1, u = lt >> 1;
+      int got = 1;
+      if (lane == 0 && ok) got = mbar_wait_f(smem_u32(&tfull[b]), (uint32_t)(u & 1), fail);
+      ok = ok && __shfl_sync(0xffffffffu, got, 0) != 0;
+      tc_fence_after();
+      const int row = m0 + quarter * 32 + lane;
+      const uint32_t tw = tmem + (uint32_t)b * tcols + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
-      float v[32];
-      if (nk > 0) {
-        tmem_ld32(tw + c0, v);
-        if (split) {
-          float w[32];
-          tmem_ld32(tw + BN + c0, w);
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        if (ok && nk > 0) {
+          uint32_t r0[32], r1[32];
+          tmem_ld32_nowait(tw + c0, r0);
+          if (split) tmem_ld32_nowait(tw + BN + c0, r1);
+          tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] += w[j];
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r0[j]) + (split ? __uint_as_float(r1[j]) : 0.f);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = 0.f;
         }
-      } else {
+        if (c0 + 32 >= BN) {
+          // the last TMEM read of this buffer: hand it back to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+        }
+        if (ok && row < d.m) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = 0.f;
-      }
-      if (row < d.m) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < d.n) {
-            float* c = d.C + row + (size_t)col * d.ldc;
-            *c = (beta == 0.f) ? alpha * v[j] : alpha * v[j] + beta * (*c);
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < d.n) {
+              float* c = d.C + row + (size_t)col * d.ldc;
+              *c = (beta == 0.f) ? alpha * v[j] : alpha * v[j] + beta * (*c);
+            }
           }
         }
       }
+      ++lt;
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == kLoaders / 32) {
+  if (warp == kMmaWarp) {
     __syncwarp();
-    tmem_dealloc(tmem, tcols);
+    tmem_dealloc(tmem, 2 * tcols);
   }
 }
 
@@ -433,6 +564,10 @@ static fde_status set_attr() {
 fde_status tc_prepare() {
   static bool done = false;
   if (done) return FDE_OK;
+  FDE_TRY((set_attr<32, false, false>()));
+  FDE_TRY((set_attr<32, false, true>()));
+  FDE_TRY((set_attr<32, true, false>()));
+  FDE_TRY((set_attr<32, true, true>()));
   FDE_TRY((set_attr<64, false, false>()));
   FDE_TRY((set_attr<64, false, true>()));
   FDE_TRY((set_attr<64, true, false>()));
@@ -454,14 +589,23 @@ static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t s
               : (which == 1) ? tc::tc_gemm_kernel<BN, false, true>
               : (which == 2) ? tc::tc_gemm_kernel<BN, true, false>
                              : tc::tc_gemm_kernel<BN, true, true>;
-  for (int z0 = 0; z0 < b.batch; z0 += 65535) {
-    const int nz = b.batch - z0 < 65535 ? b.batch - z0 : 65535;
-    dim3 grid(ceil_div(b.max_m, tc::BM), ceil_div(b.max_n, BN), nz);
-    ProfScope ps("gemm32tc", st, z0 == 0 ? b.flops : 0.0, 1);
-    kern<<<grid, tc::kThreads, smem, st>>>(b.d_desc + z0, b.alpha, b.beta, split, mslots, b.vec_a ? 1 : 0,
-                                           b.vec_b ? 1 : 0);
-    FDE_LAUNCH("tc_gemm_kernel");
+  const int mt = ceil_div(b.max_m, tc::BM), nt = ceil_div(b.max_n, BN);
+  const long long tiles = (long long)b.batch * mt * nt;
+  if (tiles > 0x7fffffffLL) {
+    set_error("tensor-core GEMM: %lld tiles", tiles);
+    return FDE_ERR_ARG;
   }
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    FDE_CUDA(cudaGetDevice(&dev));
+    FDE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  ProfScope ps("gemm32tc", st, b.flops, 1);
+  kern<<<grid, tc::kPThreads, smem, st>>>(b.d_desc, b.batch, mt, nt, b.alpha, b.beta, split, mslots,
+                                          b.vec_a ? 1 : 0, b.vec_b ? 1 : 0);
+  FDE_LAUNCH("tc_gemm_kernel");
   return FDE_OK;
 }
 
@@ -470,10 +614,12 @@ static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t s
 fde_status tc_gemm_run(const GemmBatch<float>& b, cudaStream_t st, bool* used) {
   *used = false;
   const int mode = tc_mode();
-  if (mode == 0 || b.max_m < 64 || b.max_n < 32 || b.max_k < 32) return FDE_OK;
+  if (mode == 0 || b.max_m < 64 || b.max_n < 16 || b.max_k < 32) return FDE_OK;
   FDE_TRY(tc_prepare());
   const int split = (mode == 3) ? 1 : 0;
-  if (b.max_n <= 64)
+  if (b.max_n <= 32)
+    FDE_TRY(launch_bn<32>(b, split, st));
+  else if (b.max_n <= 64)
     FDE_TRY(launch_bn<64>(b, split, st));
   else
     FDE_TRY(launch_bn<128>(b, split, st));

@@ -37,6 +37,8 @@ SHAPES = [
     (256, 40, 96, 4, 3),      # BN = 64, aligned ld
     (130, 130, 33, 1, 1),     # odd ld: scalar loads; k tail
     (512, 384, 320, 0, 1),
+    (200, 17, 160, 0, 5),     # BN = 32 (low-rank factor products, n = rank)
+    (1000, 300, 64, 3, 40),   # many tiles per persistent CTA, ragged everywhere
 ]
 
 
