@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "fft_block.cuh"
 #include "fft_df.cuh"
 #include "hodlr_internal.cuh"
 #include "schur.cuh"
@@ -424,6 +425,11 @@ struct sylv_s {
   double2 *tw = nullptr, *GhX = nullptr, *GhY = nullptr, *fft_scratch = nullptr;
   float4 *tw_df = nullptr, *GhX_df = nullptr, *GhY_df = nullptr;  // double-float copies
   bool resid_df = false;              // later sweeps update R in double-float (FP32 inner solver)
+  // N > 4096: block-Toeplitz FFTs (blocks of kFftBlock) instead of one transform per column
+  bool block = false;
+  int pair_chunk = 0;
+  double2 *HbX = nullptr, *HbY = nullptr;
+  float4 *HbX_df = nullptr, *HbY_df = nullptr;
   double *R = nullptr, *Xt = nullptr, *Yt = nullptr, *X64 = nullptr, *C64 = nullptr;
   double* acc = nullptr;              // device accumulators
   int* d_bad = nullptr;
@@ -819,6 +825,16 @@ static fde_status residual(sylv_s* S, const double* C, const double* X, double* 
   hodlr_s* ax = S->ax;
   hodlr_s* ay = S->ay;
   const int N = S->N, P = S->P, lp = S->logP;
+  if (S->block) {
+    // x direction: R = C - A_x X (columns); y direction: R -= X A_yᵀ (rows, read in place)
+    FDE_TRY(block_apply(X, false, 1, N, N, C, R, 1, N, kApplyResidual, ax->g, S->HbX, S->HbX_df, S->tw, S->tw_df,
+                        false, ax->dp, ax->dm, ax->c, ax->p.shift, N, S->fft_scratch, S->pair_chunk, st,
+                        S->fft_flops));
+    FDE_TRY(block_apply(X, false, N, 1, N, nullptr, R, N, 1, kApplySub, ay->g, S->HbY, S->HbY_df, S->tw, S->tw_df,
+                        false, ay->dp, ay->dm, ay->c, ay->p.shift, N, S->fft_scratch, S->pair_chunk, st,
+                        S->fft_flops));
+    return FDE_OK;
+  }
   const int nb = (N + 1) / 2;
   const size_t smem = (size_t)P * sizeof(double2);
   {
@@ -905,6 +921,15 @@ static fde_status residual_update_df(sylv_s* S, const float* d, cudaStream_t st)
   hodlr_s* ax = S->ax;
   hodlr_s* ay = S->ay;
   const int N = S->N;
+  if (S->block) {
+    FDE_TRY(block_apply(d, true, 1, N, N, nullptr, S->R, 1, N, kApplySub, ax->g, S->HbX, S->HbX_df, S->tw,
+                        S->tw_df, true, ax->dp, ax->dm, ax->c, ax->p.shift, N, S->fft_scratch, S->pair_chunk, st,
+                        S->fft_flops));
+    FDE_TRY(block_apply(d, true, N, 1, N, nullptr, S->R, N, 1, kApplySub, ay->g, S->HbY, S->HbY_df, S->tw,
+                        S->tw_df, true, ay->dp, ay->dm, ay->c, ay->p.shift, N, S->fft_scratch, S->pair_chunk, st,
+                        S->fft_flops));
+    return FDE_OK;
+  }
   float4* scr = reinterpret_cast<float4*>(S->fft_scratch);
   FDE_TRY(fd_apply_sub_df(d, 1, N, N, S->R, 1, N, S->GhX_df, S->tw_df, S->P, S->logP, ax->dp, ax->dm, ax->c,
                           ax->p.shift, N, scr, st, S->fft_flops));
@@ -1211,13 +1236,11 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
     S->facts64.clear();  // their memory lives in setup_pool, released on return
   }
   // ---- residual (FFT)
+  S->block = N > kFftBlock;
   S->logP = 1;
   while ((1 << S->logP) < 2 * N) ++S->logP;
+  if (S->block) S->logP = kFftBlockLogP;
   S->P = 1 << S->logP;
-  if (S->P > 8192) {
-    set_error("argument error: N = %d exceeds the single-CTA FFT residual limit (N <= 4096)", N);
-    return FDE_ERR_ARG;
-  }
   {
     std::vector<double2> tw(S->P / 2);
     for (int k = 0; k < S->P / 2; ++k) {
@@ -1227,30 +1250,48 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
     FDE_TRY(pool.alloc(&S->tw, S->P / 2));
     FDE_CUDA(cudaMemcpy(S->tw, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
   }
-  FDE_TRY(pool.alloc(&S->GhX, S->P));
-  FDE_TRY(pool.alloc(&S->GhY, S->P));
-  const size_t smem = (size_t)S->P * sizeof(double2);
-  FDE_CUDA(cudaFuncSetAttribute(fd_fft_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  FDE_CUDA(cudaFuncSetAttribute(ghat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ghat_kernel<<<1, 1024, smem, st>>>(ax->g, N, S->tw, S->P, S->logP, S->GhX);
-  FDE_LAUNCH("ghat_kernel");
-  ghat_kernel<<<1, 1024, smem, st>>>(ay->g, N, S->tw, S->P, S->logP, S->GhY);
-  FDE_LAUNCH("ghat_kernel");
   if (prec != FDE_FP64) {
     const char* rm = getenv("FDE_RESID");
     S->resid_df = !(rm && strcmp(rm, "fp64") == 0);
     FDE_TRY(pool.alloc(&S->tw_df, S->P / 2));
-    FDE_TRY(pool.alloc(&S->GhX_df, S->P));
-    FDE_TRY(pool.alloc(&S->GhY_df, S->P));
     FDE_TRY(complex_to_df(S->tw, S->tw_df, S->P / 2, st));
-    FDE_TRY(complex_to_df(S->GhX, S->GhX_df, S->P, st));
-    FDE_TRY(complex_to_df(S->GhY, S->GhY_df, S->P, st));
   }
   const size_t NN = (size_t)N * N;
-  FDE_TRY(pool.alloc(&S->fft_scratch, (size_t)((N + 1) / 2) * S->P));
-  FDE_TRY(pool.alloc(&S->R, NN));
-  FDE_TRY(pool.alloc(&S->Xt, NN));
-  FDE_TRY(pool.alloc(&S->Yt, NN));
+  if (S->block) {
+    const int nb = (N + kFftBlock - 1) / kFftBlock, npairs = (N + 1) / 2;
+    S->pair_chunk = npairs < 2048 ? npairs : 2048;
+    FDE_TRY(pool.alloc(&S->HbX, (size_t)nb * S->P));
+    FDE_TRY(pool.alloc(&S->HbY, (size_t)nb * S->P));
+    FDE_TRY(pool.alloc(&S->HbX_df, (size_t)nb * S->P));
+    FDE_TRY(pool.alloc(&S->HbY_df, (size_t)nb * S->P));
+    FDE_TRY(block_spectra(ax->g, N, S->tw, S->HbX, S->HbX_df, st));
+    FDE_TRY(block_spectra(ay->g, N, S->tw, S->HbY, S->HbY_df, st));
+    FDE_TRY(pool.alloc(&S->fft_scratch, (size_t)S->pair_chunk * nb * S->P));
+    FDE_TRY(pool.alloc(&S->R, NN));
+    S->fft_flops = block_apply_flops(N, N);
+  } else {
+    FDE_TRY(pool.alloc(&S->GhX, S->P));
+    FDE_TRY(pool.alloc(&S->GhY, S->P));
+    const size_t smem = (size_t)S->P * sizeof(double2);
+    FDE_CUDA(cudaFuncSetAttribute(fd_fft_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDE_CUDA(cudaFuncSetAttribute(ghat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ghat_kernel<<<1, 1024, smem, st>>>(ax->g, N, S->tw, S->P, S->logP, S->GhX);
+    FDE_LAUNCH("ghat_kernel");
+    ghat_kernel<<<1, 1024, smem, st>>>(ay->g, N, S->tw, S->P, S->logP, S->GhY);
+    FDE_LAUNCH("ghat_kernel");
+    if (prec != FDE_FP64) {
+      FDE_TRY(pool.alloc(&S->GhX_df, S->P));
+      FDE_TRY(pool.alloc(&S->GhY_df, S->P));
+      FDE_TRY(complex_to_df(S->GhX, S->GhX_df, S->P, st));
+      FDE_TRY(complex_to_df(S->GhY, S->GhY_df, S->P, st));
+    }
+    FDE_TRY(pool.alloc(&S->fft_scratch, (size_t)((N + 1) / 2) * S->P));
+    FDE_TRY(pool.alloc(&S->R, NN));
+    FDE_TRY(pool.alloc(&S->Xt, NN));
+    FDE_TRY(pool.alloc(&S->Yt, NN));
+    // per residual direction: (N+1)/2 column pairs x (3 complex FFTs of 5 P log2 P + 2 pointwise products)
+    S->fft_flops = (double)((N + 1) / 2) * (3.0 * 5.0 * S->P * S->logP + 12.0 * S->P);
+  }
   FDE_TRY(pool.alloc(&S->acc, 8));
   FDE_TRY(pool.alloc(&S->d_bad, 1));
   // algorithmic work for the instrumentation
@@ -1259,8 +1300,6 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
       const double n1 = ax->leaf_n[p], n2 = ay->leaf_n[q];
       S->trsyl_flops += n1 * n2 * (n1 + n2);
     }
-  // per residual direction: (N+1)/2 column pairs x (3 complex FFTs of 5 P log2 P + 2 pointwise products)
-  S->fft_flops = (double)((N + 1) / 2) * (3.0 * 5.0 * S->P * S->logP + 12.0 * S->P);
   S->refine.max_sweeps = 12;
   S->refine.tol_update = (prec == FDE_FP64) ? 1e-13 : 1e-11;
   S->refine.tol_relres = 1e-14;
