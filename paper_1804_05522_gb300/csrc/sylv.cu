@@ -200,6 +200,33 @@ __global__ void shift_residual_kernel(const double* __restrict__ C, const double
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     R[i] = C[i] - Cp[i] + R[i];
 }
+// Linear predictor for a time step from the two previous solutions:
+//   X <- 2 X_n - X_{n-1};  R <- C - A(X) = C - 2 (C_n - R_n) + (C_{n-1} - R_{n-1}),
+// exact because A X_k = C_k - R_k; the history then moves one step.
+__global__ void predict_kernel(const double* __restrict__ C, const double* __restrict__ Cn, double* __restrict__ X,
+                               double* __restrict__ R, double* __restrict__ Xp, double* __restrict__ Cp,
+                               double* __restrict__ Rp, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double x = X[i], r = R[i], cn = Cn[i];
+    X[i] = 2.0 * x - Xp[i];
+    R[i] = C[i] - 2.0 * (cn - r) + (Cp[i] - Rp[i]);
+    Xp[i] = x;
+    Cp[i] = cn;
+    Rp[i] = r;
+  }
+}
+// first step of a history: R <- C - Cn + R (as shift_residual) and save (X, Cn, R_n)
+__global__ void shift_save_kernel(const double* __restrict__ C, const double* __restrict__ Cn,
+                                  const double* __restrict__ X, double* __restrict__ R, double* __restrict__ Xp,
+                                  double* __restrict__ Cp, double* __restrict__ Rp, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double r = R[i], cn = Cn[i];
+    Xp[i] = X[i];
+    Cp[i] = cn;
+    Rp[i] = r;
+    R[i] = C[i] - cn + r;
+  }
+}
 __global__ void nonfinite_kernel(const double* __restrict__ X, size_t n, int* bad) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     if (!isfinite(X[i])) atomicExch(bad, 1);
@@ -437,6 +464,10 @@ struct sylv_s {
   std::vector<int> J;
   double trsyl_flops = 0.0, fft_flops = 0.0;
   bool R_valid = false;               // R holds C_last - A(X_last) of the last step
+  // time-step predictor: history (X, C, R) of the step before the last one
+  bool predict = false;
+  int hist = 0;                       // 1 when Xp, Cp, Rp are valid
+  double *Xp = nullptr, *Cp = nullptr, *Rp = nullptr;
   bool rational = false;              // fADI levels in precomputed rational form
   ~sylv_s() {
     if (in64.exec) cudaGraphExecDestroy(in64.exec);
@@ -999,9 +1030,19 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
   if (C_prev && S->R_valid) {
     // X is the solution computed for C_prev and S->R = C_prev - A(X): the new
     // residual follows exactly without applying the operator again.
-    shift_residual_kernel<<<grid_for(NN), 256, 0, st>>>(C, C_prev, S->R, NN);
-    FDE_LAUNCH("shift_residual_kernel");
+    if (S->predict && S->hist) {
+      predict_kernel<<<grid_for(NN), 256, 0, st>>>(C, C_prev, X, S->R, S->Xp, S->Cp, S->Rp, NN);
+      FDE_LAUNCH("predict_kernel");
+    } else if (S->predict) {
+      shift_save_kernel<<<grid_for(NN), 256, 0, st>>>(C, C_prev, X, S->R, S->Xp, S->Cp, S->Rp, NN);
+      FDE_LAUNCH("shift_save_kernel");
+    } else {
+      shift_residual_kernel<<<grid_for(NN), 256, 0, st>>>(C, C_prev, S->R, NN);
+      FDE_LAUNCH("shift_residual_kernel");
+    }
+    S->hist = S->predict ? 1 : 0;
   } else {
+    S->hist = 0;
     FDE_TRY(residual(S, C, X, S->R, st));
   }
   S->R_valid = false;
@@ -1050,6 +1091,7 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
     return FDE_ERR_NOCONV;
   }
   S->R_valid = done > 0;
+  if (!S->R_valid) S->hist = 0;
   return FDE_OK;
 }
 
@@ -1294,6 +1336,16 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
   }
   FDE_TRY(pool.alloc(&S->acc, 8));
   FDE_TRY(pool.alloc(&S->d_bad, 1));
+  {
+    // time-step predictor (used by time loops that pass the previous right-hand side)
+    const char* pe = getenv("FDE_PREDICT");
+    S->predict = !(pe && strcmp(pe, "0") == 0);
+    if (S->predict) {
+      FDE_TRY(pool.alloc(&S->Xp, NN));
+      FDE_TRY(pool.alloc(&S->Cp, NN));
+      FDE_TRY(pool.alloc(&S->Rp, NN));
+    }
+  }
   // algorithmic work for the instrumentation
   for (int p = 0; p < nl; ++p)
     for (int q = 0; q < nl; ++q) {

@@ -196,3 +196,22 @@ def test_incremental_df_residual_matches_fp64(lib, monkeypatch, N, leaf, alpha):
     Uref = O.fde2d_run(w6, steps=6)
     for mode in runs:
         assert _relerr(runs[mode], Uref) <= 1e-8, mode
+
+
+def test_time_step_predictor(lib, monkeypatch):
+    """The linear predictor X = 2 X_n - X_{n-1} (residual from the stored
+    history, no operator application) gives the same trajectory as plain warm
+    starts, within the refinement tolerance of the oracle, with no more sweeps."""
+    w = I.fd2d(N=128, alpha=(1.5, 1.5), steps=40, leaf=32)
+    Uref = O.fde2d_run(w, steps=12)
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("FDE_PREDICT", mode)
+        rp = lib.run_params(w, prec=B.FDE_FP32_REFINE)
+        rp.steps = 12
+        U0 = _dev(w.u0)
+        Uo = torch.zeros_like(U0)
+        st = lib.fde_run(rp, U0.data_ptr(), Uo.data_ptr())
+        out[mode] = (_host(Uo, 128, 128), st.sweeps_total)
+        assert _relerr(out[mode][0], Uref) <= 1e-8, mode
+    assert out["1"][1] <= out["0"][1], (out["1"][1], out["0"][1])
