@@ -237,6 +237,13 @@ typedef struct fde_runner_s* fde_runner_t;
 fde_status fde_runner_create(const fde_run_params* p, const double* U0, void* stream, fde_runner_t* out);
 fde_status fde_runner_advance(fde_runner_t r, int nsteps, void* stream);
 fde_status fde_runner_load(fde_runner_t r, const double* U, int step_index, void* stream);
+/* One 2D step with a caller-supplied source at the new time level instead of
+ * the low-rank one of the parameters: C = U^{(m)} + dt F (Eq.
+ * (sylv-timestepping) with a general F^{(m+1)}).  F: N x N column-major,
+ * leading dimension ldf >= N, host (copied on `stream`) or device pointer.
+ * Keeps the time-loop state (residual reuse, predictor) like
+ * fde_runner_advance; fde_runner_load resets it. */
+fde_status fde_runner_step_source(fde_runner_t r, const double* F, int ldf, void* stream);
 fde_status fde_runner_state(fde_runner_t r, double* U_out, void* stream);
 fde_status fde_runner_stats(fde_runner_t r, fde_run_stats* stats);
 void fde_runner_free(fde_runner_t r);

@@ -56,6 +56,7 @@ _SIGS = {
     "hodlr_solve": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "hodlr_matvec": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "hodlr_matvec_noalloc": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
+    "fde_runner_step_source": ([_P, _P, C.c_int, _P], C.c_int),
     "fde_gemm_f32": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, _P, C.c_int, C.c_longlong, _P, C.c_int,
                       C.c_longlong, C.c_float, _P, C.c_int, C.c_longlong, C.c_int, C.c_int, C.c_longlong, C.c_int, _P],
                      C.c_int),
@@ -244,6 +245,9 @@ class Lib:
         r = _P()
         self.check(self.dll.fde_runner_create(C.byref(params), U0, stream, C.byref(r)))
         return r.value
+
+    def runner_step_source(self, r: int, F: int, ldf: int, stream: int = 0):
+        self.check(self.dll.fde_runner_step_source(r, F, ldf, stream))
 
     def runner_advance(self, r: int, nsteps: int, stream: int = 0):
         self.check(self.dll.fde_runner_advance(r, nsteps, stream))

@@ -20,6 +20,16 @@ struct SrcW {
   double w[kMaxSrc];
 };
 
+// C = U + dt F   (a dense source at the new time level)
+__global__ void rhs_dense_kernel(const double* __restrict__ U, const double* __restrict__ F, int N, int ldf,
+                                 double dt, double* __restrict__ C) {
+  const size_t total = (size_t)N * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % N), j = (int)(e / N);
+    C[e] = U[e] + dt * F[i + (size_t)j * ldf];
+  }
+}
+
 // C = U + dt Σ_l w_l FL[:,l] FR[:,l]ᵀ   (source at the new time level)
 __global__ void rhs2d_kernel(const double* __restrict__ U, const double* __restrict__ FL,
                              const double* __restrict__ FR, int N, int r, SrcW w, double dt, double* __restrict__ C) {
@@ -81,6 +91,7 @@ struct fde_runner_s {
   DevPool pool;
   double *U = nullptr, *C = nullptr, *FL = nullptr, *FR = nullptr;
   double* C2 = nullptr;          // previous step's right-hand side (2D)
+  double* F = nullptr;           // caller-supplied dense source (fde_runner_step_source)
   bool have_prev = false;        // C2 / the solver's residual belong to the current U
   double *y = nullptr, *rr = nullptr, *acc = nullptr;
   int N = 0, step = 0;
@@ -245,6 +256,40 @@ extern "C" fde_status fde_runner_advance(fde_runner_t r, int nsteps, void* strea
   FDE_ARG(r != nullptr, "runner is NULL");
   FDE_ARG(nsteps >= 0, "nsteps must be >= 0");
   return runner_advance(r, nsteps, (cudaStream_t)stream);
+}
+
+extern "C" fde_status fde_runner_step_source(fde_runner_t r, const double* F, int ldf, void* stream) {
+  FDE_ARG(r != nullptr && F != nullptr, "NULL argument");
+  FDE_ARG(r->p.dim == 2, "fde_runner_step_source is for 2D runners");
+  const int N = r->N;
+  FDE_ARG(ldf >= N, "ldf < N");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double t1 = now_seconds();
+  const double dt = r->p.op_x.dt;
+  const double* Fd = F;
+  if (!is_device_ptr(F)) {
+    if (!r->F) FDE_TRY(r->pool.alloc(&r->F, (size_t)N * N));
+    FDE_CUDA(cudaMemcpy2DAsync(r->F, (size_t)N * sizeof(double), F, (size_t)ldf * sizeof(double),
+                               (size_t)N * sizeof(double), N, cudaMemcpyHostToDevice, st));
+    Fd = r->F;
+    ldf = N;
+  }
+  const size_t NN = (size_t)N * N;
+  const int nb = (int)std::min<size_t>((NN + 255) / 256, 152 * 32);
+  std::swap(r->C, r->C2);  // C2 <- previous right-hand side
+  rhs_dense_kernel<<<nb, 256, 0, st>>>(r->U, Fd, N, ldf, dt, r->C);
+  FDE_LAUNCH("rhs_dense_kernel");
+  double rel = 0.0;
+  int sw = 0;
+  fde_status s = sylv_step_internal(r->s, r->C, r->U, st, &rel, &sw, r->have_prev ? r->C2 : nullptr);
+  r->have_prev = (s == FDE_OK);
+  FDE_TRY(s);
+  r->stats.sweeps_total += sw;
+  r->stats.sweeps_max = std::max(r->stats.sweeps_max, sw);
+  r->stats.relres_max = std::max(r->stats.relres_max, rel);
+  r->step += 1;
+  r->stats.solve_s += now_seconds() - t1;
+  return FDE_OK;
 }
 
 extern "C" fde_status fde_runner_load(fde_runner_t r, const double* U, int step_index, void* stream) {

@@ -215,3 +215,32 @@ def test_time_step_predictor(lib, monkeypatch):
         out[mode] = (_host(Uo, 128, 128), st.sweeps_total)
         assert _relerr(out[mode][0], Uref) <= 1e-8, mode
     assert out["1"][1] <= out["0"][1], (out["1"][1], out["0"][1])
+
+
+def test_runner_step_source_matches_builtin_source(lib):
+    """fde_runner_step_source with the dense source field evaluated on the host
+    follows the trajectory of the runner's own low-rank source."""
+    N = 96
+    w = I.fd2d(N=N, alpha=(1.3, 1.7), steps=20, leaf=16)
+    rp = lib.run_params(w, prec=B.FDE_FP32_REFINE)
+    U0 = _dev(w.u0)
+    ra = lib.runner_create(rp, U0.data_ptr())
+    rb = lib.runner_create(rp, U0.data_ptr())
+    try:
+        lib.runner_advance(ra, 5)
+        for m in range(5):
+            t = (m + 1) * w.dt
+            wts = w.src_amp + w.src_sin_amp * np.sin(w.src_omega * t)
+            F = (w.src_left * wts) @ w.src_right.T
+            Fh = torch.from_numpy(np.asfortranarray(F).ravel(order="F").copy())  # host source
+            lib.runner_step_source(rb, Fh.data_ptr(), N)
+        Ua = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+        Ub = torch.zeros_like(Ua)
+        lib.runner_state(ra, Ua.data_ptr())
+        lib.runner_state(rb, Ub.data_ptr())
+        torch.cuda.synchronize()
+        assert _relerr(_host(Ub, N, N), _host(Ua, N, N)) <= 1e-10
+        assert _relerr(_host(Ub, N, N), O.fde2d_run(w, steps=5)) <= 1e-8
+    finally:
+        lib.runner_free(ra)
+        lib.runner_free(rb)
