@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--prof-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-threads", type=int, default=8)
     return ap.parse_args()
 
 
@@ -346,6 +347,57 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ batches
+def run_batch(args, rank, world, local_rank):
+    """64 independent instances (1D and 2D, N in 512..8192, uneven alpha and
+    coefficient scales, 20 steps each) advanced together; leaf size autotuned
+    per (dim, N) bucket.  Metric: instance time steps per second."""
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    from paper_1804_05522_gb300 import binding as B
+
+    lib = B.load()
+    ws = I.batch(count=64, steps=20)
+    dev = torch.device("cuda", local_rank)
+    params = [lib.run_params(w, prec=B.FDE_FP32_REFINE if w.dim == 2 else B.FDE_FP64) for w in ws]
+    U0 = [torch.from_numpy(np.asarray(w.u0, dtype=np.float64).ravel(order="F").copy()).to(dev) for w in ws]
+    t0 = time.perf_counter()
+    b = lib.batch_create(params, [u.data_ptr() for u in U0], threads=args.batch_threads, autotune=True)
+    setup_wall = time.perf_counter() - t0
+    lib.batch_advance(b, args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    launches0 = lib.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lib.batch_advance(b, args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = lib.launch_count() - launches0
+    setup, tune, solve, inst = lib.batch_timing(b)
+    leaves = {}
+    for i, w in enumerate(ws):
+        leaf, st = lib.batch_info(b, i)
+        leaves[f"{w.dim}d_N{w.N}"] = leaf
+    lib.batch_free(b)
+    if rank != 0:
+        return
+    value = world * len(ws) * args.steps / (ms / 1e3)
+    out = {"metric": "batched instance time steps/s (64 independent 1D/2D instances)", "value": value,
+           "unit": "instance-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "2D: f32 inner / f64 refine; 1D: f64", "data": "synthetic",
+           "config": {"workload": "batch64: 64 instances, even index 1D / odd 2D, N = 2^(9+floor(5u)), alpha ~ "
+                                  "U[1.1,1.9], coefficient scale 10^U[-1,1], dt = 1/20, leaf autotuned",
+                      "threads": args.batch_threads, "setup_s": setup_wall, "autotune_s": tune,
+                      "leaf_by_bucket": leaves},
+           "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------ reference
 def run_reference(args, rank, world):
     if rank != 0:
@@ -387,7 +439,10 @@ def main():
 
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.workload == "batch64":
+        run_batch(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
 

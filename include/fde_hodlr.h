@@ -248,6 +248,31 @@ fde_status fde_runner_state(fde_runner_t r, double* U_out, void* stream);
 fde_status fde_runner_stats(fde_runner_t r, fde_run_stats* stats);
 void fde_runner_free(fde_runner_t r);
 
+/* ------------------------------------------------------------- batches -- */
+/* Many independent instances (1D and 2D, uneven N, α, coefficients), e.g. a
+ * batch of problems served together.  fde_batch_create builds one time-loop
+ * runner per instance (params[i], initial state d_U0[i]: device pointers,
+ * copied); with opts->autotune the HODLR leaf size of each (dim, N, prec)
+ * bucket is chosen by timing trial steps of its first instance over
+ * {32, 64, 128, 256} (1D) or {64, 128, 256} (2D) and cached for the process
+ * (params' leaf is used otherwise).  fde_batch_advance advances every instance
+ * nsteps with opts->threads host worker threads, each on its own CUDA stream,
+ * and returns when all are done (errors name the instance).  Instances are
+ * indexed in the order given. */
+typedef struct fde_batch_s* fde_batch_t;
+typedef struct {
+  int threads;   /* concurrent host workers / CUDA streams, 1..64   */
+  int autotune;  /* 1: pick the leaf size per bucket by trial steps */
+} fde_batch_opts;
+fde_status fde_batch_create(const fde_run_params* params, const double* const* d_U0, int count,
+                            const fde_batch_opts* opts, void* stream, fde_batch_t* out);
+fde_status fde_batch_advance(fde_batch_t b, int nsteps);
+fde_status fde_batch_state(fde_batch_t b, int i, double* U_out, void* stream);
+fde_status fde_batch_info(fde_batch_t b, int i, int* leaf, fde_run_stats* stats);
+fde_status fde_batch_timing(fde_batch_t b, double* setup_s, double* tune_s, double* solve_s,
+                            long long* instance_steps);
+void fde_batch_free(fde_batch_t b);
+
 /* Batched FP32 GEMM of the FP32 inner solver (the dense products of the
  * Sylvester divide-and-conquer, §3.3-§3.4), exposed for checks:
  *   C_i = alpha op(A_i) op(B_i) + beta C_i,  i < batch,

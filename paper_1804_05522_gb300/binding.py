@@ -49,6 +49,10 @@ class RunStats(C.Structure):
                 ("kmax_x", C.c_int), ("kmax_y", C.c_int)]
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("threads", C.c_int), ("autotune", C.c_int)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "hodlr_build": ([C.POINTER(OpParams), _P, C.POINTER(_P)], C.c_int),
@@ -57,6 +61,13 @@ _SIGS = {
     "hodlr_matvec": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "hodlr_matvec_noalloc": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "fde_runner_step_source": ([_P, _P, C.c_int, _P], C.c_int),
+    "fde_batch_create": ([_P, _P, C.c_int, _P, _P, C.POINTER(_P)], C.c_int),
+    "fde_batch_advance": ([_P, C.c_int], C.c_int),
+    "fde_batch_state": ([_P, C.c_int, _P, _P], C.c_int),
+    "fde_batch_info": ([_P, C.c_int, C.POINTER(C.c_int), _P], C.c_int),
+    "fde_batch_timing": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                          C.POINTER(C.c_longlong)], C.c_int),
+    "fde_batch_free": ([_P], None),
     "fde_gemm_f32": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, _P, C.c_int, C.c_longlong, _P, C.c_int,
                       C.c_longlong, C.c_float, _P, C.c_int, C.c_longlong, C.c_int, C.c_int, C.c_longlong, C.c_int, _P],
                      C.c_int),
@@ -245,6 +256,38 @@ class Lib:
         r = _P()
         self.check(self.dll.fde_runner_create(C.byref(params), U0, stream, C.byref(r)))
         return r.value
+
+    # -- batches
+    def batch_create(self, params_list, U0_ptrs, threads=4, autotune=False, stream: int = 0) -> int:
+        n = len(params_list)
+        arr = (RunParams * n)(*params_list)
+        ptrs = (C.c_void_p * n)(*U0_ptrs)
+        opts = BatchOpts(threads, 1 if autotune else 0)
+        h = _P()
+        self.check(self.dll.fde_batch_create(C.cast(arr, _P), C.cast(ptrs, _P), n, C.byref(opts), stream,
+                                             C.byref(h)))
+        return h.value
+
+    def batch_advance(self, b: int, nsteps: int):
+        self.check(self.dll.fde_batch_advance(b, nsteps))
+
+    def batch_state(self, b: int, i: int, U: int, stream: int = 0):
+        self.check(self.dll.fde_batch_state(b, i, U, stream))
+
+    def batch_info(self, b: int, i: int):
+        leaf = C.c_int()
+        st = RunStats()
+        self.check(self.dll.fde_batch_info(b, i, C.byref(leaf), C.byref(st)))
+        return leaf.value, st
+
+    def batch_timing(self, b: int):
+        a, t, s, n = C.c_double(), C.c_double(), C.c_double(), C.c_longlong()
+        self.check(self.dll.fde_batch_timing(b, C.byref(a), C.byref(t), C.byref(s), C.byref(n)))
+        return a.value, t.value, s.value, n.value
+
+    def batch_free(self, b: int):
+        if b:
+            self.dll.fde_batch_free(b)
 
     def runner_step_source(self, r: int, F: int, ldf: int, stream: int = 0):
         self.check(self.dll.fde_runner_step_source(r, F, ldf, stream))

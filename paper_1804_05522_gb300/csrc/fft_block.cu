@@ -201,12 +201,15 @@ fde_status launch_block(const InT* X, long long xs, long long xc, int ncols, con
                         const typename Ar::C* tw, const double* dp, const double* dm, double c, double shift, int N,
                         typename Ar::C* scratch, int pair_chunk, cudaStream_t st) {
   const size_t smem = (size_t)P * sizeof(typename Ar::C);
-  static bool attr = false;
-  if (!attr) {
-    FDE_CUDA(cudaFuncSetAttribute(block_fwd_kernel<Ar, InT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FDE_CUDA(cudaFuncSetAttribute(block_inv_kernel<Ar, InT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  // set once per instantiation (thread-safe initialisation of a local static)
+  static const cudaError_t attr = [smem]() {
+    cudaError_t e = cudaFuncSetAttribute(block_fwd_kernel<Ar, InT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(block_inv_kernel<Ar, InT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+  }();
+  FDE_CUDA(attr);
   const int nb = (N + B - 1) / B, npairs = (ncols + 1) / 2;
   for (int p0 = 0; p0 < npairs; p0 += pair_chunk) {
     const int np = npairs - p0 < pair_chunk ? npairs - p0 : pair_chunk;

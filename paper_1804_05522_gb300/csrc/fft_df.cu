@@ -100,12 +100,9 @@ fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols
     return FDE_ERR_ARG;
   }
   const size_t smem = (size_t)P * sizeof(float4);
-  static bool attr = false;
-  if (!attr) {
-    FDE_CUDA(cudaFuncSetAttribute(fd_fft_sub_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(8192 * sizeof(float4))));
-    attr = true;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      fd_fft_sub_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8192 * sizeof(float4)));
+  FDE_CUDA(attr);
   ProfScope ps("fft_df", st, flops, 1);
   fd_fft_sub_df_kernel<<<(ncols + 1) / 2, 1024, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, dp, dm,
                                                             c, shift, N, scratch);

@@ -1003,7 +1003,16 @@ static fde_status build_impl(const fde_op_params* p, cudaStream_t st, hodlr_s* h
                                                             h->kaca);
     FDE_LAUNCH("block_factors_kernel");
     const size_t smem = (3 * (size_t)r * r + 3 * r) * sizeof(double) + r * sizeof(int);
-    FDE_CUDA(cudaFuncSetAttribute(recompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      // per-kernel attribute shared by all handles and threads: only ever raised
+      static std::mutex mu;
+      static size_t set_to = 0;
+      std::lock_guard<std::mutex> lk(mu);
+      if (smem > set_to) {
+        FDE_CUDA(cudaFuncSetAttribute(recompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        set_to = smem;
+      }
+    }
     ProfScope ps("recompress", st);
     recompress_kernel<<<(int)jobs.size(), 512, smem, st>>>(d_jobs, r, r, h->blk_tol);
     FDE_LAUNCH("recompress_kernel");

@@ -571,11 +571,9 @@ fde_status leaf_trsyl(const T* S, const T* R, int lmax, const int* d_lo_x, const
   const size_t limit = 224 * 1024;
   const int use_panel = with_panel <= limit ? 1 : 0;
   const size_t smem = use_panel ? with_panel : base;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(T) == 8]) {
-    FDE_CUDA(cudaFuncSetAttribute(trsyl_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
-    attr_set[sizeof(T) == 8] = true;
-  }
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(trsyl_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+  FDE_CUDA(attr);
   ProfScope ps(sizeof(T) == 4 ? "trsyl32" : "trsyl64", st, flops, 1);
   trsyl_kernel<T><<<nx * ny, warps * 32, smem, st>>>(S, R, lmax, d_lo_x, d_n_x, nx, d_lo_y, d_n_y, W, ldw, use_panel,
                                                      panel_elems);

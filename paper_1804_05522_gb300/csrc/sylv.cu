@@ -1315,8 +1315,10 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
     FDE_TRY(pool.alloc(&S->GhX, S->P));
     FDE_TRY(pool.alloc(&S->GhY, S->P));
     const size_t smem = (size_t)S->P * sizeof(double2);
-    FDE_CUDA(cudaFuncSetAttribute(fd_fft_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FDE_CUDA(cudaFuncSetAttribute(ghat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the attribute is per kernel, shared by every handle: always allow the largest transform
+    const int smax = 8192 * (int)sizeof(double2);
+    FDE_CUDA(cudaFuncSetAttribute(fd_fft_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    FDE_CUDA(cudaFuncSetAttribute(ghat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
     ghat_kernel<<<1, 1024, smem, st>>>(ax->g, N, S->tw, S->P, S->logP, S->GhX);
     FDE_LAUNCH("ghat_kernel");
     ghat_kernel<<<1, 1024, smem, st>>>(ay->g, N, S->tw, S->P, S->logP, S->GhY);

@@ -14,6 +14,9 @@
 // accuracy.  Accumulation is FP32.
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "dense.cuh"
 
 namespace fde {
@@ -535,17 +538,19 @@ int mslots_for(int split) {
 
 }  // namespace tc
 
-static int g_tc_mode = -1;  // -1: not read yet; 0 off; 1 tf32; 3 3xtf32
+static std::atomic<int> g_tc_mode{-1};  // -1: not read yet; 0 off; 1 tf32; 3 3xtf32
 
 int tc_mode() {
-  if (g_tc_mode < 0) {
+  int m = g_tc_mode.load();
+  if (m < 0) {
     const char* e = getenv("FDE_TC");
-    g_tc_mode = e ? atoi(e) : 3;
-    if (g_tc_mode != 0 && g_tc_mode != 1 && g_tc_mode != 3) g_tc_mode = 3;
+    m = e ? atoi(e) : 3;
+    if (m != 0 && m != 1 && m != 3) m = 3;
+    g_tc_mode.store(m);
   }
-  return g_tc_mode;
+  return m;
 }
-void set_tc_mode(int m) { g_tc_mode = m; }
+void set_tc_mode(int m) { g_tc_mode.store(m); }
 
 fde_status tc_error_flag(int* out) {
   *out = 0;
@@ -560,10 +565,17 @@ static fde_status set_attr() {
   return FDE_OK;
 }
 
-// Kernel attributes are set once, before any stream capture.
+static fde_status tc_prepare_once();
+
+// Kernel attributes are set once (thread-safe), before any stream capture.
 fde_status tc_prepare() {
-  static bool done = false;
-  if (done) return FDE_OK;
+  static std::once_flag once;
+  static fde_status status = FDE_OK;
+  std::call_once(once, []() { status = tc_prepare_once(); });
+  return status;
+}
+
+static fde_status tc_prepare_once() {
   FDE_TRY((set_attr<32, false, false>()));
   FDE_TRY((set_attr<32, false, true>()));
   FDE_TRY((set_attr<32, true, false>()));
@@ -576,7 +588,6 @@ fde_status tc_prepare() {
   FDE_TRY((set_attr<128, false, true>()));
   FDE_TRY((set_attr<128, true, false>()));
   FDE_TRY((set_attr<128, true, true>()));
-  done = true;
   return FDE_OK;
 }
 
@@ -595,12 +606,9 @@ static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t s
     set_error("tensor-core GEMM: %lld tiles", tiles);
     return FDE_ERR_ARG;
   }
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    FDE_CUDA(cudaGetDevice(&dev));
-    FDE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+  int dev = 0, sms = 0;
+  FDE_CUDA(cudaGetDevice(&dev));
+  FDE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = (int)(tiles < sms ? tiles : sms);
   ProfScope ps("gemm32tc", st, b.flops, 1);
   kern<<<grid, tc::kPThreads, smem, st>>>(b.d_desc, b.batch, mt, nt, b.alpha, b.beta, split, mslots,

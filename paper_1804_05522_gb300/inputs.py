@@ -171,6 +171,30 @@ def random_matrix_fast(m: int, n: int, seed: int) -> np.ndarray:
     return g.standard_normal((m, n))
 
 
+def batch(count=64, steps=20, sizes_log2=(9, 14), seed_index=0, leaf=64):
+    """Batch of independent instances (served together): even index -> 1D,
+    odd -> 2D; N = 2^(lo + floor((hi - lo) u)) with u ~ U[0,1) (uneven mix of
+    512 .. 8192 by default); alpha ~ U[1.1, 1.9] (independently per direction
+    in 2D); diffusion coefficients scaled by s = 10^U[-1, 1] per direction;
+    implicit Euler with dt = 1/steps.  `leaf` is the HODLR leaf used unless the
+    batch autotunes it."""
+    lo, hi = sizes_log2
+    out = []
+    for idx in range(count):
+        rng = SplitMix64(SEED_BASE + 40000 + 1000 * seed_index + idx)
+        N = 1 << (lo + int((hi - lo) * rng.uniform()))
+        a1 = 1.1 + 0.8 * rng.uniform()
+        a2 = 1.1 + 0.8 * rng.uniform()
+        s1 = 10.0 ** (2.0 * rng.uniform() - 1.0)
+        s2 = 10.0 ** (2.0 * rng.uniform() - 1.0)
+        lf = min(leaf, max(8, N // 2))
+        if idx % 2 == 0:
+            out.append(fd1d(N=N, alpha=a1, steps=steps, leaf=lf, seed_index=idx, coeff_scale=s1))
+        else:
+            out.append(fd2d(N=N, alpha=(a1, a2), steps=steps, leaf=lf, coeff_scale=(s1, s2)))
+    return out
+
+
 # Named workloads (sizes of the paper-shaped configurations).
 WORKLOADS = {
     "fd1d_n1024": lambda: fd1d(N=1024, alpha=1.5, steps=32, leaf=64, tol=1e-10),
