@@ -4,6 +4,7 @@ paper or plain mathematics fixes independently of the oracle's own formulas
 invariants).  A plausible slip in the oracle (dropped term, sign, index,
 transposed operand) fails at least one of these."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -342,3 +343,36 @@ def test_fde1d_run_residuals():
         b = u + w.dt * w.source(m * w.dt)
         u = np.linalg.solve(A, b)
     np.testing.assert_allclose(O.fde1d_run(w), u, rtol=1e-12, atol=1e-14)
+
+
+def _golden_qsrank():
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_1d_qsrank.txt")
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            a, n, r = line.split()
+            rows.append((float(a), int(n), int(r)))
+    return rows
+
+
+def test_paper_printed_qsrank_alpha18():
+    """Golden value printed by the paper (§6.1, Table tab:1Da): qsrank_eps = 11 at
+    N = 8192, alpha = 1.8, eps = 1e-8, with the experiment's grid and coefficients.
+    The oracle's operator, truncated at eps ||A||_2, has the same rank on the top
+    level cut (max of the lower and upper blocks).  (For alpha = 1.2 the paper
+    prints 11 and the SVD threshold gives 13: the paper's compression is not
+    specified, see the readings.)"""
+    rows = {(a, n): r for a, n, r in _golden_qsrank()}
+    alpha, N = 1.8, 8192
+    h = 1.0 / (N + 2)
+    x = np.arange(1, N + 1) * h
+    G = math.gamma(3 - alpha)
+    op = I.OpSpec(N, alpha, h, h, 1.0, G * x ** alpha, G * (2 - x) ** alpha, 256, 1e-8)
+    A = O.fd_operator(op)
+    nrm = O.norm2_power(A)
+    k = N // 2
+    lo = sla.svdvals(A[k:, :k])
+    up = sla.svdvals(A[:k, k:])
+    q = max(int((lo > 1e-8 * nrm).sum()), int((up > 1e-8 * nrm).sum()))
+    assert q == rows[(alpha, N)]
