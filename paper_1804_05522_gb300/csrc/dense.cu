@@ -89,6 +89,16 @@ __global__ void __launch_bounds__(256) gemm_batched_kernel(const GemmDesc<T>* __
     }
     __syncthreads();
   }
+  // beta C: every load before the first store (a store in between would order
+  // the next load behind it, as the compiler cannot rule out aliasing)
+  T cv[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gm = m0 + tx + 16 * i, gn = n0 + ty + 16 * j;
+      cv[i][j] = (beta != T(0) && gm < d.m && gn < d.n) ? d.C[gm + (size_t)gn * d.ldc] : T(0);
+    }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int gn = n0 + ty + 16 * j;
@@ -97,8 +107,7 @@ __global__ void __launch_bounds__(256) gemm_batched_kernel(const GemmDesc<T>* __
     for (int i = 0; i < 4; ++i) {
       const int gm = m0 + tx + 16 * i;
       if (gm >= d.m) continue;
-      T* c = d.C + gm + (size_t)gn * d.ldc;
-      *c = (beta == T(0)) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
+      d.C[gm + (size_t)gn * d.ldc] = alpha * acc[i][j] + beta * cv[i][j];
     }
   }
 }
@@ -138,6 +147,7 @@ fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, b
     b.vec_a = b.vec_a && vec_ok(d.A, d.lda, ta ? 0 : d.kblk, d.kstr);
     b.vec_b = b.vec_b && vec_ok(d.B, d.ldb, tb ? d.kblk : 0, d.kstr);
     b.max_m = d.m > b.max_m ? d.m : b.max_m;
+    b.max_ldc = d.ldc > b.max_ldc ? d.ldc : b.max_ldc;
     b.max_n = d.n > b.max_n ? d.n : b.max_n;
     b.max_k = d.k > b.max_k ? d.k : b.max_k;
     b.flops += 2.0 * d.m * d.n * d.k;

@@ -26,7 +26,7 @@ struct GemmDesc {
 template <typename T>
 struct GemmBatch {
   GemmDesc<T>* d_desc = nullptr;
-  int batch = 0, max_m = 0, max_n = 0, max_k = 0;
+  int batch = 0, max_m = 0, max_n = 0, max_k = 0, max_ldc = 0;
   double flops = 0.0;  // Σ 2 m n k over the batch
   bool ta = false, tb = false;
   // every descriptor's A (resp. B) base is 16-byte aligned and its ld (and

@@ -102,7 +102,6 @@ __device__ __forceinline__ uint32_t sw_off(int r, int c) {
 
 constexpr int kLoaders = 256;              // 8 warps: global -> shared, then the epilogue
 constexpr int kMaxSlots = 8;               // MMA slots (TF32 hi / lo tiles)
-constexpr int kRaw = 3;                    // raw FP32 stages filled by cp.async
 
 __device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0) : "memory");
@@ -115,8 +114,6 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
-// barrier of the loader warps only (named barrier 1)
-__device__ __forceinline__ void loader_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kLoaders) : "memory"); }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -128,49 +125,58 @@ __device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const float* src,
 // Asynchronous copy of an R x 32 tile of op(X) (element (row, k): X[k + row*ld]
 // when KCONTIG, else X[row + col(k)], col(k) = k*ld or the two-level panel
 // address) into a raw stage at dst; out-of-range elements are zero-filled.
+// Every loader thread copies exactly the 16-byte chunks that it converts
+// afterwards (tile_convert / tile_convert_mn), so it only waits for its own
+// copies and never for the other loaders.
 //  - row-contiguous X: the raw stage is row-contiguous too (raw[k * R + row]);
-//    each 16-byte copy takes 4 consecutive rows of one k, so a warp moves 512
-//    contiguous bytes per instruction; tile_convert_mn transposes.
+//    thread block b = (mg, kg) owns rows 4mg..4mg+3 x k 4kg..4kg+3, four
+//    16-byte copies; the lanes of a warp take consecutive mg, so one copy
+//    instruction moves up to 512 contiguous bytes.
 //  - k-contiguous X: the raw stage already has the swizzled K-major layout of
-//    the MMA operand; 8 lanes copy one row's 128 bytes.
+//    the MMA operand; chunk ch = (row ch / 8, k quad ch % 8), 8 lanes copy one
+//    row's 128 bytes.
 template <int R, bool KCONTIG>
 __device__ __forceinline__ void tile_copy(uint32_t dst, const float* __restrict__ X, int ld, int kblk, long long kstr,
                                           unsigned long long kmagic, int kshift, int row0, int nrows, int k0, int K,
                                           bool vec) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!KCONTIG) {
-    constexpr int C4 = R / 4;                    // 16-byte chunks per k row
-    constexpr int PER = (32 * C4) / kLoaders;    // chunks per thread
+    constexpr int NB = (R / 4) * 8;  // 4 x 4 blocks of the tile
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-      const int ch = threadIdx.x + kLoaders * i, kl = ch / C4, r = 4 * (ch % C4);
-      const int kk = k0 + kl, grow = row0 + r;
-      const uint32_t o = dst + (uint32_t)(kl * R + r) * 4u;
-      int nvalid = nrows - grow;
-      nvalid = kk < K ? (nvalid < 0 ? 0 : nvalid > 4 ? 4 : nvalid) : 0;
-      long long col = 0;
-      if (nvalid > 0) {
-        if (kblk) {
-          const int q = (int)(((unsigned long long)kk * kmagic) >> kshift);
-          col = (long long)q * kstr + (long long)(kk - q * kblk) * ld;
-        } else {
-          col = (long long)kk * ld;
+    for (int i = 0; i < (NB + kLoaders - 1) / kLoaders; ++i) {
+      const int b = threadIdx.x + kLoaders * i;
+      if (b >= NB) break;
+      const int mg = b % (R / 4), kg = b / (R / 4);
+      const int grow = row0 + 4 * mg;
+      int nrow = nrows - grow;
+      nrow = nrow < 0 ? 0 : nrow > 4 ? 4 : nrow;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const int kl = 4 * kg + kk, kabs = k0 + kl;
+        const uint32_t o = dst + (uint32_t)(kl * R + 4 * mg) * 4u;
+        const int nvalid = kabs < K ? nrow : 0;
+        long long col = 0;
+        if (nvalid > 0) {
+          if (kblk) {
+            const int q = (int)(((unsigned long long)kabs * kmagic) >> kshift);
+            col = (long long)q * kstr + (long long)(kabs - q * kblk) * ld;
+          } else {
+            col = (long long)kabs * ld;
+          }
         }
-      }
-      const float* p = X + col + grow;
-      if (vec) {
-        cp_async16_zfill(o, nvalid > 0 ? p : X, 4 * nvalid);
-      } else {
+        const float* p = X + col + grow;
+        if (vec) {
+          cp_async16_zfill(o, nvalid > 0 ? p : X, 4 * nvalid);
+        } else {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) cp_async4(o + 4 * c, c < nvalid ? p + c : X, c < nvalid);
+          for (int c = 0; c < 4; ++c) cp_async4(o + 4 * c, c < nvalid ? p + c : X, c < nvalid);
+        }
       }
     }
   } else {
-    const int kq = lane & 7, kk = k0 + 4 * kq;
 #pragma unroll
-    for (int j = 0; j < R / 32; ++j) {
-      const int r = (R / 8) * w + 4 * j + (lane >> 3);
-      const int grow = row0 + r;
+    for (int i = 0; i < R / 32; ++i) {
+      const int ch = threadIdx.x + kLoaders * i, r = ch >> 3, kq = ch & 7;
+      const int grow = row0 + r, kk = k0 + 4 * kq;
       const float* p = X + (size_t)grow * ld + kk;
       const uint32_t o = dst + sw_off(r, 4 * kq);
       if (vec && grow < nrows && kk + 3 < K) {
@@ -188,6 +194,7 @@ __device__ __forceinline__ void tile_copy(uint32_t dst, const float* __restrict_
 
 // Raw FP32 tile -> TF32 hi (and the TF32-rounded remainder lo in split mode),
 // same swizzled offsets; thread t converts 16-byte chunks t, t + 256, ...
+// (the chunks tile_copy<R, true> gave it)
 template <int R>
 __device__ __forceinline__ void tile_convert(const uint8_t* raw, uint8_t* hi, uint8_t* lo, bool split) {
 #pragma unroll
@@ -301,6 +308,49 @@ __device__ __forceinline__ bool mbar_wait_f(uint32_t bar, uint32_t parity, volat
   return false;
 }
 
+// A position in the stream of k-tiles of one CTA: tile t (flattened index),
+// k-tile kt of its nk, the tile's problem d and origin (m0, n0).
+struct KStream {
+  int t, kt, nk, m0, n0;
+  GemmDesc<float> d;
+};
+// Moves s to the first tile at or after s.t (stepping by gridDim.x) that has
+// work (inside its problem, k > 0), at k-tile 0; false at the end.
+template <int BN>
+__device__ __forceinline__ bool next_tile(KStream& s, const GemmDesc<float>* __restrict__ descs, int tiles, int mt,
+                                          int nt) {
+  for (; s.t < tiles; s.t += gridDim.x) {
+    const int z = s.t / (mt * nt), rem = s.t - z * (mt * nt), ni = rem / mt, mi = rem - ni * mt;
+    s.d = descs[z];
+    s.m0 = mi * BM;
+    s.n0 = ni * BN;
+    if (s.m0 >= s.d.m || s.n0 >= s.d.n || s.d.k <= 0) continue;
+    s.nk = (s.d.k + BK - 1) / BK;
+    s.kt = 0;
+    return true;
+  }
+  return false;
+}
+
+// The same walk for the conversion side, which needs only the tile and its
+// k-tile count (m, n, k of the problem are read, not the whole descriptor).
+struct KPos {
+  int t, kt, nk;
+};
+template <int BN>
+__device__ __forceinline__ bool next_pos(KPos& s, const GemmDesc<float>* __restrict__ descs, int tiles, int mt,
+                                         int nt) {
+  for (; s.t < tiles; s.t += gridDim.x) {
+    const int z = s.t / (mt * nt), rem = s.t - z * (mt * nt), ni = rem / mt, mi = rem - ni * mt;
+    const int m = descs[z].m, n = descs[z].n, k = descs[z].k;
+    if (mi * BM >= m || ni * BN >= n || k <= 0) continue;
+    s.nk = (k + BK - 1) / BK;
+    s.kt = 0;
+    return true;
+  }
+  return false;
+}
+
 constexpr int kEpiWarps = 4;                                   // one per TMEM lane quarter
 constexpr int kPThreads = kLoaders + 32 * kEpiWarps + 32;      // loaders, epilogue, MMA
 constexpr int kEpiWarp0 = kLoaders / 32;                       // warps 8..11
@@ -310,11 +360,11 @@ constexpr int kMmaWarp = kEpiWarp0 + kEpiWarps;                // warp 12
 // t = blockIdx.x, blockIdx.x + gridDim.x, ... of the flattened
 // (batch, n tile, m tile) space (m fastest, so neighbouring CTAs share B).
 //  - Warps 0-7 (loaders) copy the op(A) (128 x 32) and op(B) (BN x 32) tiles
-//    of k-tile kt + 2 with cp.async into a ring of kRaw raw FP32 stages, wait
-//    for k-tile kt (cp.async.wait_group + a barrier of the loader warps), round
-//    it to TF32 (hi, and lo = remainder in split mode) into MMA slot
-//    g % mslots (g counts k-tiles over all tiles of the CTA) once the slot's
-//    `empty` barrier says its MMAs are done, and arrive on its `full` barrier.
+//    with cp.async into a ring of RAW raw FP32 stages, RAW k-tiles ahead of
+//    the k-tile g they convert (g counts k-tiles over all tiles of the CTA);
+//    each thread waits for its own copies of g, rounds them to TF32 (hi, and
+//    lo = remainder in split mode) into MMA slot g % mslots once the slot's
+//    `empty` barrier says its MMAs are done, and arrives on its `full` barrier.
 //  - Warp 12 waits on `full`, issues the tcgen05 MMAs of the slot (one
 //    elected thread) into accumulator buffer b = (tile count) & 1 in TMEM and
 //    commits them to `empty`; after the last k-tile it commits to tfull[b].
@@ -324,7 +374,9 @@ constexpr int kMmaWarp = kEpiWarp0 + kEpiWarps;                // warp 12
 // Every mbarrier wait is bounded; after a failure the roles skip their work
 // but keep the loop structure (no barrier is left waiting), raise
 // g_wait_timeout and free the TMEM.
-template <int BN, bool TA, bool TB>
+// Registers: the 13 warps sit 4/3/3/3 on the four SM sub-partitions, whose
+// register files hold 16K each, so a thread gets at most 128.
+template <int BN, int RAW, bool TA, bool TB>
 __global__ void __launch_bounds__(kPThreads, 1)
     tc_gemm_kernel(const GemmDesc<float>* __restrict__ descs, int batch, int mt, int nt, float alpha, float beta,
                    int split, int mslots, int vec_a, int vec_b) {
@@ -369,55 +421,67 @@ __global__ void __launch_bounds__(kPThreads, 1)
 
   if (warp < kLoaders / 32) {
     // ---------------- loaders
-    int g = 0;  // k-tiles done by this CTA (ring position)
+    // The k-tiles of all tiles of this CTA form one stream; the copies run
+    // RAW positions ahead of the conversion, across tile boundaries, so a
+    // tile with few k-tiles does not pay the memory latency in a prologue.
+    // Position p uses raw stage p % RAW and MMA slot p % mslots.
+    KStream is;  // the next position to copy
+    KPos cv;     // the position being converted
+    cv.t = is.t = blockIdx.x;
+    bool is_ok = next_tile<BN>(is, descs, tiles, mt, nt);
+    bool cv_ok = next_pos<BN>(cv, descs, tiles, mt, nt);
+    int p_issue = 0;
+    auto issue = [&]() {
+      // copies of position p_issue (an empty group past the end of the stream)
+      if (is_ok) {
+        const uint32_t dst = smem_u32(raw + (size_t)(p_issue % RAW) * raw_bytes<BN>());
+        const GemmDesc<float>& d = is.d;
+        const int a_kblk = TA ? 0 : d.kblk, b_kblk = TB ? d.kblk : 0;
+        tile_copy<BM, TA>(dst, d.A, d.lda, a_kblk, d.kstr, d.kmagic, d.kshift, is.m0, d.m, is.kt * BK, d.k,
+                          vec_a != 0);
+        tile_copy<BN, !TB>(dst + A_BYTES, d.B, d.ldb, b_kblk, d.kstr, d.kmagic, d.kshift, is.n0, d.n, is.kt * BK,
+                           d.k, vec_b != 0);
+        if (++is.kt == is.nk) {
+          is.t += gridDim.x;
+          is_ok = next_tile<BN>(is, descs, tiles, mt, nt);
+        }
+      }
+      cp_async_commit();
+      ++p_issue;
+    };
+#pragma unroll 1
+    for (int i = 0; i < RAW; ++i) issue();
     bool ok = true;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-      const int z = t / (mt * nt), rem = t - z * (mt * nt), ni = rem / mt, mi = rem - ni * mt;
-      const GemmDesc<float> d = descs[z];
-      const int m0 = mi * BM, n0 = ni * BN;
-      if (m0 >= d.m || n0 >= d.n) continue;
-      const int nk = (d.k + BK - 1) / BK;
-      const int a_kblk = TA ? 0 : d.kblk, b_kblk = TB ? d.kblk : 0;
-      auto issue = [&](int kt) {
-        const uint32_t dst = smem_u32(raw + (size_t)((g + kt) % kRaw) * raw_bytes<BN>());
-        tile_copy<BM, TA>(dst, d.A, d.lda, a_kblk, d.kstr, d.kmagic, d.kshift, m0, d.m, kt * BK, d.k, vec_a != 0);
-        tile_copy<BN, !TB>(dst + A_BYTES, d.B, d.ldb, b_kblk, d.kstr, d.kmagic, d.kshift, n0, d.n, kt * BK, d.k,
-                           vec_b != 0);
-      };
-#pragma unroll
-      for (int kt = 0; kt < kRaw - 1; ++kt) {
-        if (kt < nk) issue(kt);
-        cp_async_commit();
+    for (int gg = 0; cv_ok; ++gg) {
+      cp_async_wait<RAW - 1>();  // this thread's copies of position gg have landed
+      const int ms = gg % mslots;
+      if (gg >= mslots) {
+        // one lane per warp polls the slot's `empty` barrier
+        int got = 1;
+        if (lane == 0 && ok) got = mbar_wait_f(smem_u32(&empty_bar[ms]), (uint32_t)((gg / mslots - 1) & 1), fail);
+        ok = ok && __shfl_sync(0xffffffffu, got, 0) != 0;
       }
-      for (int kt = 0; kt < nk; ++kt) {
-        cp_async_wait<kRaw - 2>();  // this thread's copies of k-tile kt have landed
-        loader_sync();              // everyone's have; the raw stage of k-tile kt-1 is free
-        if (kt + kRaw - 1 < nk) issue(kt + kRaw - 1);
-        cp_async_commit();
-        const int gg = g + kt, ms = gg % mslots;
-        if (gg >= mslots) {
-          // one lane per warp polls the slot's `empty` barrier
-          int got = 1;
-          if (lane == 0 && ok) got = mbar_wait_f(smem_u32(&empty_bar[ms]), (uint32_t)((gg / mslots - 1) & 1), fail);
-          ok = ok && __shfl_sync(0xffffffffu, got, 0) != 0;
-        }
-        if (ok) {
-          const uint8_t* rs = raw + (size_t)(gg % kRaw) * raw_bytes<BN>();
-          uint8_t* slot = sm + (size_t)ms * slot_bytes;
-          if (TA)
-            tile_convert<BM>(rs, slot, slot + A_BYTES + B_BYTES, split != 0);
-          else
-            tile_convert_mn<BM>(rs, slot, slot + A_BYTES + B_BYTES, split != 0);
-          if (!TB)
-            tile_convert<BN>(rs + A_BYTES, slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
-          else
-            tile_convert_mn<BN>(rs + A_BYTES, slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
-          fence_proxy_async();  // this thread's tiles -> visible to the tensor core
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&full_bar[ms]));
+      if (ok) {
+        const uint8_t* rs = raw + (size_t)(gg % RAW) * raw_bytes<BN>();
+        uint8_t* slot = sm + (size_t)ms * slot_bytes;
+        if (TA)
+          tile_convert<BM>(rs, slot, slot + A_BYTES + B_BYTES, split != 0);
+        else
+          tile_convert_mn<BM>(rs, slot, slot + A_BYTES + B_BYTES, split != 0);
+        if (!TB)
+          tile_convert<BN>(rs + A_BYTES, slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
+        else
+          tile_convert_mn<BN>(rs + A_BYTES, slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
+        fence_proxy_async();  // this thread's tiles -> visible to the tensor core
       }
-      g += nk;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&full_bar[ms]));
+      // this thread's chunks of raw stage gg % RAW are free again: refill
+      issue();
+      if (++cv.kt == cv.nk) {
+        cv.t += gridDim.x;
+        cv_ok = next_pos<BN>(cv, descs, tiles, mt, nt);
+      }
     }
     cp_async_wait<0>();
   } else if (warp == kMmaWarp) {
@@ -494,21 +558,30 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = 0.f;
         }
+        // beta C: all 32 loads are issued before any store of this chunk (a
+        // store between them would order each load behind it, since the
+        // compiler cannot rule out that the columns alias)
+        float cv[32];
+        const bool rowok = ok && row < d.m;
+        // column j of the chunk at cbase[j * ldc]: one 64-bit base, 32-bit offsets
+        float* cbase = d.C + (rowok ? row + (size_t)(n0 + c0) * d.ldc : 0);
+        const int ncol = d.n - (n0 + c0);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) cv[j] = (beta != 0.f && rowok && j < ncol) ? cbase[j * d.ldc] : 0.f;
         if (c0 + 32 >= BN) {
           // the last TMEM read of this buffer: hand it back to the MMA warp
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
         }
-        if (ok && row < d.m) {
+        if (rowok) {
+          // the stores recompute their addresses from an opaque copy of the
+          // base instead of keeping the 32 load addresses live
+          float* sbase;
+          asm("mov.b64 %0, %1;" : "=l"(sbase) : "l"(cbase));
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = n0 + c0 + j;
-            if (col < d.n) {
-              float* c = d.C + row + (size_t)col * d.ldc;
-              *c = (beta == 0.f) ? alpha * v[j] : alpha * v[j] + beta * (*c);
-            }
-          }
+          for (int j = 0; j < 32; ++j)
+            if (j < ncol) sbase[j * d.ldc] = alpha * v[j] + beta * cv[j];
         }
       }
       ++lt;
@@ -530,9 +603,17 @@ constexpr size_t slot_bytes(int split) {
 // kernel's static shared memory (227 KB per block in all)
 constexpr size_t kSmemBudget = 227 * 1024 - 2048;
 
+// Raw stages per tile width: the rest of the budget after two MMA slots of the
+// 3xTF32 split (BN = 128: 3 x 32 KB + 2 x 64 KB; 64: 5 x 24 + 2 x 48; 32:
+// 7 x 20 + 2 x 40), so narrow tiles, whose long k loops stream their operand
+// from memory, keep more copies in flight.
+template <int BN>
+constexpr int raw_stages() {
+  return BN >= 128 ? 3 : BN >= 64 ? 5 : 7;
+}
 template <int BN>
 int mslots_for(int split) {
-  int s = (int)((kSmemBudget - (size_t)kRaw * raw_bytes<BN>()) / slot_bytes<BN>(split));
+  int s = (int)((kSmemBudget - (size_t)raw_stages<BN>() * raw_bytes<BN>()) / slot_bytes<BN>(split));
   return s > kMaxSlots ? kMaxSlots : s;
 }
 
@@ -560,7 +641,8 @@ fde_status tc_error_flag(int* out) {
 
 template <int BN, bool TA, bool TB>
 static fde_status set_attr() {
-  FDE_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<BN, TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  FDE_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<BN, tc::raw_stages<BN>(), TA, TB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(1024 + tc::kSmemBudget)));
   return FDE_OK;
 }
@@ -594,12 +676,13 @@ static fde_status tc_prepare_once() {
 template <int BN>
 static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t st) {
   const int mslots = tc::mslots_for<BN>(split);
-  const size_t smem = 1024 + (size_t)mslots * tc::slot_bytes<BN>(split) + (size_t)tc::kRaw * tc::raw_bytes<BN>();
+  constexpr int RAW = tc::raw_stages<BN>();
+  const size_t smem = 1024 + (size_t)mslots * tc::slot_bytes<BN>(split) + (size_t)RAW * tc::raw_bytes<BN>();
   const int which = (b.ta ? 2 : 0) + (b.tb ? 1 : 0);
-  auto kern = (which == 0) ? tc::tc_gemm_kernel<BN, false, false>
-              : (which == 1) ? tc::tc_gemm_kernel<BN, false, true>
-              : (which == 2) ? tc::tc_gemm_kernel<BN, true, false>
-                             : tc::tc_gemm_kernel<BN, true, true>;
+  auto kern = (which == 0) ? tc::tc_gemm_kernel<BN, RAW, false, false>
+              : (which == 1) ? tc::tc_gemm_kernel<BN, RAW, false, true>
+              : (which == 2) ? tc::tc_gemm_kernel<BN, RAW, true, false>
+                             : tc::tc_gemm_kernel<BN, RAW, true, true>;
   const int mt = ceil_div(b.max_m, tc::BM), nt = ceil_div(b.max_n, BN);
   const long long tiles = (long long)b.batch * mt * nt;
   if (tiles > 0x7fffffffLL) {
@@ -622,7 +705,8 @@ static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t s
 fde_status tc_gemm_run(const GemmBatch<float>& b, cudaStream_t st, bool* used) {
   *used = false;
   const int mode = tc_mode();
-  if (mode == 0 || b.max_m < 64 || b.max_n < 16 || b.max_k < 32) return FDE_OK;
+  // (the epilogue addresses the 32 columns of a chunk with 32-bit offsets j * ldc)
+  if (mode == 0 || b.max_m < 64 || b.max_n < 16 || b.max_k < 32 || b.max_ldc > (1 << 26)) return FDE_OK;
   FDE_TRY(tc_prepare());
   const int split = (mode == 3) ? 1 : 0;
   if (b.max_n <= 32)
