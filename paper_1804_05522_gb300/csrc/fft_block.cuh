@@ -11,8 +11,9 @@ constexpr int kFftBlockLogP = 13;
 
 // Spectra of the nb = ceil(N / kFftBlock) windows of the GL weights,
 //   h_D[m] = g[(D-1) B + 1 + m],  m < 2B   (g[k] = 0 outside 0..N),
-// one per block distance D = 0..nb-1: Hhat[D * 2B + k].  FP64 (double2) and
-// the double-float split (float4) of the same values.
+// one per block distance D = 0..nb-1: Hhat[D * 2B + k], k in the digit-reversed
+// order of fft_forward (fft_core.cuh).  FP64 (double2) and the double-float
+// split (float4) of the same values.  tw: e^{-2πik/2B}, k < 2B.
 fde_status block_spectra(const double* g, int N, const double2* tw, double2* Hhat, float4* Hhat_df, cudaStream_t st);
 
 // Output modes of the operator products below.

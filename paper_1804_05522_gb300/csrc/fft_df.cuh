@@ -11,8 +11,9 @@ namespace fde {
 // double-float arithmetic (pairs of FP32 numbers, ~48 significant bits) on
 // the FP32 pipe; the result is accumulated into R in FP64.  Meant for small
 // updates x = δX of an iterative refinement, whose error budget scales with
-// ||δX||.  Ghat / tw: spectrum of g_0..g_N and twiddles e^{-2πik/P}, k < P/2,
-// as double-float complex (x = re.hi, y = re.lo, z = im.hi, w = im.lo).
+// ||δX||.  Ghat: spectrum of g_0..g_N in the digit-reversed order of
+// fft_forward (fft_core.cuh); tw: twiddles e^{-2πik/P}, k < P; both as
+// double-float complex (x = re.hi, y = re.lo, z = im.hi, w = im.lo).
 // scratch: ceil(ncols/2) * P float4.
 fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols, double* R, long long rs,
                            long long rc, const float4* Ghat, const float4* tw, int P, int logP, const double* dp,

@@ -19,6 +19,7 @@
 #include <cmath>
 
 #include "fft_block.cuh"
+#include "fft_core.cuh"
 #include "fft_df.cuh"
 #include "hodlr_internal.cuh"
 #include "schur.cuh"
@@ -254,76 +255,60 @@ __global__ void transpose_kernel(const double* __restrict__ X, double* __restric
 }
 
 // ------------------------------------------------------------- FFT (FP64)
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// in-place radix-2 DIT on buf (input in bit-reversed order); tw[k] = e^{-2πik/P}
-__device__ void fft_dit(double2* buf, int P, int logP, const double2* __restrict__ tw, bool inverse) {
-  for (int s = 1; s <= logP; ++s) {
-    const int half = 1 << (s - 1), tstride = P >> s;
-    for (int bidx = threadIdx.x; bidx < (P >> 1); bidx += blockDim.x) {
-      const int grp = bidx >> (s - 1), j = bidx & (half - 1);
-      const int i0 = (grp << s) + j, i1 = i0 + half;
-      double2 w = tw[j * tstride];
-      if (inverse) w.y = -w.y;
-      const double2 u = buf[i0], v = cmul(buf[i1], w);
-      buf[i0] = make_double2(u.x + v.x, u.y + v.y);
-      buf[i1] = make_double2(u.x - v.x, u.y - v.y);
-    }
-    __syncthreads();
-  }
-}
+// Threads of the residual's FFT kernels (radix-8 passes: P / 8 butterflies).
+constexpr int kFftThreads = 512;
 
 // Columns j0 = 2b, j1 = 2b+1 of X (N x ncols): Y = A X (mode 0) or
 // Y = C - A X (mode 1), A = s I + c (D_+ T + D_- Tᵀ) applied by FFT:
 //   (T x)_i  = -(g * x)[i+1]          (linear convolution, Eq. (toeplitz_FD))
 //   (Tᵀx)_i  = -(g ⋆ x)[i-1]          (correlation = conj(ĝ) in frequency)
-// Two real columns share one complex transform (x_0 + i x_1).
-__global__ void __launch_bounds__(1024) fd_fft_apply_kernel(const double* __restrict__ X, int ncols,
-                                                           const double* __restrict__ Cm, double* __restrict__ Y,
-                                                           const double2* __restrict__ Ghat,
-                                                           const double2* __restrict__ tw, int P, int logP,
-                                                           const double* __restrict__ dp,
-                                                           const double* __restrict__ dm, double c, double shift,
-                                                           int N, double2* __restrict__ scratch, int mode) {
+// Two real columns share one complex transform (x_0 + i x_1).  Ghat and the
+// saved transform Xh are in the digit-reversed order of fft_forward.
+__global__ void __launch_bounds__(kFftThreads) fd_fft_apply_kernel(const double* __restrict__ X, int ncols,
+                                                                  const double* __restrict__ Cm,
+                                                                  double* __restrict__ Y,
+                                                                  const double2* __restrict__ Ghat,
+                                                                  const double2* __restrict__ tw, int P, int logP,
+                                                                  const double* __restrict__ dp,
+                                                                  const double* __restrict__ dm, double c,
+                                                                  double shift, int N, double2* __restrict__ scratch,
+                                                                  int mode) {
   extern __shared__ double2 buf[];
   const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
   const bool has1 = j1 < ncols;
   const double* x0 = X + (size_t)j0 * N;
   const double* x1 = X + (size_t)j1 * N;
   double2* Xh = scratch + (size_t)blockIdx.x * P;
-  const unsigned sh = 32 - logP;
   for (int n = threadIdx.x; n < P; n += blockDim.x) {
     double2 v = make_double2(0.0, 0.0);
     if (n < N) v = make_double2(x0[n], has1 ? x1[n] : 0.0);
-    buf[__brev(n) >> sh] = v;
+    buf[fft_pad(n)] = v;
   }
   __syncthreads();
-  fft_dit(buf, P, logP, tw, false);
-  for (int k = threadIdx.x; k < P; k += blockDim.x) Xh[k] = buf[k];
+  fft_forward<ArF64>(buf, logP, tw);
+  for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    const double2 v = buf[fft_pad(k)];
+    Xh[k] = v;
+    buf[fft_pad(k)] = ArF64::mul(v, Ghat[k]);
+  }
   __syncthreads();
-  for (int k = threadIdx.x; k < P; k += blockDim.x) buf[__brev(k) >> sh] = cmul(Xh[k], Ghat[k]);
-  __syncthreads();
-  fft_dit(buf, P, logP, tw, true);
+  fft_inverse<ArF64>(buf, logP, tw);
   const double invP = 1.0 / P;
   double* y0 = Y + (size_t)j0 * N;
   double* y1 = Y + (size_t)j1 * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const double2 tx = buf[i + 1];
+    const double2 tx = buf[fft_pad(i + 1)];
     y0[i] = shift * x0[i] - c * dp[i] * tx.x * invP;
     if (has1) y1[i] = shift * x1[i] - c * dp[i] * tx.y * invP;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < P; k += blockDim.x) {
-    const double2 gh = Ghat[k];
-    buf[__brev(k) >> sh] = cmul(Xh[k], make_double2(gh.x, -gh.y));
-  }
+  for (int k = threadIdx.x; k < P; k += blockDim.x) buf[fft_pad(k)] = ArF64::mul(Xh[k], ArF64::conj(Ghat[k]));
   __syncthreads();
-  fft_dit(buf, P, logP, tw, true);
+  fft_inverse<ArF64>(buf, logP, tw);
   const double* c0 = Cm ? Cm + (size_t)j0 * N : nullptr;
   const double* c1 = Cm ? Cm + (size_t)j1 * N : nullptr;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const double2 ttx = buf[(i - 1 + P) & (P - 1)];
+    const double2 ttx = buf[fft_pad((i - 1 + P) & (P - 1))];
     double v0 = y0[i] - c * dm[i] * ttx.x * invP;
     if (mode == 1) v0 = c0[i] - v0;
     y0[i] = v0;
@@ -335,16 +320,16 @@ __global__ void __launch_bounds__(1024) fd_fft_apply_kernel(const double* __rest
   }
 }
 
-// spectrum of the zero-padded weights g_0..g_N (one transform)
-__global__ void __launch_bounds__(1024) ghat_kernel(const double* __restrict__ g, int N, const double2* __restrict__ tw,
-                                                   int P, int logP, double2* Ghat) {
+// spectrum of the zero-padded weights g_0..g_N (one transform), in the
+// digit-reversed order of fft_forward
+__global__ void __launch_bounds__(kFftThreads) ghat_kernel(const double* __restrict__ g, int N,
+                                                          const double2* __restrict__ tw, int P, int logP,
+                                                          double2* Ghat) {
   extern __shared__ double2 buf[];
-  const unsigned sh = 32 - logP;
-  for (int n = threadIdx.x; n < P; n += blockDim.x)
-    buf[__brev(n) >> sh] = make_double2(n <= N ? g[n] : 0.0, 0.0);
+  for (int n = threadIdx.x; n < P; n += blockDim.x) buf[fft_pad(n)] = make_double2(n <= N ? g[n] : 0.0, 0.0);
   __syncthreads();
-  fft_dit(buf, P, logP, tw, false);
-  for (int k = threadIdx.x; k < P; k += blockDim.x) Ghat[k] = buf[k];
+  fft_forward<ArF64>(buf, logP, tw);
+  for (int k = threadIdx.x; k < P; k += blockDim.x) Ghat[k] = buf[fft_pad(k)];
 }
 
 // Spans of the nodes of one level.
@@ -867,10 +852,10 @@ static fde_status residual(sylv_s* S, const double* C, const double* X, double* 
     return FDE_OK;
   }
   const int nb = (N + 1) / 2;
-  const size_t smem = (size_t)P * sizeof(double2);
+  const size_t smem = (size_t)fft_padded_len(P) * sizeof(double2);
   {
     ProfScope ps("fft_apply", st, S->fft_flops, 1);
-    fd_fft_apply_kernel<<<nb, 1024, smem, st>>>(X, N, C, R, S->GhX, S->tw, P, lp, ax->dp, ax->dm, ax->c,
+    fd_fft_apply_kernel<<<nb, kFftThreads, smem, st>>>(X, N, C, R, S->GhX, S->tw, P, lp, ax->dp, ax->dm, ax->c,
                                                  ax->p.shift, N, S->fft_scratch, 1);
     FDE_LAUNCH("fd_fft_apply_kernel x");
   }
@@ -882,7 +867,7 @@ static fde_status residual(sylv_s* S, const double* C, const double* X, double* 
   }
   {
     ProfScope ps("fft_apply", st, S->fft_flops, 1);
-    fd_fft_apply_kernel<<<nb, 1024, smem, st>>>(S->Xt, N, nullptr, S->Yt, S->GhY, S->tw, P, lp, ay->dp, ay->dm,
+    fd_fft_apply_kernel<<<nb, kFftThreads, smem, st>>>(S->Xt, N, nullptr, S->Yt, S->GhY, S->tw, P, lp, ay->dp, ay->dm,
                                                  ay->c, ay->p.shift, N, S->fft_scratch, 0);
     FDE_LAUNCH("fd_fft_apply_kernel y");
   }
@@ -1284,19 +1269,20 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
   if (S->block) S->logP = kFftBlockLogP;
   S->P = 1 << S->logP;
   {
-    std::vector<double2> tw(S->P / 2);
-    for (int k = 0; k < S->P / 2; ++k) {
+    // the whole circle: the radix-8 passes index up to 7P/8
+    std::vector<double2> tw(S->P);
+    for (int k = 0; k < S->P; ++k) {
       const double ang = -2.0 * M_PI * (double)k / (double)S->P;
       tw[k] = make_double2(cos(ang), sin(ang));
     }
-    FDE_TRY(pool.alloc(&S->tw, S->P / 2));
+    FDE_TRY(pool.alloc(&S->tw, S->P));
     FDE_CUDA(cudaMemcpy(S->tw, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
   }
   if (prec != FDE_FP64) {
     const char* rm = getenv("FDE_RESID");
     S->resid_df = !(rm && strcmp(rm, "fp64") == 0);
-    FDE_TRY(pool.alloc(&S->tw_df, S->P / 2));
-    FDE_TRY(complex_to_df(S->tw, S->tw_df, S->P / 2, st));
+    FDE_TRY(pool.alloc(&S->tw_df, S->P));
+    FDE_TRY(complex_to_df(S->tw, S->tw_df, S->P, st));
   }
   const size_t NN = (size_t)N * N;
   if (S->block) {
@@ -1314,14 +1300,14 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
   } else {
     FDE_TRY(pool.alloc(&S->GhX, S->P));
     FDE_TRY(pool.alloc(&S->GhY, S->P));
-    const size_t smem = (size_t)S->P * sizeof(double2);
+    const size_t smem = (size_t)fft_padded_len(S->P) * sizeof(double2);
     // the attribute is per kernel, shared by every handle: always allow the largest transform
-    const int smax = 8192 * (int)sizeof(double2);
+    const int smax = fft_padded_len(8192) * (int)sizeof(double2);
     FDE_CUDA(cudaFuncSetAttribute(fd_fft_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
     FDE_CUDA(cudaFuncSetAttribute(ghat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    ghat_kernel<<<1, 1024, smem, st>>>(ax->g, N, S->tw, S->P, S->logP, S->GhX);
+    ghat_kernel<<<1, kFftThreads, smem, st>>>(ax->g, N, S->tw, S->P, S->logP, S->GhX);
     FDE_LAUNCH("ghat_kernel");
-    ghat_kernel<<<1, 1024, smem, st>>>(ay->g, N, S->tw, S->P, S->logP, S->GhY);
+    ghat_kernel<<<1, kFftThreads, smem, st>>>(ay->g, N, S->tw, S->P, S->logP, S->GhY);
     FDE_LAUNCH("ghat_kernel");
     if (prec != FDE_FP64) {
       FDE_TRY(pool.alloc(&S->GhX_df, S->P));
