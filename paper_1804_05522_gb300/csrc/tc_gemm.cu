@@ -98,6 +98,14 @@ __device__ __forceinline__ float to_tf32(float x) {
 __device__ __forceinline__ uint32_t sw_off(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((c >> 2) ^ (r & 7)) & 7) << 4) + ((c & 3) << 2));
 }
+// Byte offset of 16-byte chunk c (rows 4c..4c+3) of k row kl in a raw
+// row-contiguous stage of R rows: R / 4 chunks per k row, the chunk column
+// XOR-ed with kl / 4 (mod 8) so that 8 different k quads of one chunk column
+// fall in 8 different bank groups (R / 4 is a multiple of 8).
+template <int R>
+__device__ __forceinline__ uint32_t mn_raw_off(int kl, int c) {
+  return (uint32_t)((kl * (R / 4) + (c ^ ((kl >> 2) & 7))) << 4);
+}
 
 
 constexpr int kLoaders = 256;              // 8 warps: global -> shared, then the epilogue
@@ -128,10 +136,10 @@ __device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const float* src,
 // Every loader thread copies exactly the 16-byte chunks that it converts
 // afterwards (tile_convert / tile_convert_mn), so it only waits for its own
 // copies and never for the other loaders.
-//  - row-contiguous X: the raw stage is row-contiguous too (raw[k * R + row]);
-//    thread block b = (mg, kg) owns rows 4mg..4mg+3 x k 4kg..4kg+3, four
-//    16-byte copies; the lanes of a warp take consecutive mg, so one copy
-//    instruction moves up to 512 contiguous bytes.
+//  - row-contiguous X: the raw stage holds per k a row of R values in 16-byte
+//    chunks, chunk c of k row kl at column c ^ (kl / 4 mod 8) (mn_raw_off);
+//    thread block b = (kg = b mod 8, mg = b / 8) owns rows 4mg..4mg+3 x k
+//    4kg..4kg+3, four 16-byte copies (64 contiguous bytes per 4 lanes).
 //  - k-contiguous X: the raw stage already has the swizzled K-major layout of
 //    the MMA operand; chunk ch = (row ch / 8, k quad ch % 8), 8 lanes copy one
 //    row's 128 bytes.
@@ -145,14 +153,14 @@ __device__ __forceinline__ void tile_copy(uint32_t dst, const float* __restrict_
     for (int i = 0; i < (NB + kLoaders - 1) / kLoaders; ++i) {
       const int b = threadIdx.x + kLoaders * i;
       if (b >= NB) break;
-      const int mg = b % (R / 4), kg = b / (R / 4);
+      const int kg = b & 7, mg = b >> 3;
       const int grow = row0 + 4 * mg;
       int nrow = nrows - grow;
       nrow = nrow < 0 ? 0 : nrow > 4 ? 4 : nrow;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const int kl = 4 * kg + kk, kabs = k0 + kl;
-        const uint32_t o = dst + (uint32_t)(kl * R + 4 * mg) * 4u;
+        const uint32_t o = dst + mn_raw_off<R>(kl, mg);
         const int nvalid = kabs < K ? nrow : 0;
         long long col = 0;
         if (nvalid > 0) {
@@ -219,15 +227,12 @@ __device__ __forceinline__ void tile_convert(const uint8_t* raw, uint8_t* hi, ui
   }
 }
 
-__device__ __forceinline__ float pick4(const float (&v)[4], int j) {
-  return j == 0 ? v[0] : j == 1 ? v[1] : j == 2 ? v[2] : v[3];
-}
-
-// Row-contiguous raw stage (raw[k * R + row]) -> swizzled K-major TF32 hi
-// (and lo).  Thread block (mg, kg): rows 4mg..4mg+3 x k 4kg..4kg+3, read as
-// four 16-byte row segments and transposed in registers; the four stores
-// visit the rows in an order rotated by (mg >> 1) & 3, so the 8 lanes of a
-// quarter warp always hit 8 different 16-byte bank groups.
+// Row-contiguous raw stage (mn_raw_off) -> swizzled K-major TF32 hi (and lo).
+// Thread block (kg = b mod 8, mg = b / 8): rows 4mg..4mg+3 x k 4kg..4kg+3,
+// read as four 16-byte row segments and transposed in registers.  The 8
+// lanes of a quarter warp share mg and take kg = 0..7: their reads hit
+// chunk columns mg ^ kg and their stores the swizzled chunks kg ^ (row mod 8),
+// 8 distinct bank groups either way, in a fixed order.
 template <int R>
 __device__ __forceinline__ void tile_convert_mn(const uint8_t* raw, uint8_t* hi, uint8_t* lo, bool split) {
   constexpr int NB = (R / 4) * 8;
@@ -235,26 +240,18 @@ __device__ __forceinline__ void tile_convert_mn(const uint8_t* raw, uint8_t* hi,
   for (int i = 0; i < (NB + kLoaders - 1) / kLoaders; ++i) {
     const int b = threadIdx.x + kLoaders * i;
     if (b >= NB) break;
-    const int mg = b % (R / 4), kg = b / (R / 4);
-    float v[4][4];  // v[kk][rr]
+    const int kg = b & 7, mg = b >> 3;
+    float4 q[4];  // q[kk] = rows 4mg..4mg+3 at k = 4kg + kk
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      const float4 q = *reinterpret_cast<const float4*>(raw + (size_t)((4 * kg + kk) * R + 4 * mg) * 4);
-      v[kk][0] = q.x;
-      v[kk][1] = q.y;
-      v[kk][2] = q.z;
-      v[kk][3] = q.w;
-    }
-    const int rot = (mg >> 1) & 3;
+    for (int kk = 0; kk < 4; ++kk) q[kk] = *reinterpret_cast<const float4*>(raw + mn_raw_off<R>(4 * kg + kk, mg));
 #pragma unroll
-    for (int st = 0; st < 4; ++st) {
-      const int rr = (st + rot) & 3;
+    for (int rr = 0; rr < 4; ++rr) {
       const uint32_t off = sw_off(4 * mg + rr, 4 * kg);
       float4 x, h;
-      x.x = pick4(v[0], rr);
-      x.y = pick4(v[1], rr);
-      x.z = pick4(v[2], rr);
-      x.w = pick4(v[3], rr);
+      x.x = rr == 0 ? q[0].x : rr == 1 ? q[0].y : rr == 2 ? q[0].z : q[0].w;
+      x.y = rr == 0 ? q[1].x : rr == 1 ? q[1].y : rr == 2 ? q[1].z : q[1].w;
+      x.z = rr == 0 ? q[2].x : rr == 1 ? q[2].y : rr == 2 ? q[2].z : q[2].w;
+      x.w = rr == 0 ? q[3].x : rr == 1 ? q[3].y : rr == 2 ? q[3].z : q[3].w;
       h.x = to_tf32(x.x);
       h.y = to_tf32(x.y);
       h.z = to_tf32(x.z);
