@@ -139,14 +139,16 @@ def family_roofline(fam, ms, launches, work, kind, peaks):
         r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
              "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     elif fam == "gemm32tc":
-        # tcgen05 kind::tf32; peak = measured bf16 (sustained: the kernel runs
-        # inside a long step) x nominal tf32/bf16 dense ratio 1.1/2.25
+        # tcgen05 kind::tf32 in the 3xTF32 split: every FP32 product costs three
+        # TF32 MMAs (hi*hi, hi*lo, lo*hi), so the peak for its algorithmic
+        # (2mnk) flops is the TF32 peak / 3; TF32 peak = measured bf16
+        # (sustained: the kernel runs inside a long step) x nominal 1.1/2.25
         achieved = work_per_launch / per_launch_s / 1e12
         bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-        peak = bf16 * 1.1 / 2.25
+        peak = bf16 * 1.1 / 2.25 / 3.0
         r = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
              "peak_source": ("measured" if "bf16_tflops_sustained" in peaks else "fallback")
-             + " sustained bf16 x 1.1/2.25 (tf32)"}
+             + " sustained bf16 x 1.1/2.25 (tf32) / 3 (3xTF32: three MMAs per FP32 product)"}
     elif fam == "fft_df":
         achieved = work_per_launch / per_launch_s / 1e12
         peak = FP32_SIMT_PEAK_TFLOPS / DF_OPS_PER_FLOP
@@ -167,8 +169,12 @@ def family_roofline(fam, ms, launches, work, kind, peaks):
 
 FAMILIES = ["gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply", "fft_df", "transpose", "refine",
             "fadi_axpy"]
-# double-float FFT: a radix-2 butterfly (10 real flops) costs ~148 FP32 operations
-DF_OPS_PER_FLOP = 14.8
+# double-float FFT: FP32 operations per algorithmic flop (5 P log2 P per
+# transform, 6 per complex product) of the radix-8 kernel with the normwise
+# double-float addition: a radix-8 butterfly costs 950 operations for 120
+# flops, a radix-2 pass butterfly 44 for 10, a complex product 50 for 6; for
+# the P = 8192 column-pair kernel (3 transforms + 2 spectral products) 7.7
+DF_OPS_PER_FLOP = 7.7
 
 
 def roofline(lib, N):

@@ -15,14 +15,19 @@ constexpr int kThreads = 512;
 // Columns j0 = 2b, j1 = 2b + 1 share one complex transform (x_0 + i x_1):
 //   (T x)_i  = -(g * x)[i+1],   (Tᵀx)_i = -(g ⋆ x)[i-1]   (correlation: conj(ĝ))
 // Ghat and the saved transform are in the digit-reversed order of fft_forward.
+// The update  R(i, j) -= shift x_j(i) - cp(i) (g * x_j)[i+1] - cm(i) (g ⋆ x_j)[i-1]
+// (cp, cm = c d_± / P as double-float pairs) is formed in double-float
+// arithmetic, the T part kept in shared memory until the Tᵀ part is known, so
+// R is read and written once with a few FP64 operations per element.
 __global__ void __launch_bounds__(kThreads) fd_fft_sub_df_kernel(const float* __restrict__ X, long long xs,
                                                                 long long xc, int ncols, double* R, long long rs,
                                                                 long long rc, const float4* __restrict__ Ghat,
                                                                 const float4* __restrict__ tw, int P, int logP,
-                                                                const double* __restrict__ dp,
-                                                                const double* __restrict__ dm, double c, double shift,
-                                                                int N, float4* __restrict__ scratch) {
+                                                                const float2* __restrict__ cp,
+                                                                const float2* __restrict__ cm, float2 shift, int N,
+                                                                float4* __restrict__ scratch) {
   extern __shared__ float4 buf[];
+  float4* side = buf + fft_padded_len(P);  // N entries: the T part of both columns
   const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
   const bool has1 = j1 < ncols;
   for (int n = threadIdx.x; n < P; n += blockDim.x) {
@@ -43,16 +48,11 @@ __global__ void __launch_bounds__(kThreads) fd_fft_sub_df_kernel(const float* __
   }
   __syncthreads();
   fft_inverse<ArDF>(buf, logP, tw);
-  const double invP = 1.0 / P;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const float4 t = buf[fft_pad(i + 1)];
-    const double conv0 = (double)t.x + (double)t.y, conv1 = (double)t.z + (double)t.w;
-    const double x0 = X[i * xs + j0 * xc];
-    R[i * rs + j0 * rc] -= shift * x0 - c * dp[i] * conv0 * invP;
-    if (has1) {
-      const double x1 = X[i * xs + j1 * xc];
-      R[i * rs + j1 * rc] -= shift * x1 - c * dp[i] * conv1 * invP;
-    }
+    const float2 c = cp[i];
+    const float2 a0 = df_mul(make_float2(t.x, t.y), c), a1 = df_mul(make_float2(t.z, t.w), c);
+    side[i] = make_float4(a0.x, a0.y, a1.x, a1.y);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < P; k += blockDim.x) buf[fft_pad(k)] = ArDF::mul(Xh[k], c_conj(Ghat[k]));
@@ -60,9 +60,19 @@ __global__ void __launch_bounds__(kThreads) fd_fft_sub_df_kernel(const float* __
   fft_inverse<ArDF>(buf, logP, tw);
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const float4 t = buf[fft_pad((i - 1 + P) & (P - 1))];
-    const double conv0 = (double)t.x + (double)t.y, conv1 = (double)t.z + (double)t.w;
-    R[i * rs + j0 * rc] += c * dm[i] * conv0 * invP;
-    if (has1) R[i * rs + j1 * rc] += c * dm[i] * conv1 * invP;
+    const float4 sT = side[i];
+    const float2 c = cm[i];
+    // u = shift x - (T part + Tᵀ part), then R -= u
+    const float2 w0 = df_add_nw(make_float2(sT.x, sT.y), df_mul(make_float2(t.x, t.y), c));
+    const float2 u0 = df_add_nw(df_mul(shift, make_float2(X[i * xs + j0 * xc], 0.f)), df_neg(w0));
+    double* r0 = R + i * rs + j0 * rc;
+    *r0 = (*r0 - (double)u0.x) - (double)u0.y;
+    if (has1) {
+      const float2 w1 = df_add_nw(make_float2(sT.z, sT.w), df_mul(make_float2(t.z, t.w), c));
+      const float2 u1 = df_add_nw(df_mul(shift, make_float2(X[i * xs + j1 * xc], 0.f)), df_neg(w1));
+      double* r1 = R + i * rs + j1 * rc;
+      *r1 = (*r1 - (double)u1.x) - (double)u1.y;
+    }
   }
 }
 
@@ -77,21 +87,25 @@ __global__ void complex_to_df_kernel(const double2* __restrict__ in, float4* __r
 }  // namespace
 
 fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols, double* R, long long rs,
-                           long long rc, const float4* Ghat, const float4* tw, int P, int logP, const double* dp,
-                           const double* dm, double c, double shift, int N, float4* scratch, cudaStream_t st,
-                           double flops) {
+                           long long rc, const float4* Ghat, const float4* tw, int P, int logP, const float2* cp,
+                           const float2* cm, double shift, int N, float4* scratch, cudaStream_t st, double flops) {
   if (ncols <= 0 || N <= 0) return FDE_OK;
   if (P > 8192 || P < 2 * N) {
     set_error("fd_apply_sub_df: transform length %d outside [2N, 8192]", P);
     return FDE_ERR_ARG;
   }
-  const size_t smem = (size_t)fft_padded_len(P) * sizeof(float4);
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      fd_fft_sub_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(fft_padded_len(8192) * sizeof(float4)));
+  // padded transform buffer + the T part of N rows
+  const size_t smem = ((size_t)fft_padded_len(P) + (size_t)N) * sizeof(float4);
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(fd_fft_sub_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((fft_padded_len(8192) + 4096) * sizeof(float4)));
   FDE_CUDA(attr);
+  // shift as a double-float pair (host side: FP32 rounding of the value and the remainder)
+  const float hi = (float)shift;
+  const float2 shift2 = make_float2(hi, (float)(shift - (double)hi));
   ProfScope ps("fft_df", st, flops, 1);
-  fd_fft_sub_df_kernel<<<(ncols + 1) / 2, kThreads, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, dp, dm,
-                                                            c, shift, N, scratch);
+  fd_fft_sub_df_kernel<<<(ncols + 1) / 2, kThreads, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, cp, cm,
+                                                                shift2, N, scratch);
   FDE_LAUNCH("fd_fft_sub_df_kernel");
   return FDE_OK;
 }

@@ -6,7 +6,8 @@ namespace fde {
 
 // R(i, j) -= (A x_j)(i), i < N, j < ncols, for the columns x_j of a float
 // matrix (x_j(i) = X[i * xs + j * xc]; R(i, j) = R[i * rs + j * rc]), with
-//   A = shift I + c (D_+ T + D_- Tᵀ),   T = -[g_{i-j+1}]   (§2.2.1, Eq. (toeplitz_FD)).
+//   A = shift I + c (D_+ T + D_- Tᵀ),   T = -[g_{i-j+1}]   (§2.2.1, Eq. (toeplitz_FD)),
+// given through cp(i), cm(i) = c d_±(i) / P (double-float pairs) and shift.
 // The Toeplitz products are evaluated by FFT of length P = 2^logP >= 2N in
 // double-float arithmetic (pairs of FP32 numbers, ~48 significant bits) on
 // the FP32 pipe; the result is accumulated into R in FP64.  Meant for small
@@ -16,8 +17,8 @@ namespace fde {
 // double-float complex (x = re.hi, y = re.lo, z = im.hi, w = im.lo).
 // scratch: ceil(ncols/2) * P float4.
 fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols, double* R, long long rs,
-                           long long rc, const float4* Ghat, const float4* tw, int P, int logP, const double* dp,
-                           const double* dm, double c, double shift, int N, float4* scratch, cudaStream_t st,
+                           long long rc, const float4* Ghat, const float4* tw, int P, int logP, const float2* cp,
+                           const float2* cm, double shift, int N, float4* scratch, cudaStream_t st,
                            double flops = 0.0);
 
 // out[k] = double-float split of the complex value in[k]

@@ -263,16 +263,17 @@ constexpr int kFftThreads = 512;
 //   (T x)_i  = -(g * x)[i+1]          (linear convolution, Eq. (toeplitz_FD))
 //   (Tᵀx)_i  = -(g ⋆ x)[i-1]          (correlation = conj(ĝ) in frequency)
 // Two real columns share one complex transform (x_0 + i x_1).  Ghat and the
-// saved transform Xh are in the digit-reversed order of fft_forward.
+// saved transform Xh are in the digit-reversed order of fft_forward;
+// cp[i] = c d_+(i) / P and cm[i] = c d_-(i) / P (the inverse transforms are
+// not divided by P).
 __global__ void __launch_bounds__(kFftThreads) fd_fft_apply_kernel(const double* __restrict__ X, int ncols,
                                                                   const double* __restrict__ Cm,
                                                                   double* __restrict__ Y,
                                                                   const double2* __restrict__ Ghat,
                                                                   const double2* __restrict__ tw, int P, int logP,
-                                                                  const double* __restrict__ dp,
-                                                                  const double* __restrict__ dm, double c,
-                                                                  double shift, int N, double2* __restrict__ scratch,
-                                                                  int mode) {
+                                                                  const double* __restrict__ cp,
+                                                                  const double* __restrict__ cm, double shift, int N,
+                                                                  double2* __restrict__ scratch, int mode) {
   extern __shared__ double2 buf[];
   const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
   const bool has1 = j1 < ncols;
@@ -293,13 +294,13 @@ __global__ void __launch_bounds__(kFftThreads) fd_fft_apply_kernel(const double*
   }
   __syncthreads();
   fft_inverse<ArF64>(buf, logP, tw);
-  const double invP = 1.0 / P;
   double* y0 = Y + (size_t)j0 * N;
   double* y1 = Y + (size_t)j1 * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const double2 tx = buf[fft_pad(i + 1)];
-    y0[i] = shift * x0[i] - c * dp[i] * tx.x * invP;
-    if (has1) y1[i] = shift * x1[i] - c * dp[i] * tx.y * invP;
+    const double ci = cp[i];
+    y0[i] = fma(-ci, tx.x, shift * x0[i]);
+    if (has1) y1[i] = fma(-ci, tx.y, shift * x1[i]);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < P; k += blockDim.x) buf[fft_pad(k)] = ArF64::mul(Xh[k], ArF64::conj(Ghat[k]));
@@ -309,14 +310,28 @@ __global__ void __launch_bounds__(kFftThreads) fd_fft_apply_kernel(const double*
   const double* c1 = Cm ? Cm + (size_t)j1 * N : nullptr;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const double2 ttx = buf[fft_pad((i - 1 + P) & (P - 1))];
-    double v0 = y0[i] - c * dm[i] * ttx.x * invP;
+    const double ci = cm[i];
+    double v0 = fma(-ci, ttx.x, y0[i]);
     if (mode == 1) v0 = c0[i] - v0;
     y0[i] = v0;
     if (has1) {
-      double v1 = y1[i] - c * dm[i] * ttx.y * invP;
+      double v1 = fma(-ci, ttx.y, y1[i]);
       if (mode == 1) v1 = c1[i] - v1;
       y1[i] = v1;
     }
+  }
+}
+
+// Row coefficients of the FFT products: c d_±(i) / P in FP64 and as
+// double-float pairs (the inverse transforms leave a factor P).
+__global__ void fft_coef_kernel(const double* __restrict__ dp, const double* __restrict__ dm, double c, double invP,
+                                int N, double* cp, double* cm, float2* cp_df, float2* cm_df) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double a = c * dp[i] * invP, b = c * dm[i] * invP;
+    cp[i] = a;
+    cm[i] = b;
+    cp_df[i] = df::split_double(a);
+    cm_df[i] = df::split_double(b);
   }
 }
 
@@ -436,6 +451,9 @@ struct sylv_s {
   int P = 0, logP = 0;
   double2 *tw = nullptr, *GhX = nullptr, *GhY = nullptr, *fft_scratch = nullptr;
   float4 *tw_df = nullptr, *GhX_df = nullptr, *GhY_df = nullptr;  // double-float copies
+  // row coefficients c d_±(i) / P of the FFT products per direction (FP64, double-float)
+  double *cpx = nullptr, *cmx = nullptr, *cpy = nullptr, *cmy = nullptr;
+  float2 *cpx_df = nullptr, *cmx_df = nullptr, *cpy_df = nullptr, *cmy_df = nullptr;
   bool resid_df = false;              // later sweeps update R in double-float (FP32 inner solver)
   // N > 4096: block-Toeplitz FFTs (blocks of kFftBlock) instead of one transform per column
   bool block = false;
@@ -855,8 +873,8 @@ static fde_status residual(sylv_s* S, const double* C, const double* X, double* 
   const size_t smem = (size_t)fft_padded_len(P) * sizeof(double2);
   {
     ProfScope ps("fft_apply", st, S->fft_flops, 1);
-    fd_fft_apply_kernel<<<nb, kFftThreads, smem, st>>>(X, N, C, R, S->GhX, S->tw, P, lp, ax->dp, ax->dm, ax->c,
-                                                 ax->p.shift, N, S->fft_scratch, 1);
+    fd_fft_apply_kernel<<<nb, kFftThreads, smem, st>>>(X, N, C, R, S->GhX, S->tw, P, lp, S->cpx, S->cmx,
+                                                       ax->p.shift, N, S->fft_scratch, 1);
     FDE_LAUNCH("fd_fft_apply_kernel x");
   }
   dim3 tg(ceil_div(N, 32), ceil_div(N, 32)), tb(32, 8);
@@ -867,8 +885,8 @@ static fde_status residual(sylv_s* S, const double* C, const double* X, double* 
   }
   {
     ProfScope ps("fft_apply", st, S->fft_flops, 1);
-    fd_fft_apply_kernel<<<nb, kFftThreads, smem, st>>>(S->Xt, N, nullptr, S->Yt, S->GhY, S->tw, P, lp, ay->dp, ay->dm,
-                                                 ay->c, ay->p.shift, N, S->fft_scratch, 0);
+    fd_fft_apply_kernel<<<nb, kFftThreads, smem, st>>>(S->Xt, N, nullptr, S->Yt, S->GhY, S->tw, P, lp, S->cpy, S->cmy,
+                                                       ay->p.shift, N, S->fft_scratch, 0);
     FDE_LAUNCH("fd_fft_apply_kernel y");
   }
   {
@@ -947,9 +965,9 @@ static fde_status residual_update_df(sylv_s* S, const float* d, cudaStream_t st)
     return FDE_OK;
   }
   float4* scr = reinterpret_cast<float4*>(S->fft_scratch);
-  FDE_TRY(fd_apply_sub_df(d, 1, N, N, S->R, 1, N, S->GhX_df, S->tw_df, S->P, S->logP, ax->dp, ax->dm, ax->c,
+  FDE_TRY(fd_apply_sub_df(d, 1, N, N, S->R, 1, N, S->GhX_df, S->tw_df, S->P, S->logP, S->cpx_df, S->cmx_df,
                           ax->p.shift, N, scr, st, S->fft_flops));
-  FDE_TRY(fd_apply_sub_df(d, N, 1, N, S->R, N, 1, S->GhY_df, S->tw_df, S->P, S->logP, ay->dp, ay->dm, ay->c,
+  FDE_TRY(fd_apply_sub_df(d, N, 1, N, S->R, N, 1, S->GhY_df, S->tw_df, S->P, S->logP, S->cpy_df, S->cmy_df,
                           ay->p.shift, N, scr, st, S->fft_flops));
   return FDE_OK;
 }
@@ -1283,6 +1301,23 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
     S->resid_df = !(rm && strcmp(rm, "fp64") == 0);
     FDE_TRY(pool.alloc(&S->tw_df, S->P));
     FDE_TRY(complex_to_df(S->tw, S->tw_df, S->P, st));
+  }
+  {
+    FDE_TRY(pool.alloc(&S->cpx, N));
+    FDE_TRY(pool.alloc(&S->cmx, N));
+    FDE_TRY(pool.alloc(&S->cpy, N));
+    FDE_TRY(pool.alloc(&S->cmy, N));
+    FDE_TRY(pool.alloc(&S->cpx_df, N));
+    FDE_TRY(pool.alloc(&S->cmx_df, N));
+    FDE_TRY(pool.alloc(&S->cpy_df, N));
+    FDE_TRY(pool.alloc(&S->cmy_df, N));
+    const double invP = 1.0 / S->P;
+    fft_coef_kernel<<<grid_for(N), 256, 0, st>>>(ax->dp, ax->dm, ax->c, invP, N, S->cpx, S->cmx, S->cpx_df,
+                                                 S->cmx_df);
+    FDE_LAUNCH("fft_coef_kernel");
+    fft_coef_kernel<<<grid_for(N), 256, 0, st>>>(ay->dp, ay->dm, ay->c, invP, N, S->cpy, S->cmy, S->cpy_df,
+                                                 S->cmy_df);
+    FDE_LAUNCH("fft_coef_kernel");
   }
   const size_t NN = (size_t)N * N;
   if (S->block) {
