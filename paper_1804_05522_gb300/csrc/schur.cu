@@ -254,16 +254,17 @@ constexpr int kMaxRowWarps = 9;   // leaves up to 256 rows: blocks of >= 31 rows
 
 template <typename T>
 __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 ? 128 : 168)
-    trsyl_kernel(const T* __restrict__ Sall, const T* __restrict__ Rall, int lmax, const int* __restrict__ lo_x,
-                 const int* __restrict__ n_x, int nx, const int* __restrict__ lo_y, const int* __restrict__ n_y,
+    trsyl_kernel(const T* __restrict__ Sall, const T* __restrict__ Rall, int ld, int lmax,
+                 const int* __restrict__ soff_x, const int* __restrict__ lo_x, const int* __restrict__ n_x, int nx,
+                 const int* __restrict__ soff_y, const int* __restrict__ lo_y, const int* __restrict__ n_y,
                  T* __restrict__ W, int ldw, int use_panel, int panel_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = blockIdx.x % nx, q = blockIdx.x / nx;
   const int n1 = n_x[p], n2 = n_y[q];
   if (n1 <= 0 || n2 <= 0) return;
   T* Y = W + lo_x[p] + (size_t)lo_y[q] * ldw;
-  const T* S = Sall + (size_t)p * lmax * lmax;
-  const T* R = Rall + (size_t)q * lmax * lmax;
+  const T* S = Sall + soff_x[p];  // leading dimension ld
+  const T* R = Rall + soff_y[q];
   // ring of solved columns: one slot per launched warp + 1 (a slot is reread
   // by the warps above for nwarps - 1 steps after it is written)
   const int ring = (int)(blockDim.x >> 5) + 1;
@@ -275,8 +276,8 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
   int* cg_cblo = cg_info + lmax;                             // first column of the group's column block
   __shared__ int rb_lo[kMaxRowWarps], rb_n[kMaxRowWarps], poff[kMaxRowWarps];
   __shared__ int s_ncg, s_nrb;
-#define SS(i, j) S[(i) + (size_t)(j)*lmax]
-#define RR(i, j) R[(i) + (size_t)(j)*lmax]
+#define SS(i, j) S[(i) + (size_t)(j)*ld]
+#define RR(i, j) R[(i) + (size_t)(j)*ld]
   if (threadIdx.x == 0) {
     int w = 0;
     for (int hi = n1; hi > 0 && w < kMaxRowWarps; ++w) {
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
 #pragma unroll 4
         for (int l = k + 1; l < n2; ++l) {
           const T yl = active ? Y[i + (size_t)l * ldw] : T(0);
-          const T* Rl = R + (size_t)l * lmax;
+          const T* Rl = R + (size_t)l * ld;
 #pragma unroll
           for (int t = 0; t < 32; ++t) {
             const int col = k - 31 + t;
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
           fa -= a0 + a1;
         } else {
           for (int j = rhi; j < n1; ++j) {
-            const T sij = __ldg(S + i + (size_t)j * lmax);
+            const T sij = __ldg(S + i + (size_t)j * ld);
             fb -= sij * yk[j];
             if (two) fa -= sij * yk[lmax + j];
           }
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
       }
       T ya_fin = T(0), yb_fin = T(0);
       if (!two) {
-        const T mu = __ldg(R + k + (size_t)k * lmax);
+        const T mu = __ldg(R + k + (size_t)k * ld);
         T inv = T(1) / (sii + mu), p00 = T(0), p01 = T(0), p10 = T(0), p11 = T(0);
         if (bottom) {  // inverse of (S_2x2 + mu I)
           const T d = (s00 + mu) * (s11 + mu) - s01 * s10;
@@ -452,8 +453,8 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
         }
       } else {
         // R block [[a, b], [c, d]] couples columns k-1 (unknown 1) and k (unknown 2)
-        const T a = __ldg(R + (k - 1) + (size_t)(k - 1) * lmax), b = __ldg(R + (k - 1) + (size_t)k * lmax);
-        const T c = __ldg(R + k + (size_t)(k - 1) * lmax), d = __ldg(R + k + (size_t)k * lmax);
+        const T a = __ldg(R + (k - 1) + (size_t)(k - 1) * ld), b = __ldg(R + (k - 1) + (size_t)k * ld);
+        const T c = __ldg(R + k + (size_t)(k - 1) * ld), d = __ldg(R + k + (size_t)k * ld);
         // 1 x 1 row: [[s+a, b], [c, s+d]]^{-1}
         const T det1 = (sii + a) * (sii + d) - b * c;
         const T e00 = (sii + d) / det1, e01 = -b / det1, e10 = -c / det1, e11 = (sii + a) / det1;
@@ -526,8 +527,8 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
         }
       }
       // remove the group's coupling from the rest of the window, then shift it
-      const T* Rk = R + (size_t)k * lmax;
-      const T* Rk1 = R + (size_t)(k - 1) * lmax;
+      const T* Rk = R + (size_t)k * ld;
+      const T* Rk1 = R + (size_t)(k - 1) * ld;
 #pragma unroll
       for (int t = 0; t < 31; ++t) {
         const int col = k - 31 + t;
@@ -555,10 +556,11 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
 }
 
 template <typename T>
-fde_status leaf_trsyl(const T* S, const T* R, int lmax, const int* d_lo_x, const int* d_n_x, int nx,
-                      const int* d_lo_y, const int* d_n_y, int ny, T* W, int ldw, cudaStream_t st, double flops) {
-  if (lmax > 32 * kMaxRowWarps - kMaxRowWarps) {
-    set_error("leaf_trsyl: leaf size %d above %d", lmax, 32 * kMaxRowWarps - kMaxRowWarps);
+fde_status leaf_trsyl(const T* S, const T* R, int ld, int lmax, const int* d_soff_x, const int* d_lo_x,
+                      const int* d_n_x, int nx, const int* d_soff_y, const int* d_lo_y, const int* d_n_y, int ny,
+                      T* W, int ldw, cudaStream_t st, double flops) {
+  if (lmax > 32 * kMaxRowWarps - kMaxRowWarps || lmax > ld) {
+    set_error("leaf_trsyl: problem size %d above %d (or above ld %d)", lmax, 32 * kMaxRowWarps - kMaxRowWarps, ld);
     return FDE_ERR_ARG;
   }
   const int warps = (lmax + 30) / 31 < kMaxRowWarps ? (lmax + 30) / 31 : kMaxRowWarps;
@@ -575,15 +577,15 @@ fde_status leaf_trsyl(const T* S, const T* R, int lmax, const int* d_lo_x, const
       cudaFuncSetAttribute(trsyl_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
   FDE_CUDA(attr);
   ProfScope ps(sizeof(T) == 4 ? "trsyl32" : "trsyl64", st, flops, 1);
-  trsyl_kernel<T><<<nx * ny, warps * 32, smem, st>>>(S, R, lmax, d_lo_x, d_n_x, nx, d_lo_y, d_n_y, W, ldw, use_panel,
-                                                     panel_elems);
+  trsyl_kernel<T><<<nx * ny, warps * 32, smem, st>>>(S, R, ld, lmax, d_soff_x, d_lo_x, d_n_x, nx, d_soff_y, d_lo_y,
+                                                     d_n_y, W, ldw, use_panel, panel_elems);
   FDE_LAUNCH("trsyl_kernel");
   return FDE_OK;
 }
 
-template fde_status leaf_trsyl<double>(const double*, const double*, int, const int*, const int*, int, const int*,
-                                       const int*, int, double*, int, cudaStream_t, double);
-template fde_status leaf_trsyl<float>(const float*, const float*, int, const int*, const int*, int, const int*,
-                                      const int*, int, float*, int, cudaStream_t, double);
+template fde_status leaf_trsyl<double>(const double*, const double*, int, int, const int*, const int*, const int*,
+                                       int, const int*, const int*, const int*, int, double*, int, cudaStream_t, double);
+template fde_status leaf_trsyl<float>(const float*, const float*, int, int, const int*, const int*, const int*, int,
+                                      const int*, const int*, const int*, int, float*, int, cudaStream_t, double);
 
 }  // namespace fde

@@ -13,14 +13,17 @@ namespace fde {
 fde_status leaf_schur(double* H, double* Q, int ld, size_t stride, const int* d_n, int count, int* d_fail,
                       cudaStream_t st);
 
-// For every leaf pair (p, q) (p over nleaves_x, q over nleaves_y) solve
-//   S_p Y + Y R_qᵀ = C   in place on the (p, q) block of W (ld ldw),
-// S_p, R_q upper quasi-triangular (leaf Schur forms).  Bartels–Stewart
-// back substitution over 1x1 / 2x2 diagonal blocks.
+// For every pair (p, q) (p < nx, q < ny) solve
+//   S_p Y + Y R_qᵀ = C   in place on rows lo_x[p].. and columns lo_y[q].. of W
+// (ld ldw), S_p = S + soff_x[p] (n_x[p] x n_x[p]) and R_q = R + soff_y[q]
+// (n_y[q] x n_y[q]), both with leading dimension ld, upper quasi-triangular
+// (leaf Schur forms or diagonal blocks of them that split no 2x2 block).
+// Bartels–Stewart back substitution over 1x1 / 2x2 diagonal blocks.
+// lmax >= every n_x[p], n_y[q] (sizes the launch).
 // flops: algorithmic work for the instrumentation (Σ n1 n2 (n1 + n2)).
 template <typename T>
-fde_status leaf_trsyl(const T* S, const T* R, int lmax, const int* d_lo_x, const int* d_n_x, int nx,
-                      const int* d_lo_y, const int* d_n_y, int ny, T* W, int ldw, cudaStream_t st,
-                      double flops = 0.0);
+fde_status leaf_trsyl(const T* S, const T* R, int ld, int lmax, const int* d_soff_x, const int* d_lo_x,
+                      const int* d_n_x, int nx, const int* d_soff_y, const int* d_lo_y, const int* d_n_y, int ny,
+                      T* W, int ldw, cudaStream_t st, double flops = 0.0);
 
 }  // namespace fde

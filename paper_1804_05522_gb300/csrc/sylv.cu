@@ -255,6 +255,11 @@ __global__ void transpose_kernel(const double* __restrict__ X, double* __restric
 }
 
 // ------------------------------------------------------------- FFT (FP64)
+// Leaves above this many rows are split into two diagonal blocks for the FP32
+// leaf Sylvester solves (each block then fits the kernel's 128-row shape,
+// three CTAs per SM instead of one).
+constexpr int kTrsylSplit = 128;
+
 // Threads of the residual's FFT kernels (radix-8 passes: P / 8 butterflies).
 constexpr int kFftThreads = 512;
 
@@ -427,6 +432,9 @@ struct Inner {
   T *Cin = nullptr, *W1 = nullptr, *W2 = nullptr, *X = nullptr;
   T *Qx = nullptr, *Sx = nullptr, *Qy = nullptr, *Sy = nullptr;
   GemmBatch<T> g_qxt, g_qy, g_qx, g_qyt;
+  // split leaves (sylv_s::trsyl_split): couplings between the diagonal blocks
+  //   F12 -= S12 Y22,  F21 -= Y22 R12ᵀ,  F11 -= S12 Y21,  F11 -= Y12 R12ᵀ
+  GemmBatch<T> g_sp1, g_sp2, g_sp3, g_sp4;
   std::vector<LevelSolve<T>> lv;
   std::vector<Fact<T>> facts;         // keeps FP32 demoted factorisations alive
 };
@@ -444,6 +452,17 @@ struct sylv_s {
   DevPool pool;
   double *Qx = nullptr, *Sx = nullptr, *Qy = nullptr, *Sy = nullptr;  // FP64 leaf Schur forms
   int *d_lo = nullptr, *d_n = nullptr;
+  // Leaf Sylvester sub-problems per part (x at [0, nl), y at [nl, 2 nl)):
+  // whole leaves, and, when leaves above kTrsylSplit rows are split for the
+  // FP32 inner solver, their top and bottom diagonal blocks (the cut moved
+  // down by one where it would split a 2 x 2 Schur block).
+  struct TrsylPart {
+    int *soff = nullptr, *lo = nullptr, *n = nullptr;
+    int nmax = 0;
+  } tp_full, tp_top, tp_bot;
+  bool trsyl_split = false;
+  std::vector<int> split_x, split_y;  // host: rows of the top blocks
+  double trsyl_flops_tt = 0.0, trsyl_flops_tb = 0.0, trsyl_flops_bt = 0.0, trsyl_flops_bb = 0.0;
   std::vector<Fact<double>> facts64;
   Inner<double> in64;
   Inner<float> in32;
@@ -703,6 +722,29 @@ static fde_status build_inner(sylv_s* S, Inner<T>& in, const std::vector<Fact<T>
     FDE_TRY(gemm_batch_upload(pool, c, false, false, T(1), T(0), &in.g_qx, st));
     FDE_TRY(gemm_batch_upload(pool, d, false, true, T(1), T(0), &in.g_qyt, st));
   }
+  if (sizeof(T) == sizeof(float) && S->trsyl_split) {
+    std::vector<GemmDesc<T>> g1, g2, g3, g4;
+    T* W = in.W2;
+    for (int p = 0; p < nl; ++p)
+      for (int q = 0; q < nl; ++q) {
+        const int lo = ax->leaf_lo[p], n = ax->leaf_n[p], h = S->split_x[p];
+        const int lo2 = ay->leaf_lo[q], n2 = ay->leaf_n[q], h2 = S->split_y[q];
+        const T* S12 = in.Sx + (size_t)p * lmax * lmax + (size_t)h * lmax;   // h x (n - h)
+        const T* R12 = in.Sy + (size_t)q * lmax * lmax + (size_t)h2 * lmax;  // h2 x (n2 - h2)
+        T* F11 = W + lo + (size_t)lo2 * N;
+        T* F12 = W + lo + (size_t)(lo2 + h2) * N;
+        T* F21 = W + (lo + h) + (size_t)lo2 * N;
+        T* F22 = W + (lo + h) + (size_t)(lo2 + h2) * N;
+        g1.push_back({S12, F22, F12, h, n2 - h2, n - h, lmax, N, N});        // F12 -= S12 Y22
+        g2.push_back({F22, R12, F21, n - h, h2, n2 - h2, N, lmax, N});       // F21 -= Y22 R12ᵀ
+        g3.push_back({S12, F21, F11, h, h2, n - h, lmax, N, N});             // F11 -= S12 Y21
+        g4.push_back({F12, R12, F11, h, h2, n2 - h2, N, lmax, N});           // F11 -= Y12 R12ᵀ
+      }
+    FDE_TRY(gemm_batch_upload(pool, g1, false, false, T(-1), T(1), &in.g_sp1, st));
+    FDE_TRY(gemm_batch_upload(pool, g2, false, true, T(-1), T(1), &in.g_sp2, st));
+    FDE_TRY(gemm_batch_upload(pool, g3, false, false, T(-1), T(1), &in.g_sp3, st));
+    FDE_TRY(gemm_batch_upload(pool, g4, false, true, T(-1), T(1), &in.g_sp4, st));
+  }
   in.lv.resize(L);
   std::vector<T*> Vx = level_V<T>(ax), Vy = level_V<T>(ay), Ux = level_U<T>(ax), Uy = level_U<T>(ay);
   size_t fi = 0;
@@ -811,8 +853,24 @@ static fde_status run_inner(sylv_s* S, Inner<T>& in, cudaStream_t st) {
   const int N = S->N, nl = ax->tree.nleaves();
   FDE_TRY(gemm_batch_run(in.g_qxt, st));
   FDE_TRY(gemm_batch_run(in.g_qy, st));
-  FDE_TRY(leaf_trsyl<T>(in.Sx, in.Sy, S->lmax, S->d_lo, S->d_n, nl, S->d_lo + nl, S->d_n + nl, nl, in.W2, N, st,
-                        S->trsyl_flops));
+  auto trsyl = [&](const sylv_s::TrsylPart& px, const sylv_s::TrsylPart& py, double flops) {
+    const int nmax = px.nmax > py.nmax ? px.nmax : py.nmax;
+    return leaf_trsyl<T>(in.Sx, in.Sy, S->lmax, nmax, px.soff, px.lo, px.n, nl, py.soff + nl, py.lo + nl, py.n + nl,
+                         nl, in.W2, N, st, flops);
+  };
+  if (sizeof(T) == sizeof(float) && S->trsyl_split) {
+    // 2 x 2 block Bartels–Stewart over the split leaves (Rᵀ is lower block triangular)
+    FDE_TRY(trsyl(S->tp_bot, S->tp_bot, S->trsyl_flops_bb));
+    FDE_TRY(gemm_batch_run(in.g_sp1, st));
+    FDE_TRY(gemm_batch_run(in.g_sp2, st));
+    FDE_TRY(trsyl(S->tp_top, S->tp_bot, S->trsyl_flops_tb));
+    FDE_TRY(trsyl(S->tp_bot, S->tp_top, S->trsyl_flops_bt));
+    FDE_TRY(gemm_batch_run(in.g_sp3, st));
+    FDE_TRY(gemm_batch_run(in.g_sp4, st));
+    FDE_TRY(trsyl(S->tp_top, S->tp_top, S->trsyl_flops_tt));
+  } else {
+    FDE_TRY(trsyl(S->tp_full, S->tp_full, S->trsyl_flops));
+  }
   FDE_TRY(gemm_batch_run(in.g_qx, st));
   FDE_TRY(gemm_batch_run(in.g_qyt, st));
   for (int l = S->L - 1; l >= 0; --l) {
@@ -1144,6 +1202,66 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
         set_error("sylv_create: leaf Schur iteration did not converge");
         return FDE_ERR_NOCONV;
       }
+  }
+  // ---- leaf Sylvester sub-problems (whole leaves; split leaves for the FP32 inner solver)
+  S->trsyl_split = prec != FDE_FP64 && S->lmax > kTrsylSplit;
+  {
+    const int lm = S->lmax;
+    std::vector<int> soff(2 * nl), lo(2 * nl), n(2 * nl);
+    std::vector<int> soff_t(2 * nl), lo_t(2 * nl), n_t(2 * nl), soff_b(2 * nl), lo_b(2 * nl), n_b(2 * nl);
+    S->split_x.assign(nl, 0);
+    S->split_y.assign(nl, 0);
+    for (int side = 0; side < 2; ++side) {
+      hodlr_s* h_ = side == 0 ? ax : ay;
+      const double* Sd = side == 0 ? S->Sx : S->Sy;
+      for (int p = 0; p < nl; ++p) {
+        const int i = side * nl + p, np = h_->leaf_n[p];
+        soff[i] = p * lm * lm;
+        lo[i] = h_->leaf_lo[p];
+        n[i] = np;
+        S->tp_full.nmax = std::max(S->tp_full.nmax, np);
+        if (!S->trsyl_split) continue;
+        int hcut = np / 2;
+        if (hcut > 0) {
+          double sub = 0.0;  // S_p(hcut, hcut - 1): nonzero inside a 2 x 2 block
+          FDE_CUDA(cudaMemcpy(&sub, Sd + (size_t)p * lm * lm + hcut + (size_t)(hcut - 1) * lm, sizeof(double),
+                              cudaMemcpyDeviceToHost));
+          if (sub != 0.0) ++hcut;
+        }
+        (side == 0 ? S->split_x : S->split_y)[p] = hcut;
+        soff_t[i] = p * lm * lm;
+        lo_t[i] = h_->leaf_lo[p];
+        n_t[i] = hcut;
+        soff_b[i] = p * lm * lm + hcut * (lm + 1);
+        lo_b[i] = h_->leaf_lo[p] + hcut;
+        n_b[i] = np - hcut;
+        S->tp_top.nmax = std::max(S->tp_top.nmax, hcut);
+        S->tp_bot.nmax = std::max(S->tp_bot.nmax, np - hcut);
+      }
+    }
+    auto upload = [&](sylv_s::TrsylPart& t, const std::vector<int>& a, const std::vector<int>& b,
+                      const std::vector<int>& c) -> fde_status {
+      FDE_TRY(pool.alloc(&t.soff, 2 * nl));
+      FDE_TRY(pool.alloc(&t.lo, 2 * nl));
+      FDE_TRY(pool.alloc(&t.n, 2 * nl));
+      FDE_CUDA(cudaMemcpy(t.soff, a.data(), 2 * nl * sizeof(int), cudaMemcpyHostToDevice));
+      FDE_CUDA(cudaMemcpy(t.lo, b.data(), 2 * nl * sizeof(int), cudaMemcpyHostToDevice));
+      FDE_CUDA(cudaMemcpy(t.n, c.data(), 2 * nl * sizeof(int), cudaMemcpyHostToDevice));
+      return FDE_OK;
+    };
+    FDE_TRY(upload(S->tp_full, soff, lo, n));
+    if (S->trsyl_split) {
+      FDE_TRY(upload(S->tp_top, soff_t, lo_t, n_t));
+      FDE_TRY(upload(S->tp_bot, soff_b, lo_b, n_b));
+      for (int p = 0; p < nl; ++p)
+        for (int q = 0; q < nl; ++q) {
+          const double t1 = n_t[p], b1 = n_b[p], t2 = n_t[nl + q], b2 = n_b[nl + q];
+          S->trsyl_flops_tt += t1 * t2 * (t1 + t2);
+          S->trsyl_flops_tb += t1 * b2 * (t1 + b2);
+          S->trsyl_flops_bt += b1 * t2 * (b1 + t2);
+          S->trsyl_flops_bb += b1 * b2 * (b1 + b2);
+        }
+    }
   }
   // ---- shifts per level (host: spectral intervals of the level's blocks)
   std::vector<double> gx(N + 2), gy(N + 2), dpx(N), dmx(N), dpy(N), dmy(N);
