@@ -256,9 +256,10 @@ __global__ void transpose_kernel(const double* __restrict__ X, double* __restric
 
 // ------------------------------------------------------------- FFT (FP64)
 // Leaves above this many rows are split into two diagonal blocks for the FP32
-// leaf Sylvester solves (each block then fits the kernel's 128-row shape,
-// three CTAs per SM instead of one).
-constexpr int kTrsylSplit = 128;
+// leaf Sylvester solves: the blocks' shorter dependency chains and smaller
+// CTAs (more of them per SM) outweigh the coupling GEMMs (leaf 128: 2.64 ->
+// 1.8 ms per sweep at N = 4096; leaf 256: 108 -> 32 ms at N = 16384).
+constexpr int kTrsylSplit = 64;
 
 // Threads of the residual's FFT kernels (radix-8 passes: P / 8 butterflies).
 constexpr int kFftThreads = 512;
