@@ -1,5 +1,6 @@
 // Shared-memory FFTs of length P = 2^p <= 8192 for the Toeplitz products of
-// the residual, in FP64 (double2) and double-float (float4) arithmetic.
+// the residual, in FP64 (double2), double-float (float4) and FP32 (float2)
+// arithmetic.
 //
 // The forward transform is a decimation in frequency: radix-8 passes from the
 // largest stride down, then one radix-2 or radix-4 pass at stride 1 (where
@@ -76,6 +77,26 @@ struct ArDF {
     const float2 p = df::df_mul(df::df_add_nw(im, df::df_neg(re)), rsqrt2());
     const float2 q = df::df_mul(df::df_add_nw(re, im), rsqrt2());
     return make_float4(p.x, p.y, -q.x, -q.y);
+  }
+};
+
+struct ArF32 {
+  using C = float2;
+  __device__ static C zero() { return make_float2(0.f, 0.f); }
+  __device__ static C mul(C a, C b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+  }
+  __device__ static C add(C a, C b) { return make_float2(a.x + b.x, a.y + b.y); }
+  __device__ static C sub(C a, C b) { return make_float2(a.x - b.x, a.y - b.y); }
+  __device__ static C conj(C a) { return make_float2(a.x, -a.y); }
+  __device__ static C mul_mi(C a) { return make_float2(a.y, -a.x); }
+  __device__ static C mul_w1(C a) {
+    const float s = 0.70710678118654752440f;
+    return make_float2(s * (a.x + a.y), s * (a.y - a.x));
+  }
+  __device__ static C mul_w3(C a) {
+    const float s = 0.70710678118654752440f;
+    return make_float2(s * (a.y - a.x), -s * (a.x + a.y));
   }
 };
 

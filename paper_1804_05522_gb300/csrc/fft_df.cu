@@ -76,6 +76,67 @@ __global__ void __launch_bounds__(kThreads) fd_fft_sub_df_kernel(const float* __
   }
 }
 
+// The same update in plain FP32 arithmetic, for the last refinement update of
+// a time step: its residual only seeds the next step's predictor, whose
+// first sweep recomputes the residual exactly (cp, cm: FP32 parts).
+__global__ void __launch_bounds__(kThreads) fd_fft_sub_f32_kernel(const float* __restrict__ X, long long xs,
+                                                                 long long xc, int ncols, double* R, long long rs,
+                                                                 long long rc, const float2* __restrict__ Ghat,
+                                                                 const float2* __restrict__ tw, int P, int logP,
+                                                                 const float2* __restrict__ cp,
+                                                                 const float2* __restrict__ cm, float shift, int N,
+                                                                 float2* __restrict__ scratch) {
+  extern __shared__ float2 fbuf[];
+  float2* side = fbuf + fft_padded_len(P);  // N entries: the T part of both columns
+  const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
+  const bool has1 = j1 < ncols;
+  for (int n = threadIdx.x; n < P; n += blockDim.x) {
+    float2 v = make_float2(0.f, 0.f);
+    if (n < N) {
+      v.x = X[n * xs + j0 * xc];
+      if (has1) v.y = X[n * xs + j1 * xc];
+    }
+    fbuf[fft_pad(n)] = v;
+  }
+  __syncthreads();
+  fft_forward<ArF32>(fbuf, logP, tw);
+  float2* Xh = scratch + (size_t)blockIdx.x * P;
+  for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    const float2 v = fbuf[fft_pad(k)];
+    Xh[k] = v;
+    fbuf[fft_pad(k)] = ArF32::mul(v, Ghat[k]);
+  }
+  __syncthreads();
+  fft_inverse<ArF32>(fbuf, logP, tw);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float2 t = fbuf[fft_pad(i + 1)];
+    const float c = cp[i].x;
+    side[i] = make_float2(c * t.x, c * t.y);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < P; k += blockDim.x) fbuf[fft_pad(k)] = ArF32::mul(Xh[k], ArF32::conj(Ghat[k]));
+  __syncthreads();
+  fft_inverse<ArF32>(fbuf, logP, tw);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float2 t = fbuf[fft_pad((i - 1 + P) & (P - 1))];
+    const float2 sT = side[i];
+    const float c = cm[i].x;
+    const float u0 = fmaf(shift, X[i * xs + j0 * xc], -fmaf(c, t.x, sT.x));
+    R[i * rs + j0 * rc] -= (double)u0;
+    if (has1) {
+      const float u1 = fmaf(shift, X[i * xs + j1 * xc], -fmaf(c, t.y, sT.y));
+      R[i * rs + j1 * rc] -= (double)u1;
+    }
+  }
+}
+
+__global__ void complex_to_f32_kernel(const double2* __restrict__ in, float2* __restrict__ out, int n) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const double2 v = in[k];
+    out[k] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
 __global__ void complex_to_df_kernel(const double2* __restrict__ in, float4* __restrict__ out, int n) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const double2 v = in[k];
@@ -107,6 +168,33 @@ fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols
   fd_fft_sub_df_kernel<<<(ncols + 1) / 2, kThreads, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, cp, cm,
                                                                 shift2, N, scratch);
   FDE_LAUNCH("fd_fft_sub_df_kernel");
+  return FDE_OK;
+}
+
+fde_status fd_apply_sub_f32(const float* X, long long xs, long long xc, int ncols, double* R, long long rs,
+                            long long rc, const float2* Ghat, const float2* tw, int P, int logP, const float2* cp,
+                            const float2* cm, double shift, int N, float2* scratch, cudaStream_t st, double flops) {
+  if (ncols <= 0 || N <= 0) return FDE_OK;
+  if (P > 8192 || P < 2 * N) {
+    set_error("fd_apply_sub_f32: transform length %d outside [2N, 8192]", P);
+    return FDE_ERR_ARG;
+  }
+  const size_t smem = ((size_t)fft_padded_len(P) + (size_t)N) * sizeof(float2);
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(fd_fft_sub_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((fft_padded_len(8192) + 4096) * sizeof(float2)));
+  FDE_CUDA(attr);
+  ProfScope ps("fft_f32", st, flops, 1);
+  fd_fft_sub_f32_kernel<<<(ncols + 1) / 2, kThreads, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, cp,
+                                                                 cm, (float)shift, N, scratch);
+  FDE_LAUNCH("fd_fft_sub_f32_kernel");
+  return FDE_OK;
+}
+
+fde_status complex_to_f32(const double2* in, float2* out, int n, cudaStream_t st) {
+  if (n <= 0) return FDE_OK;
+  complex_to_f32_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+  FDE_LAUNCH("complex_to_f32_kernel");
   return FDE_OK;
 }
 

@@ -21,7 +21,18 @@ fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols
                            const float2* cm, double shift, int N, float4* scratch, cudaStream_t st,
                            double flops = 0.0);
 
+// The same update in plain FP32 arithmetic (Ghat, tw as FP32 complex; only
+// the FP32 parts of cp, cm are used), accumulated into R in FP64.  Its error,
+// ~1e-6 ||A|| ||x||, suits a final refinement update whose residual is only
+// used to predict the next time step before an exact residual replaces it.
+fde_status fd_apply_sub_f32(const float* X, long long xs, long long xc, int ncols, double* R, long long rs,
+                            long long rc, const float2* Ghat, const float2* tw, int P, int logP, const float2* cp,
+                            const float2* cm, double shift, int N, float2* scratch, cudaStream_t st,
+                            double flops = 0.0);
+
 // out[k] = double-float split of the complex value in[k]
 fde_status complex_to_df(const double2* in, float4* out, int n, cudaStream_t st);
+// out[k] = FP32 rounding of the complex value in[k]
+fde_status complex_to_f32(const double2* in, float2* out, int n, cudaStream_t st);
 
 }  // namespace fde

@@ -475,6 +475,8 @@ struct sylv_s {
   double *cpx = nullptr, *cmx = nullptr, *cpy = nullptr, *cmy = nullptr;
   float2 *cpx_df = nullptr, *cmx_df = nullptr, *cpy_df = nullptr, *cmy_df = nullptr;
   bool resid_df = false;              // later sweeps update R in double-float (FP32 inner solver)
+  bool resid_f32_last = false;        // the last update of a step in plain FP32 (its residual only predicts)
+  float2 *tw_f32 = nullptr, *GhX_f32 = nullptr, *GhY_f32 = nullptr;  // FP32 copies
   // N > 4096: block-Toeplitz FFTs (blocks of kFftBlock) instead of one transform per column
   bool block = false;
   int pair_chunk = 0;
@@ -1031,14 +1033,33 @@ static fde_status residual_update_df(sylv_s* S, const float* d, cudaStream_t st)
   return FDE_OK;
 }
 
-// One refinement sweep: Cin = (T) R ; inner solve ; X64 += X_T ; then either
-// R = C - A(X64) exactly in FP64, or (incremental, FP32 inner solver only)
-// R -= A(δ) in double-float: the error of that update scales with ||δ||, which
-// after the first sweep of a step is ~1e-3 of ||X|| or less.
-// acc[0] = ||δ||², acc[1] = ||X||², acc[2] = ||R||² of this sweep.
+// R -= A_x δ + δ A_yᵀ in plain FP32 FFTs (N <= 4096): for the last update of a
+// step, whose residual only feeds the next step's predictor.
+static fde_status residual_update_f32(sylv_s* S, const float* d, cudaStream_t st) {
+  hodlr_s* ax = S->ax;
+  hodlr_s* ay = S->ay;
+  const int N = S->N;
+  float2* scr = reinterpret_cast<float2*>(S->fft_scratch);
+  FDE_TRY(fd_apply_sub_f32(d, 1, N, N, S->R, 1, N, S->GhX_f32, S->tw_f32, S->P, S->logP, S->cpx_df, S->cmx_df,
+                           ax->p.shift, N, scr, st, S->fft_flops));
+  FDE_TRY(fd_apply_sub_f32(d, N, 1, N, S->R, N, 1, S->GhY_f32, S->tw_f32, S->P, S->logP, S->cpy_df, S->cmy_df,
+                           ay->p.shift, N, scr, st, S->fft_flops));
+  return FDE_OK;
+}
+
+// One refinement sweep, in two halves.  sweep_solve: Cin = (T) R, inner
+// solve, X64 += X_T; acc[0] = ||δ||², acc[1] = ||X||².  sweep_residual: the
+// new residual of X64, acc[2] = ||R||², as
+//  - kResidExact: R = C - A(X64) in FP64;
+//  - kResidDF:    R -= A(δ) in double-float (FP32 inner solver), whose error
+//                 scales with ||δ||, ~1e-3 ||X|| or less after the first sweep;
+//  - kResidF32:   R -= A(δ) in FP32, for the last update of a step: that
+//                 residual only seeds the next step's predicted residual, and
+//                 the next step's first sweep recomputes R exactly.
+enum ResidKind { kResidExact = 0, kResidDF = 1, kResidF32 = 2 };
+
 template <typename T>
-static fde_status sweep(sylv_s* S, Inner<T>& in, const double* C, double* X64, cudaStream_t st,
-                        bool incremental = false) {
+static fde_status sweep_solve(sylv_s* S, Inner<T>& in, double* X64, cudaStream_t st) {
   const size_t NN = (size_t)S->N * S->N;
   if (sizeof(T) == sizeof(double)) {
     FDE_CUDA(cudaMemcpyAsync((void*)in.Cin, S->R, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1052,7 +1073,15 @@ static fde_status sweep(sylv_s* S, Inner<T>& in, const double* C, double* X64, c
     refine_update_kernel<T><<<grid_for(NN), 256, 0, st>>>(X64, in.X, NN, S->acc);
     FDE_LAUNCH("refine_update_kernel");
   }
-  if (incremental && sizeof(T) == sizeof(float))
+  return FDE_OK;
+}
+
+template <typename T>
+static fde_status sweep_residual(sylv_s* S, Inner<T>& in, const double* C, double* X64, int kind, cudaStream_t st) {
+  const size_t NN = (size_t)S->N * S->N;
+  if (sizeof(T) == sizeof(float) && kind == kResidF32)
+    FDE_TRY(residual_update_f32(S, reinterpret_cast<const float*>(in.X), st));
+  else if (sizeof(T) == sizeof(float) && kind == kResidDF)
     FDE_TRY(residual_update_df(S, reinterpret_cast<const float*>(in.X), st));
   else
     FDE_TRY(residual(S, C, X64, S->R, st));
@@ -1116,28 +1145,46 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
   bool incr_ok = S->resid_df;  // the first sweep of a step always recomputes R exactly
   for (int sw = 0; sw < nsw; ++sw) {
     if (S->prec == FDE_FP64)
-      FDE_TRY(sweep<double>(S, S->in64, C, X, st));
+      FDE_TRY(sweep_solve<double>(S, S->in64, X, st));
     else
-      FDE_TRY(sweep<float>(S, S->in32, C, X, st, incr_ok && sw > 0));
+      FDE_TRY(sweep_solve<float>(S, S->in32, X, st));
     ++done;
+    // decide on the update first: the last update of a step may take the cheap residual
+    bool stop = fixed && sw == nsw - 1;
+    if (!fixed) {
+      FDE_TRY(read_acc(S, a, 8, st));
+      if (!std::isfinite(a[0]) || !std::isfinite(a[1])) {
+        set_error("sylv_step: non-finite iterate after sweep %d", done);
+        return FDE_ERR_NUMERIC;
+      }
+      const double tol2 = rf.tol_update * rf.tol_update * a[1];
+      stop = a[0] <= tol2;
+      if (!stop && prev_d2 > 0.0 && a[0] < 0.25 * prev_d2) {
+        // the sweeps contract the error by rho ~ ||δ_k|| / ||δ_{k-1}|| < 1/2:
+        // what the next sweeps would still add is about rho ||δ_k|| / (1 - rho)
+        const double rho = sqrt(a[0] / prev_d2);
+        const double rest = rho / (1.0 - rho);
+        stop = a[0] * rest * rest <= tol2;
+      }
+      // incremental residuals only while the sweeps contract well (rho < 0.1)
+      if (prev_d2 > 0.0 && a[0] > 0.01 * prev_d2) incr_ok = false;
+      prev_d2 = a[0];
+    }
+    int kind = kResidExact;
+    if (S->prec != FDE_FP64 && incr_ok && sw > 0) kind = (stop && S->resid_f32_last) ? kResidF32 : kResidDF;
+    if (S->prec == FDE_FP64)
+      FDE_TRY(sweep_residual<double>(S, S->in64, C, X, kind, st));
+    else
+      FDE_TRY(sweep_residual<float>(S, S->in32, C, X, kind, st));
     if (fixed) continue;
-    FDE_TRY(read_acc(S, a, 8, st));
-    if (!std::isfinite(a[0]) || !std::isfinite(a[1]) || !std::isfinite(a[2])) {
-      set_error("sylv_step: non-finite iterate after sweep %d", done);
-      return FDE_ERR_NUMERIC;
+    if (!stop) {
+      FDE_TRY(read_acc(S, a, 8, st));
+      if (!std::isfinite(a[2])) {
+        set_error("sylv_step: non-finite residual after sweep %d", done);
+        return FDE_ERR_NUMERIC;
+      }
+      stop = a[2] <= rf.tol_relres * rf.tol_relres * a[4];
     }
-    const double tol2 = rf.tol_update * rf.tol_update * a[1];
-    bool stop = a[0] <= tol2 || a[2] <= rf.tol_relres * rf.tol_relres * a[4];
-    if (!stop && prev_d2 > 0.0 && a[0] < 0.25 * prev_d2) {
-      // the sweeps contract the error by rho ~ ||δ_k|| / ||δ_{k-1}|| < 1/2:
-      // what the next sweeps would still add is about rho ||δ_k|| / (1 - rho)
-      const double rho = sqrt(a[0] / prev_d2);
-      const double rest = rho / (1.0 - rho);
-      stop = a[0] * rest * rest <= tol2;
-    }
-    // incremental residuals only while the sweeps contract well (rho < 0.1)
-    if (prev_d2 > 0.0 && a[0] > 0.01 * prev_d2) incr_ok = false;
-    prev_d2 = a[0];
     if (stop) {
       converged = true;
       break;
@@ -1416,10 +1463,15 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
     FDE_CUDA(cudaMemcpy(S->tw, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
   }
   if (prec != FDE_FP64) {
+    // FDE_RESID: "fp64" = every residual exact; "df" = incremental updates in
+    // double-float only; default: also the last update of a step in FP32
     const char* rm = getenv("FDE_RESID");
     S->resid_df = !(rm && strcmp(rm, "fp64") == 0);
+    S->resid_f32_last = S->resid_df && !(rm && strcmp(rm, "df") == 0) && !S->block;
     FDE_TRY(pool.alloc(&S->tw_df, S->P));
     FDE_TRY(complex_to_df(S->tw, S->tw_df, S->P, st));
+    FDE_TRY(pool.alloc(&S->tw_f32, S->P));
+    FDE_TRY(complex_to_f32(S->tw, S->tw_f32, S->P, st));
   }
   {
     FDE_TRY(pool.alloc(&S->cpx, N));
@@ -1468,6 +1520,10 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
       FDE_TRY(pool.alloc(&S->GhY_df, S->P));
       FDE_TRY(complex_to_df(S->GhX, S->GhX_df, S->P, st));
       FDE_TRY(complex_to_df(S->GhY, S->GhY_df, S->P, st));
+      FDE_TRY(pool.alloc(&S->GhX_f32, S->P));
+      FDE_TRY(pool.alloc(&S->GhY_f32, S->P));
+      FDE_TRY(complex_to_f32(S->GhX, S->GhX_f32, S->P, st));
+      FDE_TRY(complex_to_f32(S->GhY, S->GhY_f32, S->P, st));
     }
     FDE_TRY(pool.alloc(&S->fft_scratch, (size_t)((N + 1) / 2) * S->P));
     FDE_TRY(pool.alloc(&S->R, NN));

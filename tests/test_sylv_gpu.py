@@ -160,18 +160,29 @@ def test_sylv_step_both_fadi_forms(lib, monkeypatch, prec, mode):
         P.close()
 
 
+RESID_MODES = ("auto", "df", "fp64")
+
+
+def _set_resid(monkeypatch, mode):
+    if mode == "auto":
+        monkeypatch.delenv("FDE_RESID", raising=False)
+    else:
+        monkeypatch.setenv("FDE_RESID", mode)
+
+
 @pytest.mark.parametrize("N,leaf,alpha", [(256, 64, (1.3, 1.7)), (1000, 128, (1.5, 1.5))])
 def test_incremental_df_residual_matches_fp64(lib, monkeypatch, N, leaf, alpha):
-    """FP32 inner solver: refinement with the double-float incremental residual
-    (later sweeps) and with exact FP64 residuals (every sweep) reach the same
-    solution, both within 1e-8 of the oracle; the warm-started steps of a time
-    loop (residual reuse across steps) agree as well."""
+    """FP32 inner solver: refinement with exact FP64 residuals (every sweep),
+    with double-float incremental residuals (later sweeps), and the default
+    (double-float, and FP32 for the last update of a step) reach the same
+    solution, all within 1e-8 of the oracle; the warm-started steps of a time
+    loop (residual reuse and prediction across steps) agree as well."""
     w = I.fd2d(N=N, alpha=alpha, steps=50, leaf=leaf)
     C = O.fde2d_rhs(w, w.u0, 0) + I.random_matrix_fast(N, N, seed=11)
     Xo = O.sylvester_bartels_stewart(O.fd_operator(w.ops[0]), O.fd_operator(w.ops[1]), C)
     sols = {}
-    for mode in ("df", "fp64"):
-        monkeypatch.setenv("FDE_RESID", mode)
+    for mode in RESID_MODES:
+        _set_resid(monkeypatch, mode)
         P = Pair(lib, w, B.FDE_FP32_REFINE)
         try:
             Cd = _dev(C)
@@ -182,10 +193,11 @@ def test_incremental_df_residual_matches_fp64(lib, monkeypatch, N, leaf, alpha):
         finally:
             P.close()
     assert _relerr(sols["df"], sols["fp64"]) <= 1e-9
+    assert _relerr(sols["auto"], sols["fp64"]) <= 1e-9
     # time loop: residual reuse + incremental updates over several steps
     runs = {}
-    for mode in ("df", "fp64"):
-        monkeypatch.setenv("FDE_RESID", mode)
+    for mode in RESID_MODES:
+        _set_resid(monkeypatch, mode)
         w6 = I.fd2d(N=min(N, 256), alpha=alpha, steps=50, leaf=leaf)
         rp = lib.run_params(w6, prec=B.FDE_FP32_REFINE)
         rp.steps = 6
