@@ -179,16 +179,20 @@ double block_apply_flops(int N, int ncols) {
 
 fde_status block_apply(const void* X, bool x_is_float, long long xs, long long xc, int ncols, const double* Cm,
                        double* Y, long long ys, long long yc, int mode, const double* g, const double2* Hhat,
-                       const float4* Hhat_df, const double2* tw, const float4* tw_df, bool df, const double* dp,
-                       const double* dm, double c, double shift, int N, void* scratch, int pair_chunk,
-                       cudaStream_t st, double flops) {
+                       const float4* Hhat_df, const float2* Hhat_f32, const double2* tw, const float4* tw_df,
+                       const float2* tw_f32, int prec, const double* dp, const double* dm, double c, double shift,
+                       int N, void* scratch, int pair_chunk, cudaStream_t st, double flops) {
   if (ncols <= 0 || N <= 0) return FDE_OK;
-  if (pair_chunk <= 0 || mode < kApplySet || mode > kApplySub || (mode == kApplyResidual && !Cm)) {
-    set_error("block_apply: bad chunk / mode");
+  if (pair_chunk <= 0 || mode < kApplySet || mode > kApplySub || (mode == kApplyResidual && !Cm) ||
+      prec < kBlockF64 || prec > kBlockF32 || (prec == kBlockF32 && !x_is_float)) {
+    set_error("block_apply: bad chunk / mode / precision");
     return FDE_ERR_ARG;
   }
-  ProfScope ps(df ? "fft_df" : "fft_apply", st, flops, 1);
-  if (df) {
+  ProfScope ps(prec == kBlockDF ? "fft_df" : prec == kBlockF32 ? "fft_f32" : "fft_apply", st, flops, 1);
+  if (prec == kBlockF32)
+    return launch_block<ArF32, float>((const float*)X, xs, xc, ncols, Cm, Y, ys, yc, mode, g, Hhat_f32, tw_f32, dp,
+                                      dm, c, shift, N, (float2*)scratch, pair_chunk, st);
+  if (prec == kBlockDF) {
     if (x_is_float)
       return launch_block<ArDF, float>((const float*)X, xs, xc, ncols, Cm, Y, ys, yc, mode, g, Hhat_df, tw_df, dp, dm,
                                        c, shift, N, (float4*)scratch, pair_chunk, st);

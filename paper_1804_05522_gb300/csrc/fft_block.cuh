@@ -18,6 +18,9 @@ fde_status block_spectra(const double* g, int N, const double2* tw, double2* Hha
 
 // Output modes of the operator products below.
 enum BlockApplyMode { kApplySet = 0, kApplyResidual = 1, kApplySub = 2 };
+// Arithmetic of the block products: FP64, double-float (FP32 pipe, ~48
+// bits), or plain FP32.
+enum BlockApplyPrec { kBlockF64 = 0, kBlockDF = 1, kBlockF32 = 2 };
 
 // For the columns x_j (x_j(i) = X[i * xs + j * xc], j < ncols) of an N x ncols
 // matrix:  y_j = A x_j,  A = shift I + c (D_+ T + D_- Tᵀ),  T = -[g_{i-j+1}]
@@ -28,14 +31,15 @@ enum BlockApplyMode { kApplySet = 0, kApplyResidual = 1, kApplySub = 2 };
 // middle of a circular convolution of length 2B with h_D, so
 //   (T x)_I  = -sum_{D >= 0} IFFT(Hhat_D . X_{I-D})[B + i]  (+ one g_0 corner term),
 //   (Tᵀx)_I = -sum_{D >= 0} IFFT(conj(Hhat_D) . X_{I+D})[(i + B) mod 2B] (+ corner).
-// FP64 arithmetic (X double) or double-float arithmetic on the FP32 pipe
-// (X float, df = true; the result is still accumulated in FP64).
+// prec selects the arithmetic (the spectra and twiddles of that precision are
+// used: Hhat / tw, Hhat_df / tw_df, Hhat_f32 / tw_f32); the result is
+// accumulated in FP64 in every case.
 // scratch: min(ceil(ncols/2), pair_chunk) * nb * 2B complex (16 bytes each).
 fde_status block_apply(const void* X, bool x_is_float, long long xs, long long xc, int ncols, const double* Cm,
                        double* Y, long long ys, long long yc, int mode, const double* g, const double2* Hhat,
-                       const float4* Hhat_df, const double2* tw, const float4* tw_df, bool df, const double* dp,
-                       const double* dm, double c, double shift, int N, void* scratch, int pair_chunk,
-                       cudaStream_t st, double flops = 0.0);
+                       const float4* Hhat_df, const float2* Hhat_f32, const double2* tw, const float4* tw_df,
+                       const float2* tw_f32, int prec, const double* dp, const double* dm, double c, double shift,
+                       int N, void* scratch, int pair_chunk, cudaStream_t st, double flops = 0.0);
 
 // Work of one block_apply call (algorithmic FLOPs) for the instrumentation.
 double block_apply_flops(int N, int ncols);

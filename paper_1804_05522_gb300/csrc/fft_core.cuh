@@ -83,6 +83,9 @@ struct ArDF {
 struct ArF32 {
   using C = float2;
   __device__ static C zero() { return make_float2(0.f, 0.f); }
+  __device__ static C make(double re, double im) { return make_float2((float)re, (float)im); }
+  __device__ static double re(C a) { return (double)a.x; }
+  __device__ static double im(C a) { return (double)a.y; }
   __device__ static C mul(C a, C b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
   }

@@ -482,6 +482,7 @@ struct sylv_s {
   int pair_chunk = 0;
   double2 *HbX = nullptr, *HbY = nullptr;
   float4 *HbX_df = nullptr, *HbY_df = nullptr;
+  float2 *HbX_f32 = nullptr, *HbY_f32 = nullptr;
   double *R = nullptr, *Xt = nullptr, *Yt = nullptr, *X64 = nullptr, *C64 = nullptr;
   double* acc = nullptr;              // device accumulators
   int* d_bad = nullptr;
@@ -922,12 +923,12 @@ static fde_status residual(sylv_s* S, const double* C, const double* X, double* 
   const int N = S->N, P = S->P, lp = S->logP;
   if (S->block) {
     // x direction: R = C - A_x X (columns); y direction: R -= X A_yᵀ (rows, read in place)
-    FDE_TRY(block_apply(X, false, 1, N, N, C, R, 1, N, kApplyResidual, ax->g, S->HbX, S->HbX_df, S->tw, S->tw_df,
-                        false, ax->dp, ax->dm, ax->c, ax->p.shift, N, S->fft_scratch, S->pair_chunk, st,
-                        S->fft_flops));
-    FDE_TRY(block_apply(X, false, N, 1, N, nullptr, R, N, 1, kApplySub, ay->g, S->HbY, S->HbY_df, S->tw, S->tw_df,
-                        false, ay->dp, ay->dm, ay->c, ay->p.shift, N, S->fft_scratch, S->pair_chunk, st,
-                        S->fft_flops));
+    FDE_TRY(block_apply(X, false, 1, N, N, C, R, 1, N, kApplyResidual, ax->g, S->HbX, S->HbX_df, S->HbX_f32, S->tw,
+                        S->tw_df, S->tw_f32, kBlockF64, ax->dp, ax->dm, ax->c, ax->p.shift, N, S->fft_scratch,
+                        S->pair_chunk, st, S->fft_flops));
+    FDE_TRY(block_apply(X, false, N, 1, N, nullptr, R, N, 1, kApplySub, ay->g, S->HbY, S->HbY_df, S->HbY_f32, S->tw,
+                        S->tw_df, S->tw_f32, kBlockF64, ay->dp, ay->dm, ay->c, ay->p.shift, N, S->fft_scratch,
+                        S->pair_chunk, st, S->fft_flops));
     return FDE_OK;
   }
   const int nb = (N + 1) / 2;
@@ -1017,12 +1018,12 @@ static fde_status residual_update_df(sylv_s* S, const float* d, cudaStream_t st)
   hodlr_s* ay = S->ay;
   const int N = S->N;
   if (S->block) {
-    FDE_TRY(block_apply(d, true, 1, N, N, nullptr, S->R, 1, N, kApplySub, ax->g, S->HbX, S->HbX_df, S->tw,
-                        S->tw_df, true, ax->dp, ax->dm, ax->c, ax->p.shift, N, S->fft_scratch, S->pair_chunk, st,
-                        S->fft_flops));
-    FDE_TRY(block_apply(d, true, N, 1, N, nullptr, S->R, N, 1, kApplySub, ay->g, S->HbY, S->HbY_df, S->tw,
-                        S->tw_df, true, ay->dp, ay->dm, ay->c, ay->p.shift, N, S->fft_scratch, S->pair_chunk, st,
-                        S->fft_flops));
+    FDE_TRY(block_apply(d, true, 1, N, N, nullptr, S->R, 1, N, kApplySub, ax->g, S->HbX, S->HbX_df, S->HbX_f32,
+                        S->tw, S->tw_df, S->tw_f32, kBlockDF, ax->dp, ax->dm, ax->c, ax->p.shift, N, S->fft_scratch,
+                        S->pair_chunk, st, S->fft_flops));
+    FDE_TRY(block_apply(d, true, N, 1, N, nullptr, S->R, N, 1, kApplySub, ay->g, S->HbY, S->HbY_df, S->HbY_f32,
+                        S->tw, S->tw_df, S->tw_f32, kBlockDF, ay->dp, ay->dm, ay->c, ay->p.shift, N, S->fft_scratch,
+                        S->pair_chunk, st, S->fft_flops));
     return FDE_OK;
   }
   float4* scr = reinterpret_cast<float4*>(S->fft_scratch);
@@ -1033,12 +1034,21 @@ static fde_status residual_update_df(sylv_s* S, const float* d, cudaStream_t st)
   return FDE_OK;
 }
 
-// R -= A_x δ + δ A_yᵀ in plain FP32 FFTs (N <= 4096): for the last update of a
-// step, whose residual only feeds the next step's predictor.
+// R -= A_x δ + δ A_yᵀ in plain FP32 FFTs: for the last update of a step, whose
+// residual only feeds the next step's predictor.
 static fde_status residual_update_f32(sylv_s* S, const float* d, cudaStream_t st) {
   hodlr_s* ax = S->ax;
   hodlr_s* ay = S->ay;
   const int N = S->N;
+  if (S->block) {
+    FDE_TRY(block_apply(d, true, 1, N, N, nullptr, S->R, 1, N, kApplySub, ax->g, S->HbX, S->HbX_df, S->HbX_f32,
+                        S->tw, S->tw_df, S->tw_f32, kBlockF32, ax->dp, ax->dm, ax->c, ax->p.shift, N,
+                        S->fft_scratch, S->pair_chunk, st, S->fft_flops));
+    FDE_TRY(block_apply(d, true, N, 1, N, nullptr, S->R, N, 1, kApplySub, ay->g, S->HbY, S->HbY_df, S->HbY_f32,
+                        S->tw, S->tw_df, S->tw_f32, kBlockF32, ay->dp, ay->dm, ay->c, ay->p.shift, N,
+                        S->fft_scratch, S->pair_chunk, st, S->fft_flops));
+    return FDE_OK;
+  }
   float2* scr = reinterpret_cast<float2*>(S->fft_scratch);
   FDE_TRY(fd_apply_sub_f32(d, 1, N, N, S->R, 1, N, S->GhX_f32, S->tw_f32, S->P, S->logP, S->cpx_df, S->cmx_df,
                            ax->p.shift, N, scr, st, S->fft_flops));
@@ -1467,7 +1477,7 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
     // double-float only; default: also the last update of a step in FP32
     const char* rm = getenv("FDE_RESID");
     S->resid_df = !(rm && strcmp(rm, "fp64") == 0);
-    S->resid_f32_last = S->resid_df && !(rm && strcmp(rm, "df") == 0) && !S->block;
+    S->resid_f32_last = S->resid_df && !(rm && strcmp(rm, "df") == 0);
     FDE_TRY(pool.alloc(&S->tw_df, S->P));
     FDE_TRY(complex_to_df(S->tw, S->tw_df, S->P, st));
     FDE_TRY(pool.alloc(&S->tw_f32, S->P));
@@ -1500,6 +1510,10 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
     FDE_TRY(pool.alloc(&S->HbY_df, (size_t)nb * S->P));
     FDE_TRY(block_spectra(ax->g, N, S->tw, S->HbX, S->HbX_df, st));
     FDE_TRY(block_spectra(ay->g, N, S->tw, S->HbY, S->HbY_df, st));
+    FDE_TRY(pool.alloc(&S->HbX_f32, (size_t)nb * S->P));
+    FDE_TRY(pool.alloc(&S->HbY_f32, (size_t)nb * S->P));
+    FDE_TRY(complex_to_f32(S->HbX, S->HbX_f32, nb * S->P, st));
+    FDE_TRY(complex_to_f32(S->HbY, S->HbY_f32, nb * S->P, st));
     FDE_TRY(pool.alloc(&S->fft_scratch, (size_t)S->pair_chunk * nb * S->P));
     FDE_TRY(pool.alloc(&S->R, NN));
     S->fft_flops = block_apply_flops(N, N);

@@ -58,14 +58,18 @@ def test_block_toeplitz_residual(lib, N):
 
 def test_block_toeplitz_refined_step(lib, monkeypatch):
     """FP32 inner solver + FP64 refinement at N = 6000 (2 blocks): the CPU
-    residual of the GPU solution is at the refinement's level, with the
-    double-float incremental residual and with exact FP64 residuals alike."""
+    residual of the GPU solution is at the refinement's level with exact FP64
+    residuals, with double-float incremental ones, and with the default
+    (double-float, FP32 for the last update of the step) alike."""
     N = 6000
     w = I.fd2d(N=N, alpha=(1.5, 1.5), steps=100, leaf=128)
     C = O.fde2d_rhs(w, w.u0, 0)
     sols = {}
-    for mode in ("df", "fp64"):
-        monkeypatch.setenv("FDE_RESID", mode)
+    for mode in ("auto", "df", "fp64"):
+        if mode == "auto":
+            monkeypatch.delenv("FDE_RESID", raising=False)
+        else:
+            monkeypatch.setenv("FDE_RESID", mode)
         P = Pair(lib, w, B.FDE_FP32_REFINE)
         try:
             Cd = _dev(C)
@@ -77,4 +81,5 @@ def test_block_toeplitz_refined_step(lib, monkeypatch):
             assert r_cpu < 1e-10 and sweeps <= 6, (mode, r_cpu, relres, sweeps)
         finally:
             P.close()
-    assert np.linalg.norm(sols["df"] - sols["fp64"]) <= 1e-9 * np.linalg.norm(sols["fp64"])
+    for mode in ("df", "auto"):
+        assert np.linalg.norm(sols[mode] - sols["fp64"]) <= 1e-9 * np.linalg.norm(sols["fp64"]), mode
