@@ -260,6 +260,10 @@ __global__ void transpose_kernel(const double* __restrict__ X, double* __restric
 // CTAs (more of them per SM) outweigh the coupling GEMMs (leaf 128: 2.64 ->
 // 1.8 ms per sweep at N = 4096; leaf 256: 108 -> 32 ms at N = 16384).
 constexpr int kTrsylSplit = 64;
+// ... when there are at least this many leaf pairs: with fewer, the split
+// launches leave most SMs idle and the three dependent rounds cost more than
+// they save (leaf 128 at N = 1024, 64 pairs: 0.85 -> 1.07 ms per sweep).
+constexpr int kTrsylSplitMinPairs = 512;
 
 // Threads of the residual's FFT kernels (radix-8 passes: P / 8 butterflies).
 constexpr int kFftThreads = 512;
@@ -1262,7 +1266,11 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
       }
   }
   // ---- leaf Sylvester sub-problems (whole leaves; split leaves for the FP32 inner solver)
-  S->trsyl_split = prec != FDE_FP64 && S->lmax > kTrsylSplit;
+  S->trsyl_split = prec != FDE_FP64 && S->lmax > kTrsylSplit && (long long)nl * nl >= kTrsylSplitMinPairs;
+  if (const char* ts = getenv("FDE_TRSYL_SPLIT")) {  // "1": split every leaf (tests), "0": never
+    if (!strcmp(ts, "1")) S->trsyl_split = prec != FDE_FP64 && S->lmax >= 2;
+    if (!strcmp(ts, "0")) S->trsyl_split = false;
+  }
   {
     const int lm = S->lmax;
     std::vector<int> soff(2 * nl), lo(2 * nl), n(2 * nl);
