@@ -280,10 +280,14 @@ void fde_batch_free(fde_batch_t b);
  * op(B) k x n.  kblk > 0 selects two-level addressing along k for a
  * non-transposed A and a transposed B: column k sits at
  * (k / kblk) * kstr + (k % kblk) * ld.  mode: 0 SIMT FP32 FMA, 1 tcgen05 TF32,
- * 3 tcgen05 3xTF32 (hi/lo split, FP32-level accuracy), -1 the library's
- * current setting; batches too small for the tensor cores (m < 64, n < 32 or
- * k < 32) always take the SIMT kernel.  Allocates the descriptor array and
- * synchronises `stream`.  FDE_ERR_CUDA if a tensor-core wait expired. */
+ * 3 tcgen05 3xTF32 (hi/lo split, FP32-level accuracy), 4 the skinny SIMT FP32
+ * kernel (one dimension <= 64: n <= 40 with m >= 128, or m <= 64 with
+ * n >= 128, no two-level k; other shapes as mode 3), -1 the library's own
+ * dispatch (the skinny kernel for n <= 32 or m <= 64, then the tensor
+ * cores); batches too small
+ * for the tensor cores (m < 64, n < 16 or k < 32) take a SIMT kernel.
+ * Allocates the descriptor array and synchronises `stream`.  FDE_ERR_CUDA if
+ * a tensor-core wait expired. */
 fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const float* A, int lda,
                         long long strideA, const float* B, int ldb, long long strideB, float beta, float* C,
                         int ldc, long long strideC, int batch, int kblk, long long kstr, int mode, void* stream);

@@ -1,6 +1,8 @@
 // Batched dense kernels: SIMT GEMM with per-batch descriptors, batched
 // Gauss–Jordan inversion, conversions.
+#include <atomic>
 #include <cstdint>
+#include <cstdlib>
 
 #include "dense.cuh"
 
@@ -112,6 +114,198 @@ __global__ void __launch_bounds__(256) gemm_batched_kernel(const GemmDesc<T>* __
   }
 }
 
+// FDE_SKINNY=0 turns the skinny kernel below off (comparisons);
+// set_skinny_force (fde_gemm_f32's explicit modes) overrides both ways.
+static std::atomic<int> g_skinny_force{-1};
+void set_skinny_force(int v) { g_skinny_force.store(v); }
+static bool skinny_mode() {
+  const int f = g_skinny_force.load();
+  if (f >= 0) return f != 0;
+  static const bool on = []() {
+    const char* e = getenv("FDE_SKINNY");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+// ------------------------------------------------------------ skinny GEMM
+// FP32 products with one dimension of at most 64 (the fADI right-hand-side
+// factors and the root-level rational application, n = 16..34; the
+// rank-sized products Vᵀ X, m <= 64).  Written on a "long x skinny" view:
+//   C'(l, c) = alpha sum_k A'(l, k) B'(k, c) + beta C'(l, c),  l < L, c < S <= SC,
+// with A'(l, k) = A[l * al + k * ak], B'(k, c) = B[k * bk + c * bc],
+// C'(l, c) = C[l * cl + c * cc]: for n <= 64 the problem itself (L = m), for
+// m <= 64 its transpose (L = n, A' = op(B)ᵀ, B' = op(A)ᵀ, C' = Cᵀ).
+// Tile 128 (l) x SC (c), k in steps of 16 prefetched in registers; 128
+// threads, thread (tl, tc) owns rows 8 tl..8 tl + 7 and columns
+// tc (SC/8)..: exact FP32 products (no tensor-core rounding), every column
+// of the skinny dimension used (SC is the next multiple of 16).
+constexpr int kSkL = 128, kSkK = 16, kSkThreads = 128;
+
+template <int SC, bool A_LCONT, bool B_KCONT>
+__global__ void __launch_bounds__(kSkThreads, SC <= 32 ? 4 : 2) gemm_skinny_kernel(const GemmDesc<float>* __restrict__ descs,
+                                                                  bool transposed, bool ta, bool tb, float alpha,
+                                                                  float beta) {
+  constexpr int RC = SC / 8;
+  constexpr int LDA_S = kSkL + 4, LDB_S = SC + 4;  // padded shared rows (16-byte aligned)
+  __shared__ __align__(16) float As[kSkK][LDA_S];
+  __shared__ __align__(16) float Bs[kSkK][LDB_S];
+  const GemmDesc<float> d = descs[blockIdx.y];
+  // strides of the long x skinny view
+  long long al, ak, bk, bc, cl, cc;
+  int L, S;
+  if (!transposed) {
+    L = d.m; S = d.n;
+    al = ta ? d.lda : 1; ak = ta ? 1 : d.lda;
+    bk = tb ? d.ldb : 1; bc = tb ? 1 : d.ldb;
+    cl = 1; cc = d.ldc;
+  } else {
+    L = d.n; S = d.m;
+    al = tb ? 1 : d.ldb; ak = tb ? d.ldb : 1;
+    bk = ta ? 1 : d.lda; bc = ta ? d.lda : 1;
+    cl = d.ldc; cc = 1;
+  }
+  const int K = d.k;
+  const int l0 = blockIdx.x * kSkL;
+  if (l0 >= L) return;
+  const int t = threadIdx.x, tl = t & 15, tc = t >> 4;
+  // register prefetch of one k-tile: 16 A' values, SC / 8 B' values per thread.
+  // Element q of this thread: A_LCONT: (l, k) = (t, q); else (t / 16 + 8 q, t % 16),
+  // i.e. a base address plus q steps of a fixed stride.
+  const int la = A_LCONT ? t : (t >> 4), ka = A_LCONT ? 0 : (t & 15);
+  const int dla = A_LCONT ? 0 : 8, dka = A_LCONT ? 1 : 0;
+  const long long astep = A_LCONT ? ak : 8 * al;
+  // A' and B' come from op(B) and op(A) in the transposed view
+  const float* Ap = transposed ? d.B : d.A;
+  const float* Bp = transposed ? d.A : d.B;
+  const float* abase = Ap + (long long)(l0 + la) * al + (long long)ka * ak;
+  float ra[16], rb[RC];
+  auto load = [&](int k0) {
+    const float* ap = abase + (long long)k0 * ak;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int gl = l0 + la + dla * q, gk = k0 + ka + dka * q;
+      ra[q] = (gl < L && gk < K) ? ap[q * astep] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < RC; ++q) {
+      const int e = t + kSkThreads * q;  // e < 16 * SC
+      const int c = B_KCONT ? (e >> 4) : (e % SC), kk = B_KCONT ? (e & 15) : (e / SC);
+      const int gk = k0 + kk;
+      rb[q] = (c < S && gk < K) ? Bp[(long long)gk * bk + (long long)c * bc] : 0.f;
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) As[ka + dka * q][la + dla * q] = ra[q];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) {
+      const int e = t + kSkThreads * q;
+      const int c = B_KCONT ? (e >> 4) : (e % SC), kk = B_KCONT ? (e & 15) : (e / SC);
+      Bs[kk][c] = rb[q];
+    }
+  };
+  float acc[8][RC];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < RC; ++j) acc[i][j] = 0.f;
+  load(0);
+  for (int k0 = 0; k0 < K; k0 += kSkK) {
+    __syncthreads();  // the previous tile's readers are done
+    stash();
+    __syncthreads();
+    if (k0 + kSkK < K) load(k0 + kSkK);  // in flight during the products below
+#pragma unroll
+    for (int kk = 0; kk < kSkK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][8 * tl]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][8 * tl + 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float b[RC];
+#pragma unroll
+      for (int j = 0; j < RC; ++j) b[j] = Bs[kk][tc * RC + j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < RC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+  }
+  // per row: the RC loads of beta C' before its stores
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gl = l0 + 8 * tl + i;
+    if (gl >= L) break;
+    float cv[RC];
+#pragma unroll
+    for (int j = 0; j < RC; ++j) {
+      const int c = tc * RC + j;
+      cv[j] = (beta != 0.f && c < S) ? d.C[(long long)gl * cl + (long long)c * cc] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < RC; ++j) {
+      const int c = tc * RC + j;
+      if (c < S) d.C[(long long)gl * cl + (long long)c * cc] = alpha * acc[i][j] + beta * cv[j];
+    }
+  }
+}
+
+template <int SC>
+static void launch_skinny(const GemmBatch<float>& b, bool transposed, bool a_lcont, bool b_kcont, int L,
+                          cudaStream_t st) {
+  for (int z0 = 0; z0 < b.batch; z0 += 65535) {
+    const int nz = b.batch - z0 < 65535 ? b.batch - z0 : 65535;
+    const dim3 grid(ceil_div(L, kSkL), nz);
+    const GemmDesc<float>* d = b.d_desc + z0;
+    if (a_lcont && b_kcont)
+      gemm_skinny_kernel<SC, true, true><<<grid, kSkThreads, 0, st>>>(d, transposed, b.ta, b.tb, b.alpha, b.beta);
+    else if (a_lcont)
+      gemm_skinny_kernel<SC, true, false><<<grid, kSkThreads, 0, st>>>(d, transposed, b.ta, b.tb, b.alpha, b.beta);
+    else if (b_kcont)
+      gemm_skinny_kernel<SC, false, true><<<grid, kSkThreads, 0, st>>>(d, transposed, b.ta, b.tb, b.alpha, b.beta);
+    else
+      gemm_skinny_kernel<SC, false, false><<<grid, kSkThreads, 0, st>>>(d, transposed, b.ta, b.tb, b.alpha, b.beta);
+  }
+}
+
+// Runs an FP32 batch on the skinny kernel if one dimension is small enough:
+// n <= limit_n with m >= 128, or m <= 64 with n >= 128 (no two-level k
+// panels).  In the library's own dispatch limit_n = 32: the n = 34 root-level
+// rational application streams a 1 GB operand from HBM, which this kernel's
+// one-tile register prefetch does not hide (16 against 28 TFLOP/s on the
+// tensor cores).
+static fde_status skinny_gemm_run(const GemmBatch<float>& b, int limit_n, cudaStream_t st, bool* used) {
+  *used = false;
+  if (b.any_kblk) return FDE_OK;
+  bool transposed;
+  int S, L;
+  if (b.max_n <= limit_n && b.max_m >= kSkL) {
+    transposed = false;
+    S = b.max_n;
+    L = b.max_m;
+  } else if (b.max_m <= 64 && b.max_n >= kSkL) {
+    transposed = true;
+    S = b.max_m;
+    L = b.max_n;
+  } else {
+    return FDE_OK;
+  }
+  // which index of A' and B' is contiguous (see the kernel's view)
+  const bool a_lcont = transposed ? b.tb : !b.ta;
+  const bool b_kcont = transposed ? b.ta : !b.tb;
+  ProfScope ps("gemm32", st, b.flops, 1);
+  if (S <= 16)
+    launch_skinny<16>(b, transposed, a_lcont, b_kcont, L, st);
+  else if (S <= 32)
+    launch_skinny<32>(b, transposed, a_lcont, b_kcont, L, st);
+  else if (S <= 48)
+    launch_skinny<48>(b, transposed, a_lcont, b_kcont, L, st);
+  else
+    launch_skinny<64>(b, transposed, a_lcont, b_kcont, L, st);
+  FDE_LAUNCH("gemm_skinny_kernel");
+  *used = true;
+  return FDE_OK;
+}
+
 template <typename T>
 fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, bool ta, bool tb, T alpha,
                              T beta, GemmBatch<T>* out, cudaStream_t st) {
@@ -148,6 +342,7 @@ fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, b
     b.vec_b = b.vec_b && vec_ok(d.B, d.ldb, tb ? d.kblk : 0, d.kstr);
     b.max_m = d.m > b.max_m ? d.m : b.max_m;
     b.max_ldc = d.ldc > b.max_ldc ? d.ldc : b.max_ldc;
+    b.any_kblk = b.any_kblk || d.kblk > 0;
     b.max_n = d.n > b.max_n ? d.n : b.max_n;
     b.max_k = d.k > b.max_k ? d.k : b.max_k;
     b.flops += 2.0 * d.m * d.n * d.k;
@@ -168,6 +363,11 @@ fde_status gemm_batch_run(const GemmBatch<T>& b, cudaStream_t st) {
   if (b.batch == 0 || b.max_m == 0 || b.max_n == 0) return FDE_OK;
   if constexpr (sizeof(T) == 4) {
     bool used = false;
+    if (skinny_mode()) {
+      const int limit_n = g_skinny_force.load() == 1 ? 40 : 32;
+      FDE_TRY(skinny_gemm_run(reinterpret_cast<const GemmBatch<float>&>(b), limit_n, st, &used));
+      if (used) return FDE_OK;
+    }
     FDE_TRY(tc_gemm_run(reinterpret_cast<const GemmBatch<float>&>(b), st, &used));
     if (used) return FDE_OK;
   }

@@ -32,6 +32,7 @@ struct GemmBatch {
   // every descriptor's A (resp. B) base is 16-byte aligned and its ld (and
   // kstr) a multiple of 4 elements: 4-wide vector loads are allowed
   bool vec_a = false, vec_b = false;
+  bool any_kblk = false;  // some descriptor uses two-level k panels
   T alpha = T(1), beta = T(0);
 };
 
@@ -41,6 +42,9 @@ fde_status gemm_batch_upload(DevPool& pool, const std::vector<GemmDesc<T>>& h, b
 
 template <typename T>
 fde_status gemm_batch_run(const GemmBatch<T>& b, cudaStream_t st);
+
+// -1: the skinny FP32 kernel by the library's rule (FDE_SKINNY); 0 off; 1 on.
+void set_skinny_force(int v);
 
 // Tensor-core path for FP32 batches (tc_gemm.cu).  Mode from FDE_TC
 // (0 = SIMT only, 1 = TF32, 3 = 3xTF32, the default).

@@ -725,7 +725,7 @@ extern "C" fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float al
   using namespace fde;
   FDE_ARG(m >= 0 && n >= 0 && k >= 0 && batch >= 0, "negative size");
   FDE_ARG(A != nullptr && B != nullptr && C != nullptr, "NULL matrix");
-  FDE_ARG(mode == -1 || mode == 0 || mode == 1 || mode == 3, "mode must be -1, 0, 1 or 3");
+  FDE_ARG(mode == -1 || mode == 0 || mode == 1 || mode == 3 || mode == 4, "mode must be -1, 0, 1, 3 or 4");
   FDE_ARG(kblk >= 0 && (kblk == 0 || kstr >= 0), "bad kblk / kstr");
   FDE_ARG(ldc >= (m > 1 ? m : 1), "ldc < m");
   FDE_ARG(lda >= 1 && ldb >= 1, "bad lda / ldb");
@@ -743,9 +743,13 @@ extern "C" fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float al
   GemmBatch<float> gb;
   FDE_TRY(gemm_batch_upload(scratch, h, ta != 0, tb != 0, alpha, beta, &gb, st));
   const int saved = tc_mode();
-  if (mode >= 0) set_tc_mode(mode);
+  if (mode >= 0) {
+    set_tc_mode(mode == 4 ? 3 : mode);
+    set_skinny_force(mode == 4 ? 1 : 0);
+  }
   const fde_status s = gemm_batch_run(gb, st);
   set_tc_mode(saved);
+  set_skinny_force(-1);
   FDE_TRY(s);
   FDE_CUDA(cudaStreamSynchronize(st));
   int flag = 0;

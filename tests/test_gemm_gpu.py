@@ -17,7 +17,7 @@ def _bound(mode, k):
     u = 2.0 ** -24
     if mode == 1:
         return 2 * 2.0 ** -11 + 2 * k * u
-    return 2.0 ** -20 + 2 * k * u
+    return 2.0 ** -20 + 2 * k * u  # modes 0, 4 (FP32 FMA) and 3 (3xTF32)
 
 
 def _opnd(rng, rows, cols, ld, batch):
@@ -133,3 +133,49 @@ def test_gemm_split_beats_tf32(lib):
         got = dC.cpu().numpy().reshape(n, m).T
         errs[mode] = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert errs[3] < 2e-6 and errs[1] > 100 * errs[3], errs
+
+
+SKINNY_SHAPES = [
+    # m, n, k, pad, batch: the skinny kernel's two orientations
+    (200, 17, 160, 0, 3),     # n <= 40, ragged long side (two 128-row tiles)
+    (640, 34, 300, 2, 2),     # n = 34 (the root-level rational application), k tail
+    (130, 40, 64, 1, 1),      # widest skinny n, odd ld (scalar loads)
+    (17, 300, 96, 3, 2),      # m <= 64: transposed view (rank x N products)
+    (64, 129, 50, 0, 4),      # m at the limit, ragged long side
+]
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("shape", SKINNY_SHAPES)
+def test_gemm_skinny(lib, ta, tb, shape):
+    """The skinny SIMT kernel (mode 4) against an FP64 product, every
+    transpose, alpha and beta != 0, padded leading dimensions untouched."""
+    m, n, k, pad, batch = shape
+    rng = np.random.default_rng(m * 5 + n * 11 + k + 100 * ta + 10 * tb)
+    ar, ac = (k, m) if ta else (m, k)
+    br, bc = (n, k) if tb else (k, n)
+    lda, ldb, ldc = ar + pad, br + pad, m + pad
+    A = _opnd(rng, ar, ac, lda, batch)
+    B = _opnd(rng, br, bc, ldb, batch)
+    C0 = _opnd(rng, m, n, ldc, batch)
+    alpha, beta = -1.25, 0.5
+    dA, dB, dC = (torch.from_numpy(x.ravel().copy()).cuda() for x in (A, B, C0))
+    lib.prof_reset()
+    lib.prof_enable(True)
+    lib.gemm_f32(ta, tb, m, n, k, alpha, dA.data_ptr(), lda, lda * ac, dB.data_ptr(), ldb, ldb * bc, beta,
+                 dC.data_ptr(), ldc, ldc * n, batch=batch, mode=4)
+    lib.prof_enable(False)
+    assert lib.prof_query("gemm32")[1] > 0 and lib.prof_query("gemm32tc")[1] == 0
+    lib.prof_reset()
+    Cg = dC.cpu().numpy().reshape(batch, n, ldc)
+    for i in range(batch):
+        a = _mat(A, i, ar, ac)
+        b = _mat(B, i, br, bc)
+        opa, opb = (a.T if ta else a), (b.T if tb else b)
+        ref = alpha * opa @ opb + beta * _mat(C0, i, m, n)
+        scale = abs(alpha) * np.abs(opa) @ np.abs(opb) + abs(beta) * np.abs(_mat(C0, i, m, n))
+        got = Cg[i, :, :m].T.astype(np.float64)
+        err = np.abs(got - ref)
+        assert np.all(err <= _bound(4, k) * scale + 1e-30), np.max(err / scale)
+        if pad:
+            assert np.array_equal(Cg[i, :, m:], C0[i, :, m:])
