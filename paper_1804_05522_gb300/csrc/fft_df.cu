@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kThreads) fd_fft_sub_df_kernel(const float* __
                                                                 const float4* __restrict__ tw, int P, int logP,
                                                                 const float2* __restrict__ cp,
                                                                 const float2* __restrict__ cm, float2 shift, int N,
-                                                                float4* __restrict__ scratch) {
+                                                                float4* __restrict__ scratch, int set) {
   extern __shared__ float4 buf[];
   float4* side = buf + fft_padded_len(P);  // N entries: the T part of both columns
   const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
@@ -66,12 +66,12 @@ __global__ void __launch_bounds__(kThreads) fd_fft_sub_df_kernel(const float* __
     const float2 w0 = df_add_nw(make_float2(sT.x, sT.y), df_mul(make_float2(t.x, t.y), c));
     const float2 u0 = df_add_nw(df_mul(shift, make_float2(X[i * xs + j0 * xc], 0.f)), df_neg(w0));
     double* r0 = R + i * rs + j0 * rc;
-    *r0 = (*r0 - (double)u0.x) - (double)u0.y;
+    *r0 = set ? (double)u0.x + (double)u0.y : (*r0 - (double)u0.x) - (double)u0.y;
     if (has1) {
       const float2 w1 = df_add_nw(make_float2(sT.z, sT.w), df_mul(make_float2(t.z, t.w), c));
       const float2 u1 = df_add_nw(df_mul(shift, make_float2(X[i * xs + j1 * xc], 0.f)), df_neg(w1));
       double* r1 = R + i * rs + j1 * rc;
-      *r1 = (*r1 - (double)u1.x) - (double)u1.y;
+      *r1 = set ? (double)u1.x + (double)u1.y : (*r1 - (double)u1.x) - (double)u1.y;
     }
   }
 }
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kThreads) fd_fft_sub_f32_kernel(const float* _
                                                                  const float2* __restrict__ tw, int P, int logP,
                                                                  const float2* __restrict__ cp,
                                                                  const float2* __restrict__ cm, float shift, int N,
-                                                                 float2* __restrict__ scratch) {
+                                                                 float2* __restrict__ scratch, int set) {
   extern __shared__ float2 fbuf[];
   float2* side = fbuf + fft_padded_len(P);  // N entries: the T part of both columns
   const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
@@ -122,10 +122,12 @@ __global__ void __launch_bounds__(kThreads) fd_fft_sub_f32_kernel(const float* _
     const float2 sT = side[i];
     const float c = cm[i].x;
     const float u0 = fmaf(shift, X[i * xs + j0 * xc], -fmaf(c, t.x, sT.x));
-    R[i * rs + j0 * rc] -= (double)u0;
+    double* r0 = R + i * rs + j0 * rc;
+    *r0 = set ? (double)u0 : *r0 - (double)u0;
     if (has1) {
       const float u1 = fmaf(shift, X[i * xs + j1 * xc], -fmaf(c, t.y, sT.y));
-      R[i * rs + j1 * rc] -= (double)u1;
+      double* r1 = R + i * rs + j1 * rc;
+      *r1 = set ? (double)u1 : *r1 - (double)u1;
     }
   }
 }
@@ -149,7 +151,8 @@ __global__ void complex_to_df_kernel(const double2* __restrict__ in, float4* __r
 
 fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols, double* R, long long rs,
                            long long rc, const float4* Ghat, const float4* tw, int P, int logP, const float2* cp,
-                           const float2* cm, double shift, int N, float4* scratch, cudaStream_t st, double flops) {
+                           const float2* cm, double shift, int N, float4* scratch, cudaStream_t st, double flops,
+                           bool set) {
   if (ncols <= 0 || N <= 0) return FDE_OK;
   if (P > 8192 || P < 2 * N) {
     set_error("fd_apply_sub_df: transform length %d outside [2N, 8192]", P);
@@ -166,14 +169,15 @@ fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols
   const float2 shift2 = make_float2(hi, (float)(shift - (double)hi));
   ProfScope ps("fft_df", st, flops, 1);
   fd_fft_sub_df_kernel<<<(ncols + 1) / 2, kThreads, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, cp, cm,
-                                                                shift2, N, scratch);
+                                                                shift2, N, scratch, set ? 1 : 0);
   FDE_LAUNCH("fd_fft_sub_df_kernel");
   return FDE_OK;
 }
 
 fde_status fd_apply_sub_f32(const float* X, long long xs, long long xc, int ncols, double* R, long long rs,
                             long long rc, const float2* Ghat, const float2* tw, int P, int logP, const float2* cp,
-                            const float2* cm, double shift, int N, float2* scratch, cudaStream_t st, double flops) {
+                            const float2* cm, double shift, int N, float2* scratch, cudaStream_t st, double flops,
+                            bool set) {
   if (ncols <= 0 || N <= 0) return FDE_OK;
   if (P > 8192 || P < 2 * N) {
     set_error("fd_apply_sub_f32: transform length %d outside [2N, 8192]", P);
@@ -186,7 +190,7 @@ fde_status fd_apply_sub_f32(const float* X, long long xs, long long xc, int ncol
   FDE_CUDA(attr);
   ProfScope ps("fft_f32", st, flops, 1);
   fd_fft_sub_f32_kernel<<<(ncols + 1) / 2, kThreads, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, cp,
-                                                                 cm, (float)shift, N, scratch);
+                                                                 cm, (float)shift, N, scratch, set ? 1 : 0);
   FDE_LAUNCH("fd_fft_sub_f32_kernel");
   return FDE_OK;
 }

@@ -45,6 +45,14 @@ bool prof_enabled() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
 ProfScope::ProfScope(const char* family, cudaStream_t s, double w, int k)
     : fam(family), st(s), a(nullptr), work(w), kind(k) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  // nothing is timed while the stream is being captured into a graph (an
+  // event recorded there belongs to the graph, not to this timeline)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return;
   a = take_event();
   if (a) cudaEventRecord(a, st);
 }
@@ -91,7 +99,7 @@ extern "C" void fde_prof_reset(void) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   for (auto& kv : g_prof)
     for (auto& e : kv.second) {
-      cudaEventSynchronize(e.b);
+      if (cudaEventSynchronize(e.b) != cudaSuccess) cudaGetLastError();  // leave no error pending
       g_pool.push_back(e.a);
       g_pool.push_back(e.b);
     }
