@@ -249,6 +249,125 @@ __global__ void __launch_bounds__(kSkThreads, SC <= 32 ? 4 : 2) gemm_skinny_kern
   }
 }
 
+// Pipelined variant for the common layout: A m-contiguous (ta = 0), B
+// k-contiguous (tb = 0), both 16-byte aligned with leading dimensions that
+// are multiples of 4 (the root-level rational application streams its
+// stacked operator, ~1 GB, from HBM).  NST k-tiles of A' (16 x 128) and B'
+// (stored column-major, SC x 16) in flight through cp.async, zero-filled at
+// the ragged edges; the arithmetic is the kernel above's.
+constexpr int kSkStages = 4;
+
+__device__ __forceinline__ void sk_cp16(uint32_t dst, const float* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void sk_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void sk_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int SC>
+constexpr int sk_stage_floats() {
+  return kSkK * (kSkL + 4) + SC * (kSkK + 4);
+}
+
+template <int SC>
+__global__ void __launch_bounds__(kSkThreads, 3) gemm_skinny_pipe_kernel(const GemmDesc<float>* __restrict__ descs,
+                                                                          float alpha, float beta) {
+  constexpr int RC = SC / 8, LDA_S = kSkL + 4, LDB_S = kSkK + 4, STAGE = sk_stage_floats<SC>();
+  extern __shared__ __align__(16) float skm[];
+  const GemmDesc<float> d = descs[blockIdx.y];
+  const int L = d.m, S = d.n, K = d.k;
+  const int l0 = blockIdx.x * kSkL;
+  if (l0 >= L) return;
+  const int t = threadIdx.x, tl = t & 15, tc = t >> 4;
+  const int nkt = (K + kSkK - 1) / kSkK;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(skm);
+  auto issue = [&](int kt) {
+    if (kt < nkt) {
+      const int k0 = kt * kSkK;
+      const uint32_t st = sbase + (uint32_t)((kt % kSkStages) * STAGE) * 4u;
+      // A': 16 k rows of 128 l, 16-byte chunks of 4 l
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = t + kSkThreads * q, kk = c >> 5, l4 = (c & 31) * 4;
+        const int gl = l0 + l4, gk = k0 + kk;
+        int nv = L - gl;
+        nv = gk < K ? (nv < 0 ? 0 : nv > 4 ? 4 : nv) : 0;
+        const float* src = nv > 0 ? d.A + (long long)gl + (long long)gk * d.lda : d.A;
+        sk_cp16(st + (uint32_t)(kk * LDA_S + l4) * 4u, src, 4 * nv);
+      }
+      // B': SC columns of 16 k, chunks of 4 k
+      for (int c = t; c < SC * 4; c += kSkThreads) {
+        const int col = c >> 2, k4 = (c & 3) * 4, gk = k0 + k4;
+        int nv = K - gk;
+        nv = col < S ? (nv < 0 ? 0 : nv > 4 ? 4 : nv) : 0;
+        const float* src = nv > 0 ? d.B + (long long)gk + (long long)col * d.ldb : d.B;
+        sk_cp16(st + (uint32_t)(kSkK * LDA_S + col * LDB_S + k4) * 4u, src, 4 * nv);
+      }
+    }
+    sk_commit();
+  };
+  float acc[8][RC];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < RC; ++j) acc[i][j] = 0.f;
+#pragma unroll
+  for (int s0 = 0; s0 < kSkStages - 1; ++s0) issue(s0);
+  for (int kt = 0; kt < nkt; ++kt) {
+    sk_wait<kSkStages - 2>();  // this thread's copies of k-tile kt have landed
+    __syncthreads();           // everyone's have; the stage of k-tile kt - 1 is free
+    issue(kt + kSkStages - 1);
+    const float* As = skm + (kt % kSkStages) * STAGE;
+    const float* Bs = As + kSkK * LDA_S;
+#pragma unroll
+    for (int kk = 0; kk < kSkK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(As + kk * LDA_S + 8 * tl);
+      const float4 a1 = *reinterpret_cast<const float4*>(As + kk * LDA_S + 8 * tl + 4);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float bv[RC];
+#pragma unroll
+      for (int j = 0; j < RC; ++j) bv[j] = Bs[(tc * RC + j) * LDB_S + kk];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < RC; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
+    }
+  }
+  sk_wait<0>();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gl = l0 + 8 * tl + i;
+    if (gl >= L) break;
+    float cv[RC];
+#pragma unroll
+    for (int j = 0; j < RC; ++j) {
+      const int c = tc * RC + j;
+      cv[j] = (beta != 0.f && c < S) ? d.C[(long long)gl + (long long)c * d.ldc] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < RC; ++j) {
+      const int c = tc * RC + j;
+      if (c < S) d.C[(long long)gl + (long long)c * d.ldc] = alpha * acc[i][j] + beta * cv[j];
+    }
+  }
+}
+
+template <int SC>
+static fde_status launch_skinny_pipe(const GemmBatch<float>& b, cudaStream_t st) {
+  const size_t smem = (size_t)kSkStages * sk_stage_floats<SC>() * sizeof(float);
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(gemm_skinny_pipe_kernel<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  FDE_CUDA(attr);
+  for (int z0 = 0; z0 < b.batch; z0 += 65535) {
+    const int nz = b.batch - z0 < 65535 ? b.batch - z0 : 65535;
+    const dim3 grid(ceil_div(b.max_m, kSkL), nz);
+    gemm_skinny_pipe_kernel<SC><<<grid, kSkThreads, smem, st>>>(b.d_desc + z0, b.alpha, b.beta);
+  }
+  return FDE_OK;
+}
+
 template <int SC>
 static void launch_skinny(const GemmBatch<float>& b, bool transposed, bool a_lcont, bool b_kcont, int L,
                           cudaStream_t st) {
@@ -267,18 +386,19 @@ static void launch_skinny(const GemmBatch<float>& b, bool transposed, bool a_lco
   }
 }
 
-// Runs an FP32 batch on the skinny kernel if one dimension is small enough:
-// n <= limit_n with m >= 128, or m <= 64 with n >= 128 (no two-level k
-// panels).  In the library's own dispatch limit_n = 32: the n = 34 root-level
-// rational application streams a 1 GB operand from HBM, which this kernel's
-// one-tile register prefetch does not hide (16 against 28 TFLOP/s on the
-// tensor cores).
+// Runs an FP32 batch on a skinny kernel if one dimension is small enough:
+// n <= 40 with m >= 128, or m <= 64 with n >= 128 (no two-level k panels).
+// With A m-contiguous and B k-contiguous, aligned, the pipelined kernel takes
+// any n <= 40; otherwise the register-prefetch kernel takes n <= limit_n (32 in
+// the library's own dispatch: the n = 34 root-level rational application
+// streams a 1 GB operand from HBM, which one-tile register prefetch does not
+// hide, 16 against 28 TFLOP/s on the tensor cores).
 static fde_status skinny_gemm_run(const GemmBatch<float>& b, int limit_n, cudaStream_t st, bool* used) {
   *used = false;
   if (b.any_kblk) return FDE_OK;
   bool transposed;
   int S, L;
-  if (b.max_n <= limit_n && b.max_m >= kSkL) {
+  if (b.max_n <= 40 && b.max_m >= kSkL) {
     transposed = false;
     S = b.max_n;
     L = b.max_m;
@@ -293,6 +413,18 @@ static fde_status skinny_gemm_run(const GemmBatch<float>& b, int limit_n, cudaSt
   const bool a_lcont = transposed ? b.tb : !b.ta;
   const bool b_kcont = transposed ? b.ta : !b.tb;
   ProfScope ps("gemm32", st, b.flops, 1);
+  if (!transposed && !b.ta && !b.tb && b.vec_a && b.vec_b && S <= 40) {
+    if (S <= 16)
+      FDE_TRY(launch_skinny_pipe<16>(b, st));
+    else if (S <= 32)
+      FDE_TRY(launch_skinny_pipe<32>(b, st));
+    else
+      FDE_TRY(launch_skinny_pipe<40>(b, st));
+    FDE_LAUNCH("gemm_skinny_pipe_kernel");
+    *used = true;
+    return FDE_OK;
+  }
+  if (S > limit_n && !transposed) return FDE_OK;  // (the pipelined kernel only, above)
   if (S <= 16)
     launch_skinny<16>(b, transposed, a_lcont, b_kcont, L, st);
   else if (S <= 32)

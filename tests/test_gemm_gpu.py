@@ -142,6 +142,8 @@ SKINNY_SHAPES = [
     (130, 40, 64, 1, 1),      # widest skinny n, odd ld (scalar loads)
     (17, 300, 96, 3, 2),      # m <= 64: transposed view (rank x N products)
     (64, 129, 50, 0, 4),      # m at the limit, ragged long side
+    (512, 34, 200, 0, 2),     # aligned, n = 34: the cp.async-pipelined kernel (ta = tb = 0)
+    (260, 40, 100, 0, 2),     # aligned, ragged m (4-row last tile), k tail inside a chunk
 ]
 
 
