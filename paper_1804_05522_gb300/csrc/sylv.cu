@@ -485,6 +485,7 @@ struct sylv_s {
   // every exact_every, double-float updates in between (see sylv_step_impl);
   // exact_every = 1: after the first sweep of every step.
   int exact_every = 8, cyc_streak = 0, cyc_incr = 0;
+  bool prev_large = false;            // the previous step's first update was too large to be incremental
   double incr_tol = 1e-2;             // largest ||δ_0|| / ||X|| for an incremental first update
   float2 *tw_f32 = nullptr, *GhX_f32 = nullptr, *GhY_f32 = nullptr;  // FP32 copies
   // N > 4096: block-Toeplitz FFTs (blocks of kFftBlock) instead of one transform per column
@@ -1191,11 +1192,17 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
   if (!in_chain) {
     S->cyc_streak = 0;
     S->cyc_incr = 0;
+    S->prev_large = false;
   }
   const int K = S->exact_every;
   const bool must_exact = !in_chain || fixed || K <= 2 || S->prec == FDE_FP64 || !S->resid_df ||
                           S->cyc_streak == 1 || S->cyc_incr >= K - 2;
   bool step_incremental = false;
+  // set when ||δ_0|| was too large for an incremental first update: such a
+  // step recomputes its residual exactly anyway, and when the previous step's
+  // was too large as well (a regime where the next ones will be exact too) it
+  // may take the FP32 last update and make the next two steps exact
+  bool large_first = false, used_f32 = false;
   const int nsw = fixed ? rf.fixed_sweeps : rf.max_sweeps;
   int done = 0;
   bool converged = fixed;
@@ -1231,12 +1238,20 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
     }
     int kind = kResidExact;
     if (S->prec != FDE_FP64 && incr_ok) {
-      if (sw == 0 && !must_exact && a[0] <= S->incr_tol * S->incr_tol * a[1]) step_incremental = true;
+      if (sw == 0 && !fixed && in_chain && K > 2) {
+        const bool small = a[0] <= S->incr_tol * S->incr_tol * a[1];
+        if (small && !must_exact) step_incremental = true;
+        if (!small) large_first = true;
+      }
       if (sw > 0 || step_incremental) {
         // the last update of a step may be FP32 when the next two steps are
-        // sure to recompute their residual exactly (the last step of a chain)
-        const bool next_two_exact = K <= 1 || (step_incremental && S->cyc_incr + 1 >= K - 2);
+        // sure to recompute their residual exactly: the last step of a chain,
+        // or a step with a large first update (which then forces them)
+        const bool next_two_exact =
+            K <= 1 || (step_incremental && S->cyc_incr + 1 >= K - 2) ||
+            (large_first && S->prev_large && !step_incremental);
         kind = (stop && S->resid_f32_last && next_two_exact) ? kResidF32 : kResidDF;
+        if (kind == kResidF32) used_f32 = true;
       }
     }
     if (S->prec == FDE_FP64)
@@ -1275,6 +1290,12 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
     S->cyc_streak = S->cyc_streak < 2 ? S->cyc_streak + 1 : 2;
     if (S->cyc_streak == 2) S->cyc_incr = 0;
   }
+  if (used_f32 && large_first && K > 2) {
+    // the FP32 residual may only feed exact steps: the next two
+    S->cyc_streak = 0;
+    S->cyc_incr = K;
+  }
+  S->prev_large = large_first;
   return FDE_OK;
 }
 
