@@ -20,9 +20,20 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   aca_partial_pivot          pinned: exact recovery of exactly-low-rank inputs
   truncate_lowrank           pinned: prescribed singular values
   hodlr_reference            pinned: per-block SVD error bound, rank bounds
-  solve_dense                pinned: residual / library cross-check
+  eps_rank                   pinned: prescribed singular values
+  beckermann_bound and the   pinned: the Lemma's own hypothesis (Hilbert
+  qsrank bounds                matrix, PSD Hankel) from both sides; SVD
+                               ranks of T and A below the bounds
+  solve_dense / fde1d_run    pinned: residual / library cross-check,
+                             manufactured-solution first-order convergence
   sylvester_bartels_stewart  pinned: Kronecker brute force, α=2 DST closed form
+  SchurSylvester             pinned: Kronecker brute force, reused Schur forms
+  fde2d_rhs / fde2d_run      pinned: Kronecker steps, manufactured 2D solution
+                             (first order), exactness for a solution linear
+                             in t (source at the new time level)
   apply_fd_operator_fft      pinned: dense product
+  sylvester_residual         pinned: X = 0, Kronecker solution, Kronecker
+                             product of a perturbation
 """
 from __future__ import annotations
 

@@ -345,6 +345,138 @@ def test_fde1d_run_residuals():
     np.testing.assert_allclose(O.fde1d_run(w), u, rtol=1e-12, atol=1e-14)
 
 
+class _Run2D:
+    """Minimal 2D run description with a test-chosen source f(t) (duck-typed
+    like inputs.Workload for fde2d_run / fde2d_rhs)."""
+
+    def __init__(self, ops, u0, dt, steps, source):
+        self.ops, self.u0, self.dt, self.steps, self.dim = ops, u0, dt, steps, 2
+        self._source = source
+
+    def source(self, t):
+        return self._source(t)
+
+
+def test_fde2d_manufactured_solution_first_order():
+    """u = e^{-t} p(x) p(y), p = x²(1-x)², with the separable 2D coefficients
+    (§4.2) and different orders in x and y.  The source comes from the
+    Riemann–Liouville power rule (RL = GL for smooth u, §2.1).  Shifted GL in
+    both directions + implicit Euler is first order in Δx and Δt, so halving
+    both halves the error.  A transposed y operator, a swapped d_±, a wrong
+    1/2 shift split or a dropped direction leaves an O(1) error instead."""
+    a1, a2 = 1.3, 1.7
+    coeffs = {2: 1.0, 3: -2.0, 4: 1.0}
+
+    def Dplus(x, alpha):
+        return sum(cf * _rl_power(p, alpha) * x ** (p - alpha) for p, cf in coeffs.items())
+
+    errs = []
+    for N in (31, 63, 127):
+        x = I.grid(N)
+        h = 1.0 / (N + 1)
+        dt = 2.0 * h
+        M = int(round(0.5 / dt))
+        g1, g2 = math.gamma(3 - a1), math.gamma(3 - a2)
+        d1p, d1m = g1 * x ** a1, g1 * (1 - x) ** a1
+        d2p, d2m = g2 * (1 + x) ** a2, g2 * (2 - x) ** a2
+        opx = I.OpSpec(N, a1, h, dt, 0.5, d1p, d1m, 16, 1e-12)
+        opy = I.OpSpec(N, a2, h, dt, 0.5, d2p, d2m, 16, 1e-12)
+        p = x ** 2 * (1 - x) ** 2
+        # L_x p = d_+ D_+^α p + d_- D_-^α p, with D_-^α p(x) = (D_+^α p)(1 - x) (p symmetric)
+        Lx = d1p * Dplus(x, a1) + d1m * Dplus(1 - x, a1)
+        Ly = d2p * Dplus(x, a2) + d2m * Dplus(1 - x, a2)
+        F0 = -np.outer(p, p) - np.outer(Lx, p) - np.outer(p, Ly)  # f = u_t - L u at e^{-t} = 1
+        run = _Run2D([opx, opy], np.outer(p, p), dt, M, lambda t, F0=F0: math.exp(-t) * F0)
+        U = O.fde2d_run(run)
+        errs.append(np.max(np.abs(U - math.exp(-M * dt) * np.outer(p, p))))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.6 < r1 < 2.6 and 1.6 < r2 < 2.6, errs
+
+
+def test_fde2d_time_exact_linear_in_time():
+    """Implicit Euler is exact for a solution linear in t when the source is
+    taken at the new time level (Eq. (sylv-timestepping)): with U(t) = (1 + t) P
+    and f(t) = P - (1 + t) L_h P for the discrete operator L_h (A = ½I - Δt L_h
+    per side), every step reproduces U(t_m) to rounding.  Sampling f at the old
+    level, or dropping Δt, leaves an error of the size of Δt ||L_h P||."""
+    w = I.fd2d(N=20, alpha=(1.4, 1.8), steps=7)
+    Ax = O.fd_operator(w.ops[0])
+    Ay = O.fd_operator(w.ops[1])
+    dt = w.dt
+    Lxh = (0.5 * np.eye(20) - Ax) / dt
+    Lyh = (0.5 * np.eye(20) - Ay) / dt
+    P = I.SplitMix64(21).normal_array((20, 20))
+    LP = Lxh @ P + P @ Lyh.T
+    run = _Run2D(w.ops, P.copy(), dt, 7, lambda t: P - (1 + t) * LP)
+    U, hist = O.fde2d_run(run, return_all=True)
+    for m, Um in enumerate(hist, start=1):
+        np.testing.assert_allclose(Um, (1 + m * dt) * P, atol=1e-11 * np.abs(P).max())
+    # the same holds step by step through fde2d_rhs
+    C = O.fde2d_rhs(run, P, 0)
+    np.testing.assert_allclose(C, P + dt * (P - (1 + dt) * LP), atol=1e-14 * np.abs(C).max())
+
+
+def test_schur_sylvester_reuse_vs_kronecker():
+    """The Schur forms computed once serve any right-hand side: three
+    successive solves against Kronecker brute force, nonsymmetric A and B."""
+    A = _rand_stable(9, 31, 5.0)
+    B = _rand_stable(7, 32, 5.0)
+    solver = O.SchurSylvester(A, B)
+    for k in range(3):
+        C = I.SplitMix64(40 + k).normal_array((9, 7))
+        X2 = O.sylvester_kron(A, B, C)
+        np.testing.assert_allclose(solver.solve(C), X2, atol=1e-13 * np.abs(X2).max())
+
+
+def test_sylvester_residual_definition():
+    """||C - A_x X - X A_yᵀ||_F / ||C||_F: exactly 1 at X = 0, rounding at the
+    Kronecker solution, and ||K vec E|| / ||C|| for X = X* + E with
+    K = I ⊗ A_x + A_y ⊗ I (column-major vec, §4.2)."""
+    w = I.fd2d(N=12, alpha=(1.3, 1.7), steps=5)
+    Ax = O.fd_operator(w.ops[0])
+    Ay = O.fd_operator(w.ops[1])
+    C = I.SplitMix64(50).normal_array((12, 12))
+    assert O.sylvester_residual(w.ops[0], w.ops[1], np.zeros((12, 12)), C) == pytest.approx(1.0, abs=1e-15)
+    X = O.sylvester_kron(Ax, Ay, C)
+    assert O.sylvester_residual(w.ops[0], w.ops[1], X, C) < 1e-13
+    E = 1e-3 * I.SplitMix64(51).normal_array((12, 12))
+    K = np.kron(np.eye(12), Ax) + np.kron(Ay, np.eye(12))
+    want = np.linalg.norm(K @ E.reshape(-1, order="F")) / np.linalg.norm(C)
+    got = O.sylvester_residual(w.ops[0], w.ops[1], X + E, C)
+    assert abs(got - want) < 1e-9 * want
+
+
+# ---------------------------------------------------------------- ranks
+def test_eps_rank_prescribed_spectrum():
+    rng = I.SplitMix64(60)
+    Qa, _ = np.linalg.qr(rng.normal_array((30, 8)))
+    Qb, _ = np.linalg.qr(rng.normal_array((20, 8)))
+    s = 10.0 ** -np.arange(8)  # 1, 1e-1, ..., 1e-7
+    Y = (Qa * s) @ Qb.T
+    assert O.eps_rank(Y, 5e-4) == 4
+    assert O.eps_rank(Y, 2e-8) == 8
+    assert O.eps_rank(Y, 2.0) == 0
+    assert O.eps_rank(np.zeros((0, 5)), 1e-3) == 0
+
+
+@pytest.mark.parametrize("N", [64, 256, 1024])
+def test_beckermann_bound_on_psd_hankel(N):
+    """Lemma beckermann on its own hypothesis: the Hilbert matrix
+    H_ij = 1/(i + j + 1) is a positive semidefinite Hankel matrix (moments of
+    the Lebesgue measure on [0,1]), so rank_ε(H) <= 𝔅(N, ε) with ε relative to
+    ||H||_2.  For the Hilbert matrix the bound is within a factor ~4 of the
+    true rank, so a bound off by a constant factor of 5 (a dropped 1/π², a
+    log base) fails one side or the other."""
+    H = sla.hilbert(N)
+    s = np.linalg.svd(H, compute_uv=False)
+    for eps in (1e-4, 1e-8, 1e-12):
+        r = int(np.sum(s > eps * s[0]))
+        b = O.beckermann_bound(N, eps)
+        assert r <= b and 5 * r > b, (N, eps, r, b)
+    # hand-evaluated: N = 1024, ε = 1e-8: (2/π²) ln(4096/π) ln(1.6e9) = 30.80 -> 2 + 2·31
+    assert O.beckermann_bound(1024, 1e-8) == 64
+
+
 def _golden_qsrank():
     rows = []
     path = os.path.join(os.path.dirname(__file__), "golden", "paper_1d_qsrank.txt")
