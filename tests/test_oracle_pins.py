@@ -226,6 +226,32 @@ def test_aca_exact_low_rank():
     assert len(set(rows)) == len(rows) and len(set(cols)) == len(cols)
 
 
+def test_aca_hand_worked():
+    """Partial-pivoting ACA worked by hand on a 3 x 4 integer matrix (reading of
+    the textbook rule: start at row 0, column pivot = largest residual entry of
+    the row, next row = largest entry of the new column over unused rows).
+      term 1: row 0 = [1 4 2 0] -> col 1, v = row / 4, u = col 1 = [4 2 0]
+      term 2: row 1 - 2 v = [1.5 0 7 1] -> col 2, u = col 2 - 0.5 u1 = [0 7 1]
+      term 3: row 2 - v2 -> col 0 (|4 - 1.5/7| > |2 - 1/7|), u = [0 0 4 - 1.5/7]
+    and the three terms reproduce M."""
+    M = np.array([[1.0, 4, 2, 0], [2, 2, 8, 1], [4, 0, 1, 2]])
+    U, V, rows, cols, conv = O.aca_partial_pivot(lambda i: M[i], lambda j: M[:, j], 3, 4, 1e-12, 10)
+    assert conv and rows == [0, 1, 2] and cols == [1, 2, 0]
+    np.testing.assert_array_equal(U[:, 0], [4, 2, 0])
+    np.testing.assert_array_equal(V[:, 0], [0.25, 1, 0.5, 0])
+    np.testing.assert_array_equal(U[:, 1], [0, 7, 1])
+    np.testing.assert_allclose(U[:, 2], [0, 0, 4 - 1.5 / 7], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(U @ V.T, M, rtol=0, atol=1e-14)
+    # stopping rule ||u_1|| ||v_1|| = sqrt(20 * 1.3125) = 5.12 <= abstol stops after one term
+    U1, _, rows1, _, conv1 = O.aca_partial_pivot(lambda i: M[i], lambda j: M[:, j], 3, 4, 6.0, 10)
+    assert conv1 and U1.shape[1] == 1 and rows1 == [0]
+    # an exactly zero residual row moves to the lowest unused row
+    Z = np.array([[0.0, 0.0], [1.0, 2.0]])
+    U2, V2, rows2, cols2, conv2 = O.aca_partial_pivot(lambda i: Z[i], lambda j: Z[:, j], 2, 2, 1e-12, 5)
+    assert conv2 and rows2 == [1] and cols2 == [1]
+    np.testing.assert_array_equal(U2 @ V2.T, Z)
+
+
 @pytest.mark.parametrize("alpha,N", [(1.5, 512), (1.2, 300), (1.8, 257)])
 def test_aca_toeplitz_block(alpha, N):
     # §3.4.2: the top-level block T21 is numerically low rank; ACA reaches the tolerance
@@ -241,6 +267,33 @@ def test_aca_toeplitz_block(alpha, N):
     err = np.linalg.norm(T21 - U @ V.T, 2)
     assert err < 100 * tol
     assert U.shape[1] <= O.qsrank_bound_T(N, 1e-12) + 10
+
+
+def test_hodlr_reference_known_ranks():
+    """Off-diagonal ranks of matrices whose structure fixes them (§3.4.1):
+    tridiagonal -> one nonzero corner per block, rank (1, 1) at every level;
+    min(i, j) + 1 (the inverse of a tridiagonal matrix, semiseparable) -> rank
+    (1, 1); upper triangular -> lower blocks rank 0; a coupling below ε||A||_2
+    -> rank 0, one above it -> rank 1."""
+    N = 96
+    rng = I.SplitMix64(70)
+    Tri = np.diag(2.0 + rng.normal_array((N,)) ** 2)
+    Tri += np.diag(1.0 + rng.normal_array((N - 1,)) ** 2, 1) + np.diag(1.0 + rng.normal_array((N - 1,)) ** 2, -1)
+    tree, ranks, _ = O.hodlr_reference(Tri, 8, 1e-12)
+    assert len(ranks) == sum(len(lv) for lv in tree[:-1]) and set(ranks.values()) == {(1, 1)}
+    i = np.arange(N)
+    Sm = np.minimum.outer(i, i) + 1.0
+    _, ranks, _ = O.hodlr_reference(Sm, 8, 1e-12)
+    assert set(ranks.values()) == {(1, 1)}
+    Up = np.triu(rng.normal_array((N, N))) + N * np.eye(N)
+    _, ranks, _ = O.hodlr_reference(Up, 8, 1e-12)
+    assert all(r21 == 0 and r12 > 1 for r12, r21 in ranks.values())
+    D = np.eye(N)
+    D[N - 1, 0] = 1e-9  # inside the lower block of the root only
+    _, ranks, abstol = O.hodlr_reference(D, 8, 1e-8, normA=1.0)
+    assert abstol == 1e-8 and set(ranks.values()) == {(0, 0)}
+    _, ranks, _ = O.hodlr_reference(D, 8, 1e-10, normA=1.0)
+    assert ranks[(0, N)] == (0, 1) and sum(map(sum, ranks.values())) == 1
 
 
 @pytest.mark.parametrize("alpha", [1.3, 1.7])
