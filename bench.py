@@ -45,6 +45,34 @@ def workload_for(name: str):
     return I.WORKLOADS[name]()
 
 
+# ------------------------------------------------------------------ replicas
+# N > 1: every rank runs its own replica of the workload (the path has no
+# exchange step); the timed regions are aligned by barriers and the slowest
+# rank's time counts.
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(values, world: int, device):
+    """Element-wise maximum of a list of floats over all ranks (identity at N=1)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def replica_rate(world: int, units_per_rank: float, ms_max: float) -> float:
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -220,14 +248,8 @@ def run_ours(args, rank, world, local_rank):
     lib.runner_advance(r32, args.warmup, stream)
     torch.cuda.synchronize()
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-
-            dist.barrier()
-
     clocks = ClockSampler(local_rank)
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     st0 = lib.runner_stats(r32)
     launches0 = lib.launch_count()
@@ -238,7 +260,7 @@ def run_ours(args, rank, world, local_rank):
     e1.record()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    barrier()
+    barrier(world)
     launches = lib.launch_count() - launches0
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
@@ -257,13 +279,8 @@ def run_ours(args, rank, world, local_rank):
             roof["measured"] = (f"profiled pass of {args.prof_steps} steps right after the timed region (eager "
                                 f"launches, CUDA events on the launching stream)")
         lib.prof_reset()
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    ms = max_over_ranks([ms], world, dev)[0]
+    value = replica_rate(world, args.steps, ms)
     sweeps = (st1.sweeps_total - st0.sweeps_total) / max(args.steps, 1)
 
     # ---- FP64 inner solver on the same state (comparison + agreement)
@@ -312,7 +329,7 @@ def run_ours(args, rank, world, local_rank):
             host_F.append(hf)
         host_out = torch.empty(N * N, dtype=torch.float64, pin_memory=True)
         torch.cuda.synchronize()
-        barrier()
+        barrier(world)
         t0 = time.perf_counter()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record()
@@ -321,9 +338,10 @@ def run_ours(args, rank, world, local_rank):
             lib.runner_state(r32, host_out.data_ptr(), stream)               # D2H of the step's result
         g1.record()
         torch.cuda.synchronize()
-        ems = g0.elapsed_time(g1)
         wall = time.perf_counter() - t0
-        e2e = {"value": world * args.e2e_steps / (ems / 1e3), "unit": "steps/s",
+        barrier(world)
+        ems, wall = max_over_ranks([g0.elapsed_time(g1), wall], world, dev)
+        e2e = {"value": replica_rate(world, args.e2e_steps, ems), "unit": "steps/s",
                "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8,
                "host_wall_steps_per_s": args.e2e_steps / wall,
                "input": "dense source F^(m+1) (N x N FP64) uploaded per step; state U^(m+1) read back"}
@@ -374,13 +392,16 @@ def run_batch(args, rank, world, local_rank):
     lib.batch_advance(b, args.warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank)
+    barrier(world)
+    torch.cuda.synchronize()
     launches0 = lib.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     lib.batch_advance(b, args.steps)
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    barrier(world)
+    ms = max_over_ranks([e0.elapsed_time(e1)], world, dev)[0]
     clk = clocks.stop()
     launches = lib.launch_count() - launches0
     setup, tune, solve, inst = lib.batch_timing(b)
@@ -391,7 +412,7 @@ def run_batch(args, rank, world, local_rank):
     lib.batch_free(b)
     if rank != 0:
         return
-    value = world * len(ws) * args.steps / (ms / 1e3)
+    value = replica_rate(world, len(ws) * args.steps, ms)
     out = {"metric": "batched instance time steps/s (64 independent 1D/2D instances)", "value": value,
            "unit": "instance-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
