@@ -192,6 +192,36 @@ fde_status sylv_residual(sylv_t s, const double* d_C, const double* d_X, double*
 
 void sylv_free(sylv_t s);
 
+/* ------------------------------------------- fADI shifts (host only) -- */
+/* The two host steps by which sylv_create chooses the factored-ADI shifts
+ * (§3.3) of every D&C level; neither launches device work nor needs a GPU.
+ *
+ * fde_block_interval: an interval [lam_lo, lam_hi] holding the real parts of
+ * all eigenvalues of the diagonal block A[lo:hi, lo:hi] (0 <= lo < hi <= N) of
+ * the operator of Eq. (system_FD) described by p (p->d_plus / d_minus must be
+ * HOST pointers here; leaf and tol are not used).  A is an M-matrix (positive
+ * diagonal, non-positive off-diagonal entries, diagonally dominant; §2.2.1),
+ * so by Gershgorin lam_lo = the smallest row sum of the block and
+ * lam_hi = max_i (2 a_ii - row sum_i).  sylv_create takes, per level, the
+ * union of these intervals over the level's nodes, for A_x ([a, b]) and A_y
+ * ([c, d]).
+ *
+ * fde_fadi_shifts: for A X + X Bᵀ = G Hᵀ with spec(A) in [a, b] and spec(B)
+ * in [c, d] (0 < a < b, 0 < c < d), the Zolotarev problem for E = [a, b] and
+ * F = [-d, -c] mapped by a Möbius transform to [k, 1] ∪ [-1, -k], whose optimal
+ * zeros are Jacobi dn values.  J is the smallest count <= jmax (1..64) whose
+ * ratio max_E |r| / min_F |r|, r(z) = Π_j (z - alpha_j) / (z - beta_j), on 400
+ * log-spaced points per interval, is <= target (0 < target < 1); J = jmax if
+ * none is.  h_alpha / h_beta (host, length >= jmax) receive the J zeros
+ * (in E) and poles (in F); *ratio the ratio for J.  sylv_create uses
+ * jmax = 64 and target 1e-13 (FP64 inner solver) or 1e-5 (FP32).
+ *
+ * Errors: FDE_ERR_ARG for NULL pointers, device pointers for d_plus /
+ * d_minus, or arguments outside the ranges above. */
+fde_status fde_block_interval(const fde_op_params* p, int lo, int hi, double* lam_lo, double* lam_hi);
+fde_status fde_fadi_shifts(double a, double b, double c, double d, double target, int jmax, int* J,
+                           double* h_alpha, double* h_beta, double* ratio);
+
 /* ------------------------------------------------------------ time loop -- */
 /* Source f(x[,y],t) = Σ_l w_l(t) F_L[:,l] (⊗ F_R[:,l]),
  * w_l(t) = amp_l + sin_amp_l * sin(omega_l * t), sampled at the new time level

@@ -84,6 +84,10 @@ _SIGS = {
     "sylv_inner_solve": ([_P, _P, _P, C.c_int, _P], C.c_int),
     "sylv_residual": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "sylv_free": ([_P], None),
+    "fde_block_interval": ([C.POINTER(OpParams), C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+                           C.c_int),
+    "fde_fadi_shifts": ([C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int), _P,
+                         _P, C.POINTER(C.c_double)], C.c_int),
     "fde_run": ([C.POINTER(RunParams), _P, _P, _P, C.POINTER(RunStats)], C.c_int),
     "fde_runner_create": ([C.POINTER(RunParams), _P, _P, C.POINTER(_P)], C.c_int),
     "fde_runner_advance": ([_P, C.c_int, _P], C.c_int),
@@ -230,6 +234,21 @@ class Lib:
     def sylv_free(self, s: int):
         if s:
             self.dll.sylv_free(s)
+
+    # -- fADI shift selection (host only)
+    def fde_block_interval(self, params: OpParams, lo: int, hi: int):
+        a, b = C.c_double(), C.c_double()
+        self.check(self.dll.fde_block_interval(C.byref(params), lo, hi, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def fde_fadi_shifts(self, a: float, b: float, c: float, d: float, target: float, jmax: int = 64):
+        al = np.zeros(max(jmax, 1))
+        be = np.zeros(max(jmax, 1))
+        J = C.c_int()
+        r = C.c_double()
+        self.check(self.dll.fde_fadi_shifts(a, b, c, d, target, jmax, C.byref(J), al.ctypes.data, be.ctypes.data,
+                                            C.byref(r)))
+        return al[:J.value].copy(), be[:J.value].copy(), r.value
 
     # -- time loop
     def run_params(self, w, prec: int = FDE_FP64, use_graph: int = 0) -> RunParams:

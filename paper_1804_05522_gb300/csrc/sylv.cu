@@ -54,10 +54,12 @@ static void node_interval(const std::vector<double>& S, const std::vector<double
 
 // Jacobi elliptic functions by the arithmetic–geometric mean (descending
 // Landen transformation; Abramowitz & Stegun 16.4) and K(m) = π / (2 AGM).
-static void jacobi_dn_K(double u, double m, double* dn, double* K) {
+// The parameter comes with its complement m1 = 1 - m, formed by the caller
+// without cancellation (m close to 1 is the usual case here).
+static void jacobi_dn_K(double u, double m, double m1, double* dn, double* K) {
   double a[64], cc[64];
   a[0] = 1.0;
-  double b = sqrt(1.0 - m);
+  double b = sqrt(m1);
   cc[0] = sqrt(m);
   int n = 0;
   while (n < 60 && fabs(cc[n]) > 1e-17 * a[n]) {
@@ -81,12 +83,15 @@ static void jacobi_dn_K(double u, double m, double* dn, double* K) {
 // dn((2j-1)K'/(2J), k') (Wachspress); alpha_j -> zeros near E, beta_j -> poles near F.
 static void zolotarev_shifts(double a, double b, double c, double d, int J, std::vector<double>& al,
                              std::vector<double>& be) {
+  // cross ratio m >= 1 and m - 1, formed without cancellation; k is the
+  // smaller root of k² - 2(2m - 1)k + 1 = 0, as 1 / (the larger one)
   const double m = (a + d) * (b + c) / ((a + c) * (b + d));
-  double k = 2.0 * m - 1.0 - 2.0 * sqrt(std::max(m * m - m, 0.0));
+  const double m1 = (b - a) * (d - c) / ((a + c) * (b + d));
+  double k = 1.0 / (2.0 * m - 1.0 + 2.0 * sqrt(m * m1));
   k = std::min(std::max(k, 1e-300), 1.0 - 1e-15);
-  const double mp = 1.0 - k * k;
+  const double mp = 1.0 - k * k, mp1 = k * k;  // parameter k'² and its complement k²
   double K, dn;
-  jacobi_dn_K(0.0, mp, &dn, &K);
+  jacobi_dn_K(0.0, mp, mp1, &dn, &K);
   // Möbius w -> z with k -> a, 1 -> b, -1 -> -d:  z = (A w + B)/(C w + 1)
   // rows: A w + B - z C w = z
   const double W[3] = {k, 1.0, -1.0}, Z[3] = {a, b, -d};
@@ -114,7 +119,7 @@ static void zolotarev_shifts(double a, double b, double c, double d, int J, std:
   be.resize(J);
   for (int j = 0; j < J; ++j) {
     double dnj, Kd;
-    jacobi_dn_K((2.0 * (j + 1) - 1.0) * K / (2.0 * J), mp, &dnj, &Kd);
+    jacobi_dn_K((2.0 * (j + 1) - 1.0) * K / (2.0 * J), mp, mp1, &dnj, &Kd);
     al[j] = inv(dnj);
     be[j] = inv(-dnj);
   }
@@ -137,6 +142,31 @@ static double zolotarev_bound(const std::vector<double>& al, const std::vector<d
     den = std::min(den, rw);
   }
   return num / den;
+}
+
+// Smallest J <= jmax whose ratio (zolotarev_bound) is <= target, or jmax when
+// none is; its shifts in al / be and its ratio in *ratio.
+static int select_shifts(double a, double b, double c, double d, double target, int jmax, std::vector<double>& al,
+                         std::vector<double>& be, double* ratio) {
+  double r = INFINITY;
+  int J = 1;
+  for (; J <= jmax; ++J) {
+    zolotarev_shifts(a, b, c, d, J, al, be);
+    r = zolotarev_bound(al, be, a, b, c, d);
+    if (r <= target) break;
+  }
+  if (J > jmax) J = jmax;  // al / be still hold the jmax shifts, r their ratio
+  *ratio = r;
+  return J;
+}
+
+static bool host_readable(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // no device, or a plain host pointer
+    return true;
+  }
+  return at.type != cudaMemoryTypeDevice;
 }
 
 // ================================================================ kernels
@@ -1450,14 +1480,9 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
       c = std::min(c, lo_);
       d = std::max(d, hi_);
     }
-    int J = 1;
     std::vector<double> al, be;
-    for (J = 1; J <= 64; ++J) {
-      zolotarev_shifts(a, b, c, d, J, al, be);
-      if (zolotarev_bound(al, be, a, b, c, d) <= target) break;
-    }
-    if (J > 64) J = 64;
-    zolotarev_shifts(a, b, c, d, J, al, be);
+    double ratio;
+    const int J = select_shifts(a, b, c, d, target, 64, al, be, &ratio);
     S->J[l] = J;
     A_[l] = al;
     B_[l] = be;
@@ -1767,6 +1792,49 @@ extern "C" fde_status sylv_residual(sylv_t s, const double* d_C, const double* d
 }
 
 extern "C" void sylv_free(sylv_t s) { delete s; }
+
+// Host-only views of the shift selection sylv_create performs (no device work).
+extern "C" fde_status fde_fadi_shifts(double a, double b, double c, double d, double target, int jmax, int* J,
+                                      double* h_alpha, double* h_beta, double* ratio) {
+  FDE_ARG(J != nullptr && h_alpha != nullptr && h_beta != nullptr && ratio != nullptr, "NULL output");
+  FDE_ARG(a > 0.0 && b > a && std::isfinite(b), "need 0 < a < b < inf");
+  FDE_ARG(c > 0.0 && d > c && std::isfinite(d), "need 0 < c < d < inf");
+  FDE_ARG(target > 0.0 && target < 1.0, "target must be in (0, 1)");
+  FDE_ARG(jmax >= 1 && jmax <= 64, "jmax must be in [1, 64]");
+  std::vector<double> al, be;
+  *J = fde::select_shifts(a, b, c, d, target, jmax, al, be, ratio);
+  for (int j = 0; j < *J; ++j) {
+    h_alpha[j] = al[j];
+    h_beta[j] = be[j];
+  }
+  return FDE_OK;
+}
+
+extern "C" fde_status fde_block_interval(const fde_op_params* p, int lo, int hi, double* lam_lo, double* lam_hi) {
+  FDE_ARG(p != nullptr && lam_lo != nullptr && lam_hi != nullptr, "NULL argument");
+  FDE_ARG(p->N >= 2 && p->N <= (1 << 20), "N must be in [2, 2^20]");
+  FDE_ARG(p->alpha > 1.0 && p->alpha <= 2.0, "alpha must lie in (1, 2]");
+  FDE_ARG(p->h > 0.0 && std::isfinite(p->h) && p->dt > 0.0 && std::isfinite(p->dt), "h, dt must be > 0");
+  FDE_ARG(p->shift > 0.0 && std::isfinite(p->shift), "shift must be > 0");
+  FDE_ARG(p->d_plus != nullptr && p->d_minus != nullptr, "d_plus / d_minus are NULL");
+  FDE_ARG(0 <= lo && lo < hi && hi <= p->N, "need 0 <= lo < hi <= N");
+  FDE_ARG(fde::host_readable(p->d_plus) && fde::host_readable(p->d_minus), "d_plus / d_minus must be host pointers");
+  const int N = p->N;
+  // g_0..g_{N+1} by the recurrence of Eq. (Grun) and their partial sums, as
+  // sylv_create has them from the operator
+  std::vector<double> S(N + 2), dp(p->d_plus, p->d_plus + N), dm(p->d_minus, p->d_minus + N);
+  double gk = 1.0;
+  long double acc = 1.0L;
+  S[0] = 1.0;
+  for (int k = 1; k < N + 2; ++k) {
+    gk = gk * (1.0 - (p->alpha + 1.0) / k);
+    acc += gk;
+    S[k] = (double)acc;
+  }
+  const double cc = p->dt * pow(p->h, -p->alpha);
+  fde::node_interval(S, dp, dm, cc, p->shift, p->alpha, lo, hi, lam_lo, lam_hi);
+  return FDE_OK;
+}
 
 // Exposed for the time loop (fde_run.cu)
 namespace fde {
