@@ -266,7 +266,7 @@ __global__ void block_factors_kernel(const NodeRef* __restrict__ nodes, const do
                                      const double* __restrict__ V0, const double* __restrict__ dp,
                                      const double* __restrict__ dm, double c, int N, int N1, int N2, int kaca) {
   const NodeRef nd = nodes[blockIdx.x];
-  const int t = nd.mid - nd.lo, s = nd.hi - nd.mid, r = kaca + 1;
+  const int t = nd.mid - nd.lo, r = kaca + 1;
   const int len = nd.hi - nd.lo;
   for (int e = threadIdx.x; e < len * r; e += blockDim.x) {
     const int row = nd.lo + e % len, l = e / len;
