@@ -107,6 +107,23 @@ def oracle_step_sample(name: str, repeats: int = 1):
     return dt, f"oracle Bartels-Stewart step at N={ORACLE_SAMPLE_N} (Schur setup excluded), {repeats} step(s)"
 
 
+def oracle_threads():
+    """Threads the oracle's LAPACK/BLAS calls run on, and how that was found."""
+    try:
+        from threadpoolctl import threadpool_info
+
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return max(n), "threadpoolctl"
+    except ImportError:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var, "")
+        if v.isdigit() and int(v) > 0:
+            return int(v), var
+    return os.cpu_count(), "all host cores (BLAS default)"
+
+
 def scale_to(N: int, sec_per_step: float) -> float:
     """Oracle steps/s at N from the sample by the O(N^3) per-step cost."""
     return 1.0 / (sec_per_step * (N / ORACLE_SAMPLE_N) ** 3)
@@ -352,7 +369,9 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         sec, sample = oracle_step_sample(args.workload, 1)
-        cpu = {"value": scale_to(N, sec), "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+        cores, cores_src = oracle_threads()
+        cpu = {"value": scale_to(N, sec), "unit": "steps/s", "cores": cores, "cores_source": cores_src,
+               "kind": "oracle",
                "sample": sample + f"; {sec:.2f} s/step, scaled to N={N} by (N/{ORACLE_SAMPLE_N})^3",
                "sample_steps_per_s": 1.0 / sec}
     cfg = {"workload": f"{args.workload}: 2D N={N} per side ({N*N} unknowns), alpha=({w.ops[0].alpha},{w.ops[1].alpha}), "
@@ -445,7 +464,8 @@ def run_reference(args, rank, world):
            "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": args.workload, "N": N},
-           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": oracle_threads()[0],
+                            "cores_source": oracle_threads()[1], "kind": "oracle",
                             "sample": sample + f"; mean {per:.2f} s/step over {args.steps} steps, scaled to N={N} "
                                                f"by (N/{ORACLE_SAMPLE_N})^3", "wall_s": wall},
            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
