@@ -34,6 +34,10 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   apply_fd_operator_fft      pinned: dense product
   sylvester_residual         pinned: X = 0, Kronecker solution, Kronecker
                              product of a perturbation
+  lowrank_from_dense         pinned: prescribed singular values
+  fde2d_rhs_factors          pinned: the dense right-hand side
+  fde2d_lowrank_run          pinned: reduces to fde2d_run below rounding;
+                             error and rank follow eps
 """
 from __future__ import annotations
 
@@ -354,6 +358,53 @@ def fde2d_run(w, steps: int | None = None, return_all: bool = False):
         if return_all:
             hist.append(U.copy())
     return (U, hist) if return_all else U
+
+
+# ---------------------------------------------------------------------------
+# §4.1-§4.2: the 2D time loop with the solution kept in factored form
+# ---------------------------------------------------------------------------
+def lowrank_from_dense(X: np.ndarray, eps: float):
+    """X ≈ W Zᵀ from the SVD of X, singular values <= eps·σ_1 dropped (the
+    ε-rank of §3 with ε relative to ||X||_2).  W carries the singular values."""
+    U, s, Vt = np.linalg.svd(X, full_matrices=False)
+    if s.size == 0 or s[0] == 0.0:
+        return np.zeros((X.shape[0], 0)), np.zeros((X.shape[1], 0))
+    r = int(np.sum(s > eps * s[0]))
+    return U[:, :r] * s[:r], Vt[:r].T
+
+
+def fde2d_rhs_factors(w, W: np.ndarray, Z: np.ndarray, m: int):
+    """Outer factors (L, R) of C = U^{(m)} + Δt F^{(m+1)} = L Rᵀ, with
+    U^{(m)} = W Zᵀ and F^{(m+1)} = F_L diag(w(t_{m+1})) F_Rᵀ (§4.1: both terms
+    are low rank, so their sum is, before recompression)."""
+    wt = w.source_weights((m + 1) * w.dt)
+    return np.hstack([W, w.dt * w.src_left * wt]), np.hstack([Z, w.src_right])
+
+
+def fde2d_lowrank_run(w, eps: float, steps: int | None = None):
+    """The 2D scheme with U^{(m)} in factored form (§4.1, §4.2), step by step:
+      1. factors of C = U^{(m)} + Δt F^{(m+1)} (fde2d_rhs_factors);
+      2. recompression of the sum: reduced QR of both factors, SVD of the small
+         core, singular values <= eps·||C||_2 dropped (truncate_lowrank);
+      3. the Sylvester equation A_x X + X A_yᵀ = L Rᵀ (Eq. (sylv-timestepping)),
+         solved here exactly by Bartels–Stewart in place of a low-rank solver
+         that reaches the solution within its tolerance (§4.3);
+      4. U^{(m+1)} = X truncated to its ε-rank (lowrank_from_dense).
+    eps is relative to the 2-norm at both truncations (the paper states one
+    tolerance for the solver and none for the recompressions).  Returns the
+    factors (W, Z) of U^{(M)}."""
+    solver = SchurSylvester(fd_operator(w.ops[0]), fd_operator(w.ops[1]))
+    W, Z = lowrank_from_dense(w.u0, eps)
+    M = w.steps if steps is None else steps
+    for m in range(M):
+        L, R = fde2d_rhs_factors(w, W, Z, m)
+        _, Ru = np.linalg.qr(L)
+        _, Rv = np.linalg.qr(R)
+        normC = float(np.linalg.svd(Ru @ Rv.T, compute_uv=False)[0])
+        L, R = truncate_lowrank(L, R, eps * normC)
+        X = solver.solve(L @ R.T)
+        W, Z = lowrank_from_dense(X, eps)
+    return W, Z
 
 
 # ---------------------------------------------------------------------------

@@ -469,6 +469,61 @@ def test_fde2d_time_exact_linear_in_time():
     np.testing.assert_allclose(C, P + dt * (P - (1 + dt) * LP), atol=1e-14 * np.abs(C).max())
 
 
+def test_lowrank_from_dense_prescribed_spectrum():
+    rng = I.SplitMix64(80)
+    Qa, _ = np.linalg.qr(rng.normal_array((40, 6)))
+    Qb, _ = np.linalg.qr(rng.normal_array((30, 6)))
+    s = np.array([3.0, 1.0, 1e-2, 1e-5, 1e-9, 1e-13])
+    X = (Qa * s) @ Qb.T
+    W, Z = O.lowrank_from_dense(X, 1e-6)
+    assert W.shape[1] == 4 and Z.shape[1] == 4
+    # the dropped part is exactly the tail: ||X - W Zᵀ||_2 = σ_5
+    assert abs(np.linalg.norm(X - W @ Z.T, 2) - 1e-9) < 1e-12
+    # W carries the singular values, Z has orthonormal columns
+    np.testing.assert_allclose(np.linalg.norm(W, axis=0), s[:4], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(Z.T @ Z, np.eye(4), atol=1e-13)
+    W0, Z0 = O.lowrank_from_dense(np.zeros((5, 4)), 1e-6)
+    assert W0.shape == (5, 0) and Z0.shape == (4, 0)
+
+
+def test_rhs_factors_match_dense_rhs():
+    """The factored right-hand side of §4.1 is the dense one of
+    Eq. (sylv-timestepping): L Rᵀ = W Zᵀ + Δt F(t_{m+1})."""
+    w = I.fd2d(N=48, alpha=(1.4, 1.6), steps=10)
+    rng = I.SplitMix64(81)
+    W, Z = rng.normal_array((48, 3)), rng.normal_array((48, 3))
+    for m in (0, 4):
+        L, R = O.fde2d_rhs_factors(w, W, Z, m)
+        assert L.shape[1] == R.shape[1] == 3 + w.src_left.shape[1]
+        np.testing.assert_allclose(L @ R.T, O.fde2d_rhs(w, W @ Z.T, m), rtol=0, atol=1e-12 * 100)
+
+
+def test_lowrank_run_reduces_to_dense_run():
+    """With truncation below rounding, the factored scheme is the dense one."""
+    w = I.fd2d(N=40, alpha=(1.3, 1.7), steps=6)
+    W, Z = O.fde2d_lowrank_run(w, 1e-15)
+    U = O.fde2d_run(w)
+    assert np.linalg.norm(W @ Z.T - U) <= 1e-12 * np.linalg.norm(U)
+
+
+def test_lowrank_run_error_follows_eps():
+    """Each step perturbs the dense scheme by two truncations of relative size
+    eps, which the next solves damp: the error against the dense run stays
+    within a small multiple of steps·eps and falls with eps; the rank of the
+    factored solution is the ε-rank of the dense one, within one."""
+    w = I.fd2d(N=64, alpha=(1.3, 1.7), steps=8)
+    U = O.fde2d_run(w)
+    s = np.linalg.svd(U, compute_uv=False)
+    errs = []
+    for eps in (1e-4, 1e-6, 1e-8):
+        W, Z = O.fde2d_lowrank_run(w, eps)
+        e = np.linalg.norm(W @ Z.T - U, 2) / s[0]
+        errs.append(e)
+        assert e <= 4 * w.steps * eps, (eps, e)
+        assert abs(W.shape[1] - int(np.sum(s > eps * s[0]))) <= 1, (eps, W.shape[1])
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10, errs
+
+
 def test_schur_sylvester_reuse_vs_kronecker():
     """The Schur forms computed once serve any right-hand side: three
     successive solves against Kronecker brute force, nonsymmetric A and B."""
