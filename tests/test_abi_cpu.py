@@ -26,10 +26,9 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def cpu_lib():
-    if not os.path.exists(binding.LIB_PATH):
-        from paper_1804_05522_gb300 import build
+    from paper_1804_05522_gb300 import build
 
-        build.build()
+    build.build()  # incremental: recompiles only what changed since the last build
     return binding.load()
 
 

@@ -4,7 +4,6 @@ row sums, and the Zolotarev shifts against the rational function they define,
 evaluated independently on fine grids, and against the Beckermann–Townsend
 upper bound on the Zolotarev number."""
 import math
-import os
 
 import numpy as np
 import pytest
@@ -16,10 +15,9 @@ from paper_1804_05522_gb300 import inputs as I
 
 @pytest.fixture(scope="module")
 def lib():
-    if not os.path.exists(binding.LIB_PATH):
-        from paper_1804_05522_gb300 import build
+    from paper_1804_05522_gb300 import build
 
-        build.build()
+    build.build()  # incremental: recompiles only what changed since the last build
     return binding.load()
 
 
