@@ -155,10 +155,10 @@ void hodlr_free(hodlr_t h);
 
 /* ------------------------------------------------------------------ 2D -- */
 /* Prepare the Sylvester solver for A_x X + X A_yᵀ = C (Eq. (sylv-timestepping)).
- * Ax and Ay must have the same N and leaf and be built with shift 1/2.
- * Computes the real Schur forms of every leaf block, the fADI shifts per level
- * and the shifted factorisations.  The handle keeps references to Ax, Ay:
- * free it before them. */
+ * Ax and Ay must have the same N and leaf, N > leaf, and be built with shift
+ * 1/2 (FDE_ERR_ARG otherwise).  Computes the real Schur forms of every leaf
+ * block, the fADI shifts per level and the shifted factorisations.  The
+ * handle keeps references to Ax, Ay: free it before them. */
 fde_status sylv_create(hodlr_t Ax, hodlr_t Ay, int prec, void* stream, sylv_t* out);
 
 /* Refinement controls (defaults set by sylv_create). */
@@ -228,7 +228,7 @@ fde_status fde_fadi_shifts(double a, double b, double c, double d, double target
  * t_{m+1} = (m+1) dt (implicit Euler). */
 typedef struct {
   int dim;                       /* 1 or 2                                       */
-  fde_op_params op_x;            /* shift must be 1 (1D) or 1/2 (2D)             */
+  fde_op_params op_x;            /* shift must be 1 (1D) or 1/2 (2D), else ARG   */
   fde_op_params op_y;            /* 2D only                                      */
   int steps;                     /* number of implicit-Euler steps M             */
   int rank;                      /* number of source terms r (0 allowed)         */

@@ -117,6 +117,9 @@ static fde_status check_run(const fde_run_params* p) {
   FDE_ARG(p->dim == 1 || p->rank == 0 || p->h_src_right, "NULL right source factor");
   FDE_ARG(p->prec == FDE_FP64 || p->prec == FDE_FP32_REFINE, "unknown precision");
   if (p->dim == 2) FDE_ARG(p->op_x.N == p->op_y.N && p->op_x.leaf == p->op_y.leaf, "op_x / op_y differ in N or leaf");
+  // the implicit-Euler step: I + ... in 1D (Eq. (system_FD)), 1/2 I + ... per side in 2D (Eq. (sylv-timestepping))
+  if (p->dim == 1) FDE_ARG(p->op_x.shift == 1.0, "1D: op_x.shift must be 1");
+  if (p->dim == 2) FDE_ARG(p->op_x.shift == 0.5 && p->op_y.shift == 0.5, "2D: op_x.shift and op_y.shift must be 1/2");
   return FDE_OK;
 }
 

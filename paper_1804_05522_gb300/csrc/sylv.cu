@@ -1704,6 +1704,7 @@ extern "C" fde_status sylv_create(hodlr_t Ax, hodlr_t Ay, int prec, void* stream
   FDE_ARG(prec == FDE_FP64 || prec == FDE_FP32_REFINE, "unknown precision");
   FDE_ARG(Ax->tree.N == Ay->tree.N && Ax->tree.leaf == Ay->tree.leaf, "A_x and A_y must share N and leaf");
   FDE_ARG(Ax->tree.L >= 1, "N must exceed the leaf size");
+  FDE_ARG(Ax->p.shift == 0.5 && Ay->p.shift == 0.5, "A_x and A_y must be built with shift 1/2");
   sylv_s* S = new sylv_s();
   fde_status s = create_impl(Ax, Ay, prec, (cudaStream_t)stream, S);
   if (s != FDE_OK) {

@@ -61,3 +61,17 @@ def test_null_arguments_rejected(cpu_lib):
     assert cpu_lib.dll.hodlr_solve(None, None, None, 1, 1, None) == binding.FDE_ERR_ARG
     assert cpu_lib.dll.sylv_step(None, None, None, 1, None, None, None) == binding.FDE_ERR_ARG
     assert cpu_lib.dll.fde_run(None, None, None, None, None) == binding.FDE_ERR_ARG
+
+
+@pytest.mark.parametrize("dim,shifts", [(1, (0.5, None)), (2, (1.0, 0.5)), (2, (0.5, 1.0))])
+def test_time_loop_rejects_wrong_shift(cpu_lib, dim, shifts):
+    """The time loop is implicit Euler: shift 1 in 1D (Eq. (system_FD)), 1/2 per
+    side in 2D (Eq. (sylv-timestepping)); anything else is refused on the host."""
+    w = I.fd1d(N=64) if dim == 1 else I.fd2d(N=64, leaf=16)
+    rp = cpu_lib.run_params(w)
+    rp.op_x.shift = shifts[0]
+    if dim == 2:
+        rp.op_y.shift = shifts[1]
+    with pytest.raises(binding.FdeError) as e:
+        cpu_lib.fde_run(rp, 1, 1)  # never dereferenced: the check comes first
+    assert e.value.status == binding.FDE_ERR_ARG and "shift" in str(e.value)
