@@ -1052,8 +1052,10 @@ static fde_status inner_solve(sylv_s* S, Inner<T>& in, cudaStream_t st) {
   return FDE_OK;
 }
 
-// R -= A_x δ + δ A_yᵀ for the FP32 update δ (the inner solution), both
-// directions read δ in place through strides (double-float FFT).
+// R -= A_x δ + δ A_yᵀ for the FP32 update δ (the inner solution) in
+// double-float FFTs.  The x direction reads δ in place; the y direction works
+// on δᵀ (coalesced reads and writes) and subtracts the transpose, except in the
+// block-Toeplitz form (N > 4096), which reads both directions through strides.
 static fde_status residual_update_df(sylv_s* S, const float* d, cudaStream_t st) {
   hodlr_s* ax = S->ax;
   hodlr_s* ay = S->ay;
