@@ -38,6 +38,12 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   fde2d_rhs_factors          pinned: the dense right-hand side
   fde2d_lowrank_run          pinned: reduces to fde2d_run below rounding;
                              error and rank follow eps
+  fe_weights / fe_stiffness  pinned: α=2 FE Laplacian, 50-digit evaluation,
+                             quadrature of Eq. (fe-int), structure and
+                             definiteness, manufactured-solution convergence
+  fe_mass                    pinned: quadrature
+  fe2d_operator              pinned: Kronecker brute force of
+                             Eq. (sylv-timestepping-fe)
 """
 from __future__ import annotations
 
@@ -405,6 +411,78 @@ def fde2d_lowrank_run(w, eps: float, steps: int | None = None):
         X = solver.solve(L @ R.T)
         W, Z = lowrank_from_dense(X, eps)
     return W, Z
+
+
+# ---------------------------------------------------------------------------
+# §2.2.2 and Eq. (fe-int): finite elements with hat functions on a uniform grid
+# ---------------------------------------------------------------------------
+def fe_weights(alpha: float, K: int) -> np.ndarray:
+    """w_{-1}, w_0, ..., w_K (index k + 1) with (M_+)_{ij} = h^{1-α}/Γ(4-α) w_{i-j}
+    for the left Riemann–Liouville stiffness of Eq. (fe-int) on hat functions
+    φ_j (height 1, nodes x_j = j h).
+
+    Derivation from Eq. (fe-int): g_j = I^{2-α} φ_j (the RL integral of the hat)
+    is (1/h)/Γ(4-α) times the second difference of (x - x_{j-1} - m h)_+^{3-α}
+    over m = 0, 1, 2; integrating φ_i g_j'' by parts twice turns φ_i'' into
+    (δ_{x_{i-1}} - 2 δ_{x_i} + δ_{x_{i+1}})/h.  So w_k is the fourth central
+    difference of t_+^γ, γ = 3 - α:
+        w_k = Σ_{m=-2..2} (1, -4, 6, -4, 1)_m (k + m)_+^γ,
+    zero for k <= -2.  Far from the diagonal the five terms cancel to
+    O(k^{γ-4}) (the instability of the explicit symbol that the paper's
+    footnote in its finite-element experiment points out), so for k >= 3
+    the difference is evaluated as its expansion in powers of 1/k, which
+    converges for k > 2:
+        w_k = Σ_{n = 4, 6, ...} binom(γ, n) (2^{n+1} - 8) k^{γ-n}
+    (odd moments of the symmetric stencil vanish; Σ_m c_m m^n = 2^{n+1} - 8
+    for even n >= 2, which is 0 for n = 2), summed until the terms are below
+    rounding."""
+    g = 3.0 - alpha
+    w = np.zeros(K + 2)
+    stencil = (1.0, -4.0, 6.0, -4.0, 1.0)
+    for idx in range(K + 2):
+        k = idx - 1
+        if k < 3:
+            w[idx] = sum(c * (k + m) ** g for m, c in zip(range(-2, 3), stencil) if k + m > 0)
+        else:
+            s, n, binom = 0.0, 0, 1.0
+            # binom(γ, n) by the recurrence binom(γ, n) = binom(γ, n-1) (γ - n + 1) / n
+            while True:
+                n += 1
+                binom *= (g - n + 1) / n
+                if n >= 4 and n % 2 == 0:
+                    term = binom * (2.0 ** (n + 1) - 8.0) * k ** (g - n)
+                    s += term
+                    if abs(term) <= 1e-18 * abs(s):
+                        break
+            w[idx] = s
+    return w
+
+
+def fe_mass(N: int, h: float) -> np.ndarray:
+    """M_{ij} = <φ_i, φ_j> for hat functions: h (1/6, 2/3, 1/6) tridiagonal."""
+    return h * (np.diag(np.full(N, 2.0 / 3.0)) + np.diag(np.full(N - 1, 1.0 / 6.0), 1)
+                + np.diag(np.full(N - 1, 1.0 / 6.0), -1))
+
+
+def fe_stiffness(alpha: float, N: int, h: float) -> np.ndarray:
+    """K = M_+ + M_-, the stiffness of ∂^α_+ + ∂^α_- with constant unit
+    coefficients (§2.2.2); M_- = M_+ᵀ on a uniform grid (reflection x -> -x)."""
+    w = fe_weights(alpha, N)
+    Mp = np.zeros((N, N))
+    for i in range(N):
+        for j in range(N):
+            if i - j >= -1:
+                Mp[i, j] = w[i - j + 1]
+    Mp *= h ** (1.0 - alpha) / math.gamma(4.0 - alpha)
+    return Mp + Mp.T
+
+
+def fe2d_operator(alpha: float, N: int, h: float, dt: float) -> np.ndarray:
+    """One side of Eq. (sylv-timestepping-fe) brought to the form of
+    Eq. (sylv-timestepping) by M^{-1} (the paper's first approach):
+    M^{-1}(1/2 M - Δt K)."""
+    M = fe_mass(N, h)
+    return np.linalg.solve(M, 0.5 * M - dt * fe_stiffness(alpha, N, h))
 
 
 # ---------------------------------------------------------------------------

@@ -670,3 +670,138 @@ def test_paper_printed_qsrank_alpha18():
     up = sla.svdvals(A[:k, k:])
     q = max(int((lo > 1e-8 * nrm).sum()), int((up > 1e-8 * nrm).sum()))
     assert q == rows[(alpha, N)]
+
+
+# ------------------------------------------------------ finite elements
+def test_fe_weights_alpha2_is_fe_laplacian():
+    """At α = 2 the RL derivative is the second derivative: w = (1, -2, 1) and
+    M_+ = M_- = (1/h) tridiag(1, -2, 1), minus the classical FE stiffness."""
+    w = O.fe_weights(2.0, 12)
+    np.testing.assert_array_equal(w, [1.0, -2.0, 1.0] + [0.0] * 11)
+    h = 0.1
+    K = O.fe_stiffness(2.0, 9, h)
+    lap = (np.diag(np.full(9, -2.0)) + np.diag(np.ones(8), 1) + np.diag(np.ones(8), -1)) / h
+    np.testing.assert_allclose(K, 2 * lap, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("alpha", [1.1, 1.3, 1.5, 1.7, 1.9])
+def test_fe_weights_against_high_precision(alpha):
+    """The fourth difference of t_+^{3-α} in 50-digit arithmetic against the
+    oracle's direct form (k <= 2: within the rounding of its terms) and its
+    series form (k >= 3: to 1e-14 relative, where the direct form would lose
+    up to k^4 digits' worth)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    K = 5000
+    w = O.fe_weights(alpha, K)
+    g = mp.mpf(3) - mp.mpf(alpha)
+    for k in list(range(-1, 16)) + [20, 50, 200, 1000, K]:
+        terms = [c * (mp.mpf(k) + m) ** g for m, c in zip(range(-2, 3), (1, -4, 6, -4, 1)) if k + m > 0]
+        ref = float(sum(terms))
+        tol = 4e-16 * float(sum(abs(t) for t in terms)) if k <= 2 else 1e-14 * abs(ref)
+        assert abs(w[k + 1] - ref) <= tol, (k, w[k + 1], ref)
+
+
+def test_fe_stiffness_by_quadrature():
+    """Eq. (fe-int) integrated numerically, without the double integration by
+    parts: <φ_i, ∂^α_+ φ_j> with ∂^α_+ φ_j = [(x-x_{j-1})_+^{1-α} - 2(x-x_j)_+^{1-α}
+    + (x-x_{j+1})_+^{1-α}] / (h Γ(2-α)) (the RL power rule on the three kinks
+    of the hat), against the oracle's h^{1-α}/Γ(4-α) w_{i-j}; and the mass
+    matrix <φ_i, φ_j> by the same quadrature."""
+    from scipy import integrate
+
+    alpha, N = 1.4, 10
+    h = 1.0 / (N + 1)
+    x = (np.arange(N + 2)) * h  # x_0 = 0 .. x_{N+1} = 1; φ_j peaks at x_j, j = 1..N
+    Mp = O.fe_weights(alpha, N)
+    G = math.gamma(2 - alpha)
+
+    def dphi(j, t):
+        return sum(c * max(t - x[j + m], 0.0) ** (1 - alpha) for m, c in ((-1, 1.0), (0, -2.0), (1, 1.0))
+                   if t > x[j + m]) / (h * G)
+
+    def phi(i, t):
+        return max(0.0, 1.0 - abs(t - x[i]) / h)
+
+    for i, j in [(5, 5), (5, 4), (4, 5), (6, 3), (9, 1), (8, 2)]:
+        val = 0.0
+        for a, b in ((x[i - 1], x[i]), (x[i], x[i + 1])):
+            pts = [p for p in (x[j - 1], x[j], x[j + 1]) if a < p < b]
+            val += integrate.quad(lambda t: phi(i, t) * dphi(j, t), a, b, points=pts or None, limit=200,
+                                  epsabs=1e-14, epsrel=1e-12)[0]
+        want = h ** (1 - alpha) / math.gamma(4 - alpha) * Mp[i - j + 1] if i - j >= -1 else 0.0
+        assert abs(val - want) <= 1e-8 * max(abs(want), 1e-3), (i, j, val, want)
+    # the mass matrix <φ_i, φ_j> by the same quadrature
+    M = O.fe_mass(N, h)
+    for i, j in [(3, 3), (3, 4), (4, 3), (3, 5)]:
+        val = integrate.quad(lambda t: phi(i, t) * phi(j, t), x[i] - h, x[i] + h, points=[x[i]], epsabs=1e-15)[0]
+        assert abs(val - M[i - 1, j - 1]) <= 1e-14, (i, j, val, M[i - 1, j - 1])
+
+
+@pytest.mark.parametrize("alpha", [1.2, 1.5, 1.8])
+def test_fe_stiffness_structure(alpha):
+    """M_+ lower Hessenberg Toeplitz with w_{-1} = 1 and positive, decreasing
+    w_k for k >= 2 (decay like k^{-1-α}); K = M_+ + M_+ᵀ symmetric negative
+    definite (the fractional operator dissipates, as ∂² does)."""
+    N = 60
+    w = O.fe_weights(alpha, N)
+    assert w[0] == 1.0 and np.all(w[3:] > 0) and np.all(np.diff(w[3:]) < 0)
+    g = 3 - alpha
+    k = N
+    assert abs(w[k + 1] / (g * (g - 1) * (g - 2) * (g - 3) * k ** (g - 4)) - 1) < 0.05
+    K = O.fe_stiffness(alpha, N, 1.0 / (N + 1))
+    assert np.allclose(K, K.T, rtol=0, atol=0)
+    assert np.linalg.eigvalsh(K).max() < 0
+
+
+def test_fe_manufactured_solution_first_order():
+    """1D finite elements (§2.2.2): M u_t = K u + F with F_i = <f, φ_i> and
+    implicit Euler, u = e^{-t} x²(1-x)², f = u_t - ∂^α_+ u - ∂^α_- u from the
+    RL power rule.  Halving h and Δt together halves the nodal error."""
+    from scipy import integrate
+
+    alpha = 1.5
+    coeffs = {2: 1.0, 3: -2.0, 4: 1.0}
+
+    def Dplus(t):
+        return sum(cf * _rl_power(p, alpha) * t ** (p - alpha) for p, cf in coeffs.items())
+
+    def p(t):
+        return t * t * (1 - t) * (1 - t)
+
+    errs = []
+    for N in (31, 63, 127):
+        h = 1.0 / (N + 1)
+        x = np.arange(1, N + 1) * h
+        dt = 2.0 * h
+        M_steps = int(round(0.5 / dt))
+        Mm = O.fe_mass(N, h)
+        A = Mm - dt * O.fe_stiffness(alpha, N, h)
+        # load vector of g(x) = -(p + D+ p + D- p), f = e^{-t} g
+        def g(t):
+            return -(p(t) + Dplus(t) + Dplus(1 - t))
+        Fg = np.array([integrate.quad(lambda t: g(t) * max(0.0, 1 - abs(t - xi) / h), xi - h, xi + h,
+                                      points=[xi], epsabs=1e-14, epsrel=1e-12)[0] for xi in x])
+        lu = sla.lu_factor(A)
+        U = p(x)
+        for m in range(1, M_steps + 1):
+            U = sla.lu_solve(lu, Mm @ U + dt * math.exp(-m * dt) * Fg)
+        errs.append(np.max(np.abs(U - math.exp(-M_steps * dt) * p(x))))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.6 < r1 < 2.6 and 1.6 < r2 < 2.6, errs
+
+
+def test_fe2d_operator_generalized_sylvester():
+    """Eq. (sylv-timestepping-fe), (½M - ΔtK_x) U M + M U (½M - ΔtK_y)ᵀ = M C M,
+    by Kronecker brute force, equals the Sylvester equation of
+    M^{-1}(½M - ΔtK) on both sides with right-hand side C."""
+    N, dt = 9, 0.1
+    h = 1.0 / (N + 1)
+    M = O.fe_mass(N, h)
+    Ax = 0.5 * M - dt * O.fe_stiffness(1.3, N, h)
+    Ay = 0.5 * M - dt * O.fe_stiffness(1.7, N, h)
+    C = I.SplitMix64(90).normal_array((N, N))
+    Kr = np.kron(M, Ax) + np.kron(Ay, M)  # vec(Ax U M) = (M ⊗ Ax) vec U, vec(M U Ayᵀ) = (Ay ⊗ M) vec U
+    U1 = np.linalg.solve(Kr, (M @ C @ M).reshape(-1, order="F")).reshape((N, N), order="F")
+    U2 = O.sylvester_bartels_stewart(O.fe2d_operator(1.3, N, h, dt), O.fe2d_operator(1.7, N, h, dt), C)
+    np.testing.assert_allclose(U2, U1, rtol=0, atol=1e-12 * np.abs(U1).max())
