@@ -38,6 +38,10 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   fde2d_rhs_factors          pinned: the dense right-hand side
   fde2d_lowrank_run          pinned: reduces to fde2d_run below rounding;
                              error and rank follow eps
+  fde1d_run_tv / fde2d_run_tv pinned: reduce to the constant runs;
+                             exactness for a solution linear in t with the
+                             operator at the new level; manufactured
+                             solution with time-dependent coefficients
   fe_weights / fe_stiffness  pinned: α=2 FE Laplacian, 50-digit evaluation,
                              quadrature of Eq. (fe-int), structure and
                              definiteness, manufactured-solution convergence
@@ -411,6 +415,41 @@ def fde2d_lowrank_run(w, eps: float, steps: int | None = None):
         X = solver.solve(L @ R.T)
         W, Z = lowrank_from_dense(X, eps)
     return W, Z
+
+
+# ---------------------------------------------------------------------------
+# Eq. (system_FD) with time-dependent coefficients D_±^{(m)}
+# ---------------------------------------------------------------------------
+def _with_coeffs(op, dp: np.ndarray, dm: np.ndarray):
+    return type(op)(op.N, op.alpha, op.h, op.dt, op.shift, dp, dm, op.leaf, op.tol)
+
+
+def fde1d_run_tv(w, coeff, steps: int | None = None):
+    """Implicit Euler with D_±^{(m)} sampled at the new time level t_m = m Δt
+    (Eq. (system_FD)): every step forms A^{(m)} and solves
+    A^{(m)} u^{(m)} = u^{(m-1)} + Δt f^{(m)} by dense LU.  coeff(t) -> (d_+, d_-)."""
+    op = w.ops[0]
+    u = w.u0.copy()
+    M = w.steps if steps is None else steps
+    for m in range(1, M + 1):
+        t = m * w.dt
+        dp, dm = coeff(t)
+        u = solve_dense(fd_operator(_with_coeffs(op, dp, dm)), u + w.dt * w.source(t))
+    return u
+
+
+def fde2d_run_tv(w, coeff_x, coeff_y, steps: int | None = None):
+    """The 2D step of Eq. (sylv-timestepping) with each side's coefficients at
+    the new time level t_{m+1}: A_x^{(m+1)} U + U A_y^{(m+1)ᵀ} = U^{(m)} + Δt F^{(m+1)},
+    a new pair of Schur forms per step (Bartels–Stewart)."""
+    U = w.u0.copy()
+    M = w.steps if steps is None else steps
+    for m in range(M):
+        t = (m + 1) * w.dt
+        Ax = fd_operator(_with_coeffs(w.ops[0], *coeff_x(t)))
+        Ay = fd_operator(_with_coeffs(w.ops[1], *coeff_y(t)))
+        U = sylvester_bartels_stewart(Ax, Ay, fde2d_rhs(w, U, m))
+    return U
 
 
 # ---------------------------------------------------------------------------

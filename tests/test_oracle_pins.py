@@ -805,3 +805,73 @@ def test_fe2d_operator_generalized_sylvester():
     U1 = np.linalg.solve(Kr, (M @ C @ M).reshape(-1, order="F")).reshape((N, N), order="F")
     U2 = O.sylvester_bartels_stewart(O.fe2d_operator(1.3, N, h, dt), O.fe2d_operator(1.7, N, h, dt), C)
     np.testing.assert_allclose(U2, U1, rtol=0, atol=1e-12 * np.abs(U1).max())
+
+
+# --------------------------------------------- time-dependent coefficients
+def test_time_dependent_runs_reduce_to_constant():
+    w1 = I.fd1d(N=64, alpha=1.6, steps=5)
+    op = w1.ops[0]
+    u = O.fde1d_run_tv(w1, lambda t: (op.d_plus, op.d_minus))
+    np.testing.assert_allclose(u, O.fde1d_run(w1), rtol=0, atol=1e-14 * np.abs(u).max())
+    w2 = I.fd2d(N=24, alpha=(1.3, 1.7), steps=4)
+    ox, oy = w2.ops
+    U = O.fde2d_run_tv(w2, lambda t: (ox.d_plus, ox.d_minus), lambda t: (oy.d_plus, oy.d_minus))
+    np.testing.assert_allclose(U, O.fde2d_run(w2), rtol=0, atol=1e-13 * np.abs(U).max())
+
+
+def test_time_dependent_coefficients_at_new_level():
+    """Implicit Euler is exact for U(t) = (1 + t) P when both the operator and
+    the source are taken at the new time level (Eq. (system_FD)): with
+    coefficients s(t) d_± and the source f(t) = P - (1 + t) L_h(t) P, every
+    step reproduces U(t_m) to rounding.  Coefficients from the old level
+    would leave an error of the size of Δt² ||∂_t L_h P||."""
+    w = I.fd2d(N=18, alpha=(1.4, 1.8), steps=6)
+    ox, oy = w.ops
+    sx = lambda t: 1.0 + 3.0 * t  # noqa: E731
+    sy = lambda t: 2.0 - t  # noqa: E731
+    cx = lambda t: (sx(t) * ox.d_plus, sx(t) * ox.d_minus)  # noqa: E731
+    cy = lambda t: (sy(t) * oy.d_plus, sy(t) * oy.d_minus)  # noqa: E731
+    P = I.SplitMix64(95).normal_array((18, 18))
+
+    def L_h(op, c, t):
+        A = O.fd_operator(O._with_coeffs(op, *c(t)))
+        return (0.5 * np.eye(18) - A) / w.dt
+
+    def source(t):
+        return P - (1 + t) * (L_h(ox, cx, t) @ P + P @ L_h(oy, cy, t).T)
+
+    run = _Run2D(w.ops, P.copy(), w.dt, 6, source)
+    U = O.fde2d_run_tv(run, cx, cy)
+    np.testing.assert_allclose(U, (1 + 6 * w.dt) * P, atol=1e-11 * np.abs(P).max())
+
+
+def test_time_dependent_manufactured_solution_first_order():
+    """u = e^{-t} x²(1-x)² with d_±(x, t) = (1 + t) Γ(3-α) x^α, (1 + t) Γ(3-α)(1-x)^α:
+    first order in Δx and Δt together (§2.2.1)."""
+    alpha = 1.5
+    coeffs = {2: 1.0, 3: -2.0, 4: 1.0}
+
+    def Dplus(x):
+        return sum(cf * _rl_power(p, alpha) * x ** (p - alpha) for p, cf in coeffs.items())
+
+    errs = []
+    for N in (63, 127, 255):
+        x = I.grid(N)
+        h = 1.0 / (N + 1)
+        dt = 2.0 * h
+        M = int(round(0.5 / dt))
+        G = math.gamma(3 - alpha)
+        dp0, dm0 = G * x ** alpha, G * (1 - x) ** alpha
+        u0 = x ** 2 * (1 - x) ** 2
+
+        class W:
+            pass
+
+        w = W()
+        w.ops = [I.OpSpec(N, alpha, h, dt, 1.0, dp0, dm0, 64, 1e-12)]
+        w.u0, w.dt, w.steps = u0.copy(), dt, M
+        w.source = lambda t: -math.exp(-t) * u0 - math.exp(-t) * (1 + t) * (dp0 * Dplus(x) + dm0 * Dplus(1 - x))
+        U = O.fde1d_run_tv(w, lambda t: ((1 + t) * dp0, (1 + t) * dm0))
+        errs.append(np.max(np.abs(U - math.exp(-M * dt) * u0)))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.6 < r1 < 2.6 and 1.6 < r2 < 2.6, errs
