@@ -153,6 +153,17 @@ fde_status hodlr_get_tree(hodlr_t h, int* h_lo, int* h_hi, int cap);
 
 void hodlr_free(hodlr_t h);
 
+/* The tree hodlr_build uses for N and leaf, on the host (no device work, no
+ * GPU needed): a node [lo, hi) splits into [lo, lo + (hi-lo)/2) and
+ * [lo + (hi-lo)/2, hi) (Eq. (HODLRpart)); every node of a level splits while
+ * ceil(N / 2^l) > leaf, so all leaves sit on level *levels and have size
+ * <= leaf.  Nodes are written in level order (id 2^l - 1 + p) into h_lo /
+ * h_hi (host, capacity cap >= 2^(*levels + 1) - 1).  *levels is set before
+ * the capacity check, so a call with cap = 0 returns FDE_ERR_ARG and the
+ * depth.  Errors: FDE_ERR_ARG for N outside [1, 2^20], leaf < 1, NULL
+ * pointers or a small capacity. */
+fde_status fde_tree_layout(int N, int leaf, int* h_lo, int* h_hi, int cap, int* levels);
+
 /* ------------------------------------------------------------------ 2D -- */
 /* Prepare the Sylvester solver for A_x X + X A_yᵀ = C (Eq. (sylv-timestepping)).
  * Ax and Ay must have the same N and leaf, N > leaf, and be built with shift

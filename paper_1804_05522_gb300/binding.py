@@ -77,6 +77,7 @@ _SIGS = {
     "hodlr_get_aca_pivots": ([_P, _P, _P, C.c_int, C.POINTER(C.c_int)], C.c_int),
     "hodlr_get_tree": ([_P, _P, _P, C.c_int], C.c_int),
     "hodlr_free": ([_P], None),
+    "fde_tree_layout": ([C.c_int, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_int)], C.c_int),
     "sylv_create": ([_P, _P, C.c_int, _P, C.POINTER(_P)], C.c_int),
     "sylv_get_refine": ([_P, C.POINTER(RefineParams)], C.c_int),
     "sylv_set_refine": ([_P, C.POINTER(RefineParams)], C.c_int),
@@ -204,6 +205,16 @@ class Lib:
     def hodlr_free(self, h: int):
         if h:
             self.dll.hodlr_free(h)
+
+    def fde_tree_layout(self, N: int, leaf: int):
+        """(levels, lo, hi): the host-side tree of hodlr_build, nodes in level order."""
+        L = C.c_int()
+        self.dll.fde_tree_layout(N, leaf, None, None, 0, C.byref(L))  # depth first
+        n = (1 << (L.value + 1)) - 1
+        lo = np.zeros(n, dtype=np.int32)
+        hi = np.zeros(n, dtype=np.int32)
+        self.check(self.dll.fde_tree_layout(N, leaf, lo.ctypes.data, hi.ctypes.data, n, C.byref(L)))
+        return L.value, lo, hi
 
     # -- Sylvester
     def sylv_create(self, ax: int, ay: int, prec: int, stream: int = 0) -> int:

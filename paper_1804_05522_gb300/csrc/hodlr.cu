@@ -1229,6 +1229,22 @@ extern "C" fde_status hodlr_get_tree(hodlr_t h, int* h_lo, int* h_hi, int cap) {
 
 extern "C" void hodlr_free(hodlr_t h) { delete h; }
 
+extern "C" fde_status fde_tree_layout(int N, int leaf, int* h_lo, int* h_hi, int cap, int* levels) {
+  FDE_ARG(N >= 1 && N <= (1 << 20), "N must be in [1, 2^20]");
+  FDE_ARG(leaf >= 1, "leaf must be >= 1");
+  FDE_ARG(levels != nullptr, "levels is NULL");
+  fde::Tree t;
+  t.build(N, leaf);
+  *levels = t.L;
+  FDE_ARG(h_lo != nullptr && h_hi != nullptr, "NULL node arrays");
+  FDE_ARG(cap >= (int)t.lo.size(), "capacity too small (2^(levels+1) - 1 nodes)");
+  for (size_t i = 0; i < t.lo.size(); ++i) {
+    h_lo[i] = t.lo[i];
+    h_hi[i] = t.hi[i];
+  }
+  return FDE_OK;
+}
+
 extern "C" const char* fde_strerror(fde_status s) {
   switch (s) {
     case FDE_OK: return "ok";

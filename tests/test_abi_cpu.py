@@ -75,3 +75,31 @@ def test_time_loop_rejects_wrong_shift(cpu_lib, dim, shifts):
     with pytest.raises(binding.FdeError) as e:
         cpu_lib.fde_run(rp, 1, 1)  # never dereferenced: the check comes first
     assert e.value.status == binding.FDE_ERR_ARG and "shift" in str(e.value)
+
+
+def test_tree_layout_matches_oracle(cpu_lib):
+    """The host tree of hodlr_build against the oracle's split rule
+    (Eq. (HODLRpart)), bit for bit, over many sizes including ragged ones."""
+    from oracle import fde_oracle as O
+
+    rng = np.random.default_rng(1804)
+    cases = [(1, 8), (2, 8), (8, 8), (9, 8), (1000, 64), (1024, 64), (1025, 64), (4096, 128), (16384, 256),
+             (12345, 100), (65, 64), (129, 64)]
+    cases += [(int(n), int(l)) for n, l in zip(rng.integers(2, 20000, 60), rng.integers(1, 300, 60))]
+    for N, leaf in cases:
+        L, lo, hi = cpu_lib.fde_tree_layout(N, leaf)
+        tree = O.hodlr_tree(N, leaf)
+        assert L == len(tree) - 1, (N, leaf)
+        flat = [node for lvl in tree for node in lvl]
+        assert list(zip(lo.tolist(), hi.tolist())) == flat, (N, leaf)
+
+
+def test_tree_layout_rejects_bad_arguments(cpu_lib):
+    L = ctypes.c_int()
+    lo = np.zeros(4, dtype=np.int32)
+    hi = np.zeros(4, dtype=np.int32)
+    assert cpu_lib.dll.fde_tree_layout(0, 8, lo.ctypes.data, hi.ctypes.data, 4, ctypes.byref(L)) == binding.FDE_ERR_ARG
+    assert cpu_lib.dll.fde_tree_layout(64, 0, lo.ctypes.data, hi.ctypes.data, 4, ctypes.byref(L)) == binding.FDE_ERR_ARG
+    # 100 / 16: three levels need 15 nodes, 4 are too few; the depth is still reported
+    assert cpu_lib.dll.fde_tree_layout(100, 16, lo.ctypes.data, hi.ctypes.data, 4, ctypes.byref(L)) == binding.FDE_ERR_ARG
+    assert L.value == 3
