@@ -328,3 +328,26 @@ def test_incremental_chain_long_run(lib, monkeypatch):
         runs[every] = _host(Uo, w.N, w.N)
     assert exact["8"] < exact["1"], exact
     assert _relerr(runs["8"], runs["1"]) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", [B.FDE_FP64, B.FDE_FP32_REFINE])
+def test_sylv_step_padded_leading_dimension(lib, prec):
+    """sylv_step on C and X stored with ld > N: the N x N result matches the
+    oracle and the padding rows of X are left as they were."""
+    N, ld = 100, 128
+    w = I.fd2d(N=N, alpha=(1.4, 1.6), steps=40, leaf=16)
+    P = Pair(lib, w, prec)
+    try:
+        C = I.random_matrix_fast(N, N, seed=11)
+        Cpad = np.full((ld, N), 7.0)
+        Cpad[:N] = C
+        Xpad = np.full((ld, N), -3.0)
+        Xpad[:N] = 0.0
+        Cd, Xd = _dev(Cpad), _dev(Xpad)
+        relres, sweeps = lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), ld)
+        X = _host(Xd, ld, N)
+        Xo = O.sylvester_bartels_stewart(O.fd_operator(w.ops[0]), O.fd_operator(w.ops[1]), C)
+        assert _relerr(X[:N], Xo) <= (1e-10 if prec == B.FDE_FP64 else 1e-8), (relres, sweeps)
+        assert np.all(X[N:] == -3.0)
+    finally:
+        P.close()
