@@ -143,3 +143,32 @@ def test_hodlr_solve_and_matvec(lib, case):
         assert np.linalg.norm(X - Xo) <= 10 * kappa * (2 * L + 2) * eps * np.linalg.norm(Xo) + 1e-12 * np.linalg.norm(Xo)
     finally:
         lib.hodlr_free(h)
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2]])
+def test_hodlr_solve_padded_leading_dimension(lib, case):
+    """hodlr_solve with ldb > N, out of place and in place: the N rows match
+    the dense solve within the HODLR backward-error bound, and the padding
+    rows of the output are left as they were."""
+    op = _op(case)
+    h = _build(lib, op)
+    try:
+        lib.hodlr_factor(h)
+        N, ld, nrhs = op.N, op.N + 9, 2
+        info = lib.hodlr_get_info(h)
+        A = O.fd_operator(op)
+        B = I.random_matrix(N, nrhs, seed=N + 1)
+        Bpad = np.full((ld, nrhs), 5.0)
+        Bpad[:N] = B
+        Xpad = np.full((ld, nrhs), -2.0)
+        Bd, Xd = _dev(Bpad), _dev(Xpad)
+        lib.hodlr_solve(h, Bd.data_ptr(), Xd.data_ptr(), nrhs, ld)  # out of place
+        lib.hodlr_solve(h, Bd.data_ptr(), Bd.data_ptr(), nrhs, ld)  # in place
+        torch.cuda.synchronize()
+        bound = (2 * info.levels + 2) * op.tol * info.norm2
+        for out, pad in ((_host(Xd, ld, nrhs), -2.0), (_host(Bd, ld, nrhs), 5.0)):
+            X = out[:N]
+            assert np.linalg.norm(A @ X - B) <= bound * np.linalg.norm(X) + 1e-12 * np.linalg.norm(B)
+            assert np.all(out[N:] == pad)
+    finally:
+        lib.hodlr_free(h)
