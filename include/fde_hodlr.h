@@ -249,7 +249,9 @@ typedef struct {
   const double* h_sin_amp;       /* host, r                                      */
   const double* h_omega;         /* host, r                                      */
   int prec;                      /* fde_prec                                     */
-  int use_graph;                 /* capture one step as a CUDA graph and replay  */
+  int use_graph;                 /* reserved, ignored: the 2D inner solve is     */
+                                 /* always captured once as a CUDA graph and     */
+                                 /* replayed per sweep                           */
 } fde_run_params;
 
 typedef struct {

@@ -61,6 +61,10 @@ def test_null_arguments_rejected(cpu_lib):
     assert cpu_lib.dll.hodlr_solve(None, None, None, 1, 1, None) == binding.FDE_ERR_ARG
     assert cpu_lib.dll.sylv_step(None, None, None, 1, None, None, None) == binding.FDE_ERR_ARG
     assert cpu_lib.dll.fde_run(None, None, None, None, None) == binding.FDE_ERR_ARG
+    assert cpu_lib.dll.sylv_set_refine(None, None) == binding.FDE_ERR_ARG
+    assert cpu_lib.dll.sylv_get_refine(None, None) == binding.FDE_ERR_ARG
+    assert cpu_lib.dll.fde_runner_load(None, None, 0, None) == binding.FDE_ERR_ARG
+    assert cpu_lib.dll.fde_runner_state(None, None, None) == binding.FDE_ERR_ARG
 
 
 @pytest.mark.parametrize("dim,shifts", [(1, (0.5, None)), (2, (1.0, 0.5)), (2, (0.5, 1.0))])

@@ -351,3 +351,61 @@ def test_sylv_step_padded_leading_dimension(lib, prec):
         assert np.all(X[N:] == -3.0)
     finally:
         P.close()
+
+
+def test_runner_load_restarts_from_a_host_state(lib):
+    """fde_runner_load from a host array sets the state and the time level: a
+    runner loaded with the oracle's U^(3) at step 3 and advanced two steps
+    reproduces the oracle's U^(5), as does a runner that ran all five."""
+    N = 64
+    w = I.fd2d(N=N, alpha=(1.4, 1.6), steps=20, leaf=16)
+    rp = lib.run_params(w, prec=B.FDE_FP32_REFINE)
+    U0 = _dev(w.u0)
+    U3 = O.fde2d_run(w, steps=3)
+    U5 = O.fde2d_run(w, steps=5)
+    ra = lib.runner_create(rp, U0.data_ptr())
+    rb = lib.runner_create(rp, U0.data_ptr())
+    try:
+        lib.runner_advance(ra, 5)
+        U3h = torch.from_numpy(np.asfortranarray(U3).ravel(order="F").copy())  # host state
+        lib.runner_load(rb, U3h.data_ptr(), 3)
+        lib.runner_advance(rb, 2)
+        Ua = torch.zeros(N * N, dtype=torch.float64)  # host outputs
+        Ub = torch.zeros_like(Ua)
+        lib.runner_state(ra, Ua.data_ptr())
+        lib.runner_state(rb, Ub.data_ptr())
+        torch.cuda.synchronize()
+        assert _relerr(_host(Ub, N, N), U5) <= 1e-8
+        assert _relerr(_host(Ua, N, N), U5) <= 1e-8
+    finally:
+        lib.runner_free(ra)
+        lib.runner_free(rb)
+
+
+@pytest.mark.parametrize("prec", [B.FDE_FP64, B.FDE_FP32_REFINE])
+def test_fixed_sweeps(lib, prec):
+    """sylv_set_refine with fixed_sweeps > 0 runs exactly that many sweeps
+    (no convergence test, no host synchronisation between them); four sweeps
+    from zero reach the oracle's solution.  Bad settings are refused."""
+    N = 100
+    w = I.fd2d(N=N, alpha=(1.3, 1.7), steps=50, leaf=16)
+    P = Pair(lib, w, prec)
+    try:
+        r = lib.sylv_get_refine(P.s)
+        assert r.max_sweeps == 12 and r.fixed_sweeps == 0
+        assert r.tol_update == (1e-13 if prec == B.FDE_FP64 else 1e-11)
+        r.fixed_sweeps = 4
+        lib.sylv_set_refine(P.s, r)
+        C = I.random_matrix_fast(N, N, seed=21)
+        Cd = _dev(C)
+        Xd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+        relres, sweeps = lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+        assert sweeps == 4 and relres < 1e-9
+        Xo = O.sylvester_bartels_stewart(O.fd_operator(w.ops[0]), O.fd_operator(w.ops[1]), C)
+        assert _relerr(_host(Xd, N, N), Xo) <= 1e-8
+        bad = lib.sylv_get_refine(P.s)
+        bad.max_sweeps = 0
+        with pytest.raises(B.FdeError):
+            lib.sylv_set_refine(P.s, bad)
+    finally:
+        P.close()
