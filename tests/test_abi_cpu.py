@@ -45,6 +45,18 @@ def test_strerror(cpu_lib):
         assert cpu_lib.dll.fde_strerror(s)
 
 
+def test_refused_calls_launch_nothing(cpu_lib):
+    # argument errors are caught on the host before any launch: the library's
+    # launch counter does not move
+    c0 = cpu_lib.dll.fde_launch_count()
+    p = cpu_lib.op_params(I.fd1d(N=128).ops[0])
+    p.alpha = 3.0
+    s, h = cpu_lib.hodlr_build_status(p)
+    assert s == binding.FDE_ERR_ARG and not h
+    assert cpu_lib.dll.fde_run(None, None, None, None, None) == binding.FDE_ERR_ARG
+    assert cpu_lib.dll.fde_launch_count() == c0
+
+
 @pytest.mark.parametrize("field,value", [("N", 1), ("alpha", 1.0), ("alpha", 2.5), ("leaf", 4), ("leaf", 512),
                                          ("tol", 0.0), ("tol", 1.0), ("h", -1.0), ("dt", 0.0), ("shift", 0.0)])
 def test_bad_parameters_rejected_on_host(cpu_lib, field, value):
