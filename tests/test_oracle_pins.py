@@ -9,7 +9,7 @@ import os
 import numpy as np
 import pytest
 import scipy.linalg as sla
-from scipy.special import gammaln, gamma
+from scipy.special import gamma
 
 from oracle import fde_oracle as O
 from paper_1804_05522_gb300 import inputs as I
