@@ -88,22 +88,40 @@ def parse():
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_step_sample(name: str, repeats: int = 1):
-    """Time the CPU oracle (Bartels–Stewart with precomputed real Schur forms,
-    as in the oracle's time loop) for `repeats` steps of the same workload family
-    at N = ORACLE_SAMPLE_N; returns (seconds per step, sample description)."""
-    from oracle import fde_oracle as O
+REF_BUDGET_S = 180.0  # wall-time budget of the reference arm's timed + warm-up steps
 
-    w = workload_for(name)
-    a1, a2 = w.ops[0].alpha, w.ops[1].alpha
-    ws = I.fd2d(N=ORACLE_SAMPLE_N, alpha=(a1, a2), steps=w.steps, leaf=128)
-    solver = O.SchurSylvester(O.fd_operator(ws.ops[0]), O.fd_operator(ws.ops[1]))
-    U = ws.u0.copy()
-    t0 = time.perf_counter()
-    for m in range(repeats):
-        U = solver.solve(O.fde2d_rhs(ws, U, m))
-    dt = (time.perf_counter() - t0) / repeats
-    return dt, f"oracle Bartels-Stewart step at N={ORACLE_SAMPLE_N} (Schur setup excluded), {repeats} step(s)"
+
+class OracleSampler:
+    """The CPU oracle's 2D time loop (Bartels–Stewart with the two real Schur
+    forms computed once) on the workload family `name` at N = n_sample: step()
+    advances one implicit-Euler step and returns its wall time."""
+
+    def __init__(self, name: str, n_sample: int = None):
+        from oracle import fde_oracle as O
+
+        self.O = O
+        self.n = n_sample or ORACLE_SAMPLE_N
+        w = workload_for(name)
+        self.ws = I.fd2d(N=self.n, alpha=(w.ops[0].alpha, w.ops[1].alpha), steps=w.steps, leaf=128)
+        self.solver = O.SchurSylvester(O.fd_operator(self.ws.ops[0]), O.fd_operator(self.ws.ops[1]))
+        self.U = self.ws.u0.copy()
+        self.m = 0
+
+    def step(self) -> float:
+        t0 = time.perf_counter()
+        self.U = self.solver.solve(self.O.fde2d_rhs(self.ws, self.U, self.m))
+        self.m += 1
+        return time.perf_counter() - t0
+
+    def describe(self, steps: int) -> str:
+        return f"oracle Bartels-Stewart step at N={self.n} (Schur forms once, outside the timing), {steps} step(s)"
+
+
+def oracle_step_sample(name: str, repeats: int = 1):
+    """(seconds per step, sample description) of the oracle at N = ORACLE_SAMPLE_N."""
+    sm = OracleSampler(name)
+    secs = [sm.step() for _ in range(repeats)]
+    return float(np.mean(secs)), sm.describe(repeats)
 
 
 def oracle_threads():
@@ -123,9 +141,9 @@ def oracle_threads():
     return os.cpu_count(), "all host cores (BLAS default)"
 
 
-def scale_to(N: int, sec_per_step: float) -> float:
-    """Oracle steps/s at N from the sample by the O(N^3) per-step cost."""
-    return 1.0 / (sec_per_step * (N / ORACLE_SAMPLE_N) ** 3)
+def scale_to(N: int, sec_per_step: float, n_sample: int = ORACLE_SAMPLE_N) -> float:
+    """Oracle steps/s at N from a sample at n_sample by the O(N^3) per-step cost."""
+    return 1.0 / (sec_per_step * (N / n_sample) ** 3)
 
 
 # ------------------------------------------------------------------ clocks
@@ -449,24 +467,32 @@ def run_reference(args, rank, world):
         return
     w = workload_for(args.workload)
     N = w.N
-    for _ in range(args.warmup):
-        oracle_step_sample(args.workload, 1)
+    t_wall0 = time.perf_counter()
+    sm = OracleSampler(args.workload)
+    # one probe step sizes the sample so that all warm-up and timed steps fit
+    # the budget (the per-step cost is O(n^3)); it counts as a warm-up step
+    t_probe = sm.step()
+    total = args.warmup + args.steps
+    if total * t_probe > REF_BUDGET_S:
+        n = int(ORACLE_SAMPLE_N * (REF_BUDGET_S / (total * t_probe)) ** (1.0 / 3.0)) // 32 * 32
+        sm = OracleSampler(args.workload, max(256, n))
+    for _ in range(max(args.warmup - 1, 0) if sm.n == ORACLE_SAMPLE_N else args.warmup):
+        sm.step()
     t0 = time.perf_counter()
-    secs = []
-    for _ in range(args.steps):
-        s, sample = oracle_step_sample(args.workload, 1)
-        secs.append(s)
+    secs = [sm.step() for _ in range(args.steps)]
     wall = time.perf_counter() - t0
     per = float(np.mean(secs))
-    value = scale_to(N, per)
+    value = scale_to(N, per, sm.n)
+    cores, cores_src = oracle_threads()
     out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": args.workload, "N": N},
-           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": oracle_threads()[0],
-                            "cores_source": oracle_threads()[1], "kind": "oracle",
-                            "sample": sample + f"; mean {per:.2f} s/step over {args.steps} steps, scaled to N={N} "
-                                               f"by (N/{ORACLE_SAMPLE_N})^3", "wall_s": wall},
+           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "cores_source": cores_src,
+                            "kind": "oracle",
+                            "sample": sm.describe(args.steps) + f"; mean {per:.2f} s/step, scaled to N={N} "
+                                                                f"by (N/{sm.n})^3",
+                            "wall_s": wall, "total_wall_s": time.perf_counter() - t_wall0},
            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -26,3 +26,25 @@ def test_reference_arm_json_line():
     e2e = out["e2e"]
     assert e2e["value"] == out["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert out["config"]["workload"] == "fd2d_n4096"
+
+
+def test_reference_arm_fits_its_budget(monkeypatch, capsys):
+    """With more steps than the wall-time budget allows at the default sample,
+    the reference arm shrinks the sample and scales by the O(n^3) cost."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setattr(bench, "REF_BUDGET_S", 0.5)
+
+    class Args:
+        workload = "fd2d_n4096"
+        steps = 3
+        warmup = 2
+
+    bench.run_reference(Args(), 0, 1)
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    sample = out["cpu_baseline"]["sample"]
+    assert "N=1024" not in sample.split(";")[0] and "by (N/" in sample
+    n = int(sample.split("by (N/")[1].split(")")[0])
+    assert 256 <= n < 1024 and n % 32 == 0
+    assert out["value"] > 0 and out["steps"] == 3
