@@ -465,6 +465,10 @@ def run_batch(args, rank, world, local_rank):
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    if args.workload not in I.WORKLOADS or I.WORKLOADS[args.workload]().dim != 2:
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times the 2D workloads only, not "
+                                                             f"{args.workload}"}), flush=True)
+        return
     w = workload_for(args.workload)
     N = w.N
     t_wall0 = time.perf_counter()
