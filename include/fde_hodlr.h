@@ -339,8 +339,9 @@ fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const 
  * this process so far.  fde_prof_enable(1) makes the library bracket the
  * launches of its main kernel families with CUDA events on their stream;
  * fde_prof_query returns the summed device time (ms) and launch count of a
- * family ("gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply", "schur",
- * "recompress", "fadi_axpy", "transpose", "refine"), synchronising the events
+ * family ("gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply",
+ * "fft_df", "fft_f32", "schur", "recompress", "fadi_axpy", "transpose",
+ * "refine"; an unknown name reads as no launches), synchronising the events
  * it reads;
  * fde_prof_reset clears the records. */
 unsigned long long fde_launch_count(void);

@@ -57,6 +57,13 @@ def test_refused_calls_launch_nothing(cpu_lib):
     assert cpu_lib.dll.fde_launch_count() == c0
 
 
+def test_prof_query_unknown_family_is_empty(cpu_lib):
+    ms, n = ctypes.c_double(-1.0), ctypes.c_longlong(-1)
+    assert cpu_lib.dll.fde_prof_query(b"no_such_family", ctypes.byref(ms), ctypes.byref(n), None, None) == 0
+    assert ms.value == 0.0 and n.value == 0
+    assert cpu_lib.dll.fde_prof_query(None, ctypes.byref(ms), ctypes.byref(n), None, None) == binding.FDE_ERR_ARG
+
+
 @pytest.mark.parametrize("field,value", [("N", 1), ("alpha", 1.0), ("alpha", 2.5), ("leaf", 4), ("leaf", 512),
                                          ("tol", 0.0), ("tol", 1.0), ("h", -1.0), ("dt", 0.0), ("shift", 0.0)])
 def test_bad_parameters_rejected_on_host(cpu_lib, field, value):
