@@ -117,3 +117,23 @@ def test_block_interval_rejects_bad_ranges(lib):
         with pytest.raises(binding.FdeError) as e:
             lib.fde_block_interval(p, lo, hi)
         assert e.value.status == binding.FDE_ERR_ARG
+
+
+def test_fadi_shifts_random_intervals(lib):
+    """Random interval pairs spanning 1 to 8 decades: the shifts meet the
+    target on a fine grid, stay below the Beckermann–Townsend bound, and J is
+    minimal."""
+    rng = np.random.default_rng(3305)
+    for _ in range(60):
+        a = 10.0 ** rng.uniform(-3, 1)
+        b = a * 10.0 ** rng.uniform(0.5, 8)
+        c = 10.0 ** rng.uniform(-3, 1)
+        d = c * 10.0 ** rng.uniform(0.5, 8)
+        target = 10.0 ** rng.uniform(-13, -3)
+        al, be, ratio = lib.fde_fadi_shifts(a, b, c, d, target)
+        J = len(al)
+        fine = _ratio_fine(al, be, a, b, c, d, G=4001)
+        assert fine <= target * 1.02 and fine <= ratio * 1.01, (a, b, c, d, target, J)
+        assert fine <= _bt_bound(J, a, b, c, d) * (1 + 1e-6), (a, b, c, d, J)
+        if J > 1:
+            assert lib.fde_fadi_shifts(a, b, c, d, target, jmax=J - 1)[2] > target
