@@ -172,3 +172,36 @@ def test_hodlr_solve_padded_leading_dimension(lib, case):
             assert np.all(out[N:] == pad)
     finally:
         lib.hodlr_free(h)
+
+
+def test_alpha2_degenerate_case(lib):
+    """α = 2, the upper end of the allowed orders: T is the second-difference
+    matrix, the top-level block has a single nonzero, so ACA takes one term and
+    then skips zero residual rows (the oracle's pivots, bit for bit), every
+    off-diagonal block has rank exactly 1, and the solve matches the dense one."""
+    w = I.fd1d(N=300, alpha=2.0, steps=32, leaf=32, tol=1e-10)
+    op = w.ops[0]
+    h = _build(lib, op)
+    try:
+        info = lib.hodlr_get_info(h)
+        rows, cols = lib.hodlr_get_aca_pivots(h)
+        g = O.gl_weights(op.alpha, op.N + 1)
+        N1, N2, row, col = O.toeplitz_lower_block_entries(g, op.N)
+        U, V, orows, ocols, conv = O.aca_partial_pivot(row, col, N2, N1, info.aca_tol, min(N1, N2, 90))
+        assert info.aca_rank == len(orows) == 1 and bool(info.aca_converged) and conv
+        np.testing.assert_array_equal(rows, orows)
+        np.testing.assert_array_equal(cols, ocols)
+        assert info.kmax == 1
+        lib.hodlr_factor(h)
+        N = op.N
+        A = O.fd_operator(op)
+        B = I.random_matrix(N, 2, seed=77)
+        Bd = _dev(B)
+        Xd = torch.zeros_like(Bd)
+        lib.hodlr_solve(h, Bd.data_ptr(), Xd.data_ptr(), 2, N)
+        torch.cuda.synchronize()
+        X = _host(Xd, N, 2)
+        Xo = O.solve_dense(A, B)
+        assert np.linalg.norm(X - Xo) <= 1e-10 * np.linalg.norm(Xo)
+    finally:
+        lib.hodlr_free(h)

@@ -409,3 +409,17 @@ def test_fixed_sweeps(lib, prec):
             lib.sylv_set_refine(P.s, bad)
     finally:
         P.close()
+
+
+@pytest.mark.parametrize("prec", [B.FDE_FP64, B.FDE_FP32_REFINE])
+def test_fde_run_2d_alpha2(lib, prec):
+    """α₁ = 2 (second differences in x) beside α₂ = 1.5: the 2D time loop
+    against the oracle."""
+    w = I.fd2d(N=96, alpha=(2.0, 1.5), steps=6, leaf=16)
+    rp = lib.run_params(w, prec=prec)
+    U0 = _dev(w.u0)
+    Uo = torch.zeros_like(U0)
+    st = lib.fde_run(rp, U0.data_ptr(), Uo.data_ptr())
+    U = _host(Uo, 96, 96)
+    assert _relerr(U, O.fde2d_run(w)) <= (1e-10 if prec == B.FDE_FP64 else 1e-8)
+    assert st.relres_max < 1e-9
