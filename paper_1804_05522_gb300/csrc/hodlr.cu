@@ -99,7 +99,8 @@ __global__ void finite_check_kernel(const double* __restrict__ x, int n, int* ba
 // ------------------------------------------------------- K2: ACA on T21
 // ACA with partial pivoting on T21 = [-g_{N1+i-j+1}] (N2 x N1), the block
 // that contains every lower off-diagonal block of T by restriction (§3.4.2).
-// Operation order is fixed (see the oracle's aca_partial_pivot): residual
+// Operation order is fixed, so that any FP64 implementation of the same
+// sequence reproduces the pivots exactly: residual
 // entries by sequential mul-then-sub, pivots by first argmax of |.| over
 // unused indices, stop when (Σu²)(Σv²) <= tol² with both sums sequential.
 struct ArgMax {
