@@ -50,3 +50,25 @@ def test_shared_input_module_has_no_method_arithmetic():
     names = {n.name for n in ast.walk(tree) if isinstance(n, (ast.FunctionDef, ast.ClassDef))}
     for forbidden in ("gl_weights", "fd_operator", "toeplitz", "sylvester", "residual", "solve", "hodlr", "aca"):
         assert not any(forbidden in n.lower() for n in names), (forbidden, names)
+
+
+def test_only_tests_smoke_and_bench_baseline_use_the_oracle():
+    """Outside tests/, only __graft_entry__.smoke() and bench.py's CPU-baseline and
+    reference legs may import the oracle, and only inside those functions."""
+    allowed = {"__graft_entry__.py": {"smoke"}, "bench.py": {"__init__"}}  # OracleSampler.__init__
+    for f in _py_files(ROOT):
+        rel = os.path.relpath(f, ROOT)
+        if rel.startswith(("tests" + os.sep, "oracle" + os.sep, "_work" + os.sep, "baseline" + os.sep)):
+            continue
+        tree = ast.parse(open(f).read())
+        for fn in [n for n in ast.walk(tree) if isinstance(n, (ast.FunctionDef, ast.Module))]:
+            body_imports = [n for n in ast.walk(fn) if isinstance(n, (ast.Import, ast.ImportFrom))]
+            uses = any((isinstance(n, ast.ImportFrom) and (n.module or "").startswith("oracle")) or
+                       (isinstance(n, ast.Import) and any(a.name.startswith("oracle") for a in n.names))
+                       for n in body_imports)
+            if uses and isinstance(fn, ast.FunctionDef):
+                assert fn.name in allowed.get(rel, set()), (rel, fn.name)
+        top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
+        assert not any((isinstance(n, ast.ImportFrom) and (n.module or "").startswith("oracle")) or
+                       (isinstance(n, ast.Import) and any(a.name.startswith("oracle") for a in n.names))
+                       for n in top), rel
