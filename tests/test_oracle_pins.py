@@ -228,19 +228,20 @@ def test_aca_exact_low_rank():
 
 def test_aca_hand_worked():
     """Partial-pivoting ACA worked by hand on a 3 x 4 integer matrix (reading of
-    the textbook rule: start at row 0, column pivot = largest residual entry of
-    the row, next row = largest entry of the new column over unused rows).
-      term 1: row 0 = [1 4 2 0] -> col 1, v = row / 4, u = col 1 = [4 2 0]
-      term 2: row 1 - 2 v = [1.5 0 7 1] -> col 2, u = col 2 - 0.5 u1 = [0 7 1]
-      term 3: row 2 - v2 -> col 0 (|4 - 1.5/7| > |2 - 1/7|), u = [0 0 4 - 1.5/7]
+    the textbook rule: start at row 0, column pivot = largest residual entry in
+    magnitude, next row = largest entry of the new column over unused rows).
+      term 1: row 0 = [1 -4 2 0] -> col 1 (|-4|, not the signed maximum 2),
+              v = row / (-4) = [-1/4 1 -1/2 0], u = col 1 = [-4 2 0]
+      term 2: row 1 - 2 v = [5/2 0 9 1] -> col 2, u = col 2 + u1/2 = [0 9 1]
+      term 3: row 2 - v2 -> col 0 (|4 - 2.5/9| > |2 - 1/9|), u = [0 0 4 - 2.5/9]
     and the three terms reproduce M."""
-    M = np.array([[1.0, 4, 2, 0], [2, 2, 8, 1], [4, 0, 1, 2]])
+    M = np.array([[1.0, -4, 2, 0], [2, 2, 8, 1], [4, 0, 1, 2]])
     U, V, rows, cols, conv = O.aca_partial_pivot(lambda i: M[i], lambda j: M[:, j], 3, 4, 1e-12, 10)
     assert conv and rows == [0, 1, 2] and cols == [1, 2, 0]
-    np.testing.assert_array_equal(U[:, 0], [4, 2, 0])
-    np.testing.assert_array_equal(V[:, 0], [0.25, 1, 0.5, 0])
-    np.testing.assert_array_equal(U[:, 1], [0, 7, 1])
-    np.testing.assert_allclose(U[:, 2], [0, 0, 4 - 1.5 / 7], rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(U[:, 0], [-4, 2, 0])
+    np.testing.assert_array_equal(V[:, 0], [-0.25, 1, -0.5, 0])
+    np.testing.assert_array_equal(U[:, 1], [0, 9, 1])
+    np.testing.assert_allclose(U[:, 2], [0, 0, 4 - 2.5 / 9], rtol=0, atol=1e-15)
     np.testing.assert_allclose(U @ V.T, M, rtol=0, atol=1e-14)
     # stopping rule ||u_1|| ||v_1|| = sqrt(20 * 1.3125) = 5.12 <= abstol stops after one term
     U1, _, rows1, _, conv1 = O.aca_partial_pivot(lambda i: M[i], lambda j: M[:, j], 3, 4, 6.0, 10)
@@ -731,6 +732,9 @@ def test_fe_stiffness_by_quadrature():
                                   epsabs=1e-14, epsrel=1e-12)[0]
         want = h ** (1 - alpha) / math.gamma(4 - alpha) * Mp[i - j + 1] if i - j >= -1 else 0.0
         assert abs(val - want) <= 1e-8 * max(abs(want), 1e-3), (i, j, val, want)
+        if i - j >= 2:  # there K = M_+ + M_+ᵀ has no M_+ᵀ part: the assembled stiffness itself
+            Kij = O.fe_stiffness(alpha, N, h)[i - 1, j - 1]
+            assert abs(val - Kij) <= 1e-8 * max(abs(Kij), 1e-3), (i, j, val, Kij)
     # the mass matrix <φ_i, φ_j> by the same quadrature
     M = O.fe_mass(N, h)
     for i, j in [(3, 3), (3, 4), (4, 3), (3, 5)]:
