@@ -138,6 +138,50 @@ def _residual_untransposed(opx, opy, X, C):
     return float(np.linalg.norm(R) / np.linalg.norm(C))
 
 
+def _fde1d_old_level(w, steps=None):
+    op = w.ops[0]
+    A = O.fd_operator(op)
+    u = w.u0.copy()
+    M = w.steps if steps is None else steps
+    for m in range(1, M + 1):
+        u = O.solve_dense(A, u + w.dt * w.source((m - 1) * w.dt))
+    return u
+
+
+def _kron_swapped(A, B, C):
+    n, m = C.shape
+    K = np.kron(A, np.eye(m)) + np.kron(np.eye(n), B)
+    return np.linalg.solve(K, C.reshape(-1, order="F")).reshape((n, m), order="F")
+
+
+def _hodlr_reference_abs(A, leaf, eps, normA=None):
+    return _orig["hodlr_reference"](A, leaf, eps, normA=1.0)
+
+
+def _rhs_factors_old_level(w, W, Z, m):
+    return _orig["fde2d_rhs_factors"](w, W, Z, m - 1)
+
+
+def _fe2d_without_mass(alpha, N, h, dt):
+    M = O.fe_mass(N, h)
+    return 0.5 * np.eye(N) - dt * O.fe_stiffness(alpha, N, h)
+
+
+def _fe_weights_series_sign(alpha, K):
+    w = _orig["fe_weights"](alpha, K).copy()
+    w[4:] = -w[4:]  # k >= 3: the series part
+    return w
+
+
+def _block_entries_shifted(g, N):
+    N1, N2, row, col = _orig["toeplitz_lower_block_entries"](g, N)
+    return N1, N2, (lambda i: -g[N1 + i - np.arange(N1)]), (lambda j: -g[N1 + np.arange(N2) - j])
+
+
+def _schur_untransposed_init(self, A, B):
+    _orig["SchurSylvester"].__init__(self, A, B.T)
+
+
 MUTATIONS = [
     ("gl_weights", _gl_shifted_order, lambda: P.test_gl_first_weights_exact(1.5)),
     ("gl_toeplitz", _toeplitz_transposed, lambda: P.test_toeplitz_structure(1.3)),
@@ -156,6 +200,13 @@ MUTATIONS = [
     ("fde2d_run_tv", _tv_old_level, P.test_time_dependent_coefficients_at_new_level),
     ("lowrank_from_dense", _lowrank_unscaled, P.test_lowrank_from_dense_prescribed_spectrum),
     ("sylvester_residual", _residual_untransposed, P.test_sylvester_residual_definition),
+    ("fde1d_run", _fde1d_old_level, P.test_fde1d_time_exact_linear_in_time),
+    ("sylvester_kron", _kron_swapped, P.test_bartels_stewart_vs_kronecker_random),
+    ("hodlr_reference", _hodlr_reference_abs, P.test_hodlr_reference_known_ranks),
+    ("fde2d_rhs_factors", _rhs_factors_old_level, P.test_rhs_factors_match_dense_rhs),
+    ("fe2d_operator", _fe2d_without_mass, P.test_fe2d_operator_generalized_sylvester),
+    ("fe_weights", _fe_weights_series_sign, lambda: P.test_fe_weights_against_high_precision(1.5)),
+    ("toeplitz_lower_block_entries", _block_entries_shifted, lambda: P.test_aca_toeplitz_block(1.5, 512)),
 ]
 
 

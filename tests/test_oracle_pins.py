@@ -295,6 +295,9 @@ def test_hodlr_reference_known_ranks():
     assert abstol == 1e-8 and set(ranks.values()) == {(0, 0)}
     _, ranks, _ = O.hodlr_reference(D, 8, 1e-10, normA=1.0)
     assert ranks[(0, N)] == (0, 1) and sum(map(sum, ranks.values())) == 1
+    # the threshold is relative to ||A||_2 (§3.4.1): scaling A by 1e6 scales it too
+    _, ranks, abstol = O.hodlr_reference(1e6 * D, 8, 1e-8)
+    assert abs(abstol - 1e-2) < 1e-12 and set(ranks.values()) == {(0, 0)}
 
 
 @pytest.mark.parametrize("alpha", [1.3, 1.7])
@@ -649,6 +652,24 @@ def test_paper_printed_qsrank_2d():
             assert q == printed + 1 and q1 == q and last_in < 1.2, (q, last_in)
         else:
             assert q == printed, (coeff, a1, a2, N, q, printed)
+
+
+def test_fde1d_time_exact_linear_in_time():
+    """1D analogue of the 2D exactness pin: with u(t) = (1 + t) p and the source
+    f(t) = p - (1 + t) L_h p (A = I - Δt L_h, Eq. (system_FD)), implicit Euler with
+    the source at the new time level reproduces u(t_m) to rounding."""
+    w = I.fd1d(N=40, alpha=1.6, steps=7)
+    A = O.fd_operator(w.ops[0])
+    Lh = (np.eye(40) - A) / w.dt
+    p = I.SplitMix64(96).normal_array((40,))
+
+    class Run:
+        pass
+
+    run = Run()
+    run.ops, run.u0, run.dt, run.steps = w.ops, p.copy(), w.dt, 7
+    run.source = lambda t: p - (1 + t) * (Lh @ p)
+    np.testing.assert_allclose(O.fde1d_run(run), (1 + 7 * w.dt) * p, atol=1e-11 * np.abs(p).max())
 
 
 def test_paper_printed_qsrank_alpha18():
