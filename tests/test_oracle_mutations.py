@@ -182,6 +182,36 @@ def _schur_untransposed_init(self, A, B):
     _orig["SchurSylvester"].__init__(self, A, B.T)
 
 
+def _eps_rank_scaled(Y, abstol):
+    return _orig["eps_rank"](Y, 10.0 * abstol)
+
+
+class _SchurUntransposed:
+    def __init__(self, A, B):
+        self.inner = _orig["SchurSylvester"](A, B.T)
+
+    def solve(self, C):
+        return self.inner.solve(C)
+
+
+def _lowrank_run_absolute(w, eps, steps=None):
+    return _orig["fde2d_lowrank_run"](w, eps * 1e-3, steps)
+
+
+def _tv1d_old_level(w, coeff, steps=None):
+    op = w.ops[0]
+    u = w.u0.copy()
+    M = w.steps if steps is None else steps
+    for m in range(1, M + 1):
+        dp, dm = coeff((m - 1) * w.dt)
+        u = O.solve_dense(O.fd_operator(O._with_coeffs(op, dp, dm)), u + w.dt * w.source(m * w.dt))
+    return u
+
+
+def _solve_transposed(A, B):
+    return _orig["solve_dense"](A.T, B)
+
+
 MUTATIONS = [
     ("gl_weights", _gl_shifted_order, lambda: P.test_gl_first_weights_exact(1.5)),
     ("gl_toeplitz", _toeplitz_transposed, lambda: P.test_toeplitz_structure(1.3)),
@@ -207,6 +237,11 @@ MUTATIONS = [
     ("fe2d_operator", _fe2d_without_mass, P.test_fe2d_operator_generalized_sylvester),
     ("fe_weights", _fe_weights_series_sign, lambda: P.test_fe_weights_against_high_precision(1.5)),
     ("toeplitz_lower_block_entries", _block_entries_shifted, lambda: P.test_aca_toeplitz_block(1.5, 512)),
+    ("eps_rank", _eps_rank_scaled, P.test_eps_rank_prescribed_spectrum),
+    ("SchurSylvester", _SchurUntransposed, P.test_schur_sylvester_reuse_vs_kronecker),
+    ("fde2d_lowrank_run", _lowrank_run_absolute, P.test_lowrank_run_error_follows_eps),
+    ("fde1d_run_tv", _tv1d_old_level, P.test_time_dependent_1d_coefficients_at_new_level),
+    ("solve_dense", _solve_transposed, P.test_solve_dense_residual),
 ]
 
 

@@ -870,6 +870,39 @@ def test_time_dependent_coefficients_at_new_level():
     np.testing.assert_allclose(U, (1 + 6 * w.dt) * P, atol=1e-11 * np.abs(P).max())
 
 
+def test_time_dependent_1d_coefficients_at_new_level():
+    """1D form of the time-level pin: u(t) = (1 + t) p with coefficients
+    s(t) d_± and f(t) = p - (1 + t) L_h(t) p (A^{(m)} = I - Δt L_h(t_m),
+    Eq. (system_FD)) is reproduced exactly when D_±^{(m)} is taken at t_m."""
+    w = I.fd1d(N=36, alpha=1.4, steps=6)
+    op = w.ops[0]
+    s = lambda t: 1.0 + 4.0 * t  # noqa: E731
+    coeff = lambda t: (s(t) * op.d_plus, s(t) * op.d_minus)  # noqa: E731
+    p = I.SplitMix64(97).normal_array((36,))
+
+    def Lh(t):
+        return (np.eye(36) - O.fd_operator(O._with_coeffs(op, *coeff(t)))) / w.dt
+
+    class Run:
+        pass
+
+    run = Run()
+    run.ops, run.u0, run.dt, run.steps = w.ops, p.copy(), w.dt, 6
+    run.source = lambda t: p - (1 + t) * (Lh(t) @ p)
+    np.testing.assert_allclose(O.fde1d_run_tv(run, coeff), (1 + 6 * w.dt) * p, atol=1e-11 * np.abs(p).max())
+
+
+def test_solve_dense_residual():
+    """x = A^{-1} b for a nonsymmetric A (the operator of Eq. (system_FD) with
+    different d_±): residual at rounding level, several right-hand sides."""
+    w = I.fd1d(N=50, alpha=1.3, steps=10)
+    A = O.fd_operator(w.ops[0])
+    assert np.abs(A - A.T).max() > 1e-3
+    B = I.SplitMix64(98).normal_array((50, 3))
+    X = O.solve_dense(A, B)
+    assert np.linalg.norm(A @ X - B) <= 1e-13 * np.linalg.norm(A, 2) * np.linalg.norm(X)
+
+
 def test_time_dependent_manufactured_solution_first_order():
     """u = e^{-t} x²(1-x)² with d_±(x, t) = (1 + t) Γ(3-α) x^α, (1 + t) Γ(3-α)(1-x)^α:
     first order in Δx and Δt together (§2.2.1)."""
