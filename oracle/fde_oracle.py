@@ -23,9 +23,9 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   eps_rank                   pinned: prescribed singular values
   beckermann_bound and the   pinned: the Lemma's own hypothesis (Hilbert
   qsrank bounds                matrix, PSD Hankel) from both sides; SVD
-                               ranks of T and A below the bounds (the
-                               corollary bounds from above only: a bound
-                               that is too loose is not detectable)
+                               ranks of T and A below the bounds; both
+                               qsrank bounds hand-evaluated at fixed
+                               (N, ε, norms)
   solve_dense / fde1d_run    pinned: residual / library cross-check,
                              manufactured-solution first-order convergence
   sylvester_bartels_stewart  pinned: Kronecker brute force, α=2 DST closed form

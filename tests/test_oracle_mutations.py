@@ -93,6 +93,18 @@ def _beckermann_pi(N, eps):
     return 2 + 2 * math.ceil((2.0 / math.pi) * math.log(4.0 * N / math.pi) * math.log(16.0 / eps))
 
 
+
+def _qsrank_T_full_eps(N, eps):
+    return _orig["beckermann_bound"](N, eps)
+
+
+def _qsrank_M_one_plus(N, eps, normM, normT, maxD):
+    return _orig["qsrank_bound_M"](N, eps, normM, normT, maxD) - 2
+
+
+def _qsrank_M_inverted(N, eps, normM, normT, maxD):
+    return _orig["qsrank_bound_M"](N, eps, normT * maxD, normM, 1.0)
+
 def _norm_squared(A, iters=30):
     return _orig["norm2_power"](A, iters) ** 2
 
@@ -224,6 +236,9 @@ MUTATIONS = [
     ("truncate_lowrank", _truncate_scaled, P.test_truncate_lowrank_prescribed_spectrum),
     ("beckermann_bound", _beckermann_pi, lambda: P.test_beckermann_bound_on_psd_hankel(256)),
     ("norm2_power", _norm_squared, P.test_norm2_power),
+    ("qsrank_bound_T", _qsrank_T_full_eps, P.test_qsrank_bounds_hand_evaluated),
+    ("qsrank_bound_M", _qsrank_M_one_plus, P.test_qsrank_bounds_hand_evaluated),
+    ("qsrank_bound_M", _qsrank_M_inverted, P.test_qsrank_bounds_hand_evaluated),
     ("hodlr_tree", _tree_ceil_first, lambda: P.test_hodlr_tree(1000, 64)),
     ("fe_stiffness", _fe_gamma, P.test_fe_stiffness_by_quadrature),
     ("fe_mass", _fe_lumped, P.test_fe_stiffness_by_quadrature),
@@ -245,7 +260,7 @@ MUTATIONS = [
 ]
 
 
-@pytest.mark.parametrize("name,mutant,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+@pytest.mark.parametrize("name,mutant,pin", MUTATIONS, ids=[f"{m[0]}-{m[1].__name__}" for m in MUTATIONS])
 def test_planted_mistake_is_caught(monkeypatch, name, mutant, pin):
     monkeypatch.setattr(O, name, mutant)
     with pytest.raises(AssertionError):

@@ -319,6 +319,26 @@ def test_rank_bounds(alpha):
     assert max(max(r) for r in ranksA.values()) <= bound
 
 
+
+def test_qsrank_bounds_hand_evaluated():
+    """Lemma lem:fd-qsrank and Corollary cor:fd-qsrank at fixed arguments,
+    evaluated by hand, so that a loosened or tightened bound fails (the SVD
+    checks above only bound the ranks from above).
+
+    N = 1024: ln(4N/π) = ln 4096 - ln π = 8.317766 - 1.144730 = 7.173036.
+    Lemma, ε = 1e-10: ln(32/ε) = ln 3.2e11 = 26.491587; (2/π²)·7.173036·26.491587
+    = 0.2026424·190.0251 = 38.507 -> 2 + 2·39 = 80.
+    Corollary, ||M|| = 8, ||T|| = 2, max||D±|| = 2, ε = 5e-11: ε̂ = 8ε/(2·2) =
+    1e-10, so 3 + 2⌈38.507⌉ = 81 (with ε̂ inverted, 2.5e-11: ⌈40.52⌉ -> 85)."""
+    assert O.qsrank_bound_T(1024, 1e-10) == 80
+    assert O.qsrank_bound_M(1024, 5e-11, 8.0, 2.0, 2.0) == 81
+    # N = 64: ln(256/π) = 4.400404; ε = 1e-6: ln(3.2e7) = 17.281246;
+    # 0.2026424·76.0444 = 15.410 -> Lemma 2 + 2·16 = 34; Corollary with
+    # ε̂ = ε (||M|| = ||T|| max||D±||): 3 + 2·16 = 35
+    assert O.qsrank_bound_T(64, 1e-6) == 34
+    assert O.qsrank_bound_M(64, 1e-6, 6.0, 3.0, 2.0) == 35
+
+
 # ---------------------------------------------------------------- solvers
 def _rand_stable(n, seed, shift):
     rng = I.SplitMix64(seed)
