@@ -34,6 +34,9 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
                              (first order), exactness for a solution linear
                              in t (source at the new time level)
   apply_fd_operator_fft      pinned: dense product
+  min_row_sum /              pinned: dense row sums; ||K^{-1}||_∞ of the
+  sylvester_error_bound        dense Kronecker matrix; the bound holds and is
+                               attained for a constant error
   sylvester_residual         pinned: X = 0, Kronecker solution, Kronecker
                              product of a perturbation
   lowrank_from_dense         pinned: prescribed singular values
@@ -562,3 +565,24 @@ def sylvester_residual(opx, opy, X: np.ndarray, C: np.ndarray) -> float:
     """||C - A_x X - X A_yᵀ||_F / ||C||_F with both products taken structurally."""
     R = C - apply_fd_operator_fft(opx, X, 0) - apply_fd_operator_fft(opy, X, 1)
     return float(np.linalg.norm(R) / np.linalg.norm(C))
+
+
+def min_row_sum(op) -> float:
+    """Smallest row sum of A = s I + c (D_+ T + D_- Tᵀ) (Eq. (system_FD)), from
+    A applied to the all-ones vector (structured product)."""
+    return float(np.min(apply_fd_operator_fft(op, np.ones((op.N, 1)), 0)))
+
+
+def sylvester_error_bound(opx, opy, r_maxabs: float) -> float:
+    """Bound on max|X - X*| for A_x X + X A_yᵀ = C from the largest residual
+    entry r_maxabs = max|C - A_x X - X A_yᵀ|.
+
+    A_x and A_y are M-matrices with positive row sums (§2.2.1: non-positive
+    off-diagonal entries, strict diagonal dominance), so the Kronecker matrix
+    K = I ⊗ A_x + A_y ⊗ I of §4.2 is one too, with row sums
+    rowsum_x(i) + rowsum_y(j) >= μ := min rowsum_x + min rowsum_y.  Then
+    K^{-1} >= 0 and K^{-1} 1 <= 1/μ, so ||K^{-1}||_∞ <= 1/μ and
+    max|X - X*| = ||K^{-1} vec R||_∞ <= r_maxabs / μ.  Over an implicit-Euler
+    loop whose right-hand sides are formed from the loop's own states, the
+    errors of the steps add: e_m = K^{-1}(e_{m-1} - r_m), and μ >= s_x + s_y = 1."""
+    return r_maxabs / (min_row_sum(opx) + min_row_sum(opy))

@@ -105,6 +105,10 @@ def _qsrank_M_one_plus(N, eps, normM, normT, maxD):
 def _qsrank_M_inverted(N, eps, normM, normT, maxD):
     return _orig["qsrank_bound_M"](N, eps, normT * maxD, normM, 1.0)
 
+
+def _min_row_sum_max(op):
+    return float(np.max(_orig["apply_fd_operator_fft"](op, np.ones((op.N, 1)), 0)))
+
 def _norm_squared(A, iters=30):
     return _orig["norm2_power"](A, iters) ** 2
 
@@ -236,6 +240,7 @@ MUTATIONS = [
     ("truncate_lowrank", _truncate_scaled, P.test_truncate_lowrank_prescribed_spectrum),
     ("beckermann_bound", _beckermann_pi, lambda: P.test_beckermann_bound_on_psd_hankel(256)),
     ("norm2_power", _norm_squared, P.test_norm2_power),
+    ("min_row_sum", _min_row_sum_max, P.test_mmatrix_error_bound),
     ("qsrank_bound_T", _qsrank_T_full_eps, P.test_qsrank_bounds_hand_evaluated),
     ("qsrank_bound_M", _qsrank_M_one_plus, P.test_qsrank_bounds_hand_evaluated),
     ("qsrank_bound_M", _qsrank_M_inverted, P.test_qsrank_bounds_hand_evaluated),

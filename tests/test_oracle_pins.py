@@ -953,3 +953,38 @@ def test_time_dependent_manufactured_solution_first_order():
         errs.append(np.max(np.abs(U - math.exp(-M * dt) * u0)))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 1.6 < r1 < 2.6 and 1.6 < r2 < 2.6, errs
+
+
+def test_mmatrix_error_bound():
+    """sylvester_error_bound against its definition on small problems: the
+    row sums are the dense operator's, ||K^{-1}||_∞ of the dense Kronecker
+    matrix is <= 1/μ, the bound holds for random errors, and for the
+    constant-coefficient α = 2 case (row sums equal away from the ends) it is
+    attained by the error that K maps to a constant residual."""
+    w = I.fd2d(N=24, alpha=(1.3, 1.7), steps=10, leaf=8)
+    opx, opy = w.ops
+    Ax, Ay = O.fd_operator(opx), O.fd_operator(opy)
+    assert abs(O.min_row_sum(opx) - Ax.sum(axis=1).min()) <= 1e-12 * abs(Ax).max()
+    assert abs(O.min_row_sum(opy) - Ay.sum(axis=1).min()) <= 1e-12 * abs(Ay).max()
+    n = opx.N
+    K = np.kron(np.eye(n), Ax) + np.kron(Ay, np.eye(n))
+    mu = O.min_row_sum(opx) + O.min_row_sum(opy)
+    Kinv = np.linalg.inv(K)
+    assert Kinv.min() >= -1e-14 and np.abs(Kinv).sum(axis=1).max() <= (1.0 + 1e-12) / mu
+    for seed in range(3):
+        E = I.random_matrix(n, n, seed=40 + seed)
+        R = Ax @ E + E @ Ay.T
+        assert np.abs(E).max() <= O.sylvester_error_bound(opx, opy, np.abs(R).max()) * (1 + 1e-12)
+    # the bound is sharp: with α = 2 and constant coefficients the interior
+    # row sums equal the shift (μ = 1/2 + 1/2), and for a small c = Δt/h²
+    # the error of a constant residual approaches r/μ away from the boundary
+    wl = I.fd2d(N=24, alpha=(2.0, 2.0), steps=10000, leaf=8)
+    for op in wl.ops:
+        op.d_plus = np.ones(op.N)
+        op.d_minus = np.ones(op.N)
+    Ax2, Ay2 = O.fd_operator(wl.ops[0]), O.fd_operator(wl.ops[1])
+    mu2 = O.min_row_sum(wl.ops[0]) + O.min_row_sum(wl.ops[1])
+    assert abs(mu2 - 1.0) <= 1e-12
+    E = O.sylvester_bartels_stewart(Ax2, Ay2, np.ones((24, 24)))
+    assert np.abs(E).max() <= O.sylvester_error_bound(wl.ops[0], wl.ops[1], 1.0) * (1 + 1e-12)
+    assert np.abs(E).max() >= 0.9 * O.sylvester_error_bound(wl.ops[0], wl.ops[1], 1.0)
