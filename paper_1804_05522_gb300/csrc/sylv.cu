@@ -196,34 +196,59 @@ __global__ void fadi_update_kernel(T* __restrict__ Z, T* __restrict__ G, T* __re
     H[i] -= cj * W[i];
   }
 }
-static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 32); }
+constexpr int kSumBlocks = 152 * 32;   // the largest grid of grid_for
+static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, kSumBlocks); }
 
-// X64 += (double) D ; partial sums of |D|^2 and |X64|^2 into acc[0], acc[1]
-template <typename T>
-__global__ void refine_update_kernel(double* __restrict__ X, const T* __restrict__ D, size_t n, double* acc) {
+// Deterministic grid-wide sums (the refinement's stop test and its choice of
+// residual update read them, so they must not depend on the order in which
+// blocks finish).  Each block writes its NV block sums to part[block][v]; the
+// last block to arrive (counter *count) adds the partial sums in block order
+// — a fixed sequence per thread, then a fixed tree — writes acc[v] and resets
+// the counter for the next launch.
+template <int NV>
+__device__ void grid_sums(double (&v)[NV], double* __restrict__ part, unsigned int* count, double* acc) {
   __shared__ double sh[32];
-  double sd = 0.0, sx = 0.0;
+  __shared__ bool last;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = block_sum(v[i], sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) part[(size_t)blockIdx.x * NV + i] = v[i];
+    __threadfence();
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double t = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += __ldcg(part + (size_t)b * NV + i);
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) acc[i] = t;
+  }
+  if (threadIdx.x == 0) *count = 0u;
+}
+// X64 += (double) D ; sums of |D|^2 and |X64|^2 into acc[0], acc[1]
+template <typename T>
+__global__ void refine_update_kernel(double* __restrict__ X, const T* __restrict__ D, size_t n, double* acc,
+                                     double* part, unsigned int* count) {
+  double s[2] = {0.0, 0.0};
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double d = (double)D[i];
     const double x = X[i] + d;
     X[i] = x;
-    sd += d * d;
-    sx += x * x;
+    s[0] += d * d;
+    s[1] += x * x;
   }
-  sd = block_sum(sd, sh);
-  sx = block_sum(sx, sh);
-  if (threadIdx.x == 0) {
-    atomicAdd(acc, sd);
-    atomicAdd(acc + 1, sx);
-  }
+  grid_sums<2>(s, part, count, acc);
 }
-__global__ void sumsq_kernel(const double* __restrict__ X, size_t n, double* acc) {
-  __shared__ double sh[32];
-  double s = 0.0;
+// acc[0] = |X|^2
+__global__ void sumsq_kernel(const double* __restrict__ X, size_t n, double* acc, double* part, unsigned int* count) {
+  double s[1] = {0.0};
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    s += X[i] * X[i];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) atomicAdd(acc, s);
+    s[0] += X[i] * X[i];
+  grid_sums<1>(s, part, count, acc);
 }
 // R <- C - Cprev + R  (residual of the previous solution for the new C)
 __global__ void shift_residual_kernel(const double* __restrict__ C, const double* __restrict__ Cp, double* __restrict__ R,
@@ -526,6 +551,10 @@ struct sylv_s {
   float2 *HbX_f32 = nullptr, *HbY_f32 = nullptr;
   double *R = nullptr, *Xt = nullptr, *Yt = nullptr, *X64 = nullptr, *C64 = nullptr;
   double* acc = nullptr;              // device accumulators
+  double* part = nullptr;             // per-block partial sums of the reductions into acc
+  unsigned int* count = nullptr;      // their arrival counter (0 between launches)
+  unsigned int* tc_count = nullptr;   // the tensor-core GEMM's expired-wait counter (device)
+  unsigned int* tc_base = nullptr;    // its value at the start of the current step (device)
   int* d_bad = nullptr;
   sylv_refine_t refine{};
   std::vector<int> J;
@@ -1000,9 +1029,19 @@ static fde_status residual(sylv_s* S, const double* C, const double* X, double* 
   return FDE_OK;
 }
 
+// Reads the accumulators; FDE_ERR_CUDA if a tensor-core GEMM wait of this step
+// ran out (the expired-wait counter moved past the value the step started
+// from, tc_base, which sylv_step_impl copies on the stream at its start).
 static fde_status read_acc(sylv_s* S, double* h, int n, cudaStream_t st) {
+  unsigned int tc[2] = {0u, 0u};
   FDE_CUDA(cudaMemcpyAsync(h, S->acc, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FDE_CUDA(cudaMemcpyAsync(tc, S->tc_base, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  FDE_CUDA(cudaMemcpyAsync(tc + 1, S->tc_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   FDE_CUDA(cudaStreamSynchronize(st));
+  if (tc[1] != tc[0]) {
+    set_error("sylv_step: a bounded wait of the tensor-core GEMM expired (%u)", tc[1] - tc[0]);
+    return FDE_ERR_CUDA;
+  }
   return FDE_OK;
 }
 
@@ -1143,7 +1182,7 @@ static fde_status sweep_solve(sylv_s* S, Inner<T>& in, double* X64, cudaStream_t
   FDE_CUDA(cudaMemsetAsync(S->acc, 0, 3 * sizeof(double), st));
   {
     ProfScope ps("refine", st, (16.0 + sizeof(T)) * NN, 0);
-    refine_update_kernel<T><<<grid_for(NN), 256, 0, st>>>(X64, in.X, NN, S->acc);
+    refine_update_kernel<T><<<grid_for(NN), 256, 0, st>>>(X64, in.X, NN, S->acc, S->part, S->count);
     FDE_LAUNCH("refine_update_kernel");
   }
   return FDE_OK;
@@ -1158,7 +1197,7 @@ static fde_status sweep_residual(sylv_s* S, Inner<T>& in, const double* C, doubl
     FDE_TRY(residual_update_df(S, reinterpret_cast<const float*>(in.X), st));
   else
     FDE_TRY(residual(S, C, X64, S->R, st));
-  sumsq_kernel<<<grid_for(NN), 256, 0, st>>>(S->R, NN, S->acc + 2);
+  sumsq_kernel<<<grid_for(NN), 256, 0, st>>>(S->R, NN, S->acc + 2, S->part, S->count);
   FDE_LAUNCH("sumsq_kernel");
   return FDE_OK;
 }
@@ -1177,7 +1216,8 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
   const sylv_refine_t& rf = S->refine;
   const bool fixed = rf.fixed_sweeps > 0;
   FDE_CUDA(cudaMemsetAsync(S->acc, 0, 8 * sizeof(double), st));
-  sumsq_kernel<<<grid_for(NN), 256, 0, st>>>(C, NN, S->acc + 4);
+  FDE_CUDA(cudaMemcpyAsync(S->tc_base, S->tc_count, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st));
+  sumsq_kernel<<<grid_for(NN), 256, 0, st>>>(C, NN, S->acc + 4, S->part, S->count);
   FDE_LAUNCH("sumsq_kernel");
   if (!fixed) {
     FDE_CUDA(cudaMemsetAsync(S->d_bad, 0, sizeof(int), st));
@@ -1671,6 +1711,12 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
     S->fft_flops = (double)((N + 1) / 2) * (3.0 * 5.0 * S->P * S->logP + 12.0 * S->P);
   }
   FDE_TRY(pool.alloc(&S->acc, 8));
+  FDE_TRY(pool.alloc(&S->part, 2 * (size_t)kSumBlocks));
+  FDE_TRY(pool.alloc(&S->count, 1));
+  FDE_CUDA(cudaMemsetAsync(S->count, 0, sizeof(unsigned int), st));
+  FDE_TRY(tc_timeout_counter(&S->tc_count));
+  FDE_TRY(pool.alloc(&S->tc_base, 1));
+  FDE_CUDA(cudaMemcpyAsync(S->tc_base, S->tc_count, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st));
   FDE_TRY(pool.alloc(&S->d_bad, 1));
   {
     // time-step predictor (used by time loops that pass the previous right-hand side)
