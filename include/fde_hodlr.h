@@ -191,7 +191,10 @@ fde_status sylv_set_refine(sylv_t s, const sylv_refine_t* r);
  * previous time step; zeros are fine); on exit the refined solution.
  * relres_out (host, may be NULL) receives ||C - A_x X - X A_yᵀ||_F / ||C||_F
  * computed in FP64 from the structured operators; sweeps_out (host, may be
- * NULL) the number of refinement sweeps. */
+ * NULL) the number of refinement sweeps.  Errors: FDE_ERR_NUMERIC (non-finite
+ * C, iterate or residual), FDE_ERR_NOCONV (max_sweeps reached), FDE_ERR_CUDA
+ * (also when a bounded wait of the tensor-core GEMM expired during the step;
+ * with fixed_sweeps > 0 this is only checked when relres_out is requested). */
 fde_status sylv_step(sylv_t s, const double* d_C, double* d_X, int ld, void* stream,
                      double* relres_out, int* sweeps_out);
 
@@ -288,6 +291,17 @@ fde_status fde_runner_load(fde_runner_t r, const double* U, int step_index, void
  * fde_runner_advance; fde_runner_load resets it. */
 fde_status fde_runner_step_source(fde_runner_t r, const double* F, int ldf, void* stream);
 fde_status fde_runner_state(fde_runner_t r, double* U_out, void* stream);
+/* Exact FP64 residual of the runner's current state against the right-hand
+ * side of the step that produced it (Eq. (system_FD) in 1D: b - A u; Eq.
+ * (sylv-timestepping) in 2D: C - A_x U - U A_yᵀ, Toeplitz products by FFT),
+ * whatever residual form the refinement used inside the step.  *relres
+ * (host) = ||R||_F / ||C||_F, *maxabs (host) = max |R_ij|; deterministic.
+ * With the smallest row sums m_x, m_y of A_x, A_y (both M-matrices, §2.2.1;
+ * fde_block_interval over [0, N) gives them as lam_lo), max|U - U*| <=
+ * maxabs / (m_x + m_y) for the exact solution U* of that step's equation.
+ * Synchronises `stream`.  FDE_ERR_ARG if no step was taken since
+ * fde_runner_create / fde_runner_load. */
+fde_status fde_runner_residual(fde_runner_t r, double* relres, double* maxabs, void* stream);
 fde_status fde_runner_stats(fde_runner_t r, fde_run_stats* stats);
 void fde_runner_free(fde_runner_t r);
 
@@ -330,7 +344,9 @@ void fde_batch_free(fde_batch_t b);
  * cores); batches too small
  * for the tensor cores (m < 64, n < 16 or k < 32) take a SIMT kernel.
  * Allocates the descriptor array and synchronises `stream`.  FDE_ERR_CUDA if
- * a tensor-core wait expired. */
+ * a tensor-core wait expired.  Not thread-safe: while it runs, a mode other
+ * than -1 overrides the library's process-wide kernel choice, which calls on
+ * other threads (fde_batch_advance workers) would also see. */
 fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const float* A, int lda,
                         long long strideA, const float* B, int ldb, long long strideB, float beta, float* C,
                         int ldc, long long strideC, int batch, int kblk, long long kstr, int mode, void* stream);
@@ -351,6 +367,24 @@ void fde_prof_enable(int on);
  * *work_kind == 0 (work_kind may be NULL). */
 fde_status fde_prof_query(const char* family, double* ms, long long* launches, double* work, int* work_kind);
 void fde_prof_reset(void);
+
+/* Host-side failure injection, for tests of the error paths; neither call
+ * makes a device fault.  The paper has no counterpart.
+ *
+ * fde_fail_alloc_after(n): after n more device allocations by this library
+ * (n >= 0; 0 = the next one), one allocation fails as if cudaMalloc had run
+ * out of memory, and the call that made it returns FDE_ERR_NOMEM; the hook
+ * then disarms itself.  n < 0 disarms it.  Process-wide.
+ *
+ * fde_set_wait_limit(iters): iteration limit of the tensor-core GEMM's
+ * bounded mbarrier waits on the current device (0 restores the default,
+ * 2^26).  A limit far below what a wait needs makes the waits run out: the
+ * kernel then skips its remaining work, waits for its tensor-core operations
+ * to finish, frees its tensor memory and counts the expiry in a device
+ * counter; sylv_step (at its next host synchronisation) and fde_gemm_f32
+ * return FDE_ERR_CUDA.  Results of the affected calls are meaningless. */
+void fde_fail_alloc_after(long long n);
+fde_status fde_set_wait_limit(unsigned int iters);
 
 const char* fde_strerror(fde_status s);
 /* Text of the last error on the calling thread (never NULL). */

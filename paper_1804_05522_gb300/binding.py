@@ -94,6 +94,7 @@ _SIGS = {
     "fde_runner_advance": ([_P, C.c_int, _P], C.c_int),
     "fde_runner_load": ([_P, _P, C.c_int, _P], C.c_int),
     "fde_runner_state": ([_P, _P, _P], C.c_int),
+    "fde_runner_residual": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], C.c_int),
     "fde_runner_stats": ([_P, C.POINTER(RunStats)], C.c_int),
     "fde_runner_free": ([_P], None),
     "fde_launch_count": ([], C.c_ulonglong),
@@ -101,6 +102,8 @@ _SIGS = {
     "fde_prof_query": ([C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                         C.POINTER(C.c_int)], C.c_int),
     "fde_prof_reset": ([], None),
+    "fde_fail_alloc_after": ([C.c_longlong], None),
+    "fde_set_wait_limit": ([C.c_uint], C.c_int),
     "fde_strerror": ([C.c_int], C.c_char_p),
     "fde_last_error": ([], C.c_char_p),
 }
@@ -331,6 +334,12 @@ class Lib:
     def runner_state(self, r: int, U: int, stream: int = 0):
         self.check(self.dll.fde_runner_state(r, U, stream))
 
+    def runner_residual(self, r: int, stream: int = 0):
+        """(||R||_F / ||C||_F, max |R_ij|) of the last step, exact FP64."""
+        rr, mx = C.c_double(), C.c_double()
+        self.check(self.dll.fde_runner_residual(r, C.byref(rr), C.byref(mx), stream))
+        return rr.value, mx.value
+
     def runner_stats(self, r: int) -> RunStats:
         st = RunStats()
         self.check(self.dll.fde_runner_stats(r, C.byref(st)))
@@ -339,6 +348,13 @@ class Lib:
     def runner_free(self, r: int):
         if r:
             self.dll.fde_runner_free(r)
+
+    # -- failure injection (tests of the error paths)
+    def fail_alloc_after(self, n: int):
+        self.dll.fde_fail_alloc_after(n)
+
+    def set_wait_limit(self, iters: int):
+        self.check(self.dll.fde_set_wait_limit(iters))
 
     # -- instrumentation
     def launch_count(self) -> int:

@@ -23,6 +23,9 @@ fde_status cuda_status(cudaError_t e, const char* what, const char* file, int li
 void count_launch();
 void count_launches(size_t n);
 bool prof_enabled();
+// Host-side failure injection (fde_fail_alloc_after): true when this device
+// allocation is the one that must fail.
+bool alloc_fail_now();
 
 // Brackets a kernel launch with CUDA events when profiling is on.
 // work: algorithmic FLOPs (kind 1) or bytes (kind 0) of the bracketed launches.
@@ -67,6 +70,10 @@ struct DevPool {
   fde_status alloc(T** p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
+    if (alloc_fail_now()) {
+      set_error("device allocation of %zu bytes refused (injected failure)", n * sizeof(T));
+      return FDE_ERR_NOMEM;
+    }
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, n * sizeof(T));
     if (e != cudaSuccess) {

@@ -51,7 +51,9 @@ void set_skinny_force(int v);
 fde_status tc_gemm_run(const GemmBatch<float>& b, cudaStream_t st, bool* used);
 int tc_mode();
 void set_tc_mode(int m);
-fde_status tc_error_flag(int* out);
+fde_status tc_error_flag(int* out);                 // expired tensor-core GEMM waits so far
+fde_status tc_timeout_counter(unsigned int** ptr);  // device address of that counter
+fde_status tc_set_wait_limit(unsigned int iters);   // 0: the default limit
 fde_status tc_prepare();
 
 // In-place inverse of `batch` square matrices (sizes n_i <= nmax, leading

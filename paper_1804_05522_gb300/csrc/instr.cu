@@ -38,6 +38,16 @@ static cudaEvent_t take_event() {
   return e;
 }
 
+// Allocations left before the injected failure (-1: none armed).
+static std::atomic<long long> g_alloc_countdown{-1};
+bool alloc_fail_now() {
+  long long v = g_alloc_countdown.load();
+  while (v >= 0)
+    if (g_alloc_countdown.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+void fail_alloc_after(long long n) { g_alloc_countdown.store(n < 0 ? -1 : n); }
+
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(size_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 bool prof_enabled() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
@@ -105,3 +115,5 @@ extern "C" void fde_prof_reset(void) {
     }
   g_prof.clear();
 }
+
+extern "C" void fde_fail_alloc_after(long long n) { fde::fail_alloc_after(n); }

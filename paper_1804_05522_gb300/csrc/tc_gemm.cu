@@ -23,11 +23,15 @@ namespace fde {
 
 namespace tc {
 
-// Raised by a kernel whose bounded mbarrier wait ran out (read by the host).
-__device__ int g_wait_timeout;
+// Counts the bounded mbarrier waits that ran out (read by the host; it only
+// grows, so a caller compares it with the value it saw before its launches).
+__device__ unsigned int g_wait_timeout;
+// Iteration limit of the pipeline's bounded waits (host-settable so that tests
+// can make them run out; kSpinLimit by default).
+constexpr uint32_t kSpinLimit = 1u << 26;
+__device__ uint32_t g_spin_limit = kSpinLimit;
 
 constexpr int BM = 128, BK = 32;
-constexpr uint32_t kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -47,7 +51,7 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (uint32_t it = 0; it < kSpinLimit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
-  atomicExch(&g_wait_timeout, 1);
+  atomicAdd(&g_wait_timeout, 1u);
   return false;
 }
 __device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
@@ -296,11 +300,12 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 // bounded wait that gives up at once when another role has already failed
 __device__ __forceinline__ bool mbar_wait_f(uint32_t bar, uint32_t parity, volatile int* fail) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+  const uint32_t limit = g_spin_limit;
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 255u && *fail) return false;
   }
-  atomicExch(&g_wait_timeout, 1);
+  atomicAdd(&g_wait_timeout, 1u);
   *fail = 1;
   return false;
 }
@@ -369,8 +374,10 @@ constexpr int kMmaWarp = kEpiWarp0 + kEpiWarps;                // warp 12
 //    quarter), release it on tempty[b] and write C; meanwhile the MMAs of the
 //    next tile fill the other buffer.
 // Every mbarrier wait is bounded; after a failure the roles skip their work
-// but keep the loop structure (no barrier is left waiting), raise
-// g_wait_timeout and free the TMEM.
+// but keep the loop structure (no barrier is left waiting) and count the
+// expiry in g_wait_timeout.  Before the TMEM is freed the issuing thread
+// commits once more to a drain barrier and waits for it (bounded by the fixed
+// kSpinLimit), so that no MMA it launched is still writing the accumulators.
 // Registers: the 13 warps sit 4/3/3/3 on the four SM sub-partitions, whose
 // register files hold 16K each, so a thread gets at most 128.
 template <int BN, int RAW, bool TA, bool TB>
@@ -385,7 +392,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
   // MMA slot: A_hi | B_hi | A_lo | B_lo (lo only in split mode); raw stages after the slots
   const int slot_bytes = (A_BYTES + B_BYTES) * (split ? 2 : 1);
   uint8_t* raw = sm + (size_t)mslots * slot_bytes;
-  __shared__ __align__(8) uint64_t full_bar[kMaxSlots], empty_bar[kMaxSlots], tfull[2], tempty[2];
+  __shared__ __align__(8) uint64_t full_bar[kMaxSlots], empty_bar[kMaxSlots], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   volatile int* fail = &s_fail;
@@ -399,6 +406,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
       mbar_init(smem_u32(&tfull[b]), 1);
       mbar_init(smem_u32(&tempty[b]), kEpiWarps);
     }
+    mbar_init(smem_u32(&drain), 1);
     s_fail = 0;
     fence_barrier_init();
   }
@@ -521,6 +529,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
         g += nk;
         ++lt;
       }
+      // drain: after a failed wait the epilogue may not have waited for the
+      // last tfull, so wait here until every MMA of this thread is done
+      mma_commit(smem_u32(&drain));
+      mbar_wait(smem_u32(&drain), 0u);
     }
     __syncwarp();
   } else {
@@ -632,7 +644,22 @@ void set_tc_mode(int m) { g_tc_mode.store(m); }
 
 fde_status tc_error_flag(int* out) {
   *out = 0;
-  FDE_CUDA(cudaMemcpyFromSymbol(out, tc::g_wait_timeout, sizeof(int)));
+  unsigned int n = 0;
+  FDE_CUDA(cudaMemcpyFromSymbol(&n, tc::g_wait_timeout, sizeof(n)));
+  *out = (int)n;
+  return FDE_OK;
+}
+
+// Device address of the expired-wait counter (current device), for callers
+// that read it asynchronously on their stream.
+fde_status tc_timeout_counter(unsigned int** ptr) {
+  FDE_CUDA(cudaGetSymbolAddress((void**)ptr, tc::g_wait_timeout));
+  return FDE_OK;
+}
+
+fde_status tc_set_wait_limit(unsigned int iters) {
+  const uint32_t v = iters ? iters : tc::kSpinLimit;
+  FDE_CUDA(cudaMemcpyToSymbol(tc::g_spin_limit, &v, sizeof(v)));
   return FDE_OK;
 }
 
@@ -742,6 +769,9 @@ extern "C" fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float al
   DevPool scratch;
   GemmBatch<float> gb;
   FDE_TRY(gemm_batch_upload(scratch, h, ta != 0, tb != 0, alpha, beta, &gb, st));
+  int before = 0;
+  FDE_CUDA(cudaStreamSynchronize(st));
+  FDE_TRY(tc_error_flag(&before));
   const int saved = tc_mode();
   if (mode >= 0) {
     set_tc_mode(mode == 4 ? 3 : mode);
@@ -754,9 +784,15 @@ extern "C" fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float al
   FDE_CUDA(cudaStreamSynchronize(st));
   int flag = 0;
   FDE_TRY(tc_error_flag(&flag));
-  if (flag) {
+  if (flag != before) {
     set_error("tensor-core GEMM: a bounded wait expired");
     return FDE_ERR_CUDA;
   }
+  return FDE_OK;
+}
+
+extern "C" fde_status fde_set_wait_limit(unsigned int iters) {
+  using namespace fde;
+  FDE_TRY(tc_set_wait_limit(iters));
   return FDE_OK;
 }

@@ -126,3 +126,19 @@ def test_tree_layout_rejects_bad_arguments(cpu_lib):
     # 100 / 16: three levels need 15 nodes, 4 are too few; the depth is still reported
     assert cpu_lib.dll.fde_tree_layout(100, 16, lo.ctypes.data, hi.ctypes.data, 4, ctypes.byref(L)) == binding.FDE_ERR_ARG
     assert L.value == 3
+
+
+def test_injected_allocation_failure_is_nomem(cpu_lib):
+    """The host-side allocation hook: hodlr_build's first device allocation
+    fails as if the device were out of memory; the call returns
+    FDE_ERR_NOMEM before any launch, and the hook disarms itself."""
+    c0 = cpu_lib.dll.fde_launch_count()
+    p = cpu_lib.op_params(I.fd1d(N=128).ops[0])
+    cpu_lib.fail_alloc_after(0)
+    try:
+        s, h = cpu_lib.hodlr_build_status(p)
+    finally:
+        cpu_lib.fail_alloc_after(-1)
+    assert s == binding.FDE_ERR_NOMEM and not h
+    assert "injected" in cpu_lib.last_error()
+    assert cpu_lib.dll.fde_launch_count() == c0
