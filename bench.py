@@ -79,8 +79,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fd2d_n4096")
-    ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=16)
+    ap.add_argument("--verify-steps", type=int, default=10)
     ap.add_argument("--prof-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-threads", type=int, default=8)
@@ -263,6 +264,96 @@ def roofline(lib, N):
     return r, detail
 
 
+# ------------------------------------------------------------------ accuracy
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+
+
+def read_golden(name: str):
+    """Stored oracle values of the workload's time loop (written by
+    tests/golden/make_fd2d_oracle.py from the CPU oracle): per step the norms,
+    bilinear functionals and sampled entries; None if there is no file."""
+    path = os.path.join(GOLDEN_DIR, f"{name}_oracle.txt")
+    if not os.path.exists(path):
+        return None
+    g = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        m = int(f[1])
+        e = g.setdefault(m, {"proj": {}, "ii": [], "jj": [], "val": []})
+        if f[0] == "norm":
+            e["fro"], e["maxabs"] = float(f[2]), float(f[3])
+        elif f[0] == "proj":
+            e["proj"][int(f[2])] = float(f[3])
+        elif f[0] == "entry":
+            e["ii"].append(int(f[2]))
+            e["jj"].append(int(f[3]))
+            e["val"].append(float(f[4]))
+    return g
+
+
+def compare_golden(X: np.ndarray, e: dict, N: int) -> dict:
+    """Errors of a state X (N x N) against the stored oracle values of one
+    step: Frobenius relative error estimated from the sampled entries
+    (sqrt(N^2 mean e^2) / ||X*||_F), largest sampled error relative to
+    max|X*|, largest error of the bilinear functionals relative to ||X*||_F
+    (each bounded by ||X - X*||_2 for unit vectors), and the relative
+    difference of the Frobenius norms."""
+    ii, jj = np.array(e["ii"]), np.array(e["jj"])
+    err = X[ii, jj] - np.array(e["val"])
+    Uv, Vv = I.projection_vectors(N, len(e["proj"]), seed=0)
+    proj = max(abs(Uv[:, k] @ X @ Vv[:, k] - v) for k, v in e["proj"].items())
+    return {"rel_fro_sampled": float(np.sqrt(N * N * np.mean(err ** 2)) / e["fro"]),
+            "max_abs_sampled_rel": float(np.max(np.abs(err)) / e["maxabs"]),
+            "proj_max_rel": float(proj / e["fro"]),
+            "fro_norm_rel": float(abs(np.linalg.norm(X) - e["fro"]) / e["fro"]),
+            "samples": int(len(ii))}
+
+
+def verify_run(lib, name, w, r, U0, steps: int, stream):
+    """Accuracy of the default configuration, untimed: the runner is reloaded
+    with U^(0) and advanced `steps` steps.  After every step the exact FP64
+    residual of that step's equation is formed on the device; the residual
+    bound of an M-matrix Sylvester operator (max|U - U*| <= max|R| / μ, μ the
+    sum of the smallest row sums of A_x and A_y, both M-matrices) accumulates
+    over the loop into a bound on the error against the exact time loop.  At
+    the steps with stored oracle values the state is compared with them."""
+    import torch
+
+    N = w.N
+    mu = sum(lib.fde_block_interval(lib.op_params(op), 0, N)[0] for op in w.ops)
+    golden = read_golden(name)
+    lib.runner_load(r, U0.data_ptr(), 0, stream)
+    bound, relres_max, step_max, checked = 0.0, 0.0, 0.0, {}
+    X = torch.empty_like(U0)
+    for m in range(1, steps + 1):
+        lib.runner_advance(r, 1, stream)
+        rel, mx = lib.runner_residual(r, stream)
+        relres_max = max(relres_max, rel)
+        bound += mx / mu
+        lib.runner_state(r, X.data_ptr(), stream)
+        torch.cuda.synchronize()
+        step_max = max(step_max, mx / mu / float(X.abs().max()))
+        if golden and m in golden:
+            Xh = X.cpu().numpy().reshape((N, N), order="F")
+            checked[m] = compare_golden(Xh, golden[m], N)
+    xmax = float(X.abs().max())
+    out = {"steps": steps, "relres_exact_max": relres_max, "mu": mu,
+           "error_bound_step_max_rel": step_max,
+           "error_bound_loop_max_abs_rel": bound / xmax,
+           "error_bound": "per step max|U - U*| <= max|R| / mu for that step's Sylvester equation (R its exact "
+                          "FP64 residual; A_x, A_y M-matrices, mu the sum of their smallest row sums); over the "
+                          "loop these add (loop bound after the last step), both relative to max|U|"}
+    if checked:
+        last = max(checked)
+        out["oracle_step"] = last
+        out["oracle_rel_err"] = checked[last]["rel_fro_sampled"]
+        out["oracle_checks"] = checked
+        out["oracle_source"] = f"tests/golden/{name}_oracle.txt (CPU oracle trajectory)"
+    return out
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -344,9 +435,36 @@ def run_ours(args, rank, world, local_rank):
         st64 = lib.runner_stats(r64)
         lib.runner_free(r64)
         extra["fp64_path"] = {"steps_per_s": args.fp64_steps / (ms64 / 1e3), "setup_s": setup64,
-                              "steps": args.fp64_steps, "relres_max": st64.relres_max,
+                              "steps": args.fp64_steps, "relres_running_max": st64.relres_max,
+                              "fadi_form": "per-step shifted HODLR solves",
                               "fp32_vs_fp64_rel_diff": agree, "speedup_fp32_refine": value / world /
                               (args.fp64_steps / (ms64 / 1e3))}
+    if args.fp64_steps > 0 and rank == 0 and N <= 4096:
+        # the same FP64 inner solver with the fADI levels in precomputed
+        # rational form (dense FP64 resolvent products per step; their
+        # storage grows like N^2 per level, so only up to N = 4096)
+        os.environ["FDE_FADI"] = "rational"
+        try:
+            r64r = lib.runner_create(rp64, state.data_ptr(), stream)
+        finally:
+            del os.environ["FDE_FADI"]
+        setup64r = lib.runner_stats(r64r).setup_s
+        lib.runner_load(r64r, state.data_ptr(), m0, stream)
+        torch.cuda.synchronize()
+        f0.record()
+        lib.runner_advance(r64r, args.fp64_steps, stream)
+        f1.record()
+        torch.cuda.synchronize()
+        ms64r = f0.elapsed_time(f1)
+        c = torch.empty_like(U0)
+        lib.runner_state(r64r, c.data_ptr(), stream)
+        torch.cuda.synchronize()
+        lib.runner_free(r64r)
+        extra["fp64_rational_path"] = {"steps_per_s": args.fp64_steps / (ms64r / 1e3), "setup_s": setup64r,
+                                       "steps": args.fp64_steps, "fadi_form": "precomputed rational (dense FP64)",
+                                       "fp64_rational_vs_fp64_rel_diff": float(torch.linalg.norm(c - b) /
+                                                                              torch.linalg.norm(b)),
+                                       "speedup_fp32_refine": value / world / (args.fp64_steps / (ms64r / 1e3))}
     # ---- end to end through the public API with host buffers: every step
     # uploads that step's source field F (N x N, pinned host memory) and
     # reads the new state back
@@ -379,6 +497,9 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8,
                "host_wall_steps_per_s": args.e2e_steps / wall,
                "input": "dense source F^(m+1) (N x N FP64) uploaded per step; state U^(m+1) read back"}
+    accuracy = None
+    if args.verify_steps > 0 and rank == 0:
+        accuracy = verify_run(lib, args.workload, w, r32, U0, min(args.verify_steps, w.steps), stream)
     lib.runner_free(r32)
 
     if rank != 0:
@@ -396,13 +517,13 @@ def run_ours(args, rank, world, local_rank):
                        f"FP64 refinement",
            "N": N, "leaf": w.ops[0].leaf, "tol": w.ops[0].tol, "time_steps_total": w.steps,
            "l2_policy": "working set (X, C, R FP64 = 3 x %d MB + factors) exceeds the 129 MB L2" % (N * N * 8 >> 20),
-           "setup_s": setup32, "refine_sweeps_per_step": sweeps, "relres_max": st1.relres_max,
+           "setup_s": setup32, "refine_sweeps_per_step": sweeps, "relres_running_max": st1.relres_max,
            "kmax_x": st1.kmax_x, "kmax_y": st1.kmax_y, "parallelism": "replicas" if world > 1 else "single"}
     out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 refine", "data": "synthetic",
            "config": cfg, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-           "kernels": shares, "cpu_baseline": cpu, "clocks": clk}
+           "kernels": shares, "cpu_baseline": cpu, "clocks": clk, "accuracy": accuracy}
     out.update(extra)
     print(json.dumps(out), flush=True)
 

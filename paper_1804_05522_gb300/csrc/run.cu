@@ -71,6 +71,50 @@ __global__ void add_norms_kernel(double* __restrict__ x, const double* __restric
   }
 }
 
+// Max-abs and sum of squares of x[0, n), deterministic: each block writes
+// (max |x|, Σ x²) of its grid-stride share to part[2 b], part[2 b + 1];
+// norms_final_kernel (one block) combines them in block order.
+constexpr int kNormBlocks = 1024;
+__global__ void norms_part_kernel(const double* __restrict__ x, size_t n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double m = 0.0, q = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    m = fmax(m, fabs(v));
+    q += v * v;
+  }
+  q = block_sum(q, sh);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double shm[32];
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, shm[w]);
+    part[2 * blockIdx.x] = mm;
+    part[2 * blockIdx.x + 1] = q;
+  }
+}
+__global__ void norms_final_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double m = 0.0, q = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    m = fmax(m, part[2 * b]);
+    q += part[2 * b + 1];
+  }
+  q = block_sum(q, sh);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double shm[32];
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, shm[w]);
+    out[0] = mm;
+    out[1] = q;
+  }
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, p);
@@ -94,6 +138,9 @@ struct fde_runner_s {
   double* F = nullptr;           // caller-supplied dense source (fde_runner_step_source)
   bool have_prev = false;        // C2 / the solver's residual belong to the current U
   double *y = nullptr, *rr = nullptr, *acc = nullptr;
+  double* Rres = nullptr;        // exact residual of the last step (fde_runner_residual)
+  double* npart = nullptr;       // per-block partial norms, and the two final values
+  bool c_valid = false;          // C holds the right-hand side of the current state's step
   int N = 0, step = 0;
   fde_run_stats stats{};
   ~fde_runner_s() {
@@ -227,6 +274,7 @@ static fde_status runner_advance(fde_runner_s* R, int nsteps, cudaStream_t st) {
       R->stats.sweeps_total += sw;
       R->stats.sweeps_max = std::max(R->stats.sweeps_max, sw);
       R->step = m;
+      R->c_valid = true;
     }
   } else {
     const size_t NN = (size_t)N * N;
@@ -240,6 +288,7 @@ static fde_status runner_advance(fde_runner_s* R, int nsteps, cudaStream_t st) {
       int sw = 0;
       fde_status s = sylv_step_internal(R->s, R->C, R->U, st, &rel, &sw, R->have_prev ? R->C2 : nullptr);
       R->have_prev = (s == FDE_OK);
+      R->c_valid = (s == FDE_OK);
       FDE_TRY(s);
       R->stats.sweeps_total += sw;
       R->stats.sweeps_max = std::max(R->stats.sweeps_max, sw);
@@ -298,6 +347,7 @@ extern "C" fde_status fde_runner_step_source(fde_runner_t r, const double* F, in
   int sw = 0;
   fde_status s = sylv_step_internal(r->s, r->C, r->U, st, &rel, &sw, r->have_prev ? r->C2 : nullptr);
   r->have_prev = (s == FDE_OK);
+  r->c_valid = (s == FDE_OK);
   FDE_TRY(s);
   r->stats.sweeps_total += sw;
   r->stats.sweeps_max = std::max(r->stats.sweeps_max, sw);
@@ -314,6 +364,45 @@ extern "C" fde_status fde_runner_load(fde_runner_t r, const double* U, int step_
   FDE_TRY(copy_state(r->U, U, n, (cudaStream_t)stream));
   r->step = step_index;
   r->have_prev = false;
+  r->c_valid = false;
+  return FDE_OK;
+}
+
+extern "C" fde_status fde_runner_residual(fde_runner_t r, double* relres, double* maxabs, void* stream) {
+  FDE_ARG(r != nullptr && relres != nullptr && maxabs != nullptr, "NULL argument");
+  FDE_ARG(r->c_valid, "no step since fde_runner_create / fde_runner_load");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = r->N;
+  const size_t n = (r->p.dim == 1) ? (size_t)N : (size_t)N * N;
+  if (!r->npart) FDE_TRY(r->pool.alloc(&r->npart, 2 * (size_t)kNormBlocks + 4));
+  const double* Rv;
+  if (r->p.dim == 1) {
+    // r = b - A u with the exact (dense-structured) operator
+    const int nb = std::min(1024, ceil_div(N, 256));
+    FDE_TRY(fd_apply_dense(r->ax, r->U, r->y, 0, st));
+    sub_kernel<<<nb, 256, 0, st>>>(r->C, r->y, r->rr, N);
+    FDE_LAUNCH("sub_kernel");
+    Rv = r->rr;
+  } else {
+    if (!r->Rres) FDE_TRY(r->pool.alloc(&r->Rres, n));
+    FDE_TRY(sylv_residual(r->s, r->C, r->U, r->Rres, N, stream));
+    Rv = r->Rres;
+  }
+  const int nb = (int)std::min<size_t>((n + 255) / 256, kNormBlocks);
+  double* fin = r->npart + 2 * kNormBlocks;
+  norms_part_kernel<<<nb, 256, 0, st>>>(Rv, n, r->npart);
+  FDE_LAUNCH("norms_part_kernel");
+  norms_final_kernel<<<1, 1024, 0, st>>>(r->npart, nb, fin);
+  FDE_LAUNCH("norms_final_kernel");
+  norms_part_kernel<<<nb, 256, 0, st>>>(r->C, n, r->npart);
+  FDE_LAUNCH("norms_part_kernel");
+  norms_final_kernel<<<1, 1024, 0, st>>>(r->npart, nb, fin + 2);
+  FDE_LAUNCH("norms_final_kernel");
+  double h[4];
+  FDE_CUDA(cudaMemcpyAsync(h, fin, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FDE_CUDA(cudaStreamSynchronize(st));
+  *maxabs = h[0];
+  *relres = h[3] > 0.0 ? sqrt(h[1] / h[3]) : sqrt(h[1]);
   return FDE_OK;
 }
 

@@ -195,6 +195,23 @@ def batch(count=64, steps=20, sizes_log2=(9, 14), seed_index=0, leaf=64):
     return out
 
 
+def sample_points(N: int, count: int, seed: int):
+    """Seeded (i, j) index pairs, uniform on [0, N)^2 (SplitMix64), at which
+    stored expected values of an N x N field are compared."""
+    rng = SplitMix64(SEED_BASE + 300007 * seed)
+    ii = np.array([int(rng.uniform() * N) for _ in range(count)], dtype=np.int64)
+    jj = np.array([int(rng.uniform() * N) for _ in range(count)], dtype=np.int64)
+    return ii, jj
+
+
+def projection_vectors(N: int, count: int, seed: int):
+    """Seeded unit vectors u_k, v_k (columns of two N x count arrays) for the
+    bilinear functionals u_kᵀ X v_k of an N x N field."""
+    U = random_matrix_fast(N, count, 2 * seed + 1)
+    V = random_matrix_fast(N, count, 2 * seed + 2)
+    return U / np.linalg.norm(U, axis=0), V / np.linalg.norm(V, axis=0)
+
+
 # Named workloads (sizes of the paper-shaped configurations).
 WORKLOADS = {
     "fd1d_n1024": lambda: fd1d(N=1024, alpha=1.5, steps=32, leaf=64, tol=1e-10),

@@ -1,7 +1,7 @@
 """N > 4096: the structured residual switches to block-Toeplitz FFTs (blocks of
 4096 rows).  Checked against the oracle's FFT operator (itself pinned against
-the dense operator), on ragged block counts, and through the refinement: the
-solution's residual recomputed on the CPU is a certificate of its accuracy."""
+the dense operator) on ragged block counts; the refined steps that use it are
+certified in tests/test_bench_parity_gpu.py."""
 import numpy as np
 import pytest
 
@@ -54,32 +54,3 @@ def test_block_toeplitz_residual(lib, N):
         assert np.linalg.norm(_host(Rd, N, N) - Ro) <= 1e-13 * scale
     finally:
         P.close()
-
-
-def test_block_toeplitz_refined_step(lib, monkeypatch):
-    """FP32 inner solver + FP64 refinement at N = 6000 (2 blocks): the CPU
-    residual of the GPU solution is at the refinement's level with exact FP64
-    residuals, with double-float incremental ones, and with the default
-    (double-float, FP32 for the last update of the step) alike."""
-    N = 6000
-    w = I.fd2d(N=N, alpha=(1.5, 1.5), steps=100, leaf=128)
-    C = O.fde2d_rhs(w, w.u0, 0)
-    sols = {}
-    for mode in ("auto", "df", "fp64"):
-        if mode == "auto":
-            monkeypatch.delenv("FDE_RESID", raising=False)
-        else:
-            monkeypatch.setenv("FDE_RESID", mode)
-        P = Pair(lib, w, B.FDE_FP32_REFINE)
-        try:
-            Cd = _dev(C)
-            Xd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
-            relres, sweeps = lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
-            X = _host(Xd, N, N)
-            sols[mode] = X
-            r_cpu = O.sylvester_residual(w.ops[0], w.ops[1], X, C)
-            assert r_cpu < 1e-10 and sweeps <= 6, (mode, r_cpu, relres, sweeps)
-        finally:
-            P.close()
-    for mode in ("df", "auto"):
-        assert np.linalg.norm(sols[mode] - sols["fp64"]) <= 1e-9 * np.linalg.norm(sols["fp64"]), mode
