@@ -341,7 +341,10 @@ void fde_batch_free(fde_batch_t b);
  * kernel (one dimension <= 64: n <= 40 with m >= 128, or m <= 64 with
  * n >= 128, no two-level k; other shapes as mode 3), -1 the library's own
  * dispatch (the skinny kernel for n <= 32 or m <= 64, then the tensor
- * cores); batches too small
+ * cores), 5 / 6 / 7 3xTF32 with A / B / both operands packed first (pre-split
+ * into TF32 hi and lo tiles in the kernel's shared-memory layout and loaded by
+ * bulk asynchronous copies, as the solver does for its constant operands);
+ * batches too small
  * for the tensor cores (m < 64, n < 16 or k < 32) take a SIMT kernel.
  * Allocates the descriptor array and synchronises `stream`.  FDE_ERR_CUDA if
  * a tensor-core wait expired.  Not thread-safe: while it runs, a mode other

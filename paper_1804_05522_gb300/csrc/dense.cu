@@ -495,7 +495,8 @@ fde_status gemm_batch_run(const GemmBatch<T>& b, cudaStream_t st) {
   if (b.batch == 0 || b.max_m == 0 || b.max_n == 0) return FDE_OK;
   if constexpr (sizeof(T) == 4) {
     bool used = false;
-    if (skinny_mode()) {
+    // batches with packed operands go to the tensor cores when they are eligible
+    if (skinny_mode() && !b.pk_a && !b.pk_b) {
       const int limit_n = g_skinny_force.load() == 1 ? 40 : 32;
       FDE_TRY(skinny_gemm_run(reinterpret_cast<const GemmBatch<float>&>(b), limit_n, st, &used));
       if (used) return FDE_OK;

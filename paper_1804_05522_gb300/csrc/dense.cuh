@@ -19,6 +19,13 @@ struct GemmDesc {
   // k / kblk = (k * kmagic) >> kshift for 0 <= k < 2^31 (set by gemm_batch_upload)
   unsigned long long kmagic = 0;
   int kshift = 0;
+  // Packed constant operands for the tensor-core path (gemm_batch_pack): the
+  // tiles of op(A) (128 x 32) and op(B) (BN x 32), each pre-split into TF32
+  // hi and the remainder lo and stored as the MMA reads them from shared
+  // memory (hi tile, then lo tile); tile (row tile r, k tile t) starts at
+  // pk + (r * ceil(k / 32) + t) * 2 * rows * 32.
+  const T* Apk = nullptr;
+  const T* Bpk = nullptr;
 };
 
 // A list of GEMMs with the same transposes / scalars, descriptors resident on
@@ -33,6 +40,8 @@ struct GemmBatch {
   // kstr) a multiple of 4 elements: 4-wide vector loads are allowed
   bool vec_a = false, vec_b = false;
   bool any_kblk = false;  // some descriptor uses two-level k panels
+  bool pk_a = false, pk_b = false;  // every descriptor has Apk (resp. Bpk)
+  int pk_bn = 0;                    // tile width B was packed for
   T alpha = T(1), beta = T(0);
 };
 
@@ -55,6 +64,18 @@ fde_status tc_error_flag(int* out);                 // expired tensor-core GEMM 
 fde_status tc_timeout_counter(unsigned int** ptr);  // device address of that counter
 fde_status tc_set_wait_limit(unsigned int iters);   // 0: the default limit
 fde_status tc_prepare();
+// Tile width (BN) the tensor-core path uses for a batch whose widest problem has n columns.
+int tc_bn_for(int max_n);
+// Packs the operands of a batch that stay constant for the batch's lifetime
+// (A and / or B) for the tensor-core path: allocates the packed tiles from
+// `pool`, fills them and stores their addresses in the device descriptors.
+// The batch then always runs on the tensor cores when it is eligible, reading
+// the packed operands with bulk asynchronous copies; the unpacked operands stay
+// valid for the other paths.  Does nothing (and returns FDE_OK) when the
+// tensor cores are off or the batch would not run on them, or when the packed
+// tiles would take more than *budget bytes (decremented by what is used).
+fde_status gemm_batch_pack(DevPool& pool, GemmBatch<float>* b, bool pack_a, bool pack_b, size_t* budget,
+                           cudaStream_t st);
 
 // In-place inverse of `batch` square matrices (sizes n_i <= nmax, leading
 // dimension ld, matrix i at A + i*stride) by Gauss–Jordan elimination with

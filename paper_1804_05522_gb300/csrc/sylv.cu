@@ -536,6 +536,7 @@ struct sylv_s {
   float2 *cpx_df = nullptr, *cmx_df = nullptr, *cpy_df = nullptr, *cmy_df = nullptr;
   bool resid_df = false;              // later sweeps update R in double-float (FP32 inner solver)
   bool resid_f32_last = false;        // the last update of a step in plain FP32 (its residual only predicts)
+  bool f32_last_all = false;          // ... in every step, not only before two exact steps
   // Exact FP64 residuals after the first sweep on two consecutive steps of
   // every exact_every, double-float updates in between (see sylv_step_impl);
   // exact_every = 1: after the first sweep of every step.
@@ -565,6 +566,9 @@ struct sylv_s {
   int hist = 0;                       // 1 when Xp, Cp, Rp are valid
   double *Xp = nullptr, *Cp = nullptr, *Rp = nullptr;
   bool rational = false;              // fADI levels in precomputed rational form
+  // bytes the packed constant GEMM operands of the FP32 inner solver may take
+  // (FDE_PACK_GB overrides; 0 turns packing off)
+  size_t pack_budget = (size_t)32 << 30;
   ~sylv_s() {
     if (in64.exec) cudaGraphExecDestroy(in64.exec);
     if (in32.exec) cudaGraphExecDestroy(in32.exec);
@@ -750,6 +754,17 @@ static fde_status build_level_rational(sylv_s* S, Inner<T>& in, int l, const std
   FDE_TRY(gemm_batch_upload(pool, dap, false, false, T(1), T(0), &ls.r_apply, st));
   FDE_TRY(gemm_batch_upload(pool, dup, false, true, T(1), T(1), &ls.r_update, st));
   FDE_TRY(gemm_batch_upload(pool, dup2, false, true, T(1), T(1), &ls.r_update2, st));
+  if constexpr (sizeof(T) == sizeof(float)) {
+    // the stacked resolvents and the constant update factors never change:
+    // pack them for the tensor cores (operator A of the application, ZA of
+    // the first update, WB of the second)
+    FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_apply), true, false, &S->pack_budget,
+                            st));
+    FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_update), true, false, &S->pack_budget,
+                            st));
+    FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_update2), false, true,
+                            &S->pack_budget, st));
+  }
   FDE_CUDA(cudaStreamSynchronize(st));
   return FDE_OK;
 }
@@ -795,6 +810,17 @@ static fde_status build_inner(sylv_s* S, Inner<T>& in, const std::vector<Fact<T>
     FDE_TRY(gemm_batch_upload(pool, b, false, false, T(1), T(0), &in.g_qy, st));
     FDE_TRY(gemm_batch_upload(pool, c, false, false, T(1), T(0), &in.g_qx, st));
     FDE_TRY(gemm_batch_upload(pool, d, false, true, T(1), T(0), &in.g_qyt, st));
+    if constexpr (sizeof(T) == sizeof(float)) {
+      // the leaf Schur bases are constant operands
+      FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&in.g_qxt), true, false, &S->pack_budget,
+                              st));
+      FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&in.g_qx), true, false, &S->pack_budget,
+                              st));
+      FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&in.g_qy), false, true, &S->pack_budget,
+                              st));
+      FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&in.g_qyt), false, true, &S->pack_budget,
+                              st));
+    }
   }
   if (sizeof(T) == sizeof(float) && S->trsyl_split) {
     std::vector<GemmDesc<T>> g1, g2, g3, g4;
@@ -1322,7 +1348,7 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
         const bool next_two_exact =
             K <= 1 || (step_incremental && S->cyc_incr + 1 >= K - 2) ||
             (large_first && S->prev_large && !step_incremental);
-        kind = (stop && S->resid_f32_last && next_two_exact) ? kResidF32 : kResidDF;
+        kind = (stop && S->resid_f32_last && (next_two_exact || S->f32_last_all)) ? kResidF32 : kResidDF;
         if (kind == kResidF32) used_f32 = true;
       }
     }
@@ -1419,6 +1445,7 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
       }
   }
   // ---- leaf Sylvester sub-problems (whole leaves; split leaves for the FP32 inner solver)
+  if (const char* pg = getenv("FDE_PACK_GB")) S->pack_budget = (size_t)(atof(pg) * (double)(1ull << 30));
   S->trsyl_split = prec != FDE_FP64 && S->lmax > kTrsylSplit && (long long)nl * nl >= kTrsylSplitMinPairs;
   if (const char* ts = getenv("FDE_TRSYL_SPLIT")) {  // "1": split every leaf (tests), "0": never
     if (!strcmp(ts, "1")) S->trsyl_split = prec != FDE_FP64 && S->lmax >= 2;
@@ -1634,6 +1661,10 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
     const char* rm = getenv("FDE_RESID");
     S->resid_df = !(rm && strcmp(rm, "fp64") == 0);
     S->resid_f32_last = S->resid_df && !(rm && strcmp(rm, "df") == 0);
+    // "f32last": the last update of every step in FP32, also inside a chain
+    // (its error, ~1e-7 ||A|| ||δ_last||, then enters the chain's predicted
+    // residuals until the next refresh)
+    S->f32_last_all = S->resid_f32_last && rm && strcmp(rm, "f32last") == 0;
     if (const char* it = getenv("FDE_INCR_TOL")) {
       const double v = atof(it);
       if (v > 0.0 && v < 1.0) S->incr_tol = v;

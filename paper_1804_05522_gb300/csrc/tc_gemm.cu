@@ -89,7 +89,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2u << 61;             // SWIZZLE_128B
   return d;
 }
-// round to TF32 (nearest, ties away) and the remainder
+// round to TF32 (nearest, ties away)
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -128,6 +128,18 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Adds tx bytes that the current phase of an mbarrier must also see land.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bulk asynchronous copy global -> shared of `bytes` (multiple of 16, both
+// addresses 16-byte aligned) whose completion counts as tx bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 __device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const float* src, int bytes) {
@@ -204,7 +216,7 @@ __device__ __forceinline__ void tile_copy(uint32_t dst, const float* __restrict_
   }
 }
 
-// Raw FP32 tile -> TF32 hi (and the TF32-rounded remainder lo in split mode),
+// Raw FP32 tile -> TF32 hi (and the remainder lo in split mode),
 // same swizzled offsets; thread t converts 16-byte chunks t, t + 256, ...
 // (the chunks tile_copy<R, true> gave it)
 template <int R>
@@ -221,11 +233,13 @@ __device__ __forceinline__ void tile_convert(const uint8_t* raw, uint8_t* hi, ui
     h.w = to_tf32(v.w);
     *reinterpret_cast<float4*>(hi + off) = h;
     if (split) {
+      // the remainder is exact in FP32; the MMA reads its top 19 bits
+      // (truncation to TF32), which leaves an error below 2^-21 |v|
       float4 l;
-      l.x = to_tf32(v.x - h.x);
-      l.y = to_tf32(v.y - h.y);
-      l.z = to_tf32(v.z - h.z);
-      l.w = to_tf32(v.w - h.w);
+      l.x = v.x - h.x;
+      l.y = v.y - h.y;
+      l.z = v.z - h.z;
+      l.w = v.w - h.w;
       *reinterpret_cast<float4*>(lo + off) = l;
     }
   }
@@ -262,11 +276,11 @@ __device__ __forceinline__ void tile_convert_mn(const uint8_t* raw, uint8_t* hi,
       h.w = to_tf32(x.w);
       *reinterpret_cast<float4*>(hi + off) = h;
       if (split) {
-        float4 l;
-        l.x = to_tf32(x.x - h.x);
-        l.y = to_tf32(x.y - h.y);
-        l.z = to_tf32(x.z - h.z);
-        l.w = to_tf32(x.w - h.w);
+        float4 l;  // exact remainder, truncated to TF32 by the MMA (see tile_convert)
+        l.x = x.x - h.x;
+        l.y = x.y - h.y;
+        l.z = x.z - h.z;
+        l.w = x.w - h.w;
         *reinterpret_cast<float4*>(lo + off) = l;
       }
     }
@@ -383,14 +397,17 @@ constexpr int kMmaWarp = kEpiWarp0 + kEpiWarps;                // warp 12
 template <int BN, int RAW, bool TA, bool TB>
 __global__ void __launch_bounds__(kPThreads, 1)
     tc_gemm_kernel(const GemmDesc<float>* __restrict__ descs, int batch, int mt, int nt, float alpha, float beta,
-                   int split, int mslots, int vec_a, int vec_b) {
+                   int split, int mslots, int vec_a, int vec_b, int pk_a, int pk_b) {
   constexpr int A_BYTES = BM * BK * 4, B_BYTES = BN * BK * 4;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base_u32 = smem_u32(smem_raw);
   const uint32_t pad = ((base_u32 + 1023u) & ~1023u) - base_u32;
   uint8_t* sm = smem_raw + pad;  // 1024-byte aligned
-  // MMA slot: A_hi | B_hi | A_lo | B_lo (lo only in split mode); raw stages after the slots
+  // MMA slot: A_hi | A_lo | B_hi | B_lo (lo only in split mode), so that a
+  // packed operand's hi and lo tiles arrive in one bulk copy; raw stages after the slots
   const int slot_bytes = (A_BYTES + B_BYTES) * (split ? 2 : 1);
+  const int a_lo_off = A_BYTES, b_hi_off = split ? 2 * A_BYTES : A_BYTES, b_lo_off = b_hi_off + B_BYTES;
+  const uint32_t a_copy = (uint32_t)A_BYTES * (split ? 2u : 1u), b_copy = (uint32_t)B_BYTES * (split ? 2u : 1u);
   uint8_t* raw = sm + (size_t)mslots * slot_bytes;
   __shared__ __align__(8) uint64_t full_bar[kMaxSlots], empty_bar[kMaxSlots], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_base;
@@ -442,10 +459,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const uint32_t dst = smem_u32(raw + (size_t)(p_issue % RAW) * raw_bytes<BN>());
         const GemmDesc<float>& d = is.d;
         const int a_kblk = TA ? 0 : d.kblk, b_kblk = TB ? d.kblk : 0;
-        tile_copy<BM, TA>(dst, d.A, d.lda, a_kblk, d.kstr, d.kmagic, d.kshift, is.m0, d.m, is.kt * BK, d.k,
-                          vec_a != 0);
-        tile_copy<BN, !TB>(dst + A_BYTES, d.B, d.ldb, b_kblk, d.kstr, d.kmagic, d.kshift, is.n0, d.n, is.kt * BK,
-                           d.k, vec_b != 0);
+        if (!pk_a)
+          tile_copy<BM, TA>(dst, d.A, d.lda, a_kblk, d.kstr, d.kmagic, d.kshift, is.m0, d.m, is.kt * BK, d.k,
+                            vec_a != 0);
+        if (!pk_b)
+          tile_copy<BN, !TB>(dst + A_BYTES, d.B, d.ldb, b_kblk, d.kstr, d.kmagic, d.kshift, is.n0, d.n, is.kt * BK,
+                             d.k, vec_b != 0);
         if (++is.kt == is.nk) {
           is.t += gridDim.x;
           is_ok = next_tile<BN>(is, descs, tiles, mt, nt);
@@ -457,6 +476,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll 1
     for (int i = 0; i < RAW; ++i) issue();
     bool ok = true;
+    // last position whose packed tiles were copied into each slot (thread 0)
+    int last_bulk[kMaxSlots];
+#pragma unroll
+    for (int s2 = 0; s2 < kMaxSlots; ++s2) last_bulk[s2] = -1;
     for (int gg = 0; cv_ok; ++gg) {
       cp_async_wait<RAW - 1>();  // this thread's copies of position gg have landed
       const int ms = gg % mslots;
@@ -466,17 +489,35 @@ __global__ void __launch_bounds__(kPThreads, 1)
         if (lane == 0 && ok) got = mbar_wait_f(smem_u32(&empty_bar[ms]), (uint32_t)((gg / mslots - 1) & 1), fail);
         ok = ok && __shfl_sync(0xffffffffu, got, 0) != 0;
       }
+      uint8_t* slot = sm + (size_t)ms * slot_bytes;
+      if (threadIdx.x == 0 && ok && (pk_a || pk_b)) {
+        // packed operands: the slot is free, copy their hi | lo tiles into it;
+        // the `full` barrier also waits for these bytes (this warp has not
+        // arrived on it yet)
+        const int z = cv.t / (mt * nt), rem = cv.t - z * (mt * nt), ni = rem / mt, mi = rem - ni * mt;
+        const uint32_t fb = smem_u32(&full_bar[ms]);
+        mbar_expect_tx(fb, (pk_a ? a_copy : 0u) + (pk_b ? b_copy : 0u));
+        if (pk_a)
+          bulk_g2s(smem_u32(slot), descs[z].Apk + ((size_t)mi * cv.nk + cv.kt) * (2 * BM * BK), a_copy, fb);
+        if (pk_b)
+          bulk_g2s(smem_u32(slot + b_hi_off), descs[z].Bpk + ((size_t)ni * cv.nk + cv.kt) * (2 * BN * BK), b_copy,
+                   fb);
+        last_bulk[ms] = gg;
+      }
       if (ok) {
         const uint8_t* rs = raw + (size_t)(gg % RAW) * raw_bytes<BN>();
-        uint8_t* slot = sm + (size_t)ms * slot_bytes;
-        if (TA)
-          tile_convert<BM>(rs, slot, slot + A_BYTES + B_BYTES, split != 0);
-        else
-          tile_convert_mn<BM>(rs, slot, slot + A_BYTES + B_BYTES, split != 0);
-        if (!TB)
-          tile_convert<BN>(rs + A_BYTES, slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
-        else
-          tile_convert_mn<BN>(rs + A_BYTES, slot + A_BYTES, slot + 2 * A_BYTES + B_BYTES, split != 0);
+        if (!pk_a) {
+          if (TA)
+            tile_convert<BM>(rs, slot, slot + a_lo_off, split != 0);
+          else
+            tile_convert_mn<BM>(rs, slot, slot + a_lo_off, split != 0);
+        }
+        if (!pk_b) {
+          if (!TB)
+            tile_convert<BN>(rs + A_BYTES, slot + b_hi_off, slot + b_lo_off, split != 0);
+          else
+            tile_convert_mn<BN>(rs + A_BYTES, slot + b_hi_off, slot + b_lo_off, split != 0);
+        }
         fence_proxy_async();  // this thread's tiles -> visible to the tensor core
       }
       __syncwarp();
@@ -489,6 +530,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
       }
     }
     cp_async_wait<0>();
+    if (threadIdx.x == 0 && (pk_a || pk_b)) {
+      // no bulk copy may still be writing this CTA's shared memory when it
+      // exits (after a failed wait the MMA warp may not have consumed them)
+      for (int s2 = 0; s2 < mslots; ++s2)
+        if (last_bulk[s2] >= 0) mbar_wait(smem_u32(&full_bar[s2]), (uint32_t)((last_bulk[s2] / mslots) & 1));
+    }
   } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer
     if (lane == 0) {
@@ -510,8 +557,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
           if (!ok) break;
           tc_fence_after();
           uint8_t* slot = sm + (size_t)s * slot_bytes;
-          const uint32_t a_hi = smem_u32(slot), b_hi = smem_u32(slot + A_BYTES);
-          const uint32_t a_lo = smem_u32(slot + A_BYTES + B_BYTES), b_lo = smem_u32(slot + 2 * A_BYTES + B_BYTES);
+          const uint32_t a_hi = smem_u32(slot), b_hi = smem_u32(slot + b_hi_off);
+          const uint32_t a_lo = smem_u32(slot + a_lo_off), b_lo = smem_u32(slot + b_lo_off);
 #pragma unroll
           for (int kk = 0; kk < BK / 8; ++kk) {
             const uint32_t off = kk * 32;  // 8 TF32 = 32 bytes along k inside the swizzle atom
@@ -719,7 +766,7 @@ static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t s
   const int grid = (int)(tiles < sms ? tiles : sms);
   ProfScope ps("gemm32tc", st, b.flops, 1);
   kern<<<grid, tc::kPThreads, smem, st>>>(b.d_desc, b.batch, mt, nt, b.alpha, b.beta, split, mslots,
-                                          b.vec_a ? 1 : 0, b.vec_b ? 1 : 0);
+                                          b.vec_a ? 1 : 0, b.vec_b ? 1 : 0, b.pk_a ? 1 : 0, b.pk_b ? 1 : 0);
   FDE_LAUNCH("tc_gemm_kernel");
   return FDE_OK;
 }
@@ -733,13 +780,132 @@ fde_status tc_gemm_run(const GemmBatch<float>& b, cudaStream_t st, bool* used) {
   if (mode == 0 || b.max_m < 64 || b.max_n < 16 || b.max_k < 32 || b.max_ldc > (1 << 26)) return FDE_OK;
   FDE_TRY(tc_prepare());
   const int split = (mode == 3) ? 1 : 0;
-  if (b.max_n <= 32)
+  const int bn = tc_bn_for(b.max_n);
+  if (b.pk_b && b.pk_bn != bn) {
+    set_error("tensor-core GEMM: B packed for BN = %d, launch needs %d", b.pk_bn, bn);
+    return FDE_ERR_ARG;
+  }
+  if (bn == 32)
     FDE_TRY(launch_bn<32>(b, split, st));
-  else if (b.max_n <= 64)
+  else if (bn == 64)
     FDE_TRY(launch_bn<64>(b, split, st));
   else
     FDE_TRY(launch_bn<128>(b, split, st));
   *used = true;
+  return FDE_OK;
+}
+
+int tc_bn_for(int max_n) { return max_n <= 32 ? 32 : max_n <= 64 ? 64 : 128; }
+
+namespace {
+// One packed tile per block: (problem z, row tile r, k tile t) -> dst, hi then lo.
+struct PackJob {
+  int z, r, t;
+  float* dst;
+};
+// Tile rows R x 32 k of op(X), X = A (IS_B false) or B, read with the same
+// addressing as the GEMM (transposes, two-level k), rounded to TF32 hi and
+// the exact remainder lo, written at the swizzled K-major offsets of the
+// shared-memory tile; zeros outside the problem.
+template <bool IS_B>
+__global__ void pack_tiles_kernel(const GemmDesc<float>* __restrict__ descs, const PackJob* __restrict__ jobs, int R,
+                                  int trans) {
+  const PackJob jb = jobs[blockIdx.x];
+  const GemmDesc<float> d = descs[jb.z];
+  const float* X = IS_B ? d.B : d.A;
+  const int ld = IS_B ? d.ldb : d.lda, nrows = IS_B ? d.n : d.m;
+  // k-contiguous when op(A) = Aᵀ (A: trans) or op(B) = B (B: !trans)
+  const bool kcontig = IS_B ? !trans : trans;
+  const bool two_level = d.kblk > 0 && !kcontig;
+  float* hi = jb.dst;
+  float* lo = jb.dst + (size_t)R * tc::BK;
+  for (int e = threadIdx.x; e < R * tc::BK; e += blockDim.x) {
+    const int r = e / tc::BK, c = e % tc::BK;
+    const int row = jb.r * R + r, k = jb.t * tc::BK + c;
+    float v = 0.f;
+    if (row < nrows && k < d.k) {
+      if (kcontig) {
+        v = X[(size_t)row * ld + k];
+      } else {
+        long long col = (long long)k * ld;
+        if (two_level) {
+          const int q = k / d.kblk;
+          col = (long long)q * d.kstr + (long long)(k - q * d.kblk) * ld;
+        }
+        v = X[col + row];
+      }
+    }
+    const uint32_t off = tc::sw_off(r, c) >> 2;
+    const float h = tc::to_tf32(v);
+    hi[off] = h;
+    lo[off] = v - h;
+  }
+}
+}  // namespace
+
+fde_status gemm_batch_pack(DevPool& pool, GemmBatch<float>* b, bool pack_a, bool pack_b, size_t* budget,
+                           cudaStream_t st) {
+  const int mode = tc_mode();
+  if (b->batch == 0 || mode == 0 || (!pack_a && !pack_b)) return FDE_OK;
+  if (b->max_m < 64 || b->max_n < 16 || b->max_k < 32 || b->max_ldc > (1 << 26)) return FDE_OK;
+  std::vector<GemmDesc<float>> h(b->batch);
+  FDE_CUDA(cudaMemcpy(h.data(), b->d_desc, h.size() * sizeof(GemmDesc<float>), cudaMemcpyDeviceToHost));
+  const int bn = tc_bn_for(b->max_n);
+  // tile counts and bytes
+  size_t na = 0, nb = 0;
+  for (const auto& d : h) {
+    const size_t nk = (size_t)ceil_div(d.k, tc::BK);
+    if (pack_a) na += (size_t)ceil_div(d.m, 128) * nk;
+    if (pack_b) nb += (size_t)ceil_div(d.n, bn) * nk;
+  }
+  const size_t bytes = (na * 2 * 128 * tc::BK + nb * 2 * (size_t)bn * tc::BK) * sizeof(float);
+  if (bytes > *budget) return FDE_OK;
+  *budget -= bytes;
+  float *pa = nullptr, *pb = nullptr;
+  if (na) FDE_TRY(pool.alloc(&pa, na * 2 * 128 * tc::BK));
+  if (nb) FDE_TRY(pool.alloc(&pb, nb * 2 * (size_t)bn * tc::BK));
+  std::vector<PackJob> ja, jbv;
+  size_t oa = 0, ob = 0;
+  for (int z = 0; z < b->batch; ++z) {
+    GemmDesc<float>& d = h[z];
+    const int nk = ceil_div(d.k, tc::BK);
+    if (pack_a) {
+      d.Apk = pa + oa;
+      for (int r = 0; r < ceil_div(d.m, 128); ++r)
+        for (int t = 0; t < nk; ++t) {
+          ja.push_back({z, r, t, pa + oa});
+          oa += 2 * 128 * tc::BK;
+        }
+    }
+    if (pack_b) {
+      d.Bpk = pb + ob;
+      for (int r = 0; r < ceil_div(d.n, bn); ++r)
+        for (int t = 0; t < nk; ++t) {
+          jbv.push_back({z, r, t, pb + ob});
+          ob += 2 * (size_t)bn * tc::BK;
+        }
+    }
+  }
+  DevPool scratch;
+  if (!ja.empty()) {
+    PackJob* dj;
+    FDE_TRY(scratch.alloc(&dj, ja.size()));
+    FDE_CUDA(cudaMemcpyAsync(dj, ja.data(), ja.size() * sizeof(PackJob), cudaMemcpyHostToDevice, st));
+    pack_tiles_kernel<false><<<(unsigned)ja.size(), 256, 0, st>>>(b->d_desc, dj, 128, b->ta ? 1 : 0);
+    FDE_LAUNCH("pack_tiles_kernel");
+  }
+  if (!jbv.empty()) {
+    PackJob* dj;
+    FDE_TRY(scratch.alloc(&dj, jbv.size()));
+    FDE_CUDA(cudaMemcpyAsync(dj, jbv.data(), jbv.size() * sizeof(PackJob), cudaMemcpyHostToDevice, st));
+    pack_tiles_kernel<true><<<(unsigned)jbv.size(), 256, 0, st>>>(b->d_desc, dj, bn, b->tb ? 1 : 0);
+    FDE_LAUNCH("pack_tiles_kernel");
+  }
+  FDE_CUDA(cudaStreamSynchronize(st));
+  FDE_CUDA(cudaMemcpy(b->d_desc, h.data(), h.size() * sizeof(GemmDesc<float>), cudaMemcpyHostToDevice));
+  b->pk_a = b->pk_a || pack_a;
+  b->pk_b = b->pk_b || pack_b;
+  if (pack_b) b->pk_bn = bn;
   return FDE_OK;
 }
 
@@ -752,7 +918,8 @@ extern "C" fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float al
   using namespace fde;
   FDE_ARG(m >= 0 && n >= 0 && k >= 0 && batch >= 0, "negative size");
   FDE_ARG(A != nullptr && B != nullptr && C != nullptr, "NULL matrix");
-  FDE_ARG(mode == -1 || mode == 0 || mode == 1 || mode == 3 || mode == 4, "mode must be -1, 0, 1, 3 or 4");
+  FDE_ARG(mode == -1 || mode == 0 || mode == 1 || mode == 3 || mode == 4 || (mode >= 5 && mode <= 7),
+          "mode must be -1, 0, 1, 3, 4, 5, 6 or 7");
   FDE_ARG(kblk >= 0 && (kblk == 0 || kstr >= 0), "bad kblk / kstr");
   FDE_ARG(ldc >= (m > 1 ? m : 1), "ldc < m");
   FDE_ARG(lda >= 1 && ldb >= 1, "bad lda / ldb");
@@ -774,8 +941,17 @@ extern "C" fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float al
   FDE_TRY(tc_error_flag(&before));
   const int saved = tc_mode();
   if (mode >= 0) {
-    set_tc_mode(mode == 4 ? 3 : mode);
+    set_tc_mode(mode >= 4 ? 3 : mode);
     set_skinny_force(mode == 4 ? 1 : 0);
+  }
+  if (mode >= 5) {
+    size_t budget = (size_t)1 << 40;
+    const fde_status ps = gemm_batch_pack(scratch, &gb, mode != 6, mode != 5, &budget, st);
+    if (ps != FDE_OK) {
+      set_tc_mode(saved);
+      set_skinny_force(-1);
+      return ps;
+    }
   }
   const fde_status s = gemm_batch_run(gb, st);
   set_tc_mode(saved);

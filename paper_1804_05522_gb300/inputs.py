@@ -217,6 +217,7 @@ WORKLOADS = {
     "fd1d_n1024": lambda: fd1d(N=1024, alpha=1.5, steps=32, leaf=64, tol=1e-10),
     "fd2d_n256": lambda: fd2d(N=256, alpha=(1.3, 1.7), steps=50, leaf=64, tol=1e-10),
     "fd2d_n1024": lambda: fd2d(N=1024, alpha=(1.5, 1.5), steps=100, leaf=128, tol=1e-10),
+    "fd2d_n2048": lambda: fd2d(N=2048, alpha=(1.5, 1.5), steps=100, leaf=128, tol=1e-10),
     "fd2d_n4096": lambda: fd2d(N=4096, alpha=(1.5, 1.5), steps=100, leaf=128, tol=1e-10),
     "fd2d_n16384": lambda: fd2d(N=16384, alpha=(1.2, 1.8), steps=20, leaf=256, tol=1e-10),
 }

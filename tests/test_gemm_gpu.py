@@ -17,7 +17,7 @@ def _bound(mode, k):
     u = 2.0 ** -24
     if mode == 1:
         return 2 * 2.0 ** -11 + 2 * k * u
-    return 2.0 ** -20 + 2 * k * u  # modes 0, 4 (FP32 FMA) and 3 (3xTF32)
+    return 2.0 ** -20 + 2 * k * u  # modes 0, 4 (FP32 FMA), 3 and 5-7 (3xTF32)
 
 
 def _opnd(rng, rows, cols, ld, batch):
@@ -42,10 +42,12 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("mode", [0, 1, 3, 5, 6, 7])
 @pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_gemm_f32(lib, mode, ta, tb, shape):
+    """Modes 5-7: 3xTF32 with A, B or both packed (pre-split tiles loaded by
+    bulk asynchronous copies), every transpose and the ragged shapes."""
     m, n, k, pad, batch = shape
     rng = np.random.default_rng(m * 7 + n * 3 + k + 100 * ta + 10 * tb + mode)
     ar, ac = (k, m) if ta else (m, k)
@@ -80,7 +82,7 @@ def test_gemm_f32(lib, mode, ta, tb, shape):
             assert np.array_equal(Cg[i, :, m:], C0[i, :, m:])
 
 
-@pytest.mark.parametrize("mode", [1, 3])
+@pytest.mark.parametrize("mode", [1, 3, 5, 6, 7])
 def test_gemm_two_level_k(lib, mode):
     """k runs over panels of kblk columns that sit kstr apart (non-transposed A,
     transposed B), as in the stacked low-rank update of the Sylvester solver."""
@@ -117,7 +119,8 @@ def test_gemm_two_level_k(lib, mode):
 
 
 def test_gemm_split_beats_tf32(lib):
-    """3xTF32 must be markedly more accurate than plain TF32 on the same data."""
+    """3xTF32 (also with packed operands) must be markedly more accurate than
+    plain TF32 on the same data."""
     rng = np.random.default_rng(11)
     m = n = 256
     k = 512
@@ -125,14 +128,14 @@ def test_gemm_split_beats_tf32(lib):
     B = rng.standard_normal((n, k)).astype(np.float32)
     ref = A.T.astype(np.float64) @ B.T.astype(np.float64)
     errs = {}
-    for mode in (1, 3):
+    for mode in (1, 3, 7):
         dA, dB = torch.from_numpy(A.ravel().copy()).cuda(), torch.from_numpy(B.ravel().copy()).cuda()
         dC = torch.zeros(m * n, dtype=torch.float32, device="cuda")
         lib.gemm_f32(0, 0, m, n, k, 1.0, dA.data_ptr(), m, 0, dB.data_ptr(), k, 0, 0.0, dC.data_ptr(), m, 0,
                      mode=mode)
         got = dC.cpu().numpy().reshape(n, m).T
         errs[mode] = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert errs[3] < 2e-6 and errs[1] > 100 * errs[3], errs
+    assert errs[3] < 2e-6 and errs[7] < 2e-6 and errs[1] > 100 * errs[3], errs
 
 
 SKINNY_SHAPES = [
