@@ -252,9 +252,11 @@ typedef struct {
   const double* h_sin_amp;       /* host, r                                      */
   const double* h_omega;         /* host, r                                      */
   int prec;                      /* fde_prec                                     */
-  int use_graph;                 /* reserved, ignored: the 2D inner solve is     */
-                                 /* always captured once as a CUDA graph and     */
-                                 /* replayed per sweep                           */
+  int use_graph;                 /* reserved, ignored: with the FP32 inner       */
+                                 /* solver every 2D step runs as one CUDA graph  */
+                                 /* launch (refinement decisions on the device), */
+                                 /* otherwise the inner solve is one graph per   */
+                                 /* sweep; FDE_STEP_GRAPH=0 selects the latter   */
 } fde_run_params;
 
 typedef struct {
@@ -268,7 +270,14 @@ typedef struct {
 } fde_run_stats;
 
 /* Run M implicit-Euler steps from U0 (device, N (1D) or N x N (2D),
- * column-major, ld = N) into U_out (device, same shape; may alias U0). */
+ * column-major, ld = N) into U_out (device, same shape; may alias U0).
+ * 2D with the FP32 inner solver: each step is one CUDA graph launch whose
+ * refinement loop (stopping tests, choice of residual form) is decided on
+ * the device, and the host synchronises once per call (fde_runner_advance:
+ * once per call as well); an error of any step (FDE_ERR_NUMERIC,
+ * FDE_ERR_NOCONV, an expired tensor-core wait as FDE_ERR_CUDA) is returned
+ * by the call that launched it, and the state is then undefined until
+ * fde_runner_load. */
 fde_status fde_run(const fde_run_params* p, const double* d_U0, double* d_U_out, void* stream,
                    fde_run_stats* stats);
 

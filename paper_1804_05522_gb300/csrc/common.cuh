@@ -22,6 +22,7 @@ fde_status cuda_status(cudaError_t e, const char* what, const char* file, int li
 
 void count_launch();
 void count_launches(size_t n);
+void count_suspend(bool on);  // nested: stop / resume counting on this thread
 bool prof_enabled();
 // Host-side failure injection (fde_fail_alloc_after): true when this device
 // allocation is the one that must fail.

@@ -48,8 +48,16 @@ bool alloc_fail_now() {
 }
 void fail_alloc_after(long long n) { g_alloc_countdown.store(n < 0 ? -1 : n); }
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-void count_launches(size_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// Launches recorded while a thread captures a graph are not counted: the
+// graph's kernels are counted when it runs.
+static thread_local int t_count_suspended = 0;
+void count_suspend(bool on) { t_count_suspended += on ? 1 : -1; }
+void count_launch() {
+  if (!t_count_suspended) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void count_launches(size_t n) {
+  if (!t_count_suspended) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 bool prof_enabled() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
 
 ProfScope::ProfScope(const char* family, cudaStream_t s, double w, int k)

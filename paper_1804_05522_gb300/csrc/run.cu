@@ -8,6 +8,10 @@
 
 struct sylv_s;
 namespace fde {
+bool sylv_graph_steps(sylv_s* s);
+fde_status sylv_step_graph(sylv_s* s, const double* C, double* X, cudaStream_t st, const double* C_prev);
+fde_status sylv_graph_collect(sylv_s* s, cudaStream_t st, int* steps, int* sweeps_total, int* sweeps_max,
+                              double* relres_max);
 fde_status sylv_step_internal(sylv_s* s, const double* C, double* X, cudaStream_t st, double* relres, int* sweeps,
                               const double* C_prev);
 }
@@ -225,6 +229,23 @@ static fde_status runner_create(const fde_run_params* p, const double* U0, cudaS
   return FDE_OK;
 }
 
+// Statistics and errors of the whole-step graphs launched since the last
+// collection (one host synchronisation).
+static fde_status collect_graph_steps(fde_runner_s* R, cudaStream_t st) {
+  int steps = 0, total = 0, mx = 0;
+  double rel = 0.0;
+  const fde_status s = sylv_graph_collect(R->s, st, &steps, &total, &mx, &rel);
+  if (s != FDE_OK) {
+    R->have_prev = false;
+    R->c_valid = false;
+    return s;
+  }
+  R->stats.sweeps_total += total;
+  R->stats.sweeps_max = std::max(R->stats.sweeps_max, mx);
+  R->stats.relres_max = std::max(R->stats.relres_max, rel);
+  return FDE_OK;
+}
+
 static fde_status runner_advance(fde_runner_s* R, int nsteps, cudaStream_t st) {
   const int N = R->N, r = R->p.rank;
   const double dt = R->p.op_x.dt;
@@ -279,11 +300,21 @@ static fde_status runner_advance(fde_runner_s* R, int nsteps, cudaStream_t st) {
   } else {
     const size_t NN = (size_t)N * N;
     const int nb = (int)std::min<size_t>((NN + 255) / 256, 152 * 32);
+    const bool graph = sylv_graph_steps(R->s);
     for (int i = 0; i < nsteps; ++i) {
       const int m = R->step;
       std::swap(R->C, R->C2);  // C2 <- previous right-hand side
       rhs2d_kernel<<<nb, 256, 0, st>>>(R->U, R->FL, R->FR, N, r, R->weights((m + 1) * dt), dt, R->C);
       FDE_LAUNCH("rhs2d_kernel");
+      if (graph) {
+        // the whole step is one graph launch; its results are collected below
+        fde_status s = sylv_step_graph(R->s, R->C, R->U, st, R->have_prev ? R->C2 : nullptr);
+        R->have_prev = (s == FDE_OK);
+        R->c_valid = (s == FDE_OK);
+        FDE_TRY(s);
+        R->step = m + 1;
+        continue;
+      }
       double rel = 0.0;
       int sw = 0;
       fde_status s = sylv_step_internal(R->s, R->C, R->U, st, &rel, &sw, R->have_prev ? R->C2 : nullptr);
@@ -295,6 +326,7 @@ static fde_status runner_advance(fde_runner_s* R, int nsteps, cudaStream_t st) {
       R->stats.relres_max = std::max(R->stats.relres_max, rel);
       R->step = m + 1;
     }
+    if (graph) FDE_TRY(collect_graph_steps(R, st));
   }
   FDE_CUDA(cudaStreamSynchronize(st));
   R->stats.solve_s += now_seconds() - t1;
@@ -343,6 +375,17 @@ extern "C" fde_status fde_runner_step_source(fde_runner_t r, const double* F, in
   std::swap(r->C, r->C2);  // C2 <- previous right-hand side
   rhs_dense_kernel<<<nb, 256, 0, st>>>(r->U, Fd, N, ldf, dt, r->C);
   FDE_LAUNCH("rhs_dense_kernel");
+  if (sylv_graph_steps(r->s)) {
+    // one graph launch; collected (one synchronisation) before returning
+    fde_status s = sylv_step_graph(r->s, r->C, r->U, st, r->have_prev ? r->C2 : nullptr);
+    r->have_prev = (s == FDE_OK);
+    r->c_valid = (s == FDE_OK);
+    FDE_TRY(s);
+    FDE_TRY(collect_graph_steps(r, st));
+    r->step += 1;
+    r->stats.solve_s += now_seconds() - t1;
+    return FDE_OK;
+  }
   double rel = 0.0;
   int sw = 0;
   fde_status s = sylv_step_internal(r->s, r->C, r->U, st, &rel, &sw, r->have_prev ? r->C2 : nullptr);

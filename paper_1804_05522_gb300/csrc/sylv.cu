@@ -500,6 +500,139 @@ struct Inner {
   std::vector<Fact<T>> facts;         // keeps FP32 demoted factorisations alive
 };
 
+// ====================================================== whole-step graphs
+// Device-side controller of a refinement loop captured as one CUDA graph per
+// time step (FP32 inner solver): the host decisions of sylv_step_impl, taken
+// by single-thread kernels from the same accumulators, which set the
+// conditional nodes of the graph (a WHILE node over the sweeps, a SWITCH node
+// over the residual form of each sweep).
+struct StepCtl {
+  // configuration (from the host)
+  double tol2_update, tol2_relres, incr_tol2;
+  int max_sweeps, exact_every, resid_df, f32_last, f32_last_all;
+  // incremental-residual chain across steps
+  int cyc_streak, cyc_incr, prev_large;
+  // the current step
+  int in_chain, must_exact, step_incremental, large_first, used_f32, incr_ok, sw, stop;
+  double prev_d2;
+  // results, accumulated until the host collects them
+  int status;             // FDE_OK, FDE_ERR_NUMERIC or FDE_ERR_NOCONV of the first failed step
+  int steps, sweeps_total, sweeps_max;
+  int kind_count[3];      // residual forms run: exact, double-float, FP32
+  double relres_max;
+};
+enum ResidKind { kResidExact = 0, kResidDF = 1, kResidF32 = 2 };
+
+// Start of a step: a non-finite right-hand side (flag from nonfinite_kernel)
+// or an earlier failed step skips the sweeps.
+__global__ void ctl_begin_kernel(StepCtl* c, const int* bad, int in_chain, cudaGraphConditionalHandle hloop) {
+  if (threadIdx.x != 0) return;
+  if (c->status == FDE_OK && *bad) c->status = FDE_ERR_NUMERIC;
+  if (c->status != FDE_OK) {
+    cudaGraphSetConditional(hloop, 0u);
+    return;
+  }
+  c->in_chain = in_chain;
+  if (!in_chain) {
+    c->cyc_streak = 0;
+    c->cyc_incr = 0;
+    c->prev_large = 0;
+  }
+  const int K = c->exact_every;
+  c->must_exact = !in_chain || K <= 2 || !c->resid_df || c->cyc_streak == 1 || c->cyc_incr >= K - 2;
+  c->step_incremental = c->large_first = c->used_f32 = 0;
+  c->incr_ok = c->resid_df;
+  c->sw = 0;
+  c->stop = 0;
+  c->prev_d2 = -1.0;
+  cudaGraphSetConditional(hloop, 1u);
+}
+
+// After a sweep's update (acc[0] = ||δ||², acc[1] = ||X||²): the stopping
+// test and the form of the residual update (SWITCH value; 3 = none).
+__global__ void ctl_solve_kernel(StepCtl* c, const double* acc, cudaGraphConditionalHandle hkind) {
+  if (threadIdx.x != 0) return;
+  if (c->status != FDE_OK) {
+    cudaGraphSetConditional(hkind, 3u);
+    return;
+  }
+  const double a0 = acc[0], a1 = acc[1];
+  if (!isfinite(a0) || !isfinite(a1)) {
+    c->status = FDE_ERR_NUMERIC;
+    cudaGraphSetConditional(hkind, 3u);
+    return;
+  }
+  const double tol2 = c->tol2_update * a1;
+  int stop = a0 <= tol2;
+  if (!stop && c->prev_d2 > 0.0 && a0 < 0.25 * c->prev_d2) {
+    const double rho = sqrt(a0 / c->prev_d2), rest = rho / (1.0 - rho);
+    stop = a0 * rest * rest <= tol2;
+  }
+  if (c->prev_d2 > 0.0 && a0 > 0.01 * c->prev_d2) c->incr_ok = 0;
+  c->prev_d2 = a0;
+  const int K = c->exact_every;
+  int kind = kResidExact;
+  if (c->incr_ok) {
+    if (c->sw == 0 && c->in_chain && K > 2) {
+      const int small = a0 <= c->incr_tol2 * a1;
+      if (small && !c->must_exact) c->step_incremental = 1;
+      if (!small) c->large_first = 1;
+    }
+    if (c->sw > 0 || c->step_incremental) {
+      const int next_two_exact = K <= 1 || (c->step_incremental && c->cyc_incr + 1 >= K - 2) ||
+                                 (c->large_first && c->prev_large && !c->step_incremental);
+      kind = (stop && c->f32_last && (next_two_exact || c->f32_last_all)) ? kResidF32 : kResidDF;
+      if (kind == kResidF32) c->used_f32 = 1;
+    }
+  }
+  c->stop = stop;
+  c->kind_count[kind] += 1;
+  cudaGraphSetConditional(hkind, (unsigned)kind);
+}
+
+// After the residual (acc[2] = ||R||², acc[4] = ||C||²): the residual stopping
+// test, the sweep cap and, at the end of the step, the chain bookkeeping;
+// sets the WHILE condition.
+__global__ void ctl_resid_kernel(StepCtl* c, const double* acc, cudaGraphConditionalHandle hloop) {
+  if (threadIdx.x != 0) return;
+  if (c->status != FDE_OK) {
+    cudaGraphSetConditional(hloop, 0u);
+    return;
+  }
+  const double a2 = acc[2], a4 = acc[4];
+  if (!isfinite(a2)) {
+    c->status = FDE_ERR_NUMERIC;
+    cudaGraphSetConditional(hloop, 0u);
+    return;
+  }
+  c->sw += 1;
+  int stop = c->stop || a2 <= c->tol2_relres * a4;
+  if (!stop) {
+    const int cap = c->max_sweeps > 1 ? c->max_sweeps : 1;
+    if (c->sw >= cap) c->status = FDE_ERR_NOCONV;
+    cudaGraphSetConditional(hloop, c->sw >= cap ? 0u : 1u);
+    return;
+  }
+  const int K = c->exact_every;
+  c->steps += 1;
+  c->sweeps_total += c->sw;
+  c->sweeps_max = max(c->sweeps_max, c->sw);
+  c->relres_max = fmax(c->relres_max, a4 > 0.0 ? sqrt(a2 / a4) : sqrt(a2));
+  if (c->step_incremental) {
+    c->cyc_streak = 0;
+    c->cyc_incr += 1;
+  } else {
+    c->cyc_streak = c->cyc_streak < 2 ? c->cyc_streak + 1 : 2;
+    if (c->cyc_streak == 2) c->cyc_incr = 0;
+  }
+  if (c->used_f32 && c->large_first && K > 2) {
+    c->cyc_streak = 0;
+    c->cyc_incr = K;
+  }
+  c->prev_large = c->large_first;
+  cudaGraphSetConditional(hloop, 0u);
+}
+
 }  // namespace fde
 
 using namespace fde;
@@ -569,7 +702,27 @@ struct sylv_s {
   // bytes the packed constant GEMM operands of the FP32 inner solver may take
   // (FDE_PACK_GB overrides; 0 turns packing off)
   size_t pack_budget = (size_t)32 << 30;
+  // whole-step graphs (FP32 inner solver): one executable per variant of the
+  // step's first part and per (C, C_prev, X) buffers, the controller state and
+  // the streams their sweep bodies are captured on
+  struct StepGraph {
+    int variant = 0;
+    const double *C = nullptr, *Cp = nullptr;
+    double* X = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t k_pre = 0, k_body = 0, k_br[3] = {0, 0, 0};
+  };
+  std::vector<StepGraph> sgraphs;
+  bool step_graph = false;            // runner steps run as whole-step graphs
+  bool ctl_synced = false;            // the device controller holds the chain state
+  StepCtl* ctl = nullptr;
+  cudaStream_t gs2 = nullptr, gs3 = nullptr;
+  std::vector<size_t> graph_pending;  // whole-step graphs launched since the last collect
   ~sylv_s() {
+    for (auto& g : sgraphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (gs2) cudaStreamDestroy(gs2);
+    if (gs3) cudaStreamDestroy(gs3);
     if (in64.exec) cudaGraphExecDestroy(in64.exec);
     if (in32.exec) cudaGraphExecDestroy(in32.exec);
     if (ev_in) cudaEventDestroy(ev_in);
@@ -1194,8 +1347,6 @@ static fde_status residual_update_f32(sylv_s* S, const float* d, cudaStream_t st
 //  - kResidF32:   R -= A(δ) in FP32, for the last update of a step: that
 //                 residual only seeds the next step's predicted residual, and
 //                 the next step's first sweep recomputes R exactly.
-enum ResidKind { kResidExact = 0, kResidDF = 1, kResidF32 = 2 };
-
 template <typename T>
 static fde_status sweep_solve(sylv_s* S, Inner<T>& in, double* X64, cudaStream_t st) {
   const size_t NN = (size_t)S->N * S->N;
@@ -1394,6 +1545,278 @@ static fde_status sylv_step_impl(sylv_s* S, const double* C, double* X, cudaStre
     S->cyc_incr = K;
   }
   S->prev_large = large_first;
+  S->ctl_synced = false;
+  return FDE_OK;
+}
+
+// ---------------------------------------------------- whole-step graphs
+// Kernel nodes of a graph (top level only: conditional bodies are counted
+// separately).
+static fde_status count_kernel_nodes(cudaGraph_t g, size_t* n) {
+  size_t cnt = 0;
+  FDE_CUDA(cudaGraphGetNodes(g, nullptr, &cnt));
+  std::vector<cudaGraphNode_t> nodes(cnt);
+  if (cnt) FDE_CUDA(cudaGraphGetNodes(g, nodes.data(), &cnt));
+  *n = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    FDE_CUDA(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) ++*n;
+  }
+  return FDE_OK;
+}
+
+// Appends a conditional node (handle h, `size` bodies) to the graph being
+// captured on `st`, after the stream's current dependencies, and makes it the
+// stream's only dependency.  *bodies: the node's body graphs.
+static fde_status add_conditional(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                  unsigned size, cudaGraph_t** bodies) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  FDE_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) {
+    set_error("sylv: stream not capturing");
+    return FDE_ERR_CUDA;
+  }
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = size;
+  cudaGraphNode_t node;
+  FDE_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  FDE_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  *bodies = p.conditional.phGraph_out;
+  return FDE_OK;
+}
+
+static fde_status capture_graph_of(cudaStream_t st, cudaGraph_t* g) {
+  cudaStreamCaptureStatus cs;
+  FDE_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, g, nullptr, nullptr, nullptr));
+  return FDE_OK;
+}
+
+// One refinement sweep of the FP32 inner solver as a graph body (captured on
+// gs2): Cin = (float) R, inner solve, X += δ with its norms, the controller's
+// decision, a SWITCH over the residual forms (bodies captured on gs3), ||R||²,
+// the controller's stopping test (which sets the enclosing WHILE node).
+static fde_status capture_sweep_body(sylv_s* S, cudaGraph_t body, const double* C, double* X,
+                                     cudaGraphConditionalHandle hloop, sylv_s::StepGraph* sg) {
+  Inner<float>& in = S->in32;
+  const size_t NN = (size_t)S->N * S->N;
+  cudaStream_t s2 = S->gs2, s3 = S->gs3;
+  FDE_CUDA(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  fde_status st = FDE_OK;
+  cudaGraph_t* br = nullptr;
+  cudaGraphConditionalHandle hkind = 0;
+  do {
+    if ((st = convert<double, float>(S->R, in.Cin, NN, s2)) != FDE_OK) break;
+    if ((st = run_inner<float>(S, in, s2)) != FDE_OK) break;
+    refine_update_kernel<float><<<grid_for(NN), 256, 0, s2>>>(X, in.X, NN, S->acc, S->part, S->count);
+    if (cudaGetLastError() != cudaSuccess) { st = FDE_ERR_CUDA; break; }
+    cudaGraph_t bg = nullptr;
+    if ((st = capture_graph_of(s2, &bg)) != FDE_OK) break;
+    if (cudaGraphConditionalHandleCreate(&hkind, bg, 0, 0) != cudaSuccess) { st = FDE_ERR_CUDA; break; }
+    ctl_solve_kernel<<<1, 32, 0, s2>>>(S->ctl, S->acc, hkind);
+    if ((st = add_conditional(s2, hkind, cudaGraphCondTypeSwitch, 3, &br)) != FDE_OK) break;
+    for (int k = 0; k < 3 && st == FDE_OK; ++k) {
+      if (cudaStreamBeginCaptureToGraph(s3, br[k], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+          cudaSuccess) {
+        st = FDE_ERR_CUDA;
+        break;
+      }
+      if (k == kResidExact)
+        st = residual(S, C, X, S->R, s3);
+      else if (k == kResidDF)
+        st = residual_update_df(S, in.X, s3);
+      else
+        st = residual_update_f32(S, in.X, s3);
+      cudaGraph_t g3 = nullptr;
+      const cudaError_t e3 = cudaStreamEndCapture(s3, &g3);
+      if (st == FDE_OK && e3 != cudaSuccess) st = FDE_ERR_CUDA;
+      if (st == FDE_OK) st = count_kernel_nodes(br[k], &sg->k_br[k]);
+    }
+    if (st != FDE_OK) break;
+    sumsq_kernel<<<grid_for(NN), 256, 0, s2>>>(S->R, NN, S->acc + 2, S->part, S->count);
+    ctl_resid_kernel<<<1, 32, 0, s2>>>(S->ctl, S->acc, hloop);
+    if (cudaGetLastError() != cudaSuccess) st = FDE_ERR_CUDA;
+  } while (false);
+  cudaGraph_t g2 = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s2, &g2);
+  if (st != FDE_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  FDE_CUDA(e);
+  return count_kernel_nodes(body, &sg->k_body);
+}
+
+// Captures a whole time step on S->gs: the first part (variant 0: exact
+// residual of the initial guess; 1: linear predictor; 2: residual shift with a
+// new history; 3: residual shift), then the sweeps in a WHILE node.
+static fde_status capture_step(sylv_s* S, sylv_s::StepGraph* sg) {
+  const size_t NN = (size_t)S->N * S->N;
+  const double* C = sg->C;
+  const double* Cp = sg->Cp;
+  double* X = sg->X;
+  cudaStream_t s = S->gs;
+  FDE_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  fde_status st = FDE_OK;
+  do {
+    cudaMemsetAsync(S->d_bad, 0, sizeof(int), s);
+    nonfinite_kernel<<<grid_for(NN), 256, 0, s>>>(C, NN, S->d_bad);
+    sumsq_kernel<<<grid_for(NN), 256, 0, s>>>(C, NN, S->acc + 4, S->part, S->count);
+    if (sg->variant == 0) {
+      if ((st = residual(S, C, X, S->R, s)) != FDE_OK) break;
+    } else if (sg->variant == 1) {
+      predict_kernel<<<grid_for(NN), 256, 0, s>>>(C, Cp, X, S->R, S->Xp, S->Cp, S->Rp, NN);
+      } else if (sg->variant == 2) {
+      shift_save_kernel<<<grid_for(NN), 256, 0, s>>>(C, Cp, X, S->R, S->Xp, S->Cp, S->Rp, NN);
+      } else {
+      shift_residual_kernel<<<grid_for(NN), 256, 0, s>>>(C, Cp, S->R, NN);
+      }
+    cudaGraph_t g = nullptr;
+    if ((st = capture_graph_of(s, &g)) != FDE_OK) break;
+    cudaGraphConditionalHandle hloop = 0;
+    if (cudaGraphConditionalHandleCreate(&hloop, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+      st = FDE_ERR_CUDA;
+      break;
+    }
+    ctl_begin_kernel<<<1, 32, 0, s>>>(S->ctl, S->d_bad, sg->variant == 0 ? 0 : 1, hloop);
+    if (cudaGetLastError() != cudaSuccess) {
+      st = FDE_ERR_CUDA;
+      break;
+    }
+    cudaGraph_t* body = nullptr;
+    if ((st = add_conditional(s, hloop, cudaGraphCondTypeWhile, 1, &body)) != FDE_OK) break;
+    st = capture_sweep_body(S, body[0], C, X, hloop, sg);
+  } while (false);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st != FDE_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (st != FDE_OK) return st;
+    FDE_CUDA(e);
+  }
+  st = count_kernel_nodes(g, &sg->k_pre);
+  if (st == FDE_OK) {
+    const cudaError_t ei = cudaGraphInstantiate(&sg->exec, g, 0);
+    if (ei != cudaSuccess) {
+      set_error("sylv: whole-step graph instantiation failed: %s", cudaGetErrorString(ei));
+      st = FDE_ERR_CUDA;
+    }
+  }
+  cudaGraphDestroy(g);
+  return st;
+}
+
+static fde_status ctl_upload(sylv_s* S, cudaStream_t st) {
+  StepCtl h{};
+  const sylv_refine_t& rf = S->refine;
+  h.tol2_update = rf.tol_update * rf.tol_update;
+  h.tol2_relres = rf.tol_relres * rf.tol_relres;
+  h.incr_tol2 = S->incr_tol * S->incr_tol;
+  h.max_sweeps = rf.max_sweeps;
+  h.exact_every = S->exact_every;
+  h.resid_df = S->resid_df ? 1 : 0;
+  h.f32_last = S->resid_f32_last ? 1 : 0;
+  h.f32_last_all = S->f32_last_all ? 1 : 0;
+  h.cyc_streak = S->cyc_streak;
+  h.cyc_incr = S->cyc_incr;
+  h.prev_large = S->prev_large ? 1 : 0;
+  h.status = FDE_OK;
+  FDE_CUDA(cudaMemcpyAsync(S->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+  FDE_CUDA(cudaStreamSynchronize(st));
+  return FDE_OK;
+}
+
+// One time step as one graph launch (no host synchronisation); results and
+// errors are read by sylv_graph_collect.
+static fde_status step_graph_impl(sylv_s* S, const double* C, double* X, cudaStream_t st, const double* C_prev) {
+  if (!S->ctl_synced) {
+    FDE_TRY(ctl_upload(S, st));
+    FDE_CUDA(cudaMemcpyAsync(S->tc_base, S->tc_count, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st));
+    S->ctl_synced = true;
+  }
+  const bool in_chain = C_prev && S->R_valid;
+  const int variant = !in_chain ? 0 : (S->predict && S->hist) ? 1 : S->predict ? 2 : 3;
+  sylv_s::StepGraph* sg = nullptr;
+  for (auto& g : S->sgraphs)
+    if (g.variant == variant && g.C == C && g.Cp == (in_chain ? C_prev : nullptr) && g.X == X) sg = &g;
+  if (!sg) {
+    if (!S->gs) {
+      FDE_CUDA(cudaStreamCreateWithFlags(&S->gs, cudaStreamNonBlocking));
+      FDE_CUDA(cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming));
+      FDE_CUDA(cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming));
+    }
+    if (!S->gs2) FDE_CUDA(cudaStreamCreateWithFlags(&S->gs2, cudaStreamNonBlocking));
+    if (!S->gs3) FDE_CUDA(cudaStreamCreateWithFlags(&S->gs3, cudaStreamNonBlocking));
+    sylv_s::StepGraph g;
+    g.variant = variant;
+    g.C = C;
+    g.Cp = in_chain ? C_prev : nullptr;
+    g.X = X;
+    count_suspend(true);  // a capture launches nothing: its kernels are counted per replay
+    const fde_status cs = capture_step(S, &g);
+    count_suspend(false);
+    FDE_TRY(cs);
+    S->sgraphs.push_back(g);
+    sg = &S->sgraphs.back();
+  }
+  FDE_CUDA(cudaEventRecord(S->ev_in, st));
+  FDE_CUDA(cudaStreamWaitEvent(S->gs, S->ev_in, 0));
+  FDE_CUDA(cudaGraphLaunch(sg->exec, S->gs));
+  FDE_CUDA(cudaEventRecord(S->ev_out, S->gs));
+  FDE_CUDA(cudaStreamWaitEvent(st, S->ev_out, 0));
+  S->graph_pending.push_back(sg - S->sgraphs.data());
+  S->hist = (in_chain && S->predict) ? 1 : 0;
+  S->R_valid = true;
+  return FDE_OK;
+}
+
+static fde_status graph_collect_impl(sylv_s* S, cudaStream_t st, int* steps, int* sweeps_total, int* sweeps_max,
+                                     double* relres_max) {
+  *steps = *sweeps_total = *sweeps_max = 0;
+  *relres_max = 0.0;
+  if (!S->ctl_synced) return FDE_OK;
+  StepCtl h{};
+  unsigned int tc[2] = {0u, 0u};
+  FDE_CUDA(cudaMemcpyAsync(&h, S->ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
+  FDE_CUDA(cudaMemcpyAsync(tc, S->tc_base, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  FDE_CUDA(cudaMemcpyAsync(tc + 1, S->tc_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  FDE_CUDA(cudaStreamSynchronize(st));
+  // kernels these graph launches ran: first parts, sweep bodies and residual branches
+  unsigned long long k = 0;
+  for (size_t i : S->graph_pending) k += S->sgraphs[i].k_pre;
+  if (!S->graph_pending.empty()) {
+    const sylv_s::StepGraph& g = S->sgraphs[S->graph_pending.back()];
+    k += (unsigned long long)h.sweeps_total * g.k_body;
+    for (int i = 0; i < 3; ++i) k += (unsigned long long)h.kind_count[i] * g.k_br[i];
+  }
+  count_launches(k);
+  S->graph_pending.clear();
+  *steps = h.steps;
+  *sweeps_total = h.sweeps_total;
+  *sweeps_max = h.sweeps_max;
+  *relres_max = h.relres_max;
+  S->cyc_streak = h.cyc_streak;
+  S->cyc_incr = h.cyc_incr;
+  S->prev_large = h.prev_large != 0;
+  S->ctl_synced = false;  // the next graph step re-uploads (clears the results)
+  if (tc[1] != tc[0]) {
+    S->R_valid = false;
+    set_error("sylv_step: a bounded wait of the tensor-core GEMM expired (%u)", tc[1] - tc[0]);
+    return FDE_ERR_CUDA;
+  }
+  if (h.status != FDE_OK) {
+    S->R_valid = false;
+    set_error(h.status == FDE_ERR_NUMERIC ? "sylv_step: non-finite data in a whole-step graph"
+                                          : "sylv_step: no convergence within the sweep cap in a whole-step graph");
+    return (fde_status)h.status;
+  }
   return FDE_OK;
 }
 
@@ -1745,6 +2168,13 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
   FDE_TRY(pool.alloc(&S->part, 2 * (size_t)kSumBlocks));
   FDE_TRY(pool.alloc(&S->count, 1));
   FDE_CUDA(cudaMemsetAsync(S->count, 0, sizeof(unsigned int), st));
+  if (prec != FDE_FP64) {
+    // time loops run every step of the FP32 inner solver as one graph launch
+    // (FDE_STEP_GRAPH=0: eager steps with a host decision after every sweep)
+    const char* sg = getenv("FDE_STEP_GRAPH");
+    S->step_graph = !(sg && strcmp(sg, "0") == 0);
+    FDE_TRY(pool.alloc(&S->ctl, 1));
+  }
   FDE_TRY(tc_timeout_counter(&S->tc_count));
   FDE_TRY(pool.alloc(&S->tc_base, 1));
   FDE_CUDA(cudaMemcpyAsync(S->tc_base, S->tc_count, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st));
@@ -1921,6 +2351,16 @@ namespace fde {
 fde_status sylv_step_internal(sylv_s* s, const double* C, double* X, cudaStream_t st, double* relres, int* sweeps,
                               const double* C_prev) {
   return sylv_step_impl(s, C, X, st, relres, sweeps, C_prev);
+}
+// Profiling brackets every launch with events, which a graph cannot hold:
+// profiled steps run eagerly.
+bool sylv_graph_steps(sylv_s* s) { return s->step_graph && !prof_enabled(); }
+fde_status sylv_step_graph(sylv_s* s, const double* C, double* X, cudaStream_t st, const double* C_prev) {
+  return step_graph_impl(s, C, X, st, C_prev);
+}
+fde_status sylv_graph_collect(sylv_s* s, cudaStream_t st, int* steps, int* sweeps_total, int* sweeps_max,
+                              double* relres_max) {
+  return graph_collect_impl(s, st, steps, sweeps_total, sweeps_max, relres_max);
 }
 int sylv_N(sylv_s* s) { return s->N; }
 }  // namespace fde

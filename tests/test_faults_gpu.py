@@ -144,3 +144,36 @@ def test_expired_gemm_wait_is_reported(lib):
         assert np.linalg.norm(X - Xo) <= 1e-10 * np.linalg.norm(Xo) and relres < 1e-10
     finally:
         _free(lib, ax, ay, s)
+
+
+def test_whole_step_graph_errors(lib):
+    """Errors inside a whole-step graph (the device controller records them,
+    the host reads them once the launched steps are collected): a non-finite
+    source field gives FDE_ERR_NUMERIC, an expired tensor-core wait
+    FDE_ERR_CUDA; afterwards the runner, reloaded, steps correctly."""
+    N = 256
+    w = I.fd2d(N=N, alpha=(1.3, 1.7), steps=50, leaf=64)
+    U0 = _dev(w.u0)
+    r = lib.runner_create(lib.run_params(w, prec=B.FDE_FP32_REFINE), U0.data_ptr())
+    try:
+        lib.runner_advance(r, 2)
+        F = np.zeros((N, N))
+        F[3, 4] = np.nan
+        assert _status(lib.runner_step_source, r, F.ctypes.data, N) == B.FDE_ERR_NUMERIC
+        lib.runner_load(r, U0.data_ptr(), 0)
+        lib.set_wait_limit(2)
+        try:
+            st = _status(lib.runner_advance, r, 2)
+        finally:
+            lib.set_wait_limit(0)
+        assert st == B.FDE_ERR_CUDA, st
+        lib.runner_load(r, U0.data_ptr(), 0)
+        lib.runner_advance(r, 3)
+        X = torch.empty_like(U0)
+        lib.runner_state(r, X.data_ptr())
+        torch.cuda.synchronize()
+        Xo = O.fde2d_run(w, steps=3)
+        got = X.cpu().numpy().reshape((N, N), order="F")
+        assert np.linalg.norm(got - Xo) <= 1e-8 * np.linalg.norm(Xo)
+    finally:
+        lib.runner_free(r)

@@ -423,3 +423,39 @@ def test_fde_run_2d_alpha2(lib, prec):
     U = _host(Uo, 96, 96)
     assert _relerr(U, O.fde2d_run(w)) <= (1e-10 if prec == B.FDE_FP64 else 1e-8)
     assert st.relres_max < 1e-9
+
+
+def test_whole_step_graph_matches_eager_steps(lib, monkeypatch):
+    """Time steps as one CUDA graph launch each (device-side refinement
+    control: a WHILE node over the sweeps, a SWITCH node over the residual
+    forms) against the same steps run eagerly with the decisions on the host:
+    the same kernels in the same order take the same decisions, so the states
+    agree bit for bit, with the same sweep counts, over 20 steps (two refresh
+    pairs and incremental chains), and both follow the oracle."""
+    monkeypatch.delenv("FDE_RESID", raising=False)
+    monkeypatch.delenv("FDE_EXACT_EVERY", raising=False)
+    w = I.fd2d(N=256, alpha=(1.3, 1.7), steps=50, leaf=64)
+    Uref = O.fde2d_run(w, steps=20)
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("FDE_STEP_GRAPH", mode)
+        rp = lib.run_params(w, prec=B.FDE_FP32_REFINE)
+        U0 = _dev(w.u0)
+        r = lib.runner_create(rp, U0.data_ptr())
+        try:
+            c0 = lib.launch_count()
+            for _ in range(4):
+                lib.runner_advance(r, 5)
+            launches = lib.launch_count() - c0
+            st = lib.runner_stats(r)
+            X = torch.empty_like(U0)
+            lib.runner_state(r, X.data_ptr())
+            torch.cuda.synchronize()
+            out[mode] = (_host(X, w.N, w.N), st.sweeps_total, st.sweeps_max, launches)
+        finally:
+            lib.runner_free(r)
+    assert np.array_equal(out["1"][0], out["0"][0])
+    assert out["1"][1:3] == out["0"][1:3], (out["1"][1:], out["0"][1:])
+    # launches counted per graph replay: within the eager count's range
+    assert 0.5 * out["0"][3] <= out["1"][3] <= 1.5 * out["0"][3], (out["1"][3], out["0"][3])
+    assert _relerr(out["1"][0], Uref) <= 1e-8
