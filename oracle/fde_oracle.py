@@ -37,6 +37,10 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   min_row_sum /              pinned: dense row sums; ||K^{-1}||_∞ of the
   sylvester_error_bound        dense Kronecker matrix; the bound holds and is
                                attained for a constant error
+  sym_part_exceeds /         pinned: eigenvalues of the symmetric part on
+  sylvester_error_bound_fro    both sides of θ; ||K^{-1}||_2 of the dense
+                               Kronecker matrix; the bound holds for random
+                               errors
   sylvester_residual         pinned: X = 0, Kronecker solution, Kronecker
                              product of a perturbation
   lowrank_from_dense         pinned: prescribed singular values
@@ -586,3 +590,27 @@ def sylvester_error_bound(opx, opy, r_maxabs: float) -> float:
     loop whose right-hand sides are formed from the loop's own states, the
     errors of the steps add: e_m = K^{-1}(e_{m-1} - r_m), and μ >= s_x + s_y = 1."""
     return r_maxabs / (min_row_sum(opx) + min_row_sum(opy))
+
+
+def sym_part_exceeds(op, theta: float) -> bool:
+    """True when the symmetric part (A + Aᵀ)/2 of A (Eq. (system_FD)) minus
+    θ I is positive definite, i.e. λ_min((A + Aᵀ)/2) > θ: Cholesky
+    factorisation (LAPACK potrf) of the dense matrix succeeds."""
+    A = fd_operator(op)
+    S = 0.5 * (A + A.T) - theta * np.eye(op.N)
+    try:
+        sla.cholesky(S, lower=True, check_finite=False)
+    except np.linalg.LinAlgError:
+        return False
+    return True
+
+
+def sylvester_error_bound_fro(r_fro: float, theta_x: float, theta_y: float) -> float:
+    """Bound on ||X - X*||_F for A_x X + X A_yᵀ = C from ||R||_F, when
+    λ_min((A_x + A_xᵀ)/2) >= θ_x and λ_min((A_y + A_yᵀ)/2) >= θ_y: the
+    symmetric part of K = I ⊗ A_x + A_y ⊗ I (§4.2) is then >= (θ_x + θ_y) I,
+    so ||K v|| ||v|| >= vᵀ K v >= (θ_x + θ_y) ||v||² and
+    ||X - X*||_F = ||K^{-1} vec R|| <= ||R||_F / (θ_x + θ_y).  Over an
+    implicit-Euler loop (e_m = K^{-1}(e_{m-1} - r_m)) with θ_x + θ_y >= 1
+    the bounds of the steps add."""
+    return r_fro / (theta_x + theta_y)

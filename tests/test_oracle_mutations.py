@@ -109,6 +109,10 @@ def _qsrank_M_inverted(N, eps, normM, normT, maxD):
 def _min_row_sum_max(op):
     return float(np.max(_orig["apply_fd_operator_fft"](op, np.ones((op.N, 1)), 0)))
 
+
+def _sym_part_always(op, theta):
+    return True
+
 def _norm_squared(A, iters=30):
     return _orig["norm2_power"](A, iters) ** 2
 
@@ -240,6 +244,7 @@ MUTATIONS = [
     ("truncate_lowrank", _truncate_scaled, P.test_truncate_lowrank_prescribed_spectrum),
     ("beckermann_bound", _beckermann_pi, lambda: P.test_beckermann_bound_on_psd_hankel(256)),
     ("norm2_power", _norm_squared, P.test_norm2_power),
+    ("sym_part_exceeds", _sym_part_always, P.test_sym_part_and_frobenius_error_bound),
     ("min_row_sum", _min_row_sum_max, P.test_mmatrix_error_bound),
     ("qsrank_bound_T", _qsrank_T_full_eps, P.test_qsrank_bounds_hand_evaluated),
     ("qsrank_bound_M", _qsrank_M_one_plus, P.test_qsrank_bounds_hand_evaluated),

@@ -988,3 +988,33 @@ def test_mmatrix_error_bound():
     E = O.sylvester_bartels_stewart(Ax2, Ay2, np.ones((24, 24)))
     assert np.abs(E).max() <= O.sylvester_error_bound(wl.ops[0], wl.ops[1], 1.0) * (1 + 1e-12)
     assert np.abs(E).max() >= 0.9 * O.sylvester_error_bound(wl.ops[0], wl.ops[1], 1.0)
+
+
+def test_sym_part_and_frobenius_error_bound():
+    """sym_part_exceeds against the eigenvalues of the symmetric part (just
+    below and just above λ_min), and sylvester_error_bound_fro against the
+    dense Kronecker matrix: σ_min(K) >= λ_min(sym A_x) + λ_min(sym A_y), and
+    the bound holds for random errors."""
+    w = I.fd2d(N=24, alpha=(1.3, 1.7), steps=10, leaf=8)
+    lam = []
+    for op in w.ops:
+        A = O.fd_operator(op)
+        l0 = np.linalg.eigvalsh(0.5 * (A + A.T))[0]
+        assert O.sym_part_exceeds(op, l0 - 1e-6 * abs(l0))
+        assert not O.sym_part_exceeds(op, l0 + 1e-6 * abs(l0))
+        lam.append(l0)
+    Ax, Ay = O.fd_operator(w.ops[0]), O.fd_operator(w.ops[1])
+    n = w.N
+    K = np.kron(np.eye(n), Ax) + np.kron(Ay, np.eye(n))
+    smin = np.linalg.svd(K, compute_uv=False)[-1]
+    assert smin >= (lam[0] + lam[1]) * (1 - 1e-12)
+    for seed in range(3):
+        E = I.random_matrix(n, n, seed=60 + seed)
+        R = Ax @ E + E @ Ay.T
+        assert np.linalg.norm(E) <= O.sylvester_error_bound_fro(np.linalg.norm(R), lam[0], lam[1]) * (1 + 1e-12)
+    # a wrong theta direction would not be a bound: with sym(A) >= theta
+    # replaced by the largest eigenvalue the inequality fails for some error
+    big = [np.linalg.eigvalsh(0.5 * (M + M.T))[-1] for M in (Ax, Ay)]
+    v = np.linalg.svd(K)[2][-1].reshape((n, n), order="F")
+    Rv = Ax @ v + v @ Ay.T
+    assert np.linalg.norm(v) > O.sylvester_error_bound_fro(np.linalg.norm(Rv), big[0], big[1])
