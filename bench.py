@@ -293,6 +293,21 @@ def read_golden(name: str):
     return g
 
 
+def read_sympart(name: str):
+    """theta_x + theta_y for the Frobenius error bound of the workload when the
+    oracle found lambda_min((A + A^T)/2) > theta on both sides
+    (tests/golden/sympart.txt), else None."""
+    path = os.path.join(GOLDEN_DIR, "sympart.txt")
+    if not os.path.exists(path):
+        return None
+    th = {}
+    for line in open(path):
+        f = line.split("#")[0].split()
+        if len(f) == 4 and f[0] == name and f[3] == "1":
+            th[f[1]] = float(f[2])
+    return th["x"] + th["y"] if len(th) == 2 else None
+
+
 def compare_golden(X: np.ndarray, e: dict, N: int) -> dict:
     """Errors of a state X (N x N) against the stored oracle values of one
     step: Frobenius relative error estimated from the sampled entries
@@ -323,15 +338,18 @@ def verify_run(lib, name, w, r, U0, steps: int, stream):
 
     N = w.N
     mu = sum(lib.fde_block_interval(lib.op_params(op), 0, N)[0] for op in w.ops)
+    theta = read_sympart(name)
     golden = read_golden(name)
     lib.runner_load(r, U0.data_ptr(), 0, stream)
-    bound, relres_max, step_max, checked = 0.0, 0.0, 0.0, {}
+    bound, bound_fro, relres_max, step_max, checked = 0.0, 0.0, 0.0, 0.0, {}
     X = torch.empty_like(U0)
     for m in range(1, steps + 1):
         lib.runner_advance(r, 1, stream)
-        rel, mx = lib.runner_residual(r, stream)
+        rel, mx, fro = lib.runner_residual(r, stream)
         relres_max = max(relres_max, rel)
         bound += mx / mu
+        if theta:
+            bound_fro += fro / theta
         lib.runner_state(r, X.data_ptr(), stream)
         torch.cuda.synchronize()
         step_max = max(step_max, mx / mu / float(X.abs().max()))
@@ -339,12 +357,16 @@ def verify_run(lib, name, w, r, U0, steps: int, stream):
             Xh = X.cpu().numpy().reshape((N, N), order="F")
             checked[m] = compare_golden(Xh, golden[m], N)
     xmax = float(X.abs().max())
+    xfro = float(torch.linalg.norm(X))
     out = {"steps": steps, "relres_exact_max": relres_max, "mu": mu,
+           "error_bound_fro_loop_rel": bound_fro / xfro if theta else None,
            "error_bound_step_max_rel": step_max,
            "error_bound_loop_max_abs_rel": bound / xmax,
-           "error_bound": "per step max|U - U*| <= max|R| / mu for that step's Sylvester equation (R its exact "
-                          "FP64 residual; A_x, A_y M-matrices, mu the sum of their smallest row sums); over the "
-                          "loop these add (loop bound after the last step), both relative to max|U|"}
+           "error_bound": "bounds on the error against the exact time loop from the exact FP64 residuals R_k of "
+                          "the steps: ||U - U*||_F <= sum_k ||R_k||_F / (theta_x + theta_y) with theta = 1/2 <= "
+                          "lambda_min((A + A^T)/2) per side (checked by the oracle, tests/golden/sympart.txt), "
+                          "relative to ||U||_F; max|U - U*| <= sum_k max|R_k| / mu (A_x, A_y M-matrices, mu the "
+                          "sum of their smallest row sums), per step and over the loop, relative to max|U|"}
     if checked:
         last = max(checked)
         out["oracle_step"] = last
@@ -479,15 +501,16 @@ def run_ours(args, rank, world, local_rank):
             hf = torch.empty(N * N, dtype=torch.float64, pin_memory=True)
             hf.copy_(torch.from_numpy(np.asfortranarray(F).ravel(order="F")))
             host_F.append(hf)
-        host_out = torch.empty(N * N, dtype=torch.float64, pin_memory=True)
+        host_out = [torch.empty(N * N, dtype=torch.float64, pin_memory=True) for _ in range(args.e2e_steps)]
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record()
         for i in range(args.e2e_steps):
-            lib.runner_step_source(r32, host_F[i].data_ptr(), N, stream)   # H2D of the step's input
-            lib.runner_state(r32, host_out.data_ptr(), stream)               # D2H of the step's result
+            lib.runner_step_source_async(r32, host_F[i].data_ptr(), N, stream)   # H2D of the step's input
+            lib.runner_state_async(r32, host_out[i].data_ptr(), stream)          # D2H of the step's result
+        lib.runner_sync(r32, stream)  # every read-back has landed in host memory
         g1.record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -496,7 +519,9 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": replica_rate(world, args.e2e_steps, ems), "unit": "steps/s",
                "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8,
                "host_wall_steps_per_s": args.e2e_steps / wall,
-               "input": "dense source F^(m+1) (N x N FP64) uploaded per step; state U^(m+1) read back"}
+               "input": "dense source F^(m+1) (N x N FP64, pinned host) uploaded per step; state U^(m+1) read "
+                        "back to pinned host memory per step; copies on the runner's copy stream overlap the "
+                        "steps (fde_runner_step_source_async / fde_runner_state_async / fde_runner_sync)"}
     accuracy = None
     if args.verify_steps > 0 and rank == 0:
         accuracy = verify_run(lib, args.workload, w, r32, U0, min(args.verify_steps, w.steps), stream)
@@ -582,6 +607,64 @@ def run_batch(args, rank, world, local_rank):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ 1D, time-dependent D±
+def run_tv(args, rank, world, local_rank):
+    """1D N=1024 (alpha = 1.5, dt = 1/32) with time-dependent coefficients
+    D_±^{(m)} = (1 + t_m) D_±: every step samples the coefficients at its new
+    time level on the host, rebuilds and refactors the HODLR operator
+    (construction and factorisation inside the step), then solves with FP64
+    refinement.  Metric: time steps per second."""
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    from paper_1804_05522_gb300 import binding as B
+
+    lib = B.load()
+    w = I.fd1d(N=1024, alpha=1.5, steps=32, leaf=64, tol=1e-10)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    dp0, dm0 = w.ops[0].d_plus.copy(), w.ops[0].d_minus.copy()
+    U0 = torch.from_numpy(w.u0.copy()).to(dev)
+    r = lib.runner_create(lib.run_params(w, prec=B.FDE_FP64), U0.data_ptr(), stream)
+    coeffs = [((1.0 + m * w.dt) * dp0, (1.0 + m * w.dt) * dm0) for m in range(args.warmup + args.steps + 2)]
+
+    def step(m):
+        lib.runner_set_coefficients(r, coeffs[m][0], coeffs[m][1], None, None, stream)
+        lib.runner_advance(r, 1, stream)
+
+    for m in range(1, args.warmup + 1):
+        step(m)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = lib.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for m in range(args.warmup + 1, args.warmup + args.steps + 1):
+        step(m)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks([e0.elapsed_time(e1)], world, dev)[0]
+    clk = clocks.stop()
+    launches = lib.launch_count() - launches0
+    st = lib.runner_stats(r)
+    lib.runner_free(r)
+    if rank != 0:
+        return
+    value = replica_rate(world, args.steps, ms)
+    out = {"metric": "1D FDE time steps/s with time-dependent coefficients (operator rebuilt and refactored "
+                     "every step)", "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "fd1d_tv_n1024: 1D N=1024, alpha=1.5, dt=1/32, D_pm^(m) = (1 + t_m) D_pm, "
+                                  "leaf 64, HODLR tol 1e-10, FP64", "N": 1024,
+                      "sweeps_max": st.sweeps_max, "kmax": st.kmax_x},
+           "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------ reference
 def run_reference(args, rank, world):
     if rank != 0:
@@ -638,6 +721,8 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "batch64":
         run_batch(args, rank, world, local_rank)
+    elif args.workload == "fd1d_tv_n1024":
+        run_tv(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

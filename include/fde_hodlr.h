@@ -300,17 +300,46 @@ fde_status fde_runner_load(fde_runner_t r, const double* U, int step_index, void
  * fde_runner_advance; fde_runner_load resets it. */
 fde_status fde_runner_step_source(fde_runner_t r, const double* F, int ldf, void* stream);
 fde_status fde_runner_state(fde_runner_t r, double* U_out, void* stream);
+/* Pipelined host I/O for serving loops that feed a source field and read the
+ * state back every step.  fde_runner_step_source_async is
+ * fde_runner_step_source without host synchronisation: with a host F the
+ * copy runs on the runner's own upload stream into one of two device buffers
+ * while the previous steps compute (F must be page-locked for the copy to be
+ * asynchronous, and must stay unchanged until fde_runner_sync).
+ * fde_runner_state_async enqueues a device snapshot of the state on `stream`
+ * and its copy into U_out (host, page-locked; a device pointer is copied on
+ * `stream`) on the runner's read-back stream, overlapping the next steps; U_out is valid
+ * after fde_runner_sync.  fde_runner_sync waits for all three streams and returns
+ * the first error of the steps launched since the last synchronisation (the
+ * state is then undefined until fde_runner_load); the synchronous calls on
+ * the runner do the same first.  Without whole-step graphs (FP64 inner
+ * solver, FDE_STEP_GRAPH=0) the step call is the synchronous one. */
+fde_status fde_runner_step_source_async(fde_runner_t r, const double* F, int ldf, void* stream);
+fde_status fde_runner_state_async(fde_runner_t r, double* U_out, void* stream);
+fde_status fde_runner_sync(fde_runner_t r, void* stream);
+/* Time-dependent coefficients (Eq. (system_FD) with D_±^{(m)}): the diagonals
+ * of D_± for the NEXT step, sampled by the caller at its new time level
+ * t_{m+1} (host or device pointers, length N, finite, >= 0; d_plus_y /
+ * d_minus_y for 2D, ignored in 1D).  The runner rebuilds its operators (HODLR
+ * build and factorisation in 1D; both HODLR operators and the Sylvester solver
+ * in 2D) and starts the next step from U^{(m)} with an exact residual, since
+ * its residual history belongs to the old operator.  The coefficients stay
+ * in force until the next call.  The rebuild's time counts in the runner's
+ * solve time.  On an error the old operators are kept. */
+fde_status fde_runner_set_coefficients(fde_runner_t r, const double* d_plus_x, const double* d_minus_x,
+                                       const double* d_plus_y, const double* d_minus_y, void* stream);
 /* Exact FP64 residual of the runner's current state against the right-hand
  * side of the step that produced it (Eq. (system_FD) in 1D: b - A u; Eq.
  * (sylv-timestepping) in 2D: C - A_x U - U A_yᵀ, Toeplitz products by FFT),
  * whatever residual form the refinement used inside the step.  *relres
- * (host) = ||R||_F / ||C||_F, *maxabs (host) = max |R_ij|; deterministic.
- * With the smallest row sums m_x, m_y of A_x, A_y (both M-matrices, §2.2.1;
- * fde_block_interval over [0, N) gives them as lam_lo), max|U - U*| <=
- * maxabs / (m_x + m_y) for the exact solution U* of that step's equation.
- * Synchronises `stream`.  FDE_ERR_ARG if no step was taken since
- * fde_runner_create / fde_runner_load. */
-fde_status fde_runner_residual(fde_runner_t r, double* relres, double* maxabs, void* stream);
+ * (host) = ||R||_F / ||C||_F, *maxabs (host) = max |R_ij|, *fro (host, may be
+ * NULL) = ||R||_F; deterministic.  For the exact solution U* of that step's
+ * equation: with the smallest row sums m_x, m_y of A_x, A_y (both
+ * M-matrices, §2.2.1; fde_block_interval over [0, N) gives them as lam_lo),
+ * max|U - U*| <= maxabs / (m_x + m_y); with λ_min((A + Aᵀ)/2) >= θ_x, θ_y,
+ * ||U - U*||_F <= fro / (θ_x + θ_y).  Synchronises `stream`.  FDE_ERR_ARG if
+ * no step was taken since fde_runner_create / fde_runner_load. */
+fde_status fde_runner_residual(fde_runner_t r, double* relres, double* maxabs, double* fro, void* stream);
 fde_status fde_runner_stats(fde_runner_t r, fde_run_stats* stats);
 void fde_runner_free(fde_runner_t r);
 

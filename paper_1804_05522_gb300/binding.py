@@ -94,7 +94,12 @@ _SIGS = {
     "fde_runner_advance": ([_P, C.c_int, _P], C.c_int),
     "fde_runner_load": ([_P, _P, C.c_int, _P], C.c_int),
     "fde_runner_state": ([_P, _P, _P], C.c_int),
-    "fde_runner_residual": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], C.c_int),
+    "fde_runner_residual": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), _P],
+                            C.c_int),
+    "fde_runner_set_coefficients": ([_P, _P, _P, _P, _P, _P], C.c_int),
+    "fde_runner_step_source_async": ([_P, _P, C.c_int, _P], C.c_int),
+    "fde_runner_state_async": ([_P, _P, _P], C.c_int),
+    "fde_runner_sync": ([_P, _P], C.c_int),
     "fde_runner_stats": ([_P, C.POINTER(RunStats)], C.c_int),
     "fde_runner_free": ([_P], None),
     "fde_launch_count": ([], C.c_ulonglong),
@@ -325,6 +330,15 @@ class Lib:
     def runner_step_source(self, r: int, F: int, ldf: int, stream: int = 0):
         self.check(self.dll.fde_runner_step_source(r, F, ldf, stream))
 
+    def runner_step_source_async(self, r: int, F: int, ldf: int, stream: int = 0):
+        self.check(self.dll.fde_runner_step_source_async(r, F, ldf, stream))
+
+    def runner_state_async(self, r: int, U: int, stream: int = 0):
+        self.check(self.dll.fde_runner_state_async(r, U, stream))
+
+    def runner_sync(self, r: int, stream: int = 0):
+        self.check(self.dll.fde_runner_sync(r, stream))
+
     def runner_advance(self, r: int, nsteps: int, stream: int = 0):
         self.check(self.dll.fde_runner_advance(r, nsteps, stream))
 
@@ -335,10 +349,22 @@ class Lib:
         self.check(self.dll.fde_runner_state(r, U, stream))
 
     def runner_residual(self, r: int, stream: int = 0):
-        """(||R||_F / ||C||_F, max |R_ij|) of the last step, exact FP64."""
-        rr, mx = C.c_double(), C.c_double()
-        self.check(self.dll.fde_runner_residual(r, C.byref(rr), C.byref(mx), stream))
-        return rr.value, mx.value
+        """(||R||_F / ||C||_F, max |R_ij|, ||R||_F) of the last step, exact FP64."""
+        rr, mx, fr = C.c_double(), C.c_double(), C.c_double()
+        self.check(self.dll.fde_runner_residual(r, C.byref(rr), C.byref(mx), C.byref(fr), stream))
+        return rr.value, mx.value, fr.value
+
+    def runner_set_coefficients(self, r: int, dpx, dmx, dpy=None, dmy=None, stream: int = 0):
+        """D_± of the next step (host arrays, or device addresses as ints)."""
+        held = []  # host copies live until the call returns (it synchronises)
+
+        def ptr(a):
+            if a is None or isinstance(a, int):
+                return a
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            held.append(a)
+            return a.ctypes.data
+        self.check(self.dll.fde_runner_set_coefficients(r, ptr(dpx), ptr(dmx), ptr(dpy), ptr(dmy), stream))
 
     def runner_stats(self, r: int) -> RunStats:
         st = RunStats()

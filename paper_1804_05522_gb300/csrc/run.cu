@@ -147,7 +147,30 @@ struct fde_runner_s {
   bool c_valid = false;          // C holds the right-hand side of the current state's step
   int N = 0, step = 0;
   fde_run_stats stats{};
+  // pipelined host I/O (fde_runner_step_source_async / fde_runner_state_async):
+  // copy streams for uploads (cs) and read-backs (cs_out), so that an upload
+  // never queues behind a read-back that waits for a step; two device source
+  // buffers and a snapshot of the state
+  cudaStream_t cs = nullptr, cs_out = nullptr;
+  double* Fb[2] = {nullptr, nullptr};
+  double* Usnap = nullptr;
+  int fk = 0;
+  cudaEvent_t ev_fready[2] = {nullptr, nullptr}, ev_fused[2] = {nullptr, nullptr};
+  cudaEvent_t ev_snap = nullptr, ev_d2h = nullptr;
+  bool pending = false;          // launched whole-step graphs not collected yet
   ~fde_runner_s() {
+    if (cs) cudaStreamSynchronize(cs);
+    for (int k = 0; k < 2; ++k) {
+      if (ev_fready[k]) cudaEventDestroy(ev_fready[k]);
+      if (ev_fused[k]) cudaEventDestroy(ev_fused[k]);
+    }
+    if (ev_snap) cudaEventDestroy(ev_snap);
+    if (ev_d2h) cudaEventDestroy(ev_d2h);
+    if (cs_out) {
+      cudaStreamSynchronize(cs_out);
+      cudaStreamDestroy(cs_out);
+    }
+    if (cs) cudaStreamDestroy(cs);
     sylv_free(s);
     hodlr_free(ax);
     hodlr_free(ay);
@@ -244,6 +267,13 @@ static fde_status collect_graph_steps(fde_runner_s* R, cudaStream_t st) {
   R->stats.sweeps_max = std::max(R->stats.sweeps_max, mx);
   R->stats.relres_max = std::max(R->stats.relres_max, rel);
   return FDE_OK;
+}
+
+// Steps launched by fde_runner_step_source_async and not collected yet.
+static fde_status flush_async(fde_runner_s* r, cudaStream_t st) {
+  if (!r->pending) return FDE_OK;
+  r->pending = false;
+  return collect_graph_steps(r, st);
 }
 
 static fde_status runner_advance(fde_runner_s* R, int nsteps, cudaStream_t st) {
@@ -351,6 +381,7 @@ extern "C" fde_status fde_runner_create(const fde_run_params* p, const double* U
 extern "C" fde_status fde_runner_advance(fde_runner_t r, int nsteps, void* stream) {
   FDE_ARG(r != nullptr, "runner is NULL");
   FDE_ARG(nsteps >= 0, "nsteps must be >= 0");
+  FDE_TRY(flush_async(r, (cudaStream_t)stream));
   return runner_advance(r, nsteps, (cudaStream_t)stream);
 }
 
@@ -359,6 +390,7 @@ extern "C" fde_status fde_runner_step_source(fde_runner_t r, const double* F, in
   FDE_ARG(r->p.dim == 2, "fde_runner_step_source is for 2D runners");
   const int N = r->N;
   FDE_ARG(ldf >= N, "ldf < N");
+  FDE_TRY(flush_async(r, (cudaStream_t)stream));
   cudaStream_t st = (cudaStream_t)stream;
   const double t1 = now_seconds();
   const double dt = r->p.op_x.dt;
@@ -400,9 +432,104 @@ extern "C" fde_status fde_runner_step_source(fde_runner_t r, const double* F, in
   return FDE_OK;
 }
 
+// ------------------------------------------------ pipelined host I/O
+static fde_status io_prepare(fde_runner_s* r, cudaStream_t st) {
+  if (r->cs) return FDE_OK;
+  const size_t NN = (size_t)r->N * r->N;
+  FDE_TRY(r->pool.alloc(&r->Fb[0], NN));
+  FDE_TRY(r->pool.alloc(&r->Fb[1], NN));
+  FDE_TRY(r->pool.alloc(&r->Usnap, NN));
+  FDE_CUDA(cudaStreamCreateWithFlags(&r->cs, cudaStreamNonBlocking));
+  FDE_CUDA(cudaStreamCreateWithFlags(&r->cs_out, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; ++k) {
+    FDE_CUDA(cudaEventCreateWithFlags(&r->ev_fready[k], cudaEventDisableTiming));
+    FDE_CUDA(cudaEventCreateWithFlags(&r->ev_fused[k], cudaEventDisableTiming));
+    FDE_CUDA(cudaEventRecord(r->ev_fused[k], st));
+  }
+  FDE_CUDA(cudaEventCreateWithFlags(&r->ev_snap, cudaEventDisableTiming));
+  FDE_CUDA(cudaEventCreateWithFlags(&r->ev_d2h, cudaEventDisableTiming));
+  FDE_CUDA(cudaEventRecord(r->ev_d2h, st));
+  return FDE_OK;
+}
+
+extern "C" fde_status fde_runner_step_source_async(fde_runner_t r, const double* F, int ldf, void* stream) {
+  FDE_ARG(r != nullptr && F != nullptr, "NULL argument");
+  FDE_ARG(r->p.dim == 2, "fde_runner_step_source_async is for 2D runners");
+  const int N = r->N;
+  FDE_ARG(ldf >= N, "ldf < N");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!sylv_graph_steps(r->s)) return fde_runner_step_source(r, F, ldf, stream);
+  FDE_TRY(io_prepare(r, st));
+  const double t1 = now_seconds();
+  const double* Fd = F;
+  int k = -1;
+  if (!is_device_ptr(F)) {
+    // the copy of this step's source runs on the copy stream, into the
+    // buffer the step before last used, while earlier steps compute
+    k = r->fk;
+    r->fk ^= 1;
+    FDE_CUDA(cudaStreamWaitEvent(r->cs, r->ev_fused[k], 0));
+    FDE_CUDA(cudaMemcpy2DAsync(r->Fb[k], (size_t)N * sizeof(double), F, (size_t)ldf * sizeof(double),
+                               (size_t)N * sizeof(double), N, cudaMemcpyHostToDevice, r->cs));
+    FDE_CUDA(cudaEventRecord(r->ev_fready[k], r->cs));
+    FDE_CUDA(cudaStreamWaitEvent(st, r->ev_fready[k], 0));
+    Fd = r->Fb[k];
+    ldf = N;
+  }
+  const size_t NN = (size_t)N * N;
+  const int nb = (int)std::min<size_t>((NN + 255) / 256, 152 * 32);
+  std::swap(r->C, r->C2);
+  rhs_dense_kernel<<<nb, 256, 0, st>>>(r->U, Fd, N, ldf, r->p.op_x.dt, r->C);
+  FDE_LAUNCH("rhs_dense_kernel");
+  if (k >= 0) FDE_CUDA(cudaEventRecord(r->ev_fused[k], st));
+  fde_status s = sylv_step_graph(r->s, r->C, r->U, st, r->have_prev ? r->C2 : nullptr);
+  r->have_prev = (s == FDE_OK);
+  r->c_valid = (s == FDE_OK);
+  FDE_TRY(s);
+  r->pending = true;
+  r->step += 1;
+  r->stats.solve_s += now_seconds() - t1;
+  return FDE_OK;
+}
+
+extern "C" fde_status fde_runner_state_async(fde_runner_t r, double* U_out, void* stream) {
+  FDE_ARG(r != nullptr && U_out != nullptr, "NULL argument");
+  const size_t n = (r->p.dim == 1) ? (size_t)r->N : (size_t)r->N * r->N;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (r->p.dim == 1 || is_device_ptr(U_out)) {
+    FDE_CUDA(cudaMemcpyAsync(U_out, r->U, n * sizeof(double), is_device_ptr(U_out) ? cudaMemcpyDeviceToDevice
+                                                                                    : cudaMemcpyDeviceToHost, st));
+    return FDE_OK;
+  }
+  FDE_TRY(io_prepare(r, st));
+  // snapshot on the compute stream (once the previous read-back has left the
+  // snapshot buffer), read back on the copy stream while the next steps run
+  FDE_CUDA(cudaStreamWaitEvent(st, r->ev_d2h, 0));
+  FDE_CUDA(cudaMemcpyAsync(r->Usnap, r->U, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  FDE_CUDA(cudaEventRecord(r->ev_snap, st));
+  FDE_CUDA(cudaStreamWaitEvent(r->cs_out, r->ev_snap, 0));
+  FDE_CUDA(cudaMemcpyAsync(U_out, r->Usnap, n * sizeof(double), cudaMemcpyDeviceToHost, r->cs_out));
+  FDE_CUDA(cudaEventRecord(r->ev_d2h, r->cs_out));
+  return FDE_OK;
+}
+
+extern "C" fde_status fde_runner_sync(fde_runner_t r, void* stream) {
+  FDE_ARG(r != nullptr, "runner is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (r->cs) FDE_CUDA(cudaStreamSynchronize(r->cs));
+  if (r->cs_out) FDE_CUDA(cudaStreamSynchronize(r->cs_out));
+  FDE_CUDA(cudaStreamSynchronize(st));
+  if (r->pending) {
+    r->pending = false;
+    FDE_TRY(collect_graph_steps(r, st));
+  }
+  return FDE_OK;
+}
+
 extern "C" fde_status fde_runner_load(fde_runner_t r, const double* U, int step_index, void* stream) {
   FDE_ARG(r != nullptr && U != nullptr, "NULL argument");
   FDE_ARG(step_index >= 0, "step_index must be >= 0");
+  FDE_TRY(flush_async(r, (cudaStream_t)stream));
   const size_t n = (r->p.dim == 1) ? (size_t)r->N : (size_t)r->N * r->N;
   FDE_TRY(copy_state(r->U, U, n, (cudaStream_t)stream));
   r->step = step_index;
@@ -411,8 +538,65 @@ extern "C" fde_status fde_runner_load(fde_runner_t r, const double* U, int step_
   return FDE_OK;
 }
 
-extern "C" fde_status fde_runner_residual(fde_runner_t r, double* relres, double* maxabs, void* stream) {
+// Rebuilds the runner's operators for the diagonals D_±^{(m+1)} of the next
+// step (Eq. (system_FD) with time-dependent coefficients): HODLR build and
+// factorisation in 1D; both HODLR operators and the Sylvester solver in 2D.
+// The stored residual history belongs to the old operator, so the next step
+// starts from U^{(m)} with an exact residual.
+static fde_status runner_set_coeffs(fde_runner_s* R, const double* dpx, const double* dmx, const double* dpy,
+                                    const double* dmy, cudaStream_t st) {
+  const double t0 = now_seconds();
+  fde_op_params ox = R->p.op_x;
+  ox.d_plus = dpx;
+  ox.d_minus = dmx;
+  hodlr_t ax = nullptr, ay = nullptr;
+  sylv_t sv = nullptr;
+  fde_status s = hodlr_build(&ox, st, &ax);
+  if (s == FDE_OK && R->p.dim == 1) s = hodlr_factor(ax, st);
+  if (s == FDE_OK && R->p.dim == 2) {
+    fde_op_params oy = R->p.op_y;
+    oy.d_plus = dpy;
+    oy.d_minus = dmy;
+    s = hodlr_build(&oy, st, &ay);
+    if (s == FDE_OK) s = sylv_create(ax, ay, R->p.prec, st, &sv);
+  }
+  if (s != FDE_OK) {
+    sylv_free(sv);
+    hodlr_free(ay);
+    hodlr_free(ax);
+    return s;
+  }
+  sylv_free(R->s);
+  hodlr_free(R->ay);
+  hodlr_free(R->ax);
+  R->ax = ax;
+  R->ay = ay;
+  R->s = sv;
+  R->have_prev = false;
+  R->c_valid = false;
+  hodlr_info_t ix;
+  hodlr_get_info(R->ax, &ix);
+  R->stats.kmax_x = std::max(R->stats.kmax_x, ix.kmax);
+  if (R->ay) {
+    hodlr_get_info(R->ay, &ix);
+    R->stats.kmax_y = std::max(R->stats.kmax_y, ix.kmax);
+  }
+  R->stats.solve_s += now_seconds() - t0;
+  return FDE_OK;
+}
+
+extern "C" fde_status fde_runner_set_coefficients(fde_runner_t r, const double* d_plus_x, const double* d_minus_x,
+                                                  const double* d_plus_y, const double* d_minus_y, void* stream) {
+  FDE_ARG(r != nullptr && d_plus_x != nullptr && d_minus_x != nullptr, "NULL argument");
+  FDE_ARG(r->p.dim == 1 || (d_plus_y != nullptr && d_minus_y != nullptr), "2D needs the y coefficients");
+  FDE_TRY(flush_async(r, (cudaStream_t)stream));
+  return runner_set_coeffs(r, d_plus_x, d_minus_x, d_plus_y, d_minus_y, (cudaStream_t)stream);
+}
+
+extern "C" fde_status fde_runner_residual(fde_runner_t r, double* relres, double* maxabs, double* fro,
+                                          void* stream) {
   FDE_ARG(r != nullptr && relres != nullptr && maxabs != nullptr, "NULL argument");
+  FDE_TRY(flush_async(r, (cudaStream_t)stream));
   FDE_ARG(r->c_valid, "no step since fde_runner_create / fde_runner_load");
   cudaStream_t st = (cudaStream_t)stream;
   const int N = r->N;
@@ -446,11 +630,13 @@ extern "C" fde_status fde_runner_residual(fde_runner_t r, double* relres, double
   FDE_CUDA(cudaStreamSynchronize(st));
   *maxabs = h[0];
   *relres = h[3] > 0.0 ? sqrt(h[1] / h[3]) : sqrt(h[1]);
+  if (fro) *fro = sqrt(h[1]);
   return FDE_OK;
 }
 
 extern "C" fde_status fde_runner_state(fde_runner_t r, double* U_out, void* stream) {
   FDE_ARG(r != nullptr && U_out != nullptr, "NULL argument");
+  FDE_TRY(flush_async(r, (cudaStream_t)stream));
   const size_t n = (r->p.dim == 1) ? (size_t)r->N : (size_t)r->N * r->N;
   return copy_state(U_out, r->U, n, (cudaStream_t)stream);
 }

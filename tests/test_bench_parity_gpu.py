@@ -10,11 +10,13 @@ between, and FP32 last updates.  Its states are compared with
     Eq. (sylv-timestepping)): sampled entries, bilinear functionals and norms
     stored by tests/golden/make_fd2d_oracle.py at steps 2, 4, 8 (the last step
     of an incremental chain) and 10 (a refresh step);
-  - a rigorous bound on the error against the exact time loop: A_x and A_y
-    are M-matrices (§2.2.1), so max|U - U*| <= max|R| / μ per step, μ the sum
-    of their smallest row sums, and these bounds add over the loop
-    (oracle.sylvester_error_bound).  Each step's own bound must be below the
-    tolerance, and the oracle's values must lie inside the accumulated one.
+  - rigorous bounds on the error against the exact time loop, from the
+    exact FP64 residuals of the steps: A_x and A_y are M-matrices (§2.2.1),
+    so max|U - U*| <= max|R| / μ per step, μ the sum of their smallest row
+    sums (oracle.sylvester_error_bound); and their symmetric parts exceed
+    I/2, so ||U - U*||_F <= ||R||_F (oracle.sylvester_error_bound_fro).
+    Both add over the loop.  The Frobenius bound must stay below the
+    tolerance, and the oracle's values must lie inside both.
 
 Above N = 4096 the same bound certifies the block-Toeplitz residual path."""
 import os
@@ -69,15 +71,20 @@ def test_fd2d_n4096_default_run_vs_oracle(lib):
     gold = _golden(name)
     Uv, Vv = I.projection_vectors(N, 8, seed=0)
     mu = _mu(w)
+    # λ_min of both symmetric parts above 1/2: the Frobenius bound applies
+    # with θ_x + θ_y = 1 (oracle.sylvester_error_bound_fro)
+    assert all(O.sym_part_exceeds(op, 0.5) for op in w.ops)
     U0 = torch.from_numpy(np.asarray(w.u0).ravel(order="F").copy()).to("cuda")
     r = lib.runner_create(lib.run_params(w, prec=B.FDE_FP32_REFINE), U0.data_ptr())
     try:
         bound = 0.0
+        bound_fro = 0.0
         prev = w.u0.copy()
         for m in range(1, max(gold) + 1):
             lib.runner_advance(r, 1)
-            rel, mx = lib.runner_residual(r)
+            rel, mx, fro = lib.runner_residual(r)
             bound += mx / mu
+            bound_fro += O.sylvester_error_bound_fro(fro, 0.5, 0.5)
             if m in gold or m == 1:
                 X = _state(lib, r, N)
             if m == 1:
@@ -104,7 +111,9 @@ def test_fd2d_n4096_default_run_vs_oracle(lib):
             # loop, so the oracle's values must lie inside it (up to the
             # oracle's own rounding)
             assert np.abs(err).max() <= bound + 1e-12 * e["maxabs"], (m, np.abs(err).max(), bound)
-            assert mx / mu <= TOL * e["maxabs"], (m, mx / mu)
+            # rigorous Frobenius bound against the exact loop, within the tolerance
+            assert bound_fro <= TOL * e["fro"], (m, bound_fro / e["fro"])
+            assert rel_fro <= bound_fro / e["fro"] + 1e-12, (m, rel_fro, bound_fro / e["fro"])
     finally:
         lib.runner_free(r)
 
@@ -124,7 +133,7 @@ def _certified_step(lib, N, steps, monkeypatch, resid=None):
             if m == steps:
                 prev = w.u0.copy() if m == 1 else _state(lib, r, N)
             lib.runner_advance(r, 1)
-            rel, mx = lib.runner_residual(r)
+            rel, mx, fro = lib.runner_residual(r)
             bound += mx / mu
         X = _state(lib, r, N)
         # the last step's residual recomputed by the oracle on the CPU

@@ -459,3 +459,107 @@ def test_whole_step_graph_matches_eager_steps(lib, monkeypatch):
     # launches counted per graph replay: within the eager count's range
     assert 0.5 * out["0"][3] <= out["1"][3] <= 1.5 * out["0"][3], (out["1"][3], out["0"][3])
     assert _relerr(out["1"][0], Uref) <= 1e-8
+
+
+def test_time_dependent_coefficients_1d(lib):
+    """Eq. (system_FD) with D_±^{(m)} at the new time level: the runner
+    rebuilds and refactors its HODLR operator before every step; FP64 against
+    the oracle's dense LU of every A^{(m)}."""
+    w = I.fd1d(N=512, alpha=1.6, steps=16, leaf=64, tol=1e-12)
+    op = w.ops[0]
+    dp0, dm0 = op.d_plus.copy(), op.d_minus.copy()
+
+    def coeff(t):
+        return (1.0 + 2.0 * t) * dp0, (1.0 + np.sin(3.0 * t)) * dm0
+
+    steps = 8
+    Uref = O.fde1d_run_tv(w, coeff, steps=steps)
+    rp = lib.run_params(w, prec=B.FDE_FP64)
+    U0 = torch.from_numpy(w.u0.copy()).to("cuda")
+    r = lib.runner_create(rp, U0.data_ptr())
+    try:
+        for m in range(1, steps + 1):
+            lib.runner_set_coefficients(r, *coeff(m * w.dt))
+            lib.runner_advance(r, 1)
+        U = torch.empty_like(U0)
+        lib.runner_state(r, U.data_ptr())
+        torch.cuda.synchronize()
+    finally:
+        lib.runner_free(r)
+    assert _relerr(U.cpu().numpy(), Uref) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [B.FDE_FP64, B.FDE_FP32_REFINE])
+def test_time_dependent_coefficients_2d(lib, prec):
+    """The 2D step with both sides' coefficients at the new time level t_{m+1}:
+    both HODLR operators and the Sylvester solver rebuilt per step, against
+    the oracle's Bartels–Stewart with new Schur forms per step."""
+    w = I.fd2d(N=128, alpha=(1.3, 1.7), steps=50, leaf=32)
+    ox, oy = w.ops
+    bx = (ox.d_plus.copy(), ox.d_minus.copy())
+    by = (oy.d_plus.copy(), oy.d_minus.copy())
+
+    def cx(t):
+        return (1.0 + t) * bx[0], (1.0 + 0.5 * t) * bx[1]
+
+    def cy(t):
+        return (2.0 - t) * by[0], (1.0 + t * t) * by[1]
+
+    steps = 4
+    Uref = O.fde2d_run_tv(w, cx, cy, steps=steps)
+    rp = lib.run_params(w, prec=prec)
+    U0 = _dev(w.u0)
+    r = lib.runner_create(rp, U0.data_ptr())
+    try:
+        for m in range(steps):
+            t = (m + 1) * w.dt
+            lib.runner_set_coefficients(r, *cx(t), *cy(t))
+            lib.runner_advance(r, 1)
+        U = torch.empty_like(U0)
+        lib.runner_state(r, U.data_ptr())
+        torch.cuda.synchronize()
+    finally:
+        lib.runner_free(r)
+    assert _relerr(_host(U, w.N, w.N), Uref) <= 1e-9
+
+
+def test_runner_async_host_io_matches_sync(lib):
+    """fde_runner_step_source_async / fde_runner_state_async: the source of
+    every step uploaded from page-locked host memory on the copy stream and
+    every step's state read back there, overlapping the next steps.  Each
+    read-back equals the state after its own step from the synchronous calls
+    (bit for bit: the same kernels take the same decisions), and the oracle's
+    trajectory within 1e-8."""
+    N = 160
+    w = I.fd2d(N=N, alpha=(1.3, 1.7), steps=20, leaf=32)
+    rp = lib.run_params(w, prec=B.FDE_FP32_REFINE)
+    U0 = _dev(w.u0)
+    K = 7
+    Fs = []
+    for m in range(K):
+        t = (m + 1) * w.dt
+        wts = w.src_amp + w.src_sin_amp * np.sin(w.src_omega * t)
+        F = (w.src_left * wts) @ w.src_right.T
+        Fh = torch.empty(N * N, dtype=torch.float64, pin_memory=True)
+        Fh.copy_(torch.from_numpy(np.asfortranarray(F).ravel(order="F")))
+        Fs.append(Fh)
+    ra = lib.runner_create(rp, U0.data_ptr())
+    rb = lib.runner_create(rp, U0.data_ptr())
+    try:
+        outs = [torch.zeros(N * N, dtype=torch.float64, pin_memory=True) for _ in range(K)]
+        for m in range(K):
+            lib.runner_step_source_async(rb, Fs[m].data_ptr(), N)
+            lib.runner_state_async(rb, outs[m].data_ptr())
+        lib.runner_sync(rb)
+        ref = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+        for m in range(K):
+            lib.runner_step_source(ra, Fs[m].data_ptr(), N)
+            lib.runner_state(ra, ref.data_ptr())
+            torch.cuda.synchronize()
+            assert torch.equal(outs[m], ref.cpu()), m
+        assert _relerr(_host(outs[-1], N, N), O.fde2d_run(w, steps=K)) <= 1e-8
+        st = lib.runner_stats(rb)
+        assert st.sweeps_total >= K
+    finally:
+        lib.runner_free(ra)
+        lib.runner_free(rb)
