@@ -536,7 +536,8 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": scale_to(N, sec), "unit": "steps/s", "cores": cores, "cores_source": cores_src,
                "kind": "oracle",
                "sample": sample + f"; {sec:.2f} s/step, scaled to N={N} by (N/{ORACLE_SAMPLE_N})^3",
-               "sample_steps_per_s": 1.0 / sec}
+               "sample_steps_per_s": 1.0 / sec, "sample_ms_per_step": sec * 1e3, "sample_N": ORACLE_SAMPLE_N,
+               "scaled": f"value = sample rate x ({ORACLE_SAMPLE_N}/{N})^3"}
     cfg = {"workload": f"{args.workload}: 2D N={N} per side ({N*N} unknowns), alpha=({w.ops[0].alpha},{w.ops[1].alpha}), "
                        f"dt=1/{w.steps}, leaf {w.ops[0].leaf}, HODLR tol {w.ops[0].tol:g}, FP32 D&C+fADI inner, "
                        f"FP64 refinement",
@@ -700,6 +701,10 @@ def run_reference(args, rank, world):
                             "kind": "oracle",
                             "sample": sm.describe(args.steps) + f"; mean {per:.2f} s/step, scaled to N={N} "
                                                                 f"by (N/{sm.n})^3",
+                            "sample_N": sm.n, "sample_ms_per_step": per * 1e3,
+                            "scaled": f"value and ms_per_step = the N={sm.n} steps actually timed, scaled to "
+                                      f"N={N} by (N/{sm.n})^3 (a real N={N} oracle step is dominated by "
+                                      f"single-threaded LAPACK dtrsyl, about 10 minutes)",
                             "wall_s": wall, "total_wall_s": time.perf_counter() - t_wall0},
            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

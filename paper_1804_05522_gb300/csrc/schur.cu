@@ -254,12 +254,21 @@ constexpr int kMaxRowWarps = 9;   // leaves up to 256 rows: blocks of >= 31 rows
 
 template <typename T>
 __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 ? 128 : 168)
-    trsyl_kernel(const T* __restrict__ Sall, const T* __restrict__ Rall, int ld, int lmax,
-                 const int* __restrict__ soff_x, const int* __restrict__ lo_x, const int* __restrict__ n_x, int nx,
-                 const int* __restrict__ soff_y, const int* __restrict__ lo_y, const int* __restrict__ n_y,
+    trsyl_kernel(const T* __restrict__ Sall, const T* __restrict__ Rall, int ld, int lmax, TrsylSet s0, TrsylSet s1,
                  T* __restrict__ W, int ldw, int use_panel, int panel_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int p = blockIdx.x % nx, q = blockIdx.x / nx;
+  // blocks [0, s0.count) solve the pairs of s0, the rest those of s1
+  const bool second = (int)blockIdx.x >= s0.count;
+  const TrsylSet& ps = second ? s1 : s0;
+  const int b = second ? (int)blockIdx.x - s0.count : (int)blockIdx.x;
+  const int* __restrict__ soff_x = ps.soff_x;
+  const int* __restrict__ lo_x = ps.lo_x;
+  const int* __restrict__ n_x = ps.n_x;
+  const int* __restrict__ soff_y = ps.soff_y;
+  const int* __restrict__ lo_y = ps.lo_y;
+  const int* __restrict__ n_y = ps.n_y;
+  const int nx = ps.nx;
+  const int p = b % nx, q = b / nx;
   const int n1 = n_x[p], n2 = n_y[q];
   if (n1 <= 0 || n2 <= 0) return;
   T* Y = W + lo_x[p] + (size_t)lo_y[q] * ldw;
@@ -559,6 +568,13 @@ template <typename T>
 fde_status leaf_trsyl(const T* S, const T* R, int ld, int lmax, const int* d_soff_x, const int* d_lo_x,
                       const int* d_n_x, int nx, const int* d_soff_y, const int* d_lo_y, const int* d_n_y, int ny,
                       T* W, int ldw, cudaStream_t st, double flops) {
+  const TrsylSet s0{d_soff_x, d_lo_x, d_n_x, nx, d_soff_y, d_lo_y, d_n_y, nx * ny};
+  return leaf_trsyl2<T>(S, R, ld, lmax, s0, TrsylSet{}, W, ldw, st, flops);
+}
+
+template <typename T>
+fde_status leaf_trsyl2(const T* S, const T* R, int ld, int lmax, const TrsylSet& s0, const TrsylSet& s1, T* W,
+                       int ldw, cudaStream_t st, double flops) {
   if (lmax > 32 * kMaxRowWarps - kMaxRowWarps || lmax > ld) {
     set_error("leaf_trsyl: problem size %d above %d (or above ld %d)", lmax, 32 * kMaxRowWarps - kMaxRowWarps, ld);
     return FDE_ERR_ARG;
@@ -577,12 +593,17 @@ fde_status leaf_trsyl(const T* S, const T* R, int ld, int lmax, const int* d_sof
       cudaFuncSetAttribute(trsyl_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
   FDE_CUDA(attr);
   ProfScope ps(sizeof(T) == 4 ? "trsyl32" : "trsyl64", st, flops, 1);
-  trsyl_kernel<T><<<nx * ny, warps * 32, smem, st>>>(S, R, ld, lmax, d_soff_x, d_lo_x, d_n_x, nx, d_soff_y, d_lo_y,
-                                                     d_n_y, W, ldw, use_panel, panel_elems);
+  const int blocks = s0.count + s1.count;
+  if (blocks == 0) return FDE_OK;
+  trsyl_kernel<T><<<blocks, warps * 32, smem, st>>>(S, R, ld, lmax, s0, s1, W, ldw, use_panel, panel_elems);
   FDE_LAUNCH("trsyl_kernel");
   return FDE_OK;
 }
 
+template fde_status leaf_trsyl2<double>(const double*, const double*, int, int, const TrsylSet&, const TrsylSet&,
+                                        double*, int, cudaStream_t, double);
+template fde_status leaf_trsyl2<float>(const float*, const float*, int, int, const TrsylSet&, const TrsylSet&,
+                                       float*, int, cudaStream_t, double);
 template fde_status leaf_trsyl<double>(const double*, const double*, int, int, const int*, const int*, const int*,
                                        int, const int*, const int*, const int*, int, double*, int, cudaStream_t, double);
 template fde_status leaf_trsyl<float>(const float*, const float*, int, int, const int*, const int*, const int*, int,

@@ -26,4 +26,16 @@ fde_status leaf_trsyl(const T* S, const T* R, int ld, int lmax, const int* d_sof
                       const int* d_n_x, int nx, const int* d_soff_y, const int* d_lo_y, const int* d_n_y, int ny,
                       T* W, int ldw, cudaStream_t st, double flops = 0.0);
 
+// A set of pairs for one launch: (p, q) over nx x (count / nx), as above.
+struct TrsylSet {
+  const int *soff_x = nullptr, *lo_x = nullptr, *n_x = nullptr;
+  int nx = 1;
+  const int *soff_y = nullptr, *lo_y = nullptr, *n_y = nullptr;
+  int count = 0;
+};
+// Two independent sets of pairs in one launch (blocks of s0 first).
+template <typename T>
+fde_status leaf_trsyl2(const T* S, const T* R, int ld, int lmax, const TrsylSet& s0, const TrsylSet& s1, T* W,
+                       int ldw, cudaStream_t st, double flops = 0.0);
+
 }  // namespace fde

@@ -1116,8 +1116,15 @@ static fde_status run_inner(sylv_s* S, Inner<T>& in, cudaStream_t st) {
     FDE_TRY(trsyl(S->tp_bot, S->tp_bot, S->trsyl_flops_bb));
     FDE_TRY(gemm_batch_run(in.g_sp1, st));
     FDE_TRY(gemm_batch_run(in.g_sp2, st));
-    FDE_TRY(trsyl(S->tp_top, S->tp_bot, S->trsyl_flops_tb));
-    FDE_TRY(trsyl(S->tp_bot, S->tp_top, S->trsyl_flops_bt));
+    {
+      // the top-bottom and bottom-top blocks are independent: one launch
+      auto set = [&](const sylv_s::TrsylPart& px, const sylv_s::TrsylPart& py) {
+        return TrsylSet{px.soff, px.lo, px.n, nl, py.soff + nl, py.lo + nl, py.n + nl, nl * nl};
+      };
+      int nmax = S->tp_top.nmax > S->tp_bot.nmax ? S->tp_top.nmax : S->tp_bot.nmax;
+      FDE_TRY(leaf_trsyl2<T>(in.Sx, in.Sy, S->lmax, nmax, set(S->tp_top, S->tp_bot), set(S->tp_bot, S->tp_top),
+                             in.W2, N, st, S->trsyl_flops_tb + S->trsyl_flops_bt));
+    }
     FDE_TRY(gemm_batch_run(in.g_sp3, st));
     FDE_TRY(gemm_batch_run(in.g_sp4, st));
     FDE_TRY(trsyl(S->tp_top, S->tp_top, S->trsyl_flops_tt));
