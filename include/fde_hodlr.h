@@ -343,6 +343,31 @@ fde_status fde_runner_residual(fde_runner_t r, double* relres, double* maxabs, d
 fde_status fde_runner_stats(fde_runner_t r, fde_run_stats* stats);
 void fde_runner_free(fde_runner_t r);
 
+/* -------------------------------------------------- factored 2D loop -- */
+/* The paper's own 2D time loop with the solution kept in factored form
+ * (§4.1, §4.2): U^{(m)} = W Zᵀ, the right-hand side C = U^{(m)} + Δt F^{(m+1)}
+ * = L Rᵀ recompressed by QR + SVD (singular values <= eps ||C||_2 dropped),
+ * the low-rank Sylvester equation A_x X + X A_yᵀ = L Rᵀ
+ * (Eq. (sylv-timestepping)) solved in factored form by factored ADI on the
+ * whole operators (shifted HODLR factorisations, Zolotarev shifts for their
+ * spectral intervals, §3.3; the accumulated factors recompressed after every
+ * two shifts), and U^{(m+1)} = X truncated to its eps-rank.  FP64.  The source
+ * is the low-rank one of p (dim 2; p->op_x / op_y d_plus / d_minus HOST
+ * pointers; N >= 96); h_W0, h_Z0 (host, N x r0 column-major, 1 <= r0 <= 32)
+ * give U^{(0)} = W0 Z0ᵀ.  Every factor has a capacity of 32 columns: a step
+ * whose solution needs more returns FDE_ERR_NOCONV from fde_lowrank_advance.
+ * fde_lowrank_factors copies W and Z (N x min(cap, 32) each, host or device,
+ * zero beyond *rank) and the current rank.  fde_lowrank_info: number of fADI
+ * shifts and the largest rank seen.  One CUDA graph launch per step after the
+ * right-hand side; fde_lowrank_advance synchronises once per call. */
+typedef struct fde_lowrank_s* fde_lowrank_t;
+fde_status fde_lowrank_create(const fde_run_params* p, const double* h_W0, const double* h_Z0, int r0, double eps,
+                              void* stream, fde_lowrank_t* out);
+fde_status fde_lowrank_advance(fde_lowrank_t r, int nsteps, void* stream);
+fde_status fde_lowrank_factors(fde_lowrank_t r, double* W, double* Z, int cap, int* rank, void* stream);
+fde_status fde_lowrank_info(fde_lowrank_t r, int* shifts, int* rank_max);
+void fde_lowrank_free(fde_lowrank_t r);
+
 /* ------------------------------------------------------------- batches -- */
 /* Many independent instances (1D and 2D, uneven N, α, coefficients), e.g. a
  * batch of problems served together.  fde_batch_create builds one time-loop

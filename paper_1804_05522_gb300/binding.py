@@ -100,6 +100,11 @@ _SIGS = {
     "fde_runner_step_source_async": ([_P, _P, C.c_int, _P], C.c_int),
     "fde_runner_state_async": ([_P, _P, _P], C.c_int),
     "fde_runner_sync": ([_P, _P], C.c_int),
+    "fde_lowrank_create": ([_P, _P, _P, C.c_int, C.c_double, _P, _P], C.c_int),
+    "fde_lowrank_advance": ([_P, C.c_int, _P], C.c_int),
+    "fde_lowrank_factors": ([_P, _P, _P, C.c_int, C.POINTER(C.c_int), _P], C.c_int),
+    "fde_lowrank_info": ([_P, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "fde_lowrank_free": ([_P], None),
     "fde_runner_stats": ([_P, C.POINTER(RunStats)], C.c_int),
     "fde_runner_free": ([_P], None),
     "fde_launch_count": ([], C.c_ulonglong),
@@ -294,6 +299,35 @@ class Lib:
         r = _P()
         self.check(self.dll.fde_runner_create(C.byref(params), U0, stream, C.byref(r)))
         return r.value
+
+    # -- factored 2D loop
+    def lowrank_create(self, params: RunParams, W0: np.ndarray, Z0: np.ndarray, eps: float, stream: int = 0) -> int:
+        W0 = np.asfortranarray(W0, dtype=np.float64)
+        Z0 = np.asfortranarray(Z0, dtype=np.float64)
+        h = _P()
+        self.check(self.dll.fde_lowrank_create(C.byref(params), W0.ctypes.data, Z0.ctypes.data, W0.shape[1], eps,
+                                               stream, C.byref(h)))
+        return h.value
+
+    def lowrank_advance(self, h: int, nsteps: int, stream: int = 0):
+        self.check(self.dll.fde_lowrank_advance(h, nsteps, stream))
+
+    def lowrank_factors(self, h: int, N: int, cap: int = 32, stream: int = 0):
+        """(W, Z, rank): host copies of the factors, N x rank each."""
+        W = np.zeros((cap, N))
+        Z = np.zeros((cap, N))
+        rk = C.c_int()
+        self.check(self.dll.fde_lowrank_factors(h, W.ctypes.data, Z.ctypes.data, cap, C.byref(rk), stream))
+        return W[:rk.value].T.copy(), Z[:rk.value].T.copy(), rk.value
+
+    def lowrank_info(self, h: int):
+        J, rm = C.c_int(), C.c_int()
+        self.check(self.dll.fde_lowrank_info(h, C.byref(J), C.byref(rm)))
+        return J.value, rm.value
+
+    def lowrank_free(self, h: int):
+        if h:
+            self.dll.fde_lowrank_free(h)
 
     # -- batches
     def batch_create(self, params_list, U0_ptrs, threads=4, autotune=False, stream: int = 0) -> int:

@@ -297,14 +297,6 @@ __global__ void block_factors_kernel(const NodeRef* __restrict__ nodes, const do
 }
 
 // ------------------------------------------- K3: QR + SVD recompression
-struct RecompJob {
-  double* Uin;
-  double* Vin;
-  double* Uout;
-  double* Vout;
-  int m, n, ld;  // rows of U, rows of V, leading dimension of all four
-  int* rank_out;
-};
 
 // Householder QR of A (m x r, lda), reflectors below the diagonal, tau[j];
 // R (r x r, ld r) gets the upper trapezoid (rows >= min(m,r) zero).
@@ -435,11 +427,13 @@ __device__ void jacobi_svd(double* M, int ldm, int rows, int cols, double* Z, in
   }
 }
 
+size_t recompress_smem(int r);
+
 // One CTA per job.  U Vᵀ (U: m x r, V: n x r, in place) -> U' V'ᵀ, rank r'
 // = #{σ > abstol}; U' = Q_U W Σ, V' = Q_V Z (§4.1 recompression).  Outputs
 // have rcap columns, zero beyond r'.
 __global__ void __launch_bounds__(512) recompress_kernel(const RecompJob* __restrict__ jobs, int r, int rcap,
-                                                         double abstol) {
+                                                         double abstol, double reltol) {
   extern __shared__ double smem[];
   const RecompJob jb = jobs[blockIdx.x];
   double* Ru = smem;          // r x r (later Z)
@@ -478,10 +472,15 @@ __global__ void __launch_bounds__(512) recompress_kernel(const RecompJob* __rest
     perm[rk] = j;
   }
   if (threadIdx.x == 0) {
+    // drop σ <= max(abstol, reltol σ_max)
+    double smax = 0.0;
+    for (int j = 0; j < qn; ++j) smax = fmax(smax, sig[j]);
+    const double thr = fmax(abstol, reltol * smax);
     int cnt = 0;
     for (int j = 0; j < qn; ++j)
-      if (sig[j] > abstol) ++cnt;
+      if (sig[j] > thr) ++cnt;
     s_rank = min(cnt, rcap);
+    if (jb.rank_full) atomicMax(jb.rank_full, cnt);
   }
   __syncthreads();
   const int rr = s_rank;
@@ -497,6 +496,97 @@ __global__ void __launch_bounds__(512) recompress_kernel(const RecompJob* __rest
   house_apply(jb.Uin, ld, m, qm, tau_u, jb.Uout, ld, rr);
   house_apply(jb.Vin, ld, n, qn, tau_v, jb.Vout, ld, rr);
   if (threadIdx.x == 0) *jb.rank_out = rr;
+}
+
+// The same recompression in three launches, so that the two factors' QR and
+// their final products run in separate CTAs (one per factor and job): the
+// FP64 pipe of one SM is the limit of a single-CTA QR of a tall factor.
+// Workspace per job (RecompWork): tau and R of both factors, the small
+// factors of the kept part of the core's SVD, the core's rank.
+__global__ void __launch_bounds__(512) recomp_qr_kernel(const RecompJob* __restrict__ jobs, int r,
+                                                         RecompWork wk) {
+  extern __shared__ double smem[];
+  __shared__ double red[32];
+  const int j = blockIdx.x >> 1, side = blockIdx.x & 1;
+  const RecompJob jb = jobs[j];
+  double* R = smem;  // r x r
+  double* tau = wk.tau + ((size_t)j * 2 + side) * r;
+  house_qr(side ? jb.Vin : jb.Uin, jb.ld, side ? jb.n : jb.m, r, tau, R, red);
+  double* Rout = wk.R + ((size_t)j * 2 + side) * r * r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) Rout[e] = R[e];
+}
+
+__global__ void __launch_bounds__(512) recomp_core_kernel(const RecompJob* __restrict__ jobs, int r, int rcap,
+                                                           double abstol, double reltol, RecompWork wk) {
+  extern __shared__ double smem[];
+  const int j = blockIdx.x;
+  const RecompJob jb = jobs[j];
+  double* M = smem;           // r x r
+  double* Z = M + r * r;      // r x r
+  double* sig = Z + r * r;    // r
+  int* perm = (int*)(sig + r);
+  __shared__ int s_rot, s_rank;
+  const double* Ru = wk.R + (size_t)j * 2 * r * r;
+  const double* Rv = Ru + (size_t)r * r;
+  const int qm = min(jb.m, r), qn = min(jb.n, r);
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, c = e / r;
+    double s = 0.0;
+    if (i < qm && c < qn)
+      for (int k = 0; k < r; ++k) s += Ru[i + k * r] * Rv[c + k * r];
+    M[e] = s;
+  }
+  __syncthreads();
+  jacobi_svd(M, r, qm, qn, Z, r, &s_rot);
+  __syncthreads();
+  for (int c = threadIdx.x; c < qn; c += blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < qm; ++i) s += M[i + c * r] * M[i + c * r];
+    sig[c] = sqrt(s);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < qn; c += blockDim.x) {
+    int rk = 0;
+    for (int q = 0; q < qn; ++q)
+      if (sig[q] > sig[c] || (sig[q] == sig[c] && q < c)) ++rk;
+    perm[rk] = c;
+  }
+  if (threadIdx.x == 0) {
+    double smax = 0.0;
+    for (int c = 0; c < qn; ++c) smax = fmax(smax, sig[c]);
+    const double thr = fmax(abstol, reltol * smax);
+    int cnt = 0;
+    for (int c = 0; c < qn; ++c)
+      if (sig[c] > thr) ++cnt;
+    s_rank = min(cnt, rcap);
+    *jb.rank_out = s_rank;
+    if (jb.rank_full) atomicMax(jb.rank_full, cnt);
+    wk.rank[j] = s_rank;
+  }
+  __syncthreads();
+  const int rr = s_rank;
+  double* Cu = wk.C + (size_t)j * 2 * r * rcap;  // r x rcap: W Σ (kept columns)
+  double* Cv = Cu + (size_t)r * rcap;           // r x rcap: Z
+  for (int e = threadIdx.x; e < r * rcap; e += blockDim.x) {
+    const int i = e % r, c = e / r;
+    Cu[e] = (c < rr && i < qm) ? M[i + perm[c] * r] : 0.0;
+    Cv[e] = (c < rr && i < qn) ? Z[i + perm[c] * r] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(512) recomp_apply_kernel(const RecompJob* __restrict__ jobs, int r, int rcap,
+                                                            RecompWork wk) {
+  const int j = blockIdx.x >> 1, side = blockIdx.x & 1;
+  const RecompJob jb = jobs[j];
+  const int m = side ? jb.n : jb.m, q = min(m, r);
+  const double* C = wk.C + ((size_t)j * 2 + side) * r * rcap;
+  double* out = side ? jb.Vout : jb.Uout;
+  for (int e = threadIdx.x; e < m * rcap; e += blockDim.x) {
+    const int i = e % m, c = e / m;
+    out[i + (size_t)c * jb.ld] = (i < q) ? C[i + (size_t)c * r] : 0.0;
+  }
+  __syncthreads();
+  house_apply(side ? jb.Vin : jb.Uin, jb.ld, m, q, wk.tau + ((size_t)j * 2 + side) * r, out, jb.ld, wk.rank[j]);
 }
 
 // --------------------------------------------------------- leaves (dense)
@@ -1003,19 +1093,11 @@ static fde_status build_impl(const fde_op_params* p, cudaStream_t st, hodlr_s* h
     block_factors_kernel<<<(int)nodes.size(), 256, 0, st>>>(d_nodes, h->U0, h->V0, h->dp, h->dm, h->c, N, N1, N2,
                                                             h->kaca);
     FDE_LAUNCH("block_factors_kernel");
-    const size_t smem = (3 * (size_t)r * r + 3 * r) * sizeof(double) + r * sizeof(int);
-    {
-      // per-kernel attribute shared by all handles and threads: only ever raised
-      static std::mutex mu;
-      static size_t set_to = 0;
-      std::lock_guard<std::mutex> lk(mu);
-      if (smem > set_to) {
-        FDE_CUDA(cudaFuncSetAttribute(recompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        set_to = smem;
-      }
-    }
+    const size_t smem = recompress_smem(r);
+    // per-kernel attribute shared by all handles and threads: only ever raised
+    FDE_TRY(recompress_prepare(r));
     ProfScope ps("recompress", st);
-    recompress_kernel<<<(int)jobs.size(), 512, smem, st>>>(d_jobs, r, r, h->blk_tol);
+    recompress_kernel<<<(int)jobs.size(), 512, smem, st>>>(d_jobs, r, r, h->blk_tol, 0.0);
     FDE_LAUNCH("recompress_kernel");
     std::vector<int> ranks(njobs);
     FDE_CUDA(cudaMemcpyAsync(ranks.data(), d_ranks, njobs * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1053,6 +1135,51 @@ static fde_status build_impl(const fde_op_params* p, cudaStream_t st, hodlr_s* h
   FDE_CUDA(cudaStreamSynchronize(st));
   return FDE_OK;
 }
+
+namespace fde {
+size_t recompress_smem(int r) { return (3 * (size_t)r * r + 3 * r) * sizeof(double) + r * sizeof(int); }
+
+fde_status recompress_prepare(int rmax) {
+  static std::mutex mu;
+  static size_t set_to = 0;
+  const size_t smem = recompress_smem(rmax);
+  std::lock_guard<std::mutex> lk(mu);
+  if (smem > set_to) {
+    FDE_CUDA(cudaFuncSetAttribute(recompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDE_CUDA(cudaFuncSetAttribute(recomp_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDE_CUDA(cudaFuncSetAttribute(recomp_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set_to = smem;
+  }
+  return FDE_OK;
+}
+
+fde_status recompress_split(const RecompJob* d_jobs, int njobs, int r, int rcap, double abstol, double reltol,
+                            const RecompWork& wk, cudaStream_t st) {
+  if (r > kRecompMax || rcap > r) {
+    set_error("recompression of rank %d above %d", r, kRecompMax);
+    return FDE_ERR_ARG;
+  }
+  recomp_qr_kernel<<<2 * njobs, 512, (size_t)r * r * sizeof(double), st>>>(d_jobs, r, wk);
+  FDE_LAUNCH("recomp_qr_kernel");
+  recomp_core_kernel<<<njobs, 512, (2 * (size_t)r * r + r) * sizeof(double) + r * sizeof(int), st>>>(
+      d_jobs, r, rcap, abstol, reltol, wk);
+  FDE_LAUNCH("recomp_core_kernel");
+  recomp_apply_kernel<<<2 * njobs, 512, 0, st>>>(d_jobs, r, rcap, wk);
+  FDE_LAUNCH("recomp_apply_kernel");
+  return FDE_OK;
+}
+
+fde_status recompress_jobs(const RecompJob* d_jobs, int njobs, int r, int rcap, double abstol, double reltol,
+                           cudaStream_t st) {
+  if (r > kRecompMax || rcap > r) {
+    set_error("recompression of rank %d above %d", r, kRecompMax);
+    return FDE_ERR_ARG;
+  }
+  recompress_kernel<<<njobs, 512, recompress_smem(r), st>>>(d_jobs, r, rcap, abstol, reltol);
+  FDE_LAUNCH("recompress_kernel");
+  return FDE_OK;
+}
+}  // namespace fde
 
 static fde_status check_op(const fde_op_params* p) {
   FDE_ARG(p != nullptr, "params is NULL");

@@ -113,4 +113,35 @@ fde_status upload_specs(const std::vector<std::vector<HostOp<T>>>& specs, DevPoo
                         cudaStream_t st);
 size_t solve_scratch_elems(const hodlr_s* h, int ncols, int lvl0);
 
+// QR + SVD recompression U Vᵀ -> U' V'ᵀ (§4.1), one CTA per job: Uin (m x r)
+// and Vin (n x r) are overwritten by their Householder QR; Uout, Vout get
+// rcap columns, zero beyond the kept rank, which counts the singular values
+// above max(abstol, reltol σ_max) (capped at rcap).  *rank_out = kept rank;
+// rank_full (may be NULL) receives the uncapped count by atomic maximum.
+struct RecompJob {
+  double* Uin;
+  double* Vin;
+  double* Uout;
+  double* Vout;
+  int m, n, ld;  // rows of U, rows of V, leading dimension of all four
+  int* rank_out;
+  int* rank_full = nullptr;
+};
+constexpr int kRecompMax = 96;  // largest r (shared memory 3 r² + 3 r doubles)
+// Workspace of recompress_split for njobs jobs of rank r, capacity rcap:
+// tau 2 njobs r, R 2 njobs r², C 2 njobs r rcap doubles, rank njobs ints.
+struct RecompWork {
+  double* tau;
+  double* R;
+  double* C;
+  int* rank;
+};
+// recompress_jobs in three launches (QR of each factor in its own CTA, the
+// small core, the products with the Householder factors in their own CTAs).
+fde_status recompress_split(const RecompJob* d_jobs, int njobs, int r, int rcap, double abstol, double reltol,
+                            const RecompWork& wk, cudaStream_t st);
+fde_status recompress_prepare(int rmax);  // once, before launches (and before any capture)
+fde_status recompress_jobs(const RecompJob* d_jobs, int njobs, int r, int rcap, double abstol, double reltol,
+                           cudaStream_t st);
+
 }  // namespace fde

@@ -158,6 +158,29 @@ def fd2d(N=256, alpha=(1.3, 1.7), steps=50, leaf=64, tol=1e-10, coeff_scale=(1.0
                     np.array([100.0, 0.0]), np.array([0.0, 100.0]), np.array([0.0, 10.0]))
 
 
+def fd2d_paper(N=4096, alpha=(1.3, 1.7), steps=8, leaf=256, tol=1e-8) -> Workload:
+    """The shape of the paper's 2D experiment (§6.2): constant diffusion
+    coefficients d_{1,±} = d_{2,±} = 1, Δt = 1, 8 implicit-Euler steps, the
+    paper's source f (rank <= 2), on the grid x_i = i/(N+1) (the printed
+    Δx = 1/(N+2) is read as the grid of §2.2.1), U0 = u0(x) u0(y)ᵀ."""
+    w = fd2d(N=N, alpha=alpha, steps=steps, leaf=leaf, tol=tol)
+    w.dt = 1.0
+    for op in w.ops:
+        op.dt = 1.0
+        op.d_plus = np.ones(N)
+        op.d_minus = np.ones(N)
+    w.name = f"fd2d_paper_n{N}_a{alpha[0]}_{alpha[1]}"
+    return w
+
+
+def u0_factors(w: Workload):
+    """Factors (W0, Z0) of the 2D initial value U0 = u0(x) u0(y)ᵀ (rank one),
+    for the factored time loop."""
+    x = grid(w.N)
+    u = u0_profile(x)
+    return u[:, None].copy(), u[:, None].copy()
+
+
 def random_matrix(m: int, n: int, seed: int) -> np.ndarray:
     """Seeded dense test matrix (standard normal entries), column-major semantics."""
     rng = SplitMix64(SEED_BASE + 7919 * seed)
