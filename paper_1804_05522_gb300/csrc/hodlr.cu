@@ -368,7 +368,10 @@ __device__ void house_apply(const double* A, int lda, int m, int kq, const doubl
 
 // One-sided (Hestenes) Jacobi SVD of M (rows x cols, ld ldm), Z accumulates
 // the right rotations (cols x cols, ld ldz); columns of M end up W Σ.
-__device__ void jacobi_svd(double* M, int ldm, int rows, int cols, double* Z, int ldz, int* s_rot) {
+// A pair is rotated while |γ| > ortho_tol sqrt(αβ); pairs with a column of
+// squared norm <= floor2 (negligible against the matrix) are left alone.
+__device__ void jacobi_svd(double* M, int ldm, int rows, int cols, double* Z, int ldz, int* s_rot,
+                           double ortho_tol = 1e-15, double floor2 = 0.0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) Z[(e % cols) + (e / cols) * ldz] = (e % cols == e / cols);
   __syncthreads();
@@ -403,7 +406,7 @@ __device__ void jacobi_svd(double* M, int ldm, int rows, int cols, double* Z, in
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
+        if (ga != 0.0 && fabs(ga) > ortho_tol * sqrt(al * be) && al > floor2 && be > floor2) {
           const double zeta = (be - al) / (2.0 * ga);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
@@ -537,7 +540,17 @@ __global__ void __launch_bounds__(512) recomp_core_kernel(const RecompJob* __res
     M[e] = s;
   }
   __syncthreads();
-  jacobi_svd(M, r, qm, qn, Z, r, &s_rot);
+  {
+    // orthogonality to the rounding level of an r-column FP64 rotation
+    // sequence, and no rotations among columns below 1e-15 ||M||_F (their
+    // singular values are far below any truncation threshold): without these
+    // the sweeps run to their cap on the rank-deficient cores of padded factors
+    __shared__ double red[32];
+    double part = 0.0;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) part += M[e] * M[e];
+    const double fro2 = block_sum(part, red);
+    jacobi_svd(M, r, qm, qn, Z, r, &s_rot, 4.0 * r * 1.1102230246251565e-16, 1e-30 * fro2);
+  }
   __syncthreads();
   for (int c = threadIdx.x; c < qn; c += blockDim.x) {
     double s = 0.0;
@@ -1166,6 +1179,14 @@ fde_status recompress_split(const RecompJob* d_jobs, int njobs, int r, int rcap,
   FDE_LAUNCH("recomp_core_kernel");
   recomp_apply_kernel<<<2 * njobs, 512, 0, st>>>(d_jobs, r, rcap, wk);
   FDE_LAUNCH("recomp_apply_kernel");
+  return FDE_OK;
+}
+
+fde_status recompress_core(const RecompJob* d_job, int r, int rcap, double abstol, double reltol,
+                           const RecompWork& wk, cudaStream_t st) {
+  recomp_core_kernel<<<1, 512, (2 * (size_t)r * r + r) * sizeof(double) + r * sizeof(int), st>>>(
+      d_job, r, rcap, abstol, reltol, wk);
+  FDE_LAUNCH("recomp_core_kernel");
   return FDE_OK;
 }
 

@@ -140,6 +140,19 @@ struct RecompWork {
 // small core, the products with the Householder factors in their own CTAs).
 fde_status recompress_split(const RecompJob* d_jobs, int njobs, int r, int rcap, double abstol, double reltol,
                             const RecompWork& wk, cudaStream_t st);
+// The core of recompress_split alone: R_U, R_V (r x r each, ld r) in wk.R,
+// the kept factors to wk.C, the rank to wk.rank[0] and the job's rank fields.
+fde_status recompress_core(const RecompJob* d_job, int r, int rcap, double abstol, double reltol,
+                           const RecompWork& wk, cudaStream_t st);
+// The same recompression for one job with m = n >= 128 rows, the QR spread over
+// many CTAs (tsqr.cu).  A plan fixes the job's buffers and shapes (device
+// workspace from `pool`); tsqr_run launches it (no allocation, capturable).
+struct TsqrPlan;
+fde_status tsqr_prepare(int rmax);  // once, before any capture
+fde_status tsqr_plan_create(const RecompJob& job, const RecompJob* d_job, int r, int rcap, const RecompWork& wk,
+                            DevPool& pool, TsqrPlan** out);
+fde_status tsqr_run(const TsqrPlan* plan, double abstol, double reltol, cudaStream_t st);
+void tsqr_plan_free(TsqrPlan* plan);
 fde_status recompress_prepare(int rmax);  // once, before launches (and before any capture)
 fde_status recompress_jobs(const RecompJob* d_jobs, int njobs, int r, int rcap, double abstol, double reltol,
                            cudaStream_t st);

@@ -99,12 +99,14 @@ struct fde_lowrank_s {
   RecompJob* jobs = nullptr;              // 0: right-hand side, 1: accumulation, 2: final
   int* ranks = nullptr;                   // kept ranks of the three jobs, then their uncapped maxima
   RecompWork wk{};                        // workspace of the recompressions
+  TsqrPlan* tp[3] = {nullptr, nullptr, nullptr};  // their TSQR plans
   cudaStream_t gs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t exec = nullptr;
   size_t graph_kernels = 0;
   int rank = 0;
   ~fde_lowrank_s() {
+    for (auto* t : tp) tsqr_plan_free(t);
     if (exec) cudaGraphExecDestroy(exec);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -129,7 +131,7 @@ fde_status lr_step_body(fde_lowrank_s* S, cudaStream_t st) {
   // truncation: eps relative to ||C||_2 and to ||X||_2 (as the paper's single
   // tolerance); the accumulation keeps 100 x more than the final truncation
   const double rel_rhs = S->eps, rel_acc = 0.01 * S->eps, rel_fin = S->eps;
-  FDE_TRY(recompress_split(S->jobs + 0, 1, kRcap + S->r_src, kRcap, 0.0, rel_rhs, S->wk, st));
+  FDE_TRY(tsqr_run(S->tp[0], 0.0, rel_rhs, st));
   lr_zero_kernel<<<grid_n(nf), 256, 0, st>>>(S->XL, S->XR, nf);
   FDE_LAUNCH("lr_zero_kernel");
   // two fADI steps per recompression of [XL | Z_j | Z_j+1] [XR | W_j | W_j+1]ᵀ
@@ -146,9 +148,9 @@ fde_status lr_step_body(fde_lowrank_s* S, cudaStream_t st) {
         FDE_LAUNCH("lr_zero_kernel");
       }
     }
-    FDE_TRY(recompress_split(S->jobs + 1, 1, 3 * kRcap, kRcap, 0.0, rel_acc, S->wk, st));
+    FDE_TRY(tsqr_run(S->tp[1], 0.0, rel_acc, st));
   }
-  FDE_TRY(recompress_split(S->jobs + 2, 1, kRcap, kRcap, 0.0, rel_fin, S->wk, st));
+  FDE_TRY(tsqr_run(S->tp[2], 0.0, rel_fin, st));
   return FDE_OK;
 }
 
@@ -251,6 +253,9 @@ fde_status lr_create(const fde_run_params* p, const double* hW0, const double* h
   FDE_TRY(pool.alloc(&S->jobs, 3));
   FDE_CUDA(cudaMemcpy(S->jobs, jb.data(), 3 * sizeof(RecompJob), cudaMemcpyHostToDevice));
   FDE_TRY(recompress_prepare(3 * kRcap));
+  FDE_TRY(tsqr_prepare(3 * kRcap));
+  const int rj[3] = {kRcap + r, 3 * kRcap, kRcap};
+  for (int k = 0; k < 3; ++k) FDE_TRY(tsqr_plan_create(jb[k], S->jobs + k, rj[k], kRcap, S->wk, pool, &S->tp[k]));
   // shifted factorisations and their solve plans (kRcap columns)
   S->fx.resize(J);
   S->fy.resize(J);
