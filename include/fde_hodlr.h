@@ -204,6 +204,17 @@ fde_status sylv_inner_solve(sylv_t s, const double* d_C, double* d_X, int ld, vo
 /* R = C - A_x X - X A_yᵀ in FP64 (structured, FFT based).  For checks. */
 fde_status sylv_residual(sylv_t s, const double* d_C, const double* d_X, double* d_R, int ld, void* stream);
 
+/* Work model of one inner solve (one refinement sweep), host only, no device
+ * work.  *method_flops: the tensor-core-eligible flops the method itself needs
+ * (§3.4 divide and conquer with §3.3 fADI by shifted HODLR solves): the leaf
+ * Bartels–Stewart transforms 4 n_i n_j (n_i + n_j) per leaf pair; per level and
+ * node pair the X0-dependent right-hand-side factors, J shifted HODLR solves of
+ * the 2K-column factors (2 n s + 4 K s log2(s/n) per column) and the rank
+ * 2J(K_x + K_y) update, with the counted leaf sizes, level ranks K and shift
+ * counts J.  *impl_flops: Σ 2 m n k of the batched GEMMs the implementation
+ * launches per inner solve.  Errors: FDE_ERR_ARG (NULL argument). */
+fde_status sylv_flop_model(sylv_t s, double* method_flops, double* impl_flops);
+
 void sylv_free(sylv_t s);
 
 /* ------------------------------------------- fADI shifts (host only) -- */
@@ -340,6 +351,9 @@ fde_status fde_runner_set_coefficients(fde_runner_t r, const double* d_plus_x, c
  * ||U - U*||_F <= fro / (θ_x + θ_y).  Synchronises `stream`.  FDE_ERR_ARG if
  * no step was taken since fde_runner_create / fde_runner_load. */
 fde_status fde_runner_residual(fde_runner_t r, double* relres, double* maxabs, double* fro, void* stream);
+/* sylv_flop_model of a 2D runner's Sylvester solver (per refinement sweep).
+ * FDE_ERR_ARG for a 1D runner or a NULL argument. */
+fde_status fde_runner_flop_model(fde_runner_t r, double* method_flops, double* impl_flops);
 fde_status fde_runner_stats(fde_runner_t r, fde_run_stats* stats);
 void fde_runner_free(fde_runner_t r);
 

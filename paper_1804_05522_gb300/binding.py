@@ -84,6 +84,7 @@ _SIGS = {
     "sylv_step": ([_P, _P, _P, C.c_int, _P, C.POINTER(C.c_double), C.POINTER(C.c_int)], C.c_int),
     "sylv_inner_solve": ([_P, _P, _P, C.c_int, _P], C.c_int),
     "sylv_residual": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
+    "sylv_flop_model": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "sylv_free": ([_P], None),
     "fde_block_interval": ([C.POINTER(OpParams), C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
                            C.c_int),
@@ -97,6 +98,7 @@ _SIGS = {
     "fde_runner_residual": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), _P],
                             C.c_int),
     "fde_runner_set_coefficients": ([_P, _P, _P, _P, _P, _P], C.c_int),
+    "fde_runner_flop_model": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "fde_runner_step_source_async": ([_P, _P, C.c_int, _P], C.c_int),
     "fde_runner_state_async": ([_P, _P, _P], C.c_int),
     "fde_runner_sync": ([_P, _P], C.c_int),
@@ -387,6 +389,18 @@ class Lib:
         rr, mx, fr = C.c_double(), C.c_double(), C.c_double()
         self.check(self.dll.fde_runner_residual(r, C.byref(rr), C.byref(mx), C.byref(fr), stream))
         return rr.value, mx.value, fr.value
+
+    def runner_flop_model(self, r: int):
+        """(method flops, implementation GEMM flops) of one refinement sweep."""
+        a, b = C.c_double(), C.c_double()
+        self.check(self.dll.fde_runner_flop_model(r, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def sylv_flop_model(self, s: int):
+        """(method flops, implementation GEMM flops) of one inner solve."""
+        a, b = C.c_double(), C.c_double()
+        self.check(self.dll.sylv_flop_model(s, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def runner_set_coefficients(self, r: int, dpx, dmx, dpy=None, dmy=None, stream: int = 0):
         """D_± of the next step (host arrays, or device addresses as ints)."""

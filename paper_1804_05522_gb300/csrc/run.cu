@@ -593,6 +593,11 @@ extern "C" fde_status fde_runner_set_coefficients(fde_runner_t r, const double* 
   return runner_set_coeffs(r, d_plus_x, d_minus_x, d_plus_y, d_minus_y, (cudaStream_t)stream);
 }
 
+extern "C" fde_status fde_runner_flop_model(fde_runner_t r, double* method_flops, double* impl_flops) {
+  FDE_ARG(r != nullptr && r->p.dim == 2, "needs a 2D runner");
+  return sylv_flop_model(r->s, method_flops, impl_flops);
+}
+
 extern "C" fde_status fde_runner_residual(fde_runner_t r, double* relres, double* maxabs, double* fro,
                                           void* stream) {
   FDE_ARG(r != nullptr && relres != nullptr && maxabs != nullptr, "NULL argument");

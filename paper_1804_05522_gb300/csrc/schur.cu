@@ -252,15 +252,129 @@ fde_status leaf_schur(double* H, double* Q, int ld, size_t stride, const int* d_
 // coupling is subtracted from the rest of the window, which then shifts.
 constexpr int kMaxRowWarps = 9;   // leaves up to 256 rows: blocks of >= 31 rows
 
+// FP32: 128 registers.  A 96-register build (no spills, seven 3-warp CTAs per
+// SM instead of five) was 19 % slower on the 1024-pair launches: the SM's
+// issue slots, not the resident chains, bound the solve.
+// Blocks of at most this many rows stage their R block in shared memory.
+constexpr int kTrsylStageR = 64;
+
+// Shared-memory elements in front of the diagonal blocks: the ring of solved
+// columns, or the 32 x kStg staging tile of the coupling prologue (larger).
+constexpr int kStg = 36;  // row stride of the staging tile: 16-byte aligned rows
+__host__ __device__ inline int trsyl_ring_elems(int warps, int lmax) {
+  const int ring = (warps + 1) * 2 * lmax;
+  return ring > 32 * kStg ? ring : 32 * kStg;
+}
+
+// Left-looking block coupling (FP32): F -= S[block, after] Y[after, block]
+// + Y[block, after] R[block, after]ᵀ for the rx rows and ry columns of the
+// leaf after this block (Y there already solved).  Lane = row of the block
+// (warp w: rows rlo..rlo+nr), 32 columns of F per pass in registers; the
+// 32-row chunks of Y (S term) and 32-column chunks of R (R term) are staged
+// in shared memory and read as broadcasts.  Every global load is issued in
+// batches (16 per thread for a staging pass, 32 per lane for the lane's own
+// S row or Y row chunk) ahead of its use, so each chunk waits on memory a
+// few times instead of once per element.
 template <typename T>
+__device__ __forceinline__ void trsyl_stage(T* stg, const T* __restrict__ src, size_t s_minor, size_t s_major,
+                                            int lim_minor, int lim_major) {
+  // stg[major * kStg + minor] = src[minor * s_minor + major * s_major] inside
+  // the limits, 0 outside; consecutive threads take consecutive minor indices
+  for (int e0 = threadIdx.x; e0 < 32 * 32; e0 += 16 * blockDim.x) {
+    T v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = e0 + u * (int)blockDim.x, mi = e & 31, ma = e >> 5;
+      v[u] = (e < 32 * 32 && mi < lim_minor && ma < lim_major) ? src[mi * s_minor + ma * s_major] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < 32 * 32) stg[(e >> 5) * kStg + (e & 31)] = v[u];
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void trsyl_couple(const T* __restrict__ S, const T* __restrict__ R, int ld,
+                                             T* __restrict__ Y, int ldw, int n1, int n2, int rx, int ry, int rlo,
+                                             int nr, T* stg) {
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < nr;
+  const int i = rlo + lane;
+  for (int c0 = 0; c0 < n2; c0 += 32) {
+    T acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = T(0);
+    const int nc = n2 - c0 < 32 ? n2 - c0 : 32;
+    for (int t0 = 0; t0 < rx; t0 += 32) {
+      const int tn = rx - t0 < 32 ? rx - t0 : 32;
+      T sv[32];  // S(i, n1 + t0 + r)
+#pragma unroll
+      for (int r = 0; r < 32; ++r) sv[r] = (act && r < tn) ? S[i + (size_t)(n1 + t0 + r) * ld] : T(0);
+      __syncthreads();
+      // stg[r][c] = Y(n1 + t0 + r, c0 + c): minor = row r of Y (contiguous)
+      trsyl_stage<T>(stg, Y + (n1 + t0) + (size_t)c0 * ldw, 1, (size_t)ldw, tn, nc);
+      __syncthreads();
+      // stg[c][r .. r + 3] as one 16-byte broadcast read
+#pragma unroll
+      for (int r = 0; r < 32; r += 4) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(stg + c * kStg + r);
+          acc[c] += sv[r] * v.x;
+          acc[c] += sv[r + 1] * v.y;
+          acc[c] += sv[r + 2] * v.z;
+          acc[c] += sv[r + 3] * v.w;
+        }
+      }
+    }
+    for (int t0 = 0; t0 < ry; t0 += 32) {
+      const int tn = ry - t0 < 32 ? ry - t0 : 32;
+      T yv[32];  // Y(i, n2 + t0 + r)
+#pragma unroll
+      for (int r = 0; r < 32; ++r) yv[r] = (act && r < tn) ? Y[i + (size_t)(n2 + t0 + r) * ldw] : T(0);
+      __syncthreads();
+      // stg[r][c] = R(c0 + c, n2 + t0 + r): minor = row c of R (contiguous)
+      trsyl_stage<T>(stg, R + c0 + (size_t)(n2 + t0) * ld, 1, (size_t)ld, nc, tn);
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const float4* row = reinterpret_cast<const float4*>(stg + r * kStg);
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) {
+          const float4 v = row[c >> 2];
+          acc[c] += yv[r] * v.x;
+          acc[c + 1] += yv[r] * v.y;
+          acc[c + 2] += yv[r] * v.z;
+          acc[c + 3] += yv[r] * v.w;
+        }
+      }
+    }
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < nc) Y[i + (size_t)(c0 + c) * ldw] -= acc[c];
+    }
+  }
+  __syncthreads();
+}
+
+// RSM: the R block (n2 x n2, ld lmax) is staged in shared memory at the start
+// (blocks of blocked leaves), so the per-column reads of R on the dependency
+// chain do not wait on L2.
+template <typename T, bool RSM>
 __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 ? 128 : 168)
-    trsyl_kernel(const T* __restrict__ Sall, const T* __restrict__ Rall, int ld, int lmax, TrsylSet s0, TrsylSet s1,
-                 T* __restrict__ W, int ldw, int use_panel, int panel_elems) {
+    trsyl_kernel(const T* __restrict__ Sall, const T* __restrict__ Rall, int ld, int lmax,
+                 const __grid_constant__ TrsylSets sets, T* __restrict__ W, int ldw, int use_panel, int panel_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // blocks [0, s0.count) solve the pairs of s0, the rest those of s1
-  const bool second = (int)blockIdx.x >= s0.count;
-  const TrsylSet& ps = second ? s1 : s0;
-  const int b = second ? (int)blockIdx.x - s0.count : (int)blockIdx.x;
+  // the CTAs walk the sets in order: blocks [0, count_0) solve set 0, ...
+  int b = (int)blockIdx.x, si = 0;
+  while (si + 1 < sets.n && b >= sets.s[si].count) {
+    b -= sets.s[si].count;
+    ++si;
+  }
+  const TrsylSet& ps = sets.s[si];
   const int* __restrict__ soff_x = ps.soff_x;
   const int* __restrict__ lo_x = ps.lo_x;
   const int* __restrict__ n_x = ps.n_x;
@@ -278,15 +392,34 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
   // by the warps above for nwarps - 1 steps after it is written)
   const int ring = (int)(blockDim.x >> 5) + 1;
   T* ycol = reinterpret_cast<T*>(smem_raw);                  // ring x [col k | col k-1] x lmax
-  T* sdiag = ycol + (size_t)ring * 2 * lmax;                 // per warp: its diagonal S block, 32 x 33
+  T* sdiag = ycol + trsyl_ring_elems((int)(blockDim.x >> 5), lmax);  // per warp: its diagonal S block, 32 x 33
   T* panel = sdiag + (size_t)(blockDim.x >> 5) * 32 * 33;    // S panels (use_panel), see below
   int* cg_top = reinterpret_cast<int*>(panel + (use_panel ? panel_elems : 0));
   int* cg_info = cg_top + lmax;                              // bit 0: two columns; bit 1: block start
   int* cg_cblo = cg_info + lmax;                             // first column of the group's column block
+  T* Rsm = reinterpret_cast<T*>(((uintptr_t)(cg_cblo + lmax) + 15) & ~(uintptr_t)15);  // RSM: R block, ld lmax
   __shared__ int rb_lo[kMaxRowWarps], rb_n[kMaxRowWarps], poff[kMaxRowWarps];
   __shared__ int s_ncg, s_nrb;
 #define SS(i, j) S[(i) + (size_t)(j)*ld]
 #define RR(i, j) R[(i) + (size_t)(j)*ld]
+#define RV(i, j) (RSM ? Rsm[(i) + (j)*lmax] : __ldg(R + (i) + (size_t)(j)*ld))
+  if constexpr (RSM) {
+    // loads in batches of 16 per thread, then the stores
+    const int tot = n2 * n2;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 16 * blockDim.x) {
+      T v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = e0 + u * (int)blockDim.x;
+        v[u] = e < tot ? R[(e % n2) + (size_t)(e / n2) * ld] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = e0 + u * (int)blockDim.x;
+        if (e < tot) Rsm[(e % n2) + (e / n2) * lmax] = v[u];
+      }
+    }
+  }
   if (threadIdx.x == 0) {
     int w = 0;
     for (int hi = n1; hi > 0 && w < kMaxRowWarps; ++w) {
@@ -328,12 +461,26 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
   __syncthreads();
   const int ncg = s_ncg, nrb = s_nrb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    const int rx = ps.rest_x ? ps.rest_x[p] : 0, ry = ps.rest_y ? ps.rest_y[q] : 0;
+    if (rx > 0 || ry > 0)  // the staging tile overlays the (not yet used) ring
+      trsyl_couple<T>(S, R, ld, Y, ldw, n1, n2, rx, ry, warp < nrb ? rb_lo[warp] : 0, warp < nrb ? rb_n[warp] : 0,
+                      ycol);
+  }
   {
-    // every warp's diagonal block (the back-substitution chain reads a column per row)
+    // every warp's diagonal block (the back-substitution chain reads a column
+    // per row), without the lane's own 1 x 1 or 2 x 2 diagonal block: the
+    // chain then leaves a solved row's right-hand side as it is, and the row
+    // solves its own unknown from it after the chain
     const int w_ = threadIdx.x >> 5, l_ = threadIdx.x & 31;
     const int vlo = w_ < s_nrb ? rb_lo[w_] : 0, vn = w_ < s_nrb ? rb_n[w_] : 0;
     T* sv = sdiag + (size_t)w_ * 32 * 33 + l_;
-    for (int t = 0; t < 32; ++t) sv[t * 33] = (l_ < vn && t < vn) ? SS(vlo + l_, vlo + t) : T(0);
+    const bool pr_lo = l_ < vn && l_ > 0 && SS(vlo + l_, vlo + l_ - 1) != T(0);       // pair (l_-1, l_)
+    const bool pr_hi = l_ + 1 < vn && SS(vlo + l_ + 1, vlo + l_) != T(0);            // pair (l_, l_+1)
+    for (int t = 0; t < 32; ++t) {
+      const bool own = t == l_ || (t == l_ - 1 && pr_lo) || (t == l_ + 1 && pr_hi);
+      sv[t * 33] = (l_ < vn && t < vn && !own) ? SS(vlo + l_, vlo + t) : T(0);
+    }
   }
   if (use_panel) {
     // the S coupling of every column group rereads these entries: stage them
@@ -384,11 +531,10 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
 #pragma unroll 4
         for (int l = k + 1; l < n2; ++l) {
           const T yl = active ? Y[i + (size_t)l * ldw] : T(0);
-          const T* Rl = R + (size_t)l * ld;
 #pragma unroll
           for (int t = 0; t < 32; ++t) {
             const int col = k - 31 + t;
-            if (col >= cb_lo) yb[t] -= __ldg(Rl + col) * yl;
+            if (col >= cb_lo) yb[t] -= RV(col, l) * yl;
           }
         }
       }
@@ -427,7 +573,7 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
       }
       T ya_fin = T(0), yb_fin = T(0);
       if (!two) {
-        const T mu = __ldg(R + k + (size_t)k * ld);
+        const T mu = RV(k, k);
         T inv = T(1) / (sii + mu), p00 = T(0), p01 = T(0), p10 = T(0), p11 = T(0);
         if (bottom) {  // inverse of (S_2x2 + mu I)
           const T d = (s00 + mu) * (s11 + mu) - s01 * s10;
@@ -436,34 +582,34 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
           p10 = -s10 / d;
           p11 = (s00 + mu) / d;
         }
-        for (int rr = nr - 1; rr >= 0;) {
-          if (rr > 0 && ((pair_mask >> rr) & 1u)) {
-            const T st = sd[(rr - 1) * 33], sb = sd[rr * 33];
-            const T ftop = __shfl_sync(0xffffffffu, fb, rr - 1);
-            T y0 = T(0), y1 = T(0);
-            if (lane == rr) {
-              y0 = p00 * ftop + p01 * fb;
-              y1 = p10 * ftop + p11 * fb;
+        // rows bottom-up, unrolled (a block has at most 32 rows): the owner
+        // lane's solution is broadcast, every row removes its coupling (the
+        // owner's own diagonal block is zero in sd, so its fb stays final)
+#pragma unroll
+        for (int rr = 31; rr >= 0; --rr) {
+          if (rr < nr) {
+            if (rr > 0 && ((pair_mask >> rr) & 1u)) {
+              const T ftop = __shfl_sync(0xffffffffu, fb, rr - 1);
+              const T y0 = __shfl_sync(0xffffffffu, p00 * ftop + p01 * fb, rr);
+              const T y1 = __shfl_sync(0xffffffffu, p10 * ftop + p11 * fb, rr);
+              fb -= sd[(rr - 1) * 33] * y0 + sd[rr * 33] * y1;
+            } else if (!(rr + 1 < nr && ((pair_mask >> (rr + 1)) & 1u))) {
+              const T y = __shfl_sync(0xffffffffu, fb * inv, rr);
+              fb -= sd[rr * 33] * y;
             }
-            y0 = __shfl_sync(0xffffffffu, y0, rr);
-            y1 = __shfl_sync(0xffffffffu, y1, rr);
-            if (lane == rr - 1) yb_fin = y0;
-            if (lane == rr) yb_fin = y1;
-            fb -= st * y0 + sb * y1;
-            rr -= 2;
-          } else {
-            const T sb = sd[rr * 33];
-            T y = (lane == rr) ? fb * inv : T(0);
-            y = __shfl_sync(0xffffffffu, y, rr);
-            if (lane == rr) yb_fin = y;
-            fb -= sb * y;
-            rr -= 1;
           }
         }
+        // this row's unknown from its final right-hand side (2 x 2 blocks:
+        // solved by the bottom lane, the top one's value shifted up)
+        const T fdn = __shfl_up_sync(0xffffffffu, fb, 1);
+        const T ytop = p00 * fdn + p01 * fb, ybot = p10 * fdn + p11 * fb;
+        const T ytop_below = __shfl_down_sync(0xffffffffu, ytop, 1);
+        const bool is_top = lane + 1 < nr && ((pair_mask >> (lane + 1)) & 1u);
+        yb_fin = bottom ? ybot : (is_top ? ytop_below : fb * inv);
       } else {
         // R block [[a, b], [c, d]] couples columns k-1 (unknown 1) and k (unknown 2)
-        const T a = __ldg(R + (k - 1) + (size_t)(k - 1) * ld), b = __ldg(R + (k - 1) + (size_t)k * ld);
-        const T c = __ldg(R + k + (size_t)(k - 1) * ld), d = __ldg(R + k + (size_t)k * ld);
+        const T a = RV(k - 1, k - 1), b = RV(k - 1, k);
+        const T c = RV(k, k - 1), d = RV(k, k);
         // 1 x 1 row: [[s+a, b], [c, s+d]]^{-1}
         const T det1 = (sii + a) * (sii + d) - b * c;
         const T e00 = (sii + d) / det1, e01 = -b / det1, e10 = -c / det1, e11 = (sii + a) / det1;
@@ -536,14 +682,12 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
         }
       }
       // remove the group's coupling from the rest of the window, then shift it
-      const T* Rk = R + (size_t)k * ld;
-      const T* Rk1 = R + (size_t)(k - 1) * ld;
 #pragma unroll
       for (int t = 0; t < 31; ++t) {
         const int col = k - 31 + t;
         if (col >= cb_lo && (t < 30 || !two)) {
-          T v = __ldg(Rk + col) * yb_fin;
-          if (two) v += __ldg(Rk1 + col) * ya_fin;
+          T v = RV(col, k) * yb_fin;
+          if (two) v += RV(col, k - 1) * ya_fin;
           yb[t] -= v;
         }
       }
@@ -562,48 +706,80 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
   }
 #undef SS
 #undef RR
+#undef RV
 }
 
 template <typename T>
 fde_status leaf_trsyl(const T* S, const T* R, int ld, int lmax, const int* d_soff_x, const int* d_lo_x,
                       const int* d_n_x, int nx, const int* d_soff_y, const int* d_lo_y, const int* d_n_y, int ny,
                       T* W, int ldw, cudaStream_t st, double flops) {
-  const TrsylSet s0{d_soff_x, d_lo_x, d_n_x, nx, d_soff_y, d_lo_y, d_n_y, nx * ny};
-  return leaf_trsyl2<T>(S, R, ld, lmax, s0, TrsylSet{}, W, ldw, st, flops);
+  TrsylSets sets;
+  sets.s[0] = TrsylSet{d_soff_x, d_lo_x, d_n_x, nx, d_soff_y, d_lo_y, d_n_y, nx * ny};
+  sets.n = 1;
+  return leaf_trsyl_sets<T>(S, R, ld, lmax, sets, W, ldw, st, flops);
 }
 
 template <typename T>
-fde_status leaf_trsyl2(const T* S, const T* R, int ld, int lmax, const TrsylSet& s0, const TrsylSet& s1, T* W,
-                       int ldw, cudaStream_t st, double flops) {
+fde_status leaf_trsyl_sets(const T* S, const T* R, int ld, int lmax, const TrsylSets& sets, T* W, int ldw,
+                           cudaStream_t st, double flops) {
   if (lmax > 32 * kMaxRowWarps - kMaxRowWarps || lmax > ld) {
     set_error("leaf_trsyl: problem size %d above %d (or above ld %d)", lmax, 32 * kMaxRowWarps - kMaxRowWarps, ld);
     return FDE_ERR_ARG;
   }
-  const int warps = (lmax + 30) / 31 < kMaxRowWarps ? (lmax + 30) / 31 : kMaxRowWarps;
+  if (sets.n < 1 || sets.n > kTrsylMaxSets) {
+    set_error("leaf_trsyl: %d sets (1..%d)", sets.n, kTrsylMaxSets);
+    return FDE_ERR_ARG;
+  }
+  if (sizeof(T) != sizeof(float))
+    for (int k = 0; k < sets.n; ++k)
+      if (sets.s[k].rest_x || sets.s[k].rest_y) {
+        set_error("leaf_trsyl: block coupling is FP32 only");
+        return FDE_ERR_ARG;
+      }
+  // blocks of at most 32 rows need one warp; longer ones are cut into blocks
+  // of 31 or 32 rows (a cut never splits a 2 x 2 block)
+  int warps = lmax <= 32 ? 1 : (lmax + 30) / 31;
+  if (warps > kMaxRowWarps) warps = kMaxRowWarps;
   // largest panel total: warp w has at most 32 w rows below its block
   int panel_elems = 0;
   for (int w = 0; w < warps; ++w) panel_elems += 33 * (32 * w < lmax ? 32 * w : lmax);
-  const size_t base = ((size_t)(warps + 1) * 2 * lmax + (size_t)warps * 32 * 33) * sizeof(T) +
+  const size_t base = ((size_t)trsyl_ring_elems(warps, lmax) + (size_t)warps * 32 * 33) * sizeof(T) +
                       3 * (size_t)lmax * sizeof(int);
   const size_t with_panel = base + (size_t)panel_elems * sizeof(T);
   const size_t limit = 224 * 1024;
   const int use_panel = with_panel <= limit ? 1 : 0;
   const size_t smem = use_panel ? with_panel : base;
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(trsyl_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
-  FDE_CUDA(attr);
+  // small blocks: R staged in shared memory (16 bytes of alignment slack)
+  const bool rsm = lmax <= kTrsylStageR;
+  const size_t smem_launch = smem + (rsm ? 16 + (size_t)lmax * lmax * sizeof(T) : 0);
+  static const cudaError_t attr0 =
+      cudaFuncSetAttribute(trsyl_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+  static const cudaError_t attr1 = cudaFuncSetAttribute(trsyl_kernel<T, true>,
+                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+  FDE_CUDA(attr0);
+  FDE_CUDA(attr1);
+  if (smem_launch > limit) {
+    set_error("leaf_trsyl: %zu bytes of shared memory above %zu", smem_launch, limit);
+    return FDE_ERR_ARG;
+  }
   ProfScope ps(sizeof(T) == 4 ? "trsyl32" : "trsyl64", st, flops, 1);
-  const int blocks = s0.count + s1.count;
+  long long blocks = 0;
+  for (int k = 0; k < sets.n; ++k) blocks += sets.s[k].count;
   if (blocks == 0) return FDE_OK;
-  trsyl_kernel<T><<<blocks, warps * 32, smem, st>>>(S, R, ld, lmax, s0, s1, W, ldw, use_panel, panel_elems);
+  if (rsm)
+    trsyl_kernel<T, true><<<(unsigned)blocks, warps * 32, smem_launch, st>>>(S, R, ld, lmax, sets, W, ldw, use_panel,
+                                                                             panel_elems);
+  else
+    trsyl_kernel<T, false><<<(unsigned)blocks, warps * 32, smem_launch, st>>>(S, R, ld, lmax, sets, W, ldw,
+                                                                              use_panel, panel_elems);
   FDE_LAUNCH("trsyl_kernel");
   return FDE_OK;
 }
 
-template fde_status leaf_trsyl2<double>(const double*, const double*, int, int, const TrsylSet&, const TrsylSet&,
-                                        double*, int, cudaStream_t, double);
-template fde_status leaf_trsyl2<float>(const float*, const float*, int, int, const TrsylSet&, const TrsylSet&,
-                                       float*, int, cudaStream_t, double);
+template fde_status leaf_trsyl_sets<double>(const double*, const double*, int, int, const TrsylSets&, double*, int,
+                                            cudaStream_t, double);
+template fde_status leaf_trsyl_sets<float>(const float*, const float*, int, int, const TrsylSets&, float*, int,
+                                           cudaStream_t, double);
 template fde_status leaf_trsyl<double>(const double*, const double*, int, int, const int*, const int*, const int*,
                                        int, const int*, const int*, const int*, int, double*, int, cudaStream_t, double);
 template fde_status leaf_trsyl<float>(const float*, const float*, int, int, const int*, const int*, const int*, int,

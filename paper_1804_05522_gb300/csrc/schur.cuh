@@ -27,15 +27,28 @@ fde_status leaf_trsyl(const T* S, const T* R, int ld, int lmax, const int* d_sof
                       T* W, int ldw, cudaStream_t st, double flops = 0.0);
 
 // A set of pairs for one launch: (p, q) over nx x (count / nx), as above.
+// rest_x[p] / rest_y[q] (device, may be NULL = 0): when the S_p (R_q) above
+// is a diagonal block of a larger leaf Schur form, the rows (columns) of that
+// leaf after the block.  The solve then first subtracts the coupling with the
+// already solved blocks of Y there (block Bartels–Stewart, left-looking):
+//   F -= S_p[block, after] Y[after, block] + Y[block, after] R_q[block, after]ᵀ
+// (FP32 only).
 struct TrsylSet {
   const int *soff_x = nullptr, *lo_x = nullptr, *n_x = nullptr;
   int nx = 1;
   const int *soff_y = nullptr, *lo_y = nullptr, *n_y = nullptr;
   int count = 0;
+  const int *rest_x = nullptr, *rest_y = nullptr;
 };
-// Two independent sets of pairs in one launch (blocks of s0 first).
+// Up to kTrsylMaxSets independent sets of pairs in one launch (blocks of set 0
+// first).
+constexpr int kTrsylMaxSets = 16;
+struct TrsylSets {
+  TrsylSet s[kTrsylMaxSets];
+  int n = 0;
+};
 template <typename T>
-fde_status leaf_trsyl2(const T* S, const T* R, int ld, int lmax, const TrsylSet& s0, const TrsylSet& s1, T* W,
-                       int ldw, cudaStream_t st, double flops = 0.0);
+fde_status leaf_trsyl_sets(const T* S, const T* R, int ld, int lmax, const TrsylSets& sets, T* W, int ldw,
+                           cudaStream_t st, double flops = 0.0);
 
 }  // namespace fde

@@ -311,14 +311,17 @@ __global__ void transpose_kernel(const T* __restrict__ X, T* __restrict__ Y, int
 }
 
 // ------------------------------------------------------------- FFT (FP64)
-// Leaves above this many rows are split into two diagonal blocks for the FP32
-// leaf Sylvester solves: the blocks' shorter dependency chains and smaller
-// CTAs (more of them per SM) outweigh the coupling GEMMs (leaf 128: 2.64 ->
-// 1.8 ms per sweep at N = 4096; leaf 256: 108 -> 32 ms at N = 16384).
+// Leaves above this many rows are cut into diagonal blocks of about
+// kTrsylPart rows (a cut never splits a 2 x 2 block) for the FP32 leaf
+// Sylvester solves, solved as a block Bartels–Stewart wavefront: one launch
+// per anti-diagonal of the block grid of every leaf pair, each block first
+// subtracting its coupling with the blocks solved before it.  A block of at
+// most 32 rows is one warp, whose dependency chain per column has no barrier.
 constexpr int kTrsylSplit = 64;
+constexpr int kTrsylPart = 32;
 // ... when there are at least this many leaf pairs: with fewer, the split
-// launches leave most SMs idle and the three dependent rounds cost more than
-// they save (leaf 128 at N = 1024, 64 pairs: 0.85 -> 1.07 ms per sweep).
+// launches leave most SMs idle and the dependent rounds cost more than they
+// save (leaf 128 at N = 1024, 64 pairs).
 constexpr int kTrsylSplitMinPairs = 512;
 
 // Threads of the residual's FFT kernels (radix-8 passes: P / 8 butterflies).
@@ -495,7 +498,6 @@ struct Inner {
   GemmBatch<T> g_qxt, g_qy, g_qx, g_qyt;
   // split leaves (sylv_s::trsyl_split): couplings between the diagonal blocks
   //   F12 -= S12 Y22,  F21 -= Y22 R12ᵀ,  F11 -= S12 Y21,  F11 -= Y12 R12ᵀ
-  GemmBatch<T> g_sp1, g_sp2, g_sp3, g_sp4;
   std::vector<LevelSolve<T>> lv;
   std::vector<Fact<T>> facts;         // keeps FP32 demoted factorisations alive
 };
@@ -652,11 +654,15 @@ struct sylv_s {
   // down by one where it would split a 2 x 2 Schur block).
   struct TrsylPart {
     int *soff = nullptr, *lo = nullptr, *n = nullptr;
+    int* rest = nullptr;              // rows of the leaf after the block (blocked leaves)
     int nmax = 0;
-  } tp_full, tp_top, tp_bot;
+  } tp_full;
   bool trsyl_split = false;
-  std::vector<int> split_x, split_y;  // host: rows of the top blocks
-  double trsyl_flops_tt = 0.0, trsyl_flops_tb = 0.0, trsyl_flops_bt = 0.0, trsyl_flops_bb = 0.0;
+  // blocked leaves: tp_part[a] = the block a-th from the bottom of every leaf
+  // (n = 0 where a leaf has fewer blocks); one launch per anti-diagonal
+  // a + b = d of the (a, b) block grid, with its algorithmic flops
+  std::vector<TrsylPart> tp_part;
+  std::vector<double> trsyl_step_flops;
   std::vector<Fact<double>> facts64;
   Inner<double> in64;
   Inner<float> in32;
@@ -975,29 +981,6 @@ static fde_status build_inner(sylv_s* S, Inner<T>& in, const std::vector<Fact<T>
                               st));
     }
   }
-  if (sizeof(T) == sizeof(float) && S->trsyl_split) {
-    std::vector<GemmDesc<T>> g1, g2, g3, g4;
-    T* W = in.W2;
-    for (int p = 0; p < nl; ++p)
-      for (int q = 0; q < nl; ++q) {
-        const int lo = ax->leaf_lo[p], n = ax->leaf_n[p], h = S->split_x[p];
-        const int lo2 = ay->leaf_lo[q], n2 = ay->leaf_n[q], h2 = S->split_y[q];
-        const T* S12 = in.Sx + (size_t)p * lmax * lmax + (size_t)h * lmax;   // h x (n - h)
-        const T* R12 = in.Sy + (size_t)q * lmax * lmax + (size_t)h2 * lmax;  // h2 x (n2 - h2)
-        T* F11 = W + lo + (size_t)lo2 * N;
-        T* F12 = W + lo + (size_t)(lo2 + h2) * N;
-        T* F21 = W + (lo + h) + (size_t)lo2 * N;
-        T* F22 = W + (lo + h) + (size_t)(lo2 + h2) * N;
-        g1.push_back({S12, F22, F12, h, n2 - h2, n - h, lmax, N, N});        // F12 -= S12 Y22
-        g2.push_back({F22, R12, F21, n - h, h2, n2 - h2, N, lmax, N});       // F21 -= Y22 R12ᵀ
-        g3.push_back({S12, F21, F11, h, h2, n - h, lmax, N, N});             // F11 -= S12 Y21
-        g4.push_back({F12, R12, F11, h, h2, n2 - h2, N, lmax, N});           // F11 -= Y12 R12ᵀ
-      }
-    FDE_TRY(gemm_batch_upload(pool, g1, false, false, T(-1), T(1), &in.g_sp1, st));
-    FDE_TRY(gemm_batch_upload(pool, g2, false, true, T(-1), T(1), &in.g_sp2, st));
-    FDE_TRY(gemm_batch_upload(pool, g3, false, false, T(-1), T(1), &in.g_sp3, st));
-    FDE_TRY(gemm_batch_upload(pool, g4, false, true, T(-1), T(1), &in.g_sp4, st));
-  }
   in.lv.resize(L);
   std::vector<T*> Vx = level_V<T>(ax), Vy = level_V<T>(ay), Ux = level_U<T>(ax), Uy = level_U<T>(ay);
   size_t fi = 0;
@@ -1112,22 +1095,26 @@ static fde_status run_inner(sylv_s* S, Inner<T>& in, cudaStream_t st) {
                          nl, in.W2, N, st, flops);
   };
   if (sizeof(T) == sizeof(float) && S->trsyl_split) {
-    // 2 x 2 block Bartels–Stewart over the split leaves (Rᵀ is lower block triangular)
-    FDE_TRY(trsyl(S->tp_bot, S->tp_bot, S->trsyl_flops_bb));
-    FDE_TRY(gemm_batch_run(in.g_sp1, st));
-    FDE_TRY(gemm_batch_run(in.g_sp2, st));
-    {
-      // the top-bottom and bottom-top blocks are independent: one launch
-      auto set = [&](const sylv_s::TrsylPart& px, const sylv_s::TrsylPart& py) {
-        return TrsylSet{px.soff, px.lo, px.n, nl, py.soff + nl, py.lo + nl, py.n + nl, nl * nl};
-      };
-      int nmax = S->tp_top.nmax > S->tp_bot.nmax ? S->tp_top.nmax : S->tp_bot.nmax;
-      FDE_TRY(leaf_trsyl2<T>(in.Sx, in.Sy, S->lmax, nmax, set(S->tp_top, S->tp_bot), set(S->tp_bot, S->tp_top),
-                             in.W2, N, st, S->trsyl_flops_tb + S->trsyl_flops_bt));
+    // block Bartels–Stewart over the blocked leaves: anti-diagonal d holds the
+    // blocks (a, b) a-th from the bottom of the row leaf and b-th from the
+    // right of the column leaf, a + b = d; they need only blocks of smaller d
+    const int nb = (int)S->tp_part.size();
+    for (int d = 0; d <= 2 * nb - 2; ++d) {
+      TrsylSets sets;
+      int nmax = 0;
+      for (int a = (d - nb + 1 > 0 ? d - nb + 1 : 0); a <= d && a < nb; ++a) {
+        const sylv_s::TrsylPart& px = S->tp_part[a];
+        const sylv_s::TrsylPart& py = S->tp_part[d - a];
+        if (sets.n == kTrsylMaxSets) {
+          set_error("sylv: %d leaf blocks per anti-diagonal (at most %d)", nb, kTrsylMaxSets);
+          return FDE_ERR_ARG;
+        }
+        sets.s[sets.n++] = TrsylSet{px.soff, px.lo, px.n, nl, py.soff + nl, py.lo + nl, py.n + nl, nl * nl,
+                                    px.rest, py.rest + nl};
+        nmax = std::max(nmax, std::max(px.nmax, py.nmax));
+      }
+      FDE_TRY(leaf_trsyl_sets<T>(in.Sx, in.Sy, S->lmax, nmax, sets, in.W2, N, st, S->trsyl_step_flops[d]));
     }
-    FDE_TRY(gemm_batch_run(in.g_sp3, st));
-    FDE_TRY(gemm_batch_run(in.g_sp4, st));
-    FDE_TRY(trsyl(S->tp_top, S->tp_top, S->trsyl_flops_tt));
   } else {
     FDE_TRY(trsyl(S->tp_full, S->tp_full, S->trsyl_flops));
   }
@@ -1874,19 +1861,24 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
         return FDE_ERR_NOCONV;
       }
   }
-  // ---- leaf Sylvester sub-problems (whole leaves; split leaves for the FP32 inner solver)
+  // ---- leaf Sylvester sub-problems (whole leaves; blocked leaves for the FP32 inner solver)
   if (const char* pg = getenv("FDE_PACK_GB")) S->pack_budget = (size_t)(atof(pg) * (double)(1ull << 30));
   S->trsyl_split = prec != FDE_FP64 && S->lmax > kTrsylSplit && (long long)nl * nl >= kTrsylSplitMinPairs;
-  if (const char* ts = getenv("FDE_TRSYL_SPLIT")) {  // "1": split every leaf (tests), "0": never
+  int part = kTrsylPart;
+  if (const char* ts = getenv("FDE_TRSYL_SPLIT")) {  // "1": block every leaf (tests), "0": never
     if (!strcmp(ts, "1")) S->trsyl_split = prec != FDE_FP64 && S->lmax >= 2;
     if (!strcmp(ts, "0")) S->trsyl_split = false;
+  }
+  if (const char* tp = getenv("FDE_TRSYL_PART")) {  // block rows (tests, experiments)
+    const int v = atoi(tp);
+    if (v >= 2) part = v;
   }
   {
     const int lm = S->lmax;
     std::vector<int> soff(2 * nl), lo(2 * nl), n(2 * nl);
-    std::vector<int> soff_t(2 * nl), lo_t(2 * nl), n_t(2 * nl), soff_b(2 * nl), lo_b(2 * nl), n_b(2 * nl);
-    S->split_x.assign(nl, 0);
-    S->split_y.assign(nl, 0);
+    // blocked leaves: cuts[side][p] = block boundaries of leaf p, bottom block last
+    std::vector<std::vector<int>> cuts(2 * nl);
+    int nb = 0;
     for (int side = 0; side < 2; ++side) {
       hodlr_s* h_ = side == 0 ? ax : ay;
       const double* Sd = side == 0 ? S->Sx : S->Sy;
@@ -1897,46 +1889,75 @@ static fde_status create_impl(hodlr_s* ax, hodlr_s* ay, int prec, cudaStream_t s
         n[i] = np;
         S->tp_full.nmax = std::max(S->tp_full.nmax, np);
         if (!S->trsyl_split) continue;
-        int hcut = np / 2;
-        if (hcut > 0) {
-          double sub = 0.0;  // S_p(hcut, hcut - 1): nonzero inside a 2 x 2 block
-          FDE_CUDA(cudaMemcpy(&sub, Sd + (size_t)p * lm * lm + hcut + (size_t)(hcut - 1) * lm, sizeof(double),
-                              cudaMemcpyDeviceToHost));
-          if (sub != 0.0) ++hcut;
+        // q blocks of about np / q <= part - 1 rows, so that a cut inside a
+        // 2 x 2 block, moved down by one, still leaves every block at most
+        // `part` rows (one warp per block for part = 32: a launch takes the
+        // warps of its largest block)
+        const int q = np > part ? (np + part - 2) / (part - 1) : (np >= 2 ? 2 : 1);
+        std::vector<double> sub(np > 0 ? np : 1, 0.0);  // sub[r] = S_p(r, r - 1)
+        if (np > 1)
+          FDE_CUDA(cudaMemcpy2D(&sub[1], sizeof(double), Sd + (size_t)p * lm * lm + 1, (size_t)(lm + 1) * sizeof(double),
+                                sizeof(double), np - 1, cudaMemcpyDeviceToHost));
+        std::vector<int>& c = cuts[i];
+        c.push_back(0);
+        for (int k = 1; k < q; ++k) {
+          int cut = (int)(((long long)np * k) / q);
+          if (cut > 0 && cut < np && sub[cut] != 0.0) ++cut;
+          if (cut > c.back() && cut < np) c.push_back(cut);
         }
-        (side == 0 ? S->split_x : S->split_y)[p] = hcut;
-        soff_t[i] = p * lm * lm;
-        lo_t[i] = h_->leaf_lo[p];
-        n_t[i] = hcut;
-        soff_b[i] = p * lm * lm + hcut * (lm + 1);
-        lo_b[i] = h_->leaf_lo[p] + hcut;
-        n_b[i] = np - hcut;
-        S->tp_top.nmax = std::max(S->tp_top.nmax, hcut);
-        S->tp_bot.nmax = std::max(S->tp_bot.nmax, np - hcut);
+        c.push_back(np);
+        nb = std::max(nb, (int)c.size() - 1);
       }
     }
-    auto upload = [&](sylv_s::TrsylPart& t, const std::vector<int>& a, const std::vector<int>& b,
-                      const std::vector<int>& c) -> fde_status {
-      FDE_TRY(pool.alloc(&t.soff, 2 * nl));
-      FDE_TRY(pool.alloc(&t.lo, 2 * nl));
-      FDE_TRY(pool.alloc(&t.n, 2 * nl));
-      FDE_CUDA(cudaMemcpy(t.soff, a.data(), 2 * nl * sizeof(int), cudaMemcpyHostToDevice));
-      FDE_CUDA(cudaMemcpy(t.lo, b.data(), 2 * nl * sizeof(int), cudaMemcpyHostToDevice));
-      FDE_CUDA(cudaMemcpy(t.n, c.data(), 2 * nl * sizeof(int), cudaMemcpyHostToDevice));
+    auto upload_arr = [&](int** d, const std::vector<int>& a) -> fde_status {
+      FDE_TRY(pool.alloc(d, a.size()));
+      FDE_CUDA(cudaMemcpy(*d, a.data(), a.size() * sizeof(int), cudaMemcpyHostToDevice));
       return FDE_OK;
     };
-    FDE_TRY(upload(S->tp_full, soff, lo, n));
+    FDE_TRY(upload_arr(&S->tp_full.soff, soff));
+    FDE_TRY(upload_arr(&S->tp_full.lo, lo));
+    FDE_TRY(upload_arr(&S->tp_full.n, n));
     if (S->trsyl_split) {
-      FDE_TRY(upload(S->tp_top, soff_t, lo_t, n_t));
-      FDE_TRY(upload(S->tp_bot, soff_b, lo_b, n_b));
-      for (int p = 0; p < nl; ++p)
-        for (int q = 0; q < nl; ++q) {
-          const double t1 = n_t[p], b1 = n_b[p], t2 = n_t[nl + q], b2 = n_b[nl + q];
-          S->trsyl_flops_tt += t1 * t2 * (t1 + t2);
-          S->trsyl_flops_tb += t1 * b2 * (t1 + b2);
-          S->trsyl_flops_bt += b1 * t2 * (b1 + t2);
-          S->trsyl_flops_bb += b1 * b2 * (b1 + b2);
+      if (2 * nb - 1 > 0 && nb > kTrsylMaxSets) {
+        set_error("sylv_create: %d leaf blocks per leaf (at most %d)", nb, kTrsylMaxSets);
+        return FDE_ERR_ARG;
+      }
+      // part a (from the bottom) of every leaf, x entries then y entries
+      std::vector<std::vector<int>> bsoff(nb), blo(nb), bn(nb), brest(nb);
+      S->tp_part.assign(nb, sylv_s::TrsylPart{});
+      for (int a = 0; a < nb; ++a) {
+        bsoff[a].assign(2 * nl, 0);
+        blo[a].assign(2 * nl, 0);
+        bn[a].assign(2 * nl, 0);
+        brest[a].assign(2 * nl, 0);
+        for (int i = 0; i < 2 * nl; ++i) {
+          const std::vector<int>& c = cuts[i];
+          const int nblk = (int)c.size() - 1;
+          if (a >= nblk) continue;
+          const int k = nblk - 1 - a, r0 = c[k], r1 = c[k + 1];
+          bsoff[a][i] = soff[i] + r0 * (lm + 1);
+          blo[a][i] = lo[i] + r0;
+          bn[a][i] = r1 - r0;
+          brest[a][i] = n[i] - r1;
+          S->tp_part[a].nmax = std::max(S->tp_part[a].nmax, r1 - r0);
         }
+        FDE_TRY(upload_arr(&S->tp_part[a].soff, bsoff[a]));
+        FDE_TRY(upload_arr(&S->tp_part[a].lo, blo[a]));
+        FDE_TRY(upload_arr(&S->tp_part[a].n, bn[a]));
+        FDE_TRY(upload_arr(&S->tp_part[a].rest, brest[a]));
+      }
+      // algorithmic flops per anti-diagonal: the block solves n1 n2 (n1 + n2)
+      // and their couplings 2 n1 n2 (rest_x + rest_y)
+      S->trsyl_step_flops.assign(2 * nb - 1, 0.0);
+      for (int a = 0; a < nb; ++a)
+        for (int b2 = 0; b2 < nb; ++b2)
+          for (int p = 0; p < nl; ++p)
+            for (int q = 0; q < nl; ++q) {
+              const double n1 = bn[a][p], n2 = bn[b2][nl + q];
+              if (n1 <= 0 || n2 <= 0) continue;
+              S->trsyl_step_flops[a + b2] +=
+                  n1 * n2 * (n1 + n2) + 2.0 * n1 * n2 * (brest[a][p] + brest[b2][nl + q]);
+            }
     }
   }
   // ---- shifts per level (host: spectral intervals of the level's blocks)
@@ -2306,6 +2327,64 @@ extern "C" fde_status sylv_residual(sylv_t s, const double* d_C, const double* d
   FDE_ARG(d_C != nullptr && d_X != nullptr && d_R != nullptr, "NULL buffer");
   FDE_ARG(ld == s->N, "sylv_residual requires ld == N");
   return residual(s, d_C, d_X, d_R, (cudaStream_t)stream);
+}
+
+// Work model of one inner solve (§3.4 D&C with §3.3 fADI on every level),
+// from the counted leaf sizes n_i, level ranks K_l and shift counts J_l:
+//  - leaf Bartels–Stewart: the four orthogonal transforms, 4 n_i n_j (n_i + n_j)
+//    per leaf pair (the quasi-triangular solve itself is not a GEMM);
+//  - per level l and node pair (s_x, s_y): the X0-dependent right-hand-side
+//    factors X0ᵀ V_A and X0 U_B, 2 K_x s_x s_y + 2 K_y s_x s_y; J_l shifted
+//    HODLR solves of 2K_y columns of size s_x and 2K_x columns of size s_y,
+//    each 2 n s + 4 K s log2(s / n) (leaf LU solves, then one rank-K product
+//    pair per level below); the update X += Z Wᵀ of rank 2 J_l (K_x + K_y),
+//    2 s_x s_y J_l · 2 (K_x + K_y).
+// impl: Σ 2 m n k of the batched GEMMs the implementation launches per inner
+// solve (the rational fADI form applies dense stacked resolvents).
+static double hodlr_solve_flops(double s, double n, double K) {
+  const double lv = s > n ? std::log2(s / n) : 0.0;
+  return 2.0 * n * s + 4.0 * K * s * lv;
+}
+
+template <typename T>
+static double impl_gemm_flops(const sylv_s* S, const Inner<T>& in) {
+  double f = in.g_qxt.flops + in.g_qy.flops + in.g_qx.flops + in.g_qyt.flops;
+  for (int l = 0; l < S->L; ++l) {
+    const LevelSolve<T>& ls = in.lv[l];
+    f += ls.g_rhs_x.flops + ls.g_rhs_y.flops + ls.g_update.flops;
+    f += ls.r_rhs_h.flops + ls.r_rhs_g.flops + ls.r_apply.flops + ls.r_update.flops + ls.r_update2.flops;
+  }
+  return f;
+}
+
+extern "C" fde_status sylv_flop_model(sylv_t s, double* method_flops, double* impl_flops) {
+  FDE_ARG(s != nullptr && method_flops != nullptr && impl_flops != nullptr, "NULL argument");
+  const Tree& tx = s->ax->tree;
+  const Tree& ty = s->ay->tree;
+  const int nl = tx.nleaves();
+  const double n = (double)tx.maxleaf;
+  double m = 0.0;
+  for (int i = 0; i < nl; ++i)
+    for (int j = 0; j < nl; ++j) {
+      const double a = tx.hi[tx.id(s->L, i)] - tx.lo[tx.id(s->L, i)];
+      const double b = ty.hi[ty.id(s->L, j)] - ty.lo[ty.id(s->L, j)];
+      m += 4.0 * a * b * (a + b);
+    }
+  for (int l = 0; l < s->L; ++l) {
+    const double Kx = s->ax->K[l], Ky = s->ay->K[l];
+    const double J = (l < (int)s->J.size()) ? s->J[l] : 0.0;
+    for (int p = 0; p < (1 << l); ++p)
+      for (int q = 0; q < (1 << l); ++q) {
+        const double sx = tx.hi[tx.id(l, p)] - tx.lo[tx.id(l, p)];
+        const double sy = ty.hi[ty.id(l, q)] - ty.lo[ty.id(l, q)];
+        m += 2.0 * (Kx + Ky) * sx * sy;
+        m += J * (2.0 * Ky * hodlr_solve_flops(sx, n, Kx) + 2.0 * Kx * hodlr_solve_flops(sy, n, Ky));
+        m += 2.0 * sx * sy * J * 2.0 * (Kx + Ky);
+      }
+  }
+  *method_flops = m;
+  *impl_flops = (s->prec == FDE_FP32_REFINE) ? impl_gemm_flops(s, s->in32) : impl_gemm_flops(s, s->in64);
+  return FDE_OK;
 }
 
 extern "C" void sylv_free(sylv_t s) { delete s; }

@@ -258,27 +258,37 @@ def test_runner_step_source_matches_builtin_source(lib):
         lib.runner_free(rb)
 
 
-@pytest.mark.parametrize("N,leaf,alpha", [(100, 16, (1.5, 1.2)), (256, 64, (1.3, 1.7)), (300, 150, (1.2, 1.8))])
-def test_split_leaf_sylvester_matches_oracle(lib, monkeypatch, N, leaf, alpha):
-    """Leaf Sylvester solves as 2 x 2 block Bartels–Stewart over split leaves
-    (forced here on small problems; the library splits by itself for large
-    leaf counts): the refined step matches the oracle within 1e-8 and the
-    unsplit solve within 1e-9."""
+@pytest.mark.parametrize("N,leaf,alpha,part", [(100, 16, (1.5, 1.2), "32"), (256, 64, (1.3, 1.7), "32"),
+                                                (256, 64, (1.3, 1.7), "8"), (300, 150, (1.2, 1.8), "32"),
+                                                (300, 150, (1.2, 1.8), "48")])
+def test_split_leaf_sylvester_matches_oracle(lib, monkeypatch, N, leaf, alpha, part):
+    """Leaf Sylvester solves as block Bartels–Stewart over blocked leaves
+    (forced here on small problems; the library blocks by itself for large
+    leaf counts): blocks of about `part` rows (2 .. 8 per leaf, one warp or
+    several per block, every anti-diagonal of the block grid one launch with
+    the couplings subtracted first); one unrefined FP32 inner solve agrees
+    with the unblocked one within 2e-5 (rounding order only), the refined
+    step matches the oracle within 1e-8 and the unblocked step within 1e-9."""
     w = I.fd2d(N=N, alpha=alpha, steps=50, leaf=leaf)
     C = O.fde2d_rhs(w, w.u0, 0) + I.random_matrix_fast(N, N, seed=13)
     Xo = O.sylvester_bartels_stewart(O.fd_operator(w.ops[0]), O.fd_operator(w.ops[1]), C)
-    sols = {}
+    sols, inner = {}, {}
+    monkeypatch.setenv("FDE_TRSYL_PART", part)
     for mode in ("1", "0"):
         monkeypatch.setenv("FDE_TRSYL_SPLIT", mode)
         P = Pair(lib, w, B.FDE_FP32_REFINE)
         try:
             Cd = _dev(C)
+            Xi = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+            lib.sylv_inner_solve(P.s, Cd.data_ptr(), Xi.data_ptr(), N)
+            inner[mode] = _host(Xi, N, N)
             Xd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
             relres, sweeps = lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
             sols[mode] = _host(Xd, N, N)
             assert _relerr(sols[mode], Xo) <= 1e-8, (mode, relres, sweeps)
         finally:
             P.close()
+    assert _relerr(inner["1"], inner["0"]) <= 2e-5
     assert _relerr(sols["1"], sols["0"]) <= 1e-9
 
 
