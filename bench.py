@@ -75,14 +75,14 @@ def replica_rate(world: int, units_per_rank: float, ms_max: float) -> float:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fd2d_n4096")
     ap.add_argument("--fp64-steps", type=int, default=8)
-    ap.add_argument("--e2e-steps", type=int, default=16)
-    ap.add_argument("--verify-steps", type=int, default=10)
-    ap.add_argument("--prof-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=32)
+    ap.add_argument("--verify-steps", type=int, default=20)
+    ap.add_argument("--prof-steps", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-threads", type=int, default=8)
     return ap.parse_args()
@@ -240,7 +240,38 @@ FAMILIES = ["gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply", "
 DF_OPS_PER_FLOP = 7.7
 
 
-def roofline(lib, N):
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one
+# ncu capture of the timed steps) of a family on a workload, with a digest of
+# the sources that decide its kernels and their launch mix: once any of them
+# changes, the figure no longer describes the kernel and `traffic` reads null.
+TRAFFIC_SOURCES = ["paper_1804_05522_gb300/csrc/tc_gemm.cu", "paper_1804_05522_gb300/csrc/dense.cu",
+                   "paper_1804_05522_gb300/csrc/dense.cuh", "paper_1804_05522_gb300/csrc/sylv.cu"]
+TRAFFIC = {
+    ("fd2d_n4096", "gemm32tc"): {"bytes_per_launch": 568.8e6, "sources_sha256_16": "3d858ef606b33b49",
+                                 "profile": "profiles/tc_gemm_kernel_fd2d_n4096_traffic.md"},
+}
+
+
+def sources_digest(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(workload, family):
+    t = TRAFFIC.get((workload, family))
+    if t is None:
+        return None, "no ncu capture of this kernel on this workload"
+    if sources_digest(TRAFFIC_SOURCES) != t["sources_sha256_16"]:
+        return None, "kernel sources changed since the ncu capture (" + t["profile"] + ")"
+    return t["bytes_per_launch"], "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean per launch over the " \
+                                  "timed steps (" + t["profile"] + ")"
+
+
+def roofline(lib, N, workload=None):
     """Every instrumented kernel family against its roofline; the dominant one
     (largest device time) is the headline."""
     rec = {}
@@ -257,7 +288,7 @@ def roofline(lib, N):
         fams[f]["share_of_instrumented_time"] = rec[f][0] / total
     dom = max(rec, key=lambda f: rec[f][0])
     r = dict(fams[dom])
-    r["traffic"] = None
+    r["traffic"], r["traffic_source"] = traffic_for(workload, dom)
     detail = {f: {"share": round(v["share_of_instrumented_time"], 4), "avg_launch_ms": round(v["avg_launch_ms"], 4),
                   "launches": v["launches"], "achieved": round(v["achieved"], 3), "unit": v["unit"],
                   "frac": round(v["frac"], 4), "bound": v["bound"]} for f, v in fams.items()}
@@ -309,6 +340,8 @@ def read_golden(name: str):
             e["fro"], e["maxabs"] = float(f[2]), float(f[3])
         elif f[0] == "proj":
             e["proj"][int(f[2])] = float(f[3])
+        elif f[0] == "bound":
+            e["obound_fro"] = float(f[3])
         elif f[0] == "entry":
             e["ii"].append(int(f[2]))
             e["jj"].append(int(f[3]))
@@ -346,6 +379,7 @@ def compare_golden(X: np.ndarray, e: dict, N: int) -> dict:
             "max_abs_sampled_rel": float(np.max(np.abs(err)) / e["maxabs"]),
             "proj_max_rel": float(proj / e["fro"]),
             "fro_norm_rel": float(abs(np.linalg.norm(X) - e["fro"]) / e["fro"]),
+            "oracle_own_bound_fro_rel": (float(e["obound_fro"] / e["fro"]) if "obound_fro" in e else None),
             "samples": int(len(ii))}
 
 
@@ -446,7 +480,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         lib.prof_enable(False)
         prof_sweeps = lib.runner_stats(r32).sweeps_total - sp0
-        roof, shares = roofline(lib, N)
+        roof, shares = roofline(lib, N, args.workload)
         if roof is not None:
             roof["measured"] = (f"profiled pass of {args.prof_steps} steps right after the timed region (eager "
                                 f"launches, CUDA events on the launching stream)")

@@ -30,6 +30,8 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
                              manufactured-solution first-order convergence
   sylvester_bartels_stewart  pinned: Kronecker brute force, α=2 DST closed form
   SchurSylvester             pinned: Kronecker brute force, reused Schur forms
+  quasi_triangular_sylvester pinned: Kronecker brute force on Schur forms with
+                               2 x 2 blocks, every cut (base 1 .. 8)
   fde2d_rhs / fde2d_run      pinned: Kronecker steps, manufactured 2D solution
                              (first order), exactness for a solution linear
                              in t (source at the new time level)
@@ -332,16 +334,60 @@ def sylvester_bartels_stewart(A: np.ndarray, B: np.ndarray, C: np.ndarray) -> np
     return Q @ (Y / scale) @ Z.T
 
 
+def quasi_triangular_sylvester(S: np.ndarray, R: np.ndarray, F: np.ndarray, base: int = 128) -> np.ndarray:
+    """S Y + Y Rᵀ = F for upper quasi-triangular S (m x m) and R (n x n), the
+    middle stage of Bartels–Stewart, in the recursive block form of the same
+    back substitution (Jonsson & Kågström, ACM TOMS 28, 2002): the larger side
+    is cut in two where no 2 x 2 diagonal block is split,
+      S = [S11 S12; 0 S22]:  S22 Y2 + Y2 Rᵀ = F2,  then  S11 Y1 + Y1 Rᵀ = F1 - S12 Y2;
+      R = [R11 R12; 0 R22]:  S Y2 + Y2 R22ᵀ = F2,  then  S Y1 + Y1 R11ᵀ = F1 - Y2 R12ᵀ
+    (Y = [Y1; Y2] resp. [Y1, Y2]); problems of at most `base` rows and
+    columns go to LAPACK trsyl.  Same result as trsyl on the whole problem up
+    to rounding order, with the couplings as matrix products (base >= 2, so
+    that every cut leaves two non-empty parts)."""
+    if base < 2:
+        raise ValueError("base must be at least 2")
+    m, n = F.shape
+    if m == 0 or n == 0:
+        return np.zeros_like(F)
+    if m <= base and n <= base:
+        Y, scale, info = lapack.dtrsyl(S, R, F, trana="N", tranb="T", isgn=1)
+        if info < 0 or scale != 1.0:
+            raise RuntimeError(f"dtrsyl info={info} scale={scale}")
+        return Y
+
+    def cut(T, k):
+        h = k // 2
+        if h > 0 and T[h, h - 1] != 0.0:  # inside a 2 x 2 block
+            h += 1
+        return h
+
+    if m >= n:
+        h = cut(S, m)
+        Y2 = quasi_triangular_sylvester(S[h:, h:], R, F[h:], base)
+        Y1 = quasi_triangular_sylvester(S[:h, :h], R, F[:h] - S[:h, h:] @ Y2, base)
+        return np.vstack([Y1, Y2])
+    h = cut(R, n)
+    Y2 = quasi_triangular_sylvester(S, R[h:, h:], F[:, h:], base)
+    Y1 = quasi_triangular_sylvester(S, R[:h, :h], F[:, :h] - Y2 @ R[:h, h:].T, base)
+    return np.hstack([Y1, Y2])
+
+
 class SchurSylvester:
     """Bartels–Stewart with the two real Schur forms computed once (the
-    coefficients of Eq. (sylv-timestepping) do not depend on time)."""
+    coefficients of Eq. (sylv-timestepping) do not depend on time).  With
+    `base`, the quasi-triangular stage runs in the recursive block form
+    (quasi_triangular_sylvester); without, as one LAPACK trsyl call."""
 
-    def __init__(self, A: np.ndarray, B: np.ndarray):
+    def __init__(self, A: np.ndarray, B: np.ndarray, base: int | None = None):
         self.S, self.Q = sla.schur(A, output="real")
         self.R, self.Z = sla.schur(B, output="real")
+        self.base = base
 
     def solve(self, C: np.ndarray) -> np.ndarray:
         Ct = self.Q.T @ C @ self.Z
+        if self.base is not None:
+            return self.Q @ quasi_triangular_sylvester(self.S, self.R, Ct, self.base) @ self.Z.T
         Y, scale, info = lapack.dtrsyl(self.S, self.R, Ct, trana="N", tranb="T", isgn=1)
         if info < 0:
             raise RuntimeError(f"dtrsyl info={info}")
@@ -363,12 +409,14 @@ def fde2d_rhs(w, U: np.ndarray, m: int) -> np.ndarray:
     return U + w.dt * w.source((m + 1) * w.dt)
 
 
-def fde2d_run(w, steps: int | None = None, return_all: bool = False):
+def fde2d_run(w, steps: int | None = None, return_all: bool = False, base: int | None = None):
     """M implicit-Euler steps of the 2D problem, each one Sylvester equation
-    A_x U^{(m+1)} + U^{(m+1)} A_yᵀ = U^{(m)} + Δt F^{(m+1)} (Eq. (sylv-timestepping))."""
+    A_x U^{(m+1)} + U^{(m+1)} A_yᵀ = U^{(m)} + Δt F^{(m+1)} (Eq. (sylv-timestepping)).
+    base: see SchurSylvester (large N: LAPACK trsyl on the whole problem is
+    memory-bound and takes tens of minutes per step at N = 4096)."""
     Ax = fd_operator(w.ops[0])
     Ay = fd_operator(w.ops[1])
-    solver = SchurSylvester(Ax, Ay)
+    solver = SchurSylvester(Ax, Ay, base)
     U = w.u0.copy()
     M = w.steps if steps is None else steps
     hist = []

@@ -2,21 +2,24 @@
 
 The 2D N = 4096 workload (α = 1.5, 1.5; Δt = 1/100; leaf 128) runs through the
 time-loop runner with every default switch of the benchmark: FP32 inner solver
-with split leaf Sylvester solves, the time-step predictor, exact residuals on
-two consecutive steps of every 8 with double-float incremental residuals in
-between, and FP32 last updates.  Its states are compared with
+with blocked leaf Sylvester solves, the time-step predictor, exact residuals on
+two consecutive steps of every 16 with double-float incremental residuals in
+between, and FP32 last updates before them.  Its states are compared with
 
   - the oracle's own time loop (Bartels–Stewart per step, §4.2,
     Eq. (sylv-timestepping)): sampled entries, bilinear functionals and norms
-    stored by tests/golden/make_fd2d_oracle.py at steps 2, 4, 8 (the last step
-    of an incremental chain) and 10 (a refresh step);
+    stored by tests/golden/make_fd2d_oracle.py at steps 2, 4, 8, 10, 16 (the
+    last step of an incremental chain), 18 (a refresh step) and 20;
   - rigorous bounds on the error against the exact time loop, from the
     exact FP64 residuals of the steps: A_x and A_y are M-matrices (§2.2.1),
     so max|U - U*| <= max|R| / μ per step, μ the sum of their smallest row
     sums (oracle.sylvester_error_bound); and their symmetric parts exceed
     I/2, so ||U - U*||_F <= ||R||_F (oracle.sylvester_error_bound_fro).
     Both add over the loop.  The Frobenius bound must stay below the
-    tolerance, and the oracle's values must lie inside both.
+    tolerance, and the oracle's values must lie inside both, widened by the
+    oracle's own bounds of the same kind (stored with its values: with a
+    condition near 1e4, its FP64 Bartels–Stewart is itself about 1e-11 off
+    per step).
 
 Above N = 4096 the same bound certifies the block-Toeplitz residual path."""
 import os
@@ -45,6 +48,8 @@ def _golden(name):
         e = g.setdefault(int(f[1]), {"proj": {}, "ij": [], "val": []})
         if f[0] == "norm":
             e["fro"], e["maxabs"] = float(f[2]), float(f[3])
+        elif f[0] == "bound":
+            e["obound_max"], e["obound_fro"] = float(f[2]), float(f[3])
         elif f[0] == "proj":
             e["proj"][int(f[2])] = float(f[3])
         else:
@@ -110,10 +115,13 @@ def test_fd2d_n4096_default_run_vs_oracle(lib):
             # the accumulated residual bound is rigorous against the exact
             # loop, so the oracle's values must lie inside it (up to the
             # oracle's own rounding)
-            assert np.abs(err).max() <= bound + 1e-12 * e["maxabs"], (m, np.abs(err).max(), bound)
+            assert np.abs(err).max() <= bound + e["obound_max"], (m, np.abs(err).max(), bound, e["obound_max"])
             # rigorous Frobenius bound against the exact loop, within the tolerance
             assert bound_fro <= TOL * e["fro"], (m, bound_fro / e["fro"])
-            assert rel_fro <= bound_fro / e["fro"] + 1e-12, (m, rel_fro, bound_fro / e["fro"])
+            # the sampled entries estimate ||U - U_oracle||_F, so this one
+            # allows for the sampling as well (a factor 2)
+            assert rel_fro <= 2.0 * (bound_fro + e["obound_fro"]) / e["fro"], \
+                (m, rel_fro, bound_fro / e["fro"], e["obound_fro"] / e["fro"])
     finally:
         lib.runner_free(r)
 

@@ -232,6 +232,23 @@ def _solve_transposed(A, B):
     return _orig["solve_dense"](A.T, B)
 
 
+def _qts_coupling_sign(S, R, F, base=128):
+    """The recursive quasi-triangular stage with the S coupling added instead
+    of subtracted, otherwise the oracle's recursion."""
+    m, n = F.shape
+    if m <= base and n <= base:
+        return _orig["quasi_triangular_sylvester"](S, R, F, base)
+    if m >= n:
+        h = m // 2 + (1 if S[m // 2, m // 2 - 1] != 0.0 else 0)
+        Y2 = _qts_coupling_sign(S[h:, h:], R, F[h:], base)
+        Y1 = _qts_coupling_sign(S[:h, :h], R, F[:h] + S[:h, h:] @ Y2, base)
+        return np.vstack([Y1, Y2])
+    h = n // 2 + (1 if R[n // 2, n // 2 - 1] != 0.0 else 0)
+    Y2 = _qts_coupling_sign(S, R[h:, h:], F[:, h:], base)
+    Y1 = _qts_coupling_sign(S, R[:h, :h], F[:, :h] - Y2 @ R[:h, h:].T, base)
+    return np.hstack([Y1, Y2])
+
+
 MUTATIONS = [
     ("gl_weights", _gl_shifted_order, lambda: P.test_gl_first_weights_exact(1.5)),
     ("gl_toeplitz", _toeplitz_transposed, lambda: P.test_toeplitz_structure(1.3)),
@@ -267,6 +284,7 @@ MUTATIONS = [
     ("fde2d_lowrank_run", _lowrank_run_absolute, P.test_lowrank_run_error_follows_eps),
     ("fde1d_run_tv", _tv1d_old_level, P.test_time_dependent_1d_coefficients_at_new_level),
     ("solve_dense", _solve_transposed, P.test_solve_dense_residual),
+    ("quasi_triangular_sylvester", _qts_coupling_sign, P.test_quasi_triangular_sylvester_recursive_vs_kronecker),
 ]
 
 

@@ -356,6 +356,24 @@ def test_bartels_stewart_vs_kronecker_random():
     assert np.linalg.norm(A @ X1 + X1 @ B.T - C) < 1e-12 * np.linalg.norm(C)
 
 
+def test_quasi_triangular_sylvester_recursive_vs_kronecker():
+    """The recursive block form of the quasi-triangular stage against the
+    Kronecker brute force, on real Schur forms with 2 x 2 blocks, for bases
+    that force cuts next to and between those blocks."""
+    S = sla.schur(_rand_stable(23, 5, 6.0), output="real")[0]
+    R = sla.schur(_rand_stable(17, 6, 6.0), output="real")[0]
+    assert np.count_nonzero(np.diag(S, -1)) > 0 and np.count_nonzero(np.diag(R, -1)) > 0
+    F = I.SplitMix64(7).normal_array((23, 17))
+    Yk = O.sylvester_kron(S, R, F)
+    for base in (2, 3, 5, 8):
+        Y = O.quasi_triangular_sylvester(S, R, F, base)
+        np.testing.assert_allclose(Y, Yk, rtol=0, atol=1e-12 * np.abs(Yk).max())
+    solver = O.SchurSylvester(_rand_stable(23, 5, 6.0), _rand_stable(17, 6, 6.0), base=4)
+    A, B = _rand_stable(23, 5, 6.0), _rand_stable(17, 6, 6.0)
+    np.testing.assert_allclose(solver.solve(F), O.sylvester_kron(A, B, F), rtol=0,
+                               atol=1e-12 * np.abs(O.sylvester_kron(A, B, F)).max())
+
+
 def test_bartels_stewart_vs_kronecker_fd():
     w = I.fd2d(N=16, alpha=(1.3, 1.7), steps=50)
     Ax = O.fd_operator(w.ops[0])

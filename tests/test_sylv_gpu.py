@@ -293,16 +293,17 @@ def test_split_leaf_sylvester_matches_oracle(lib, monkeypatch, N, leaf, alpha, p
 
 
 def test_periodic_exact_residual_chain(lib, monkeypatch):
-    """20 time steps, so two refresh pairs and three chains of incremental
-    steps: the default schedule of residuals (exact after the first sweep on
-    two consecutive steps of every 8, double-float updates in between) and
+    """20 time steps, so refresh pairs and chains of incremental steps
+    between them: the default schedule of residuals (exact after the first sweep on
+    two consecutive steps of every 16 (and of every 8), double-float updates in
+    between) and
     exact residuals on every step give the oracle's trajectory within 1e-8
     and agree within 1e-9."""
     monkeypatch.delenv("FDE_RESID", raising=False)
     w = I.fd2d(N=256, alpha=(1.3, 1.7), steps=50, leaf=64)
     Uref = O.fde2d_run(w, steps=20)
     runs = {}
-    for every in ("8", "1"):
+    for every in ("16", "8", "1"):
         monkeypatch.setenv("FDE_EXACT_EVERY", every)
         rp = lib.run_params(w, prec=B.FDE_FP32_REFINE)
         rp.steps = 20
@@ -312,18 +313,19 @@ def test_periodic_exact_residual_chain(lib, monkeypatch):
         runs[every] = _host(Uo, w.N, w.N)
         assert _relerr(runs[every], Uref) <= 1e-8, every
     assert _relerr(runs["8"], runs["1"]) <= 1e-9
+    assert _relerr(runs["16"], runs["1"]) <= 1e-9
 
 
 def test_incremental_chain_long_run(lib, monkeypatch):
-    """40 steps at N = 1024 (chains of up to 6 incremental steps between
-    refresh pairs): the incremental first updates are actually taken (fewer
-    exact FP64 residuals than steps) and the trajectory agrees with exact
-    residuals after every first sweep within 1e-9 (both runs refined to
-    1e-11 on the update)."""
+    """40 steps at N = 1024 (chains of up to 14 or 6 incremental steps
+    between refresh pairs of every 16 or 8 steps): the incremental first
+    updates are actually taken (fewer exact FP64 residuals than steps) and
+    the trajectory agrees with exact residuals after every first sweep within
+    1e-9."""
     monkeypatch.delenv("FDE_RESID", raising=False)
     w = I.fd2d(N=1024, alpha=(1.5, 1.5), steps=100, leaf=128)
     runs, exact = {}, {}
-    for every in ("8", "1"):
+    for every in ("16", "8", "1"):
         monkeypatch.setenv("FDE_EXACT_EVERY", every)
         rp = lib.run_params(w, prec=B.FDE_FP32_REFINE)
         rp.steps = 40
@@ -336,8 +338,9 @@ def test_incremental_chain_long_run(lib, monkeypatch):
         exact[every] = lib.prof_query("fft_apply")[1]
         lib.prof_reset()
         runs[every] = _host(Uo, w.N, w.N)
-    assert exact["8"] < exact["1"], exact
+    assert exact["16"] < exact["8"] < exact["1"], exact
     assert _relerr(runs["8"], runs["1"]) <= 1e-9
+    assert _relerr(runs["16"], runs["1"]) <= 1e-9
 
 
 @pytest.mark.parametrize("prec", [B.FDE_FP64, B.FDE_FP32_REFINE])
