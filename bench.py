@@ -37,7 +37,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SMS, SM_MHZ = 152, 2070.0
 FP32_SIMT_PEAK_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MHZ * 1e6 / 1e12
-ORACLE_SAMPLE_N = 1024
+ORACLE_SAMPLE_N = 4096  # largest N the oracle arm times for real (Schur forms ~1-5 min)
+CPU_BASELINE_N = 1024   # the bounded sample of the bench line's cpu_baseline
 
 
 def workload_for(name: str):
@@ -83,28 +84,37 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=32)
     ap.add_argument("--verify-steps", type=int, default=20)
     ap.add_argument("--prof-steps", type=int, default=16)
+    ap.add_argument("--bf16-steps", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-threads", type=int, default=8)
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ oracle
-REF_BUDGET_S = 180.0  # wall-time budget of the reference arm's timed + warm-up steps
+REF_BUDGET_S = 240.0  # wall-time budget of the reference arm's timed + warm-up steps
 
 
 class OracleSampler:
     """The CPU oracle's 2D time loop (Bartels–Stewart with the two real Schur
-    forms computed once) on the workload family `name` at N = n_sample: step()
-    advances one implicit-Euler step and returns its wall time."""
+    forms computed once, outside the timing; the quasi-triangular stage in the
+    oracle's recursive block form, LAPACK trsyl on blocks of at most 256) on
+    the workload `name` itself when N <= ORACLE_SAMPLE_N, else on the same
+    workload family at N = n_sample: step() advances one implicit-Euler step
+    and returns its wall time."""
 
     def __init__(self, name: str, n_sample: int = None):
         from oracle import fde_oracle as O
 
         self.O = O
-        self.n = n_sample or ORACLE_SAMPLE_N
         w = workload_for(name)
-        self.ws = I.fd2d(N=self.n, alpha=(w.ops[0].alpha, w.ops[1].alpha), steps=w.steps, leaf=128)
-        self.solver = O.SchurSylvester(O.fd_operator(self.ws.ops[0]), O.fd_operator(self.ws.ops[1]))
+        self.n = n_sample or min(w.N, ORACLE_SAMPLE_N)
+        if self.n == w.N:
+            self.ws = w
+        else:
+            self.ws = I.fd2d(N=self.n, alpha=(w.ops[0].alpha, w.ops[1].alpha), steps=w.steps, leaf=128)
+        t0 = time.perf_counter()
+        self.solver = O.SchurSylvester(O.fd_operator(self.ws.ops[0]), O.fd_operator(self.ws.ops[1]), base=256)
+        self.setup_s = time.perf_counter() - t0
         self.U = self.ws.u0.copy()
         self.m = 0
 
@@ -115,14 +125,15 @@ class OracleSampler:
         return time.perf_counter() - t0
 
     def describe(self, steps: int) -> str:
-        return f"oracle Bartels-Stewart step at N={self.n} (Schur forms once, outside the timing), {steps} step(s)"
+        return (f"oracle Bartels-Stewart step at N={self.n} (Schur forms once, {self.setup_s:.0f} s, outside the "
+                f"timing; recursive block quasi-triangular stage), {steps} step(s)")
 
 
-def oracle_step_sample(name: str, repeats: int = 1):
-    """(seconds per step, sample description) of the oracle at N = ORACLE_SAMPLE_N."""
-    sm = OracleSampler(name)
+def oracle_step_sample(name: str, repeats: int = 1, n_sample: int = None):
+    """(seconds per step, sample description, sample N) of the oracle."""
+    sm = OracleSampler(name, n_sample)
     secs = [sm.step() for _ in range(repeats)]
-    return float(np.mean(secs)), sm.describe(repeats)
+    return float(np.mean(secs)), sm.describe(repeats), sm.n
 
 
 def oracle_threads():
@@ -434,6 +445,56 @@ def verify_run(lib, name, w, r, U0, steps: int, stream):
 
 
 # ------------------------------------------------------------------ ours
+def bf16_leg(lib, w, state, args, stream, fp32_rate):
+    """The same workload with FDE_BF16_REFINE (the D&C level products on BF16
+    tensor cores, FP64 refinement to the same tolerance), from the state after
+    the warm-up steps: steps/s over bf16_steps steps after two untimed ones,
+    sweeps per step, and the exact FP64 residual of each timed step with the
+    error bounds summed from it (as in the accuracy block)."""
+    import torch
+    from paper_1804_05522_gb300 import binding as B
+
+    N = w.N
+    mu = sum(lib.fde_block_interval(lib.op_params(op), 0, N)[0] for op in w.ops)
+    rp = lib.run_params(w, prec=B.FDE_BF16_REFINE)
+    r = lib.runner_create(rp, state.data_ptr(), stream)
+    try:
+        setup = lib.runner_stats(r).setup_s
+        lib.runner_load(r, state.data_ptr(), args.warmup, stream)
+        lib.runner_advance(r, 2, stream)
+        torch.cuda.synchronize()
+        s0 = lib.runner_stats(r).sweeps_total
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lib.runner_advance(r, args.bf16_steps, stream)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sweeps = (lib.runner_stats(r).sweeps_total - s0) / args.bf16_steps
+        # accuracy of the following steps, one at a time (untimed)
+        bound, bound_fro, relres_max = 0.0, 0.0, 0.0
+        X = torch.empty_like(state)
+        for _ in range(4):
+            lib.runner_advance(r, 1, stream)
+            rel, mx, fro = lib.runner_residual(r, stream)
+            lib.runner_state(r, X.data_ptr(), stream)
+            torch.cuda.synchronize()
+            relres_max = max(relres_max, rel)
+            bound = max(bound, mx / mu / float(X.abs().max()))
+            bound_fro = max(bound_fro, fro / float(torch.linalg.norm(X)))
+        rate = args.bf16_steps / (ms / 1e3)
+        split = os.environ.get("FDE_BF16_SPLIT", "1") != "0"
+        return {"steps_per_s": rate, "steps": args.bf16_steps, "setup_s": setup, "sweeps_per_step": sweeps,
+                "relres_exact_max": relres_max, "error_bound_step_max_rel": bound,
+                "error_bound_step_fro_rel": bound_fro, "vs_fp32_refine": rate / fp32_rate,
+                "operands": "D&C level products (fADI applications, low-rank updates) with BF16 operands on "
+                            "tcgen05 kind::f16" + (", split into BF16 hi + lo (three products)" if split else
+                                                   ", rounded to BF16 (one product)") +
+                            ", FP32 accumulation; leaf transforms 3xTF32, leaf solves FP32, FP64 refinement"}
+    finally:
+        lib.runner_free(r)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -585,19 +646,32 @@ def run_ours(args, rank, world, local_rank):
     accuracy = None
     if args.verify_steps > 0 and rank == 0:
         accuracy = verify_run(lib, args.workload, w, r32, U0, min(args.verify_steps, w.steps), stream)
+    if args.bf16_steps > 0 and rank == 0:
+        state16 = torch.empty_like(U0)
+        lib.runner_load(r32, U0.data_ptr(), 0, stream)
+        lib.runner_advance(r32, args.warmup, stream)
+        lib.runner_state(r32, state16.data_ptr(), stream)
+        torch.cuda.synchronize()
     lib.runner_free(r32)
+    if args.bf16_steps > 0 and rank == 0:
+        for key, split in (("bf16_path", "1"), ("bf16_single_path", "0")):
+            os.environ["FDE_BF16_SPLIT"] = split
+            try:
+                extra[key] = bf16_leg(lib, w, state16, args, stream, value / world)
+            finally:
+                del os.environ["FDE_BF16_SPLIT"]
 
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        sec, sample = oracle_step_sample(args.workload, 1)
+        sec, sample, ns = oracle_step_sample(args.workload, 1, min(N, CPU_BASELINE_N))
         cores, cores_src = oracle_threads()
-        cpu = {"value": scale_to(N, sec), "unit": "steps/s", "cores": cores, "cores_source": cores_src,
-               "kind": "oracle",
-               "sample": sample + f"; {sec:.2f} s/step, scaled to N={N} by (N/{ORACLE_SAMPLE_N})^3",
-               "sample_steps_per_s": 1.0 / sec, "sample_ms_per_step": sec * 1e3, "sample_N": ORACLE_SAMPLE_N,
-               "scaled": f"value = sample rate x ({ORACLE_SAMPLE_N}/{N})^3"}
+        cpu = {"value": scale_to(N, sec, ns), "unit": "steps/s", "cores": cores, "cores_source": cores_src,
+               "kind": "oracle", "sample": sample + f"; {sec:.2f} s/step" +
+                                           (f", scaled to N={N} by (N/{ns})^3" if ns != N else ""),
+               "sample_steps_per_s": 1.0 / sec, "sample_ms_per_step": sec * 1e3, "sample_N": ns,
+               "scaled": (f"value = sample rate x ({ns}/{N})^3" if ns != N else None)}
     cfg = {"workload": f"{args.workload}: 2D N={N} per side ({N*N} unknowns), alpha=({w.ops[0].alpha},{w.ops[1].alpha}), "
                        f"dt=1/{w.steps}, leaf {w.ops[0].leaf}, HODLR tol {w.ops[0].tol:g}, FP32 D&C+fADI inner, "
                        f"FP64 refinement",
@@ -798,10 +872,11 @@ def run_reference(args, rank, world):
     # the budget (the per-step cost is O(n^3)); it counts as a warm-up step
     t_probe = sm.step()
     total = args.warmup + args.steps
+    n0 = sm.n
     if total * t_probe > REF_BUDGET_S:
-        n = int(ORACLE_SAMPLE_N * (REF_BUDGET_S / (total * t_probe)) ** (1.0 / 3.0)) // 32 * 32
+        n = int(n0 * (REF_BUDGET_S / (total * t_probe)) ** (1.0 / 3.0)) // 32 * 32
         sm = OracleSampler(args.workload, max(256, n))
-    for _ in range(max(args.warmup - 1, 0) if sm.n == ORACLE_SAMPLE_N else args.warmup):
+    for _ in range(max(args.warmup - 1, 0) if sm.n == n0 else args.warmup):
         sm.step()
     t0 = time.perf_counter()
     secs = [sm.step() for _ in range(args.steps)]
@@ -815,12 +890,11 @@ def run_reference(args, rank, world):
            "config": {"workload": args.workload, "N": N},
            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "cores_source": cores_src,
                             "kind": "oracle",
-                            "sample": sm.describe(args.steps) + f"; mean {per:.2f} s/step, scaled to N={N} "
-                                                                f"by (N/{sm.n})^3",
+                            "sample": sm.describe(args.steps) + f"; mean {per:.2f} s/step" +
+                                      (f", scaled to N={N} by (N/{sm.n})^3" if sm.n != N else ""),
                             "sample_N": sm.n, "sample_ms_per_step": per * 1e3,
-                            "scaled": f"value and ms_per_step = the N={sm.n} steps actually timed, scaled to "
-                                      f"N={N} by (N/{sm.n})^3 (a real N={N} oracle step is dominated by "
-                                      f"single-threaded LAPACK dtrsyl, about 10 minutes)",
+                            "scaled": (f"value and ms_per_step = the N={sm.n} steps actually timed, scaled "
+                                       f"to N={N} by (N/{sm.n})^3" if sm.n != N else None),
                             "wall_s": wall, "total_wall_s": time.perf_counter() - t_wall0},
            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

@@ -62,7 +62,16 @@ typedef enum {
  * solution iterate are always FP64. */
 typedef enum {
   FDE_FP64 = 0,         /* all inner kernels in FP64                    */
-  FDE_FP32_REFINE = 1   /* inner kernels in FP32, FP64 refinement        */
+  FDE_FP32_REFINE = 1,  /* inner kernels in FP32, FP64 refinement        */
+  FDE_BF16_REFINE = 2   /* 2D only: as FDE_FP32_REFINE, but the low-rank */
+                        /* products of the divide-and-conquer levels     */
+                        /* (fADI applications and updates, §3.3-§3.4)    */
+                        /* take BF16 operands on the tensor cores (FP32  */
+                        /* accumulation), split into BF16 hi + lo (three */
+                        /* products); environment FDE_BF16_SPLIT=0 rounds */
+                        /* them to BF16 instead (one product, more       */
+                        /* refinement sweeps); leaf solves stay FP32;    */
+                        /* FP64 refinement to the same tolerance         */
 } fde_prec;
 
 /* One 1D operator  A = shift*I + (dt/h^alpha) (D_+ T_alpha + D_- T_alphaᵀ)
@@ -421,7 +430,9 @@ void fde_batch_free(fde_batch_t b);
  * cores), 5 / 6 / 7 3xTF32 with A / B / both operands packed first (pre-split
  * into TF32 hi and lo tiles in the kernel's shared-memory layout and loaded by
  * bulk asynchronous copies, as the solver does for its constant operands);
- * batches too small
+ * 8 BF16 operands (tcgen05 kind::f16, FP32 accumulation), 9 BF16 hi/lo split
+ * (three products, about 16 significant bits), 10 / 11 modes 9 / 8 with both
+ * operands packed first; batches too small
  * for the tensor cores (m < 64, n < 16 or k < 32) take a SIMT kernel.
  * Allocates the descriptor array and synchronises `stream`.  FDE_ERR_CUDA if
  * a tensor-core wait expired.  Not thread-safe: while it runs, a mode other

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libfde_hodlr.so")
 
 FDE_OK, FDE_ERR_ARG, FDE_ERR_NOMEM, FDE_ERR_NOCONV, FDE_ERR_NUMERIC, FDE_ERR_CUDA = range(6)
-FDE_FP64, FDE_FP32_REFINE = 0, 1
+FDE_FP64, FDE_FP32_REFINE, FDE_BF16_REFINE = 0, 1, 2
 
 
 class OpParams(C.Structure):

@@ -42,6 +42,11 @@ struct GemmBatch {
   bool any_kblk = false;  // some descriptor uses two-level k panels
   bool pk_a = false, pk_b = false;  // every descriptor has Apk (resp. Bpk)
   int pk_bn = 0;                    // tile width B was packed for
+  // Operand precision on the tensor cores: kTcDefault follows the library's
+  // mode (3xTF32 by default), kTcBF16 rounds both operands to BF16 (one
+  // product), kTcBF16x3 splits them into BF16 hi + lo (three products);
+  // FP32 accumulation in every case.  Packed tiles are packed for this kind.
+  int kind = 0;
   T alpha = T(1), beta = T(0);
 };
 
@@ -54,6 +59,8 @@ fde_status gemm_batch_run(const GemmBatch<T>& b, cudaStream_t st);
 
 // -1: the skinny FP32 kernel by the library's rule (FDE_SKINNY); 0 off; 1 on.
 void set_skinny_force(int v);
+
+constexpr int kTcDefault = 0, kTcBF16 = 1, kTcBF16x3 = 2;
 
 // Tensor-core path for FP32 batches (tc_gemm.cu).  Mode from FDE_TC
 // (0 = SIMT only, 1 = TF32, 3 = 3xTF32, the default).

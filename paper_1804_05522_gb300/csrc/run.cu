@@ -189,7 +189,8 @@ static fde_status check_run(const fde_run_params* p) {
   FDE_ARG(p->rank >= 0 && p->rank <= kMaxSrc, "source rank must be in [0, 8]");
   FDE_ARG(p->rank == 0 || (p->h_src_left && p->h_amp && p->h_sin_amp && p->h_omega), "NULL source arrays");
   FDE_ARG(p->dim == 1 || p->rank == 0 || p->h_src_right, "NULL right source factor");
-  FDE_ARG(p->prec == FDE_FP64 || p->prec == FDE_FP32_REFINE, "unknown precision");
+  FDE_ARG(p->prec == FDE_FP64 || p->prec == FDE_FP32_REFINE || (p->prec == FDE_BF16_REFINE && p->dim == 2),
+          "unknown precision (FDE_BF16_REFINE: 2D only)");
   if (p->dim == 2) FDE_ARG(p->op_x.N == p->op_y.N && p->op_x.leaf == p->op_y.leaf, "op_x / op_y differ in N or leaf");
   // the implicit-Euler step: I + ... in 1D (Eq. (system_FD)), 1/2 I + ... per side in 2D (Eq. (sylv-timestepping))
   if (p->dim == 1) FDE_ARG(p->op_x.shift == 1.0, "1D: op_x.shift must be 1");

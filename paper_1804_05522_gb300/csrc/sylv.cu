@@ -708,6 +708,9 @@ struct sylv_s {
   // bytes the packed constant GEMM operands of the FP32 inner solver may take
   // (FDE_PACK_GB overrides; 0 turns packing off)
   size_t pack_budget = (size_t)32 << 30;
+  // operand kind of the tensor-core level products (fADI applications and
+  // low-rank updates): kTcDefault (3xTF32) or BF16 (FDE_BF16_REFINE)
+  int level_kind = kTcDefault;
   // whole-step graphs (FP32 inner solver): one executable per variant of the
   // step's first part and per (C, C_prev, X) buffers, the controller state and
   // the streams their sweep bodies are captured on
@@ -914,6 +917,9 @@ static fde_status build_level_rational(sylv_s* S, Inner<T>& in, int l, const std
   FDE_TRY(gemm_batch_upload(pool, dup, false, true, T(1), T(1), &ls.r_update, st));
   FDE_TRY(gemm_batch_upload(pool, dup2, false, true, T(1), T(1), &ls.r_update2, st));
   if constexpr (sizeof(T) == sizeof(float)) {
+    // operand kind of the level products (BF16 for FDE_BF16_REFINE), set
+    // before packing: the packed tiles are in that kind's format
+    ls.r_apply.kind = ls.r_update.kind = ls.r_update2.kind = S->level_kind;
     // the stacked resolvents and the constant update factors never change:
     // pack them for the tensor cores (operator A of the application, ZA of
     // the first update, WB of the second)
@@ -2243,11 +2249,20 @@ extern "C" fde_status sylv_create(hodlr_t Ax, hodlr_t Ay, int prec, void* stream
   FDE_ARG(out != nullptr, "out is NULL");
   *out = nullptr;
   FDE_ARG(Ax != nullptr && Ay != nullptr, "NULL operator");
-  FDE_ARG(prec == FDE_FP64 || prec == FDE_FP32_REFINE, "unknown precision");
+  FDE_ARG(prec == FDE_FP64 || prec == FDE_FP32_REFINE || prec == FDE_BF16_REFINE, "unknown precision");
   FDE_ARG(Ax->tree.N == Ay->tree.N && Ax->tree.leaf == Ay->tree.leaf, "A_x and A_y must share N and leaf");
   FDE_ARG(Ax->tree.L >= 1, "N must exceed the leaf size");
   FDE_ARG(Ax->p.shift == 0.5 && Ay->p.shift == 0.5, "A_x and A_y must be built with shift 1/2");
   sylv_s* S = new sylv_s();
+  // BF16: the FP32 inner solver with BF16 operands in the level products,
+  // split into BF16 hi + lo (three products); FDE_BF16_SPLIT=0 rounds them to
+  // BF16 (one product: a coarser inner solve, more refinement sweeps)
+  if (prec == FDE_BF16_REFINE) {
+    S->level_kind = kTcBF16x3;
+    if (const char* e = getenv("FDE_BF16_SPLIT"))
+      if (!strcmp(e, "0")) S->level_kind = kTcBF16;
+    prec = FDE_FP32_REFINE;
+  }
   fde_status s = create_impl(Ax, Ay, prec, (cudaStream_t)stream, S);
   if (s != FDE_OK) {
     delete S;

@@ -11,8 +11,14 @@
 // the accumulator with tcgen05.ld and writes C with coalesced stores.
 // Precision: mode 1 = TF32 inputs (inputs rounded to TF32), mode 3 = 3xTF32
 // split (a = a_hi + a_lo, products hi*hi + hi*lo + lo*hi) which keeps FP32-level
-// accuracy.  Accumulation is FP32.
+// accuracy.  Per batch, the operands may instead be BF16 (kind::f16, K = 16
+// per instruction): rounded to BF16 (one product), or split into BF16 hi and
+// lo (three products, about 16 significant bits).  A BF16 tile uses the same
+// slot geometry as a TF32 one: each 128-byte row holds the tile's 32 k as 16
+// pairs in its first 64 logical bytes.  Accumulation is FP32.
 #include <stdint.h>
+
+#include <cuda_bf16.h>
 
 #include <atomic>
 #include <mutex>
@@ -74,6 +80,21 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// Two FP32 values as a BF16 pair (round to nearest even), e0 in the low half,
+// and the pair of their exact FP32 remainders rounded to BF16 in *lo.
+__device__ __forceinline__ uint32_t bf16_pair(float e0, float e1, uint32_t* lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(e0, e1);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(e0 - hf.x, e1 - hf.y);
+  *lo = *reinterpret_cast<const uint32_t*>(&l);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -219,13 +240,24 @@ __device__ __forceinline__ void tile_copy(uint32_t dst, const float* __restrict_
 // Raw FP32 tile -> TF32 hi (and the remainder lo in split mode),
 // same swizzled offsets; thread t converts 16-byte chunks t, t + 256, ...
 // (the chunks tile_copy<R, true> gave it)
+// BF16 operands (bf): the four k of the chunk become two pairs (8 bytes) at
+// pair positions 2 kq, 2 kq + 1 of the row, i.e. logical bytes 8 kq .. 8 kq + 7.
 template <int R>
-__device__ __forceinline__ void tile_convert(const uint8_t* raw, uint8_t* hi, uint8_t* lo, bool split) {
+__device__ __forceinline__ void tile_convert(const uint8_t* raw, uint8_t* hi, uint8_t* lo, bool split, bool bf) {
 #pragma unroll
   for (int i = 0; i < R / 32; ++i) {
     const int ch = threadIdx.x + kLoaders * i, r = ch >> 3, kq = ch & 7;
     const uint32_t off = sw_off(r, 4 * kq);
     const float4 v = *reinterpret_cast<const float4*>(raw + off);
+    if (bf) {
+      const uint32_t o2 = sw_off(r, 2 * kq);
+      uint2 hv, lv;
+      hv.x = bf16_pair(v.x, v.y, &lv.x);
+      hv.y = bf16_pair(v.z, v.w, &lv.y);
+      *reinterpret_cast<uint2*>(hi + o2) = hv;
+      if (split) *reinterpret_cast<uint2*>(lo + o2) = lv;
+      continue;
+    }
     float4 h;
     h.x = to_tf32(v.x);
     h.y = to_tf32(v.y);
@@ -252,7 +284,7 @@ __device__ __forceinline__ void tile_convert(const uint8_t* raw, uint8_t* hi, ui
 // chunk columns mg ^ kg and their stores the swizzled chunks kg ^ (row mod 8),
 // 8 distinct bank groups either way, in a fixed order.
 template <int R>
-__device__ __forceinline__ void tile_convert_mn(const uint8_t* raw, uint8_t* hi, uint8_t* lo, bool split) {
+__device__ __forceinline__ void tile_convert_mn(const uint8_t* raw, uint8_t* hi, uint8_t* lo, bool split, bool bf) {
   constexpr int NB = (R / 4) * 8;
 #pragma unroll
   for (int i = 0; i < (NB + kLoaders - 1) / kLoaders; ++i) {
@@ -270,6 +302,15 @@ __device__ __forceinline__ void tile_convert_mn(const uint8_t* raw, uint8_t* hi,
       x.y = rr == 0 ? q[1].x : rr == 1 ? q[1].y : rr == 2 ? q[1].z : q[1].w;
       x.z = rr == 0 ? q[2].x : rr == 1 ? q[2].y : rr == 2 ? q[2].z : q[2].w;
       x.w = rr == 0 ? q[3].x : rr == 1 ? q[3].y : rr == 2 ? q[3].z : q[3].w;
+      if (bf) {
+        const uint32_t o2 = sw_off(4 * mg + rr, 2 * kg);
+        uint2 hv, lv;
+        hv.x = bf16_pair(x.x, x.y, &lv.x);
+        hv.y = bf16_pair(x.z, x.w, &lv.y);
+        *reinterpret_cast<uint2*>(hi + o2) = hv;
+        if (split) *reinterpret_cast<uint2*>(lo + o2) = lv;
+        continue;
+      }
       h.x = to_tf32(x.x);
       h.y = to_tf32(x.y);
       h.z = to_tf32(x.z);
@@ -291,6 +332,13 @@ __device__ __forceinline__ void tile_convert_mn(const uint8_t* raw, uint8_t* hi,
 template <int BN>
 __host__ __device__ constexpr uint32_t idesc_tf32_n() {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+// Instruction descriptor for kind::f16: D = F32, A = B = BF16, both K-major,
+// M = 128, N = BN.
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc_bf16_n() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 template <int BN>
@@ -397,7 +445,7 @@ constexpr int kMmaWarp = kEpiWarp0 + kEpiWarps;                // warp 12
 template <int BN, int RAW, bool TA, bool TB>
 __global__ void __launch_bounds__(kPThreads, 1)
     tc_gemm_kernel(const GemmDesc<float>* __restrict__ descs, int batch, int mt, int nt, float alpha, float beta,
-                   int split, int mslots, int vec_a, int vec_b, int pk_a, int pk_b) {
+                   int split, int mslots, int vec_a, int vec_b, int pk_a, int pk_b, int bf) {
   constexpr int A_BYTES = BM * BK * 4, B_BYTES = BN * BK * 4;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base_u32 = smem_u32(smem_raw);
@@ -508,15 +556,15 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const uint8_t* rs = raw + (size_t)(gg % RAW) * raw_bytes<BN>();
         if (!pk_a) {
           if (TA)
-            tile_convert<BM>(rs, slot, slot + a_lo_off, split != 0);
+            tile_convert<BM>(rs, slot, slot + a_lo_off, split != 0, bf != 0);
           else
-            tile_convert_mn<BM>(rs, slot, slot + a_lo_off, split != 0);
+            tile_convert_mn<BM>(rs, slot, slot + a_lo_off, split != 0, bf != 0);
         }
         if (!pk_b) {
           if (!TB)
-            tile_convert<BN>(rs + A_BYTES, slot + b_hi_off, slot + b_lo_off, split != 0);
+            tile_convert<BN>(rs + A_BYTES, slot + b_hi_off, slot + b_lo_off, split != 0, bf != 0);
           else
-            tile_convert_mn<BN>(rs + A_BYTES, slot + b_hi_off, slot + b_lo_off, split != 0);
+            tile_convert_mn<BN>(rs + A_BYTES, slot + b_hi_off, slot + b_lo_off, split != 0, bf != 0);
         }
         fence_proxy_async();  // this thread's tiles -> visible to the tensor core
       }
@@ -559,6 +607,23 @@ __global__ void __launch_bounds__(kPThreads, 1)
           uint8_t* slot = sm + (size_t)s * slot_bytes;
           const uint32_t a_hi = smem_u32(slot), b_hi = smem_u32(slot + b_hi_off);
           const uint32_t a_lo = smem_u32(slot + a_lo_off), b_lo = smem_u32(slot + b_lo_off);
+          if (bf) {
+            // BF16: K = 16 per instruction, 32 bytes along the row; the tile's
+            // 32 k are the row's first 64 logical bytes
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t off = kk * 32;
+              const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
+              if (split) {
+                mma_bf16(acc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_bf16_n<2 * BN>(), acc0);
+                mma_bf16(acc + BN, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc_bf16_n<BN>(), 1u);
+              } else {
+                mma_bf16(acc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_bf16_n<BN>(), acc0);
+              }
+            }
+            mma_commit(smem_u32(&empty_bar[s]));
+            continue;
+          }
 #pragma unroll
           for (int kk = 0; kk < BK / 8; ++kk) {
             const uint32_t off = kk * 32;  // 8 TF32 = 32 bytes along k inside the swizzle atom
@@ -745,7 +810,7 @@ static fde_status tc_prepare_once() {
 }
 
 template <int BN>
-static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t st) {
+static fde_status launch_bn(const GemmBatch<float>& b, int split, int bf, cudaStream_t st) {
   const int mslots = tc::mslots_for<BN>(split);
   constexpr int RAW = tc::raw_stages<BN>();
   const size_t smem = 1024 + (size_t)mslots * tc::slot_bytes<BN>(split) + (size_t)RAW * tc::raw_bytes<BN>();
@@ -766,7 +831,7 @@ static fde_status launch_bn(const GemmBatch<float>& b, int split, cudaStream_t s
   const int grid = (int)(tiles < sms ? tiles : sms);
   ProfScope ps("gemm32tc", st, b.flops, 1);
   kern<<<grid, tc::kPThreads, smem, st>>>(b.d_desc, b.batch, mt, nt, b.alpha, b.beta, split, mslots,
-                                          b.vec_a ? 1 : 0, b.vec_b ? 1 : 0, b.pk_a ? 1 : 0, b.pk_b ? 1 : 0);
+                                          b.vec_a ? 1 : 0, b.vec_b ? 1 : 0, b.pk_a ? 1 : 0, b.pk_b ? 1 : 0, bf);
   FDE_LAUNCH("tc_gemm_kernel");
   return FDE_OK;
 }
@@ -779,18 +844,19 @@ fde_status tc_gemm_run(const GemmBatch<float>& b, cudaStream_t st, bool* used) {
   // (the epilogue addresses the 32 columns of a chunk with 32-bit offsets j * ldc)
   if (mode == 0 || b.max_m < 64 || b.max_n < 16 || b.max_k < 32 || b.max_ldc > (1 << 26)) return FDE_OK;
   FDE_TRY(tc_prepare());
-  const int split = (mode == 3) ? 1 : 0;
+  const int bf = b.kind == kTcDefault ? 0 : 1;
+  const int split = b.kind == kTcBF16x3 ? 1 : b.kind == kTcBF16 ? 0 : (mode == 3) ? 1 : 0;
   const int bn = tc_bn_for(b.max_n);
   if (b.pk_b && b.pk_bn != bn) {
     set_error("tensor-core GEMM: B packed for BN = %d, launch needs %d", b.pk_bn, bn);
     return FDE_ERR_ARG;
   }
   if (bn == 32)
-    FDE_TRY(launch_bn<32>(b, split, st));
+    FDE_TRY(launch_bn<32>(b, split, bf, st));
   else if (bn == 64)
-    FDE_TRY(launch_bn<64>(b, split, st));
+    FDE_TRY(launch_bn<64>(b, split, bf, st));
   else
-    FDE_TRY(launch_bn<128>(b, split, st));
+    FDE_TRY(launch_bn<128>(b, split, bf, st));
   *used = true;
   return FDE_OK;
 }
@@ -809,7 +875,7 @@ struct PackJob {
 // shared-memory tile; zeros outside the problem.
 template <bool IS_B>
 __global__ void pack_tiles_kernel(const GemmDesc<float>* __restrict__ descs, const PackJob* __restrict__ jobs, int R,
-                                  int trans) {
+                                  int trans, int bf) {
   const PackJob jb = jobs[blockIdx.x];
   const GemmDesc<float> d = descs[jb.z];
   const float* X = IS_B ? d.B : d.A;
@@ -819,22 +885,39 @@ __global__ void pack_tiles_kernel(const GemmDesc<float>* __restrict__ descs, con
   const bool two_level = d.kblk > 0 && !kcontig;
   float* hi = jb.dst;
   float* lo = jb.dst + (size_t)R * tc::BK;
+  auto elem = [&](int r, int c) -> float {
+    const int row = jb.r * R + r, k = jb.t * tc::BK + c;
+    if (row >= nrows || k >= d.k) return 0.f;
+    if (kcontig) return X[(size_t)row * ld + k];
+    long long col = (long long)k * ld;
+    if (two_level) {
+      const int q = k / d.kblk;
+      col = (long long)q * d.kstr + (long long)(k - q * d.kblk) * ld;
+    }
+    return X[col + row];
+  };
+  if (bf) {
+    // BF16: pair p of row r (k = 2p, 2p + 1) at pair position p; the second
+    // half of each row stays unused
+    uint32_t* hu = reinterpret_cast<uint32_t*>(hi);
+    uint32_t* lu = reinterpret_cast<uint32_t*>(lo);
+    for (int e = threadIdx.x; e < R * tc::BK; e += blockDim.x) {
+      const int r = e / tc::BK, p = e % tc::BK;
+      const uint32_t off = tc::sw_off(r, p) >> 2;
+      if (p >= tc::BK / 2) {
+        hu[off] = 0u;
+        lu[off] = 0u;
+        continue;
+      }
+      uint32_t l;
+      hu[off] = tc::bf16_pair(elem(r, 2 * p), elem(r, 2 * p + 1), &l);
+      lu[off] = l;
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < R * tc::BK; e += blockDim.x) {
     const int r = e / tc::BK, c = e % tc::BK;
-    const int row = jb.r * R + r, k = jb.t * tc::BK + c;
-    float v = 0.f;
-    if (row < nrows && k < d.k) {
-      if (kcontig) {
-        v = X[(size_t)row * ld + k];
-      } else {
-        long long col = (long long)k * ld;
-        if (two_level) {
-          const int q = k / d.kblk;
-          col = (long long)q * d.kstr + (long long)(k - q * d.kblk) * ld;
-        }
-        v = X[col + row];
-      }
-    }
+    const float v = elem(r, c);
     const uint32_t off = tc::sw_off(r, c) >> 2;
     const float h = tc::to_tf32(v);
     hi[off] = h;
@@ -891,14 +974,16 @@ fde_status gemm_batch_pack(DevPool& pool, GemmBatch<float>* b, bool pack_a, bool
     PackJob* dj;
     FDE_TRY(scratch.alloc(&dj, ja.size()));
     FDE_CUDA(cudaMemcpyAsync(dj, ja.data(), ja.size() * sizeof(PackJob), cudaMemcpyHostToDevice, st));
-    pack_tiles_kernel<false><<<(unsigned)ja.size(), 256, 0, st>>>(b->d_desc, dj, 128, b->ta ? 1 : 0);
+    pack_tiles_kernel<false><<<(unsigned)ja.size(), 256, 0, st>>>(b->d_desc, dj, 128, b->ta ? 1 : 0,
+                                                                 b->kind == kTcDefault ? 0 : 1);
     FDE_LAUNCH("pack_tiles_kernel");
   }
   if (!jbv.empty()) {
     PackJob* dj;
     FDE_TRY(scratch.alloc(&dj, jbv.size()));
     FDE_CUDA(cudaMemcpyAsync(dj, jbv.data(), jbv.size() * sizeof(PackJob), cudaMemcpyHostToDevice, st));
-    pack_tiles_kernel<true><<<(unsigned)jbv.size(), 256, 0, st>>>(b->d_desc, dj, bn, b->tb ? 1 : 0);
+    pack_tiles_kernel<true><<<(unsigned)jbv.size(), 256, 0, st>>>(b->d_desc, dj, bn, b->tb ? 1 : 0,
+                                                                 b->kind == kTcDefault ? 0 : 1);
     FDE_LAUNCH("pack_tiles_kernel");
   }
   FDE_CUDA(cudaStreamSynchronize(st));
@@ -918,8 +1003,8 @@ extern "C" fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float al
   using namespace fde;
   FDE_ARG(m >= 0 && n >= 0 && k >= 0 && batch >= 0, "negative size");
   FDE_ARG(A != nullptr && B != nullptr && C != nullptr, "NULL matrix");
-  FDE_ARG(mode == -1 || mode == 0 || mode == 1 || mode == 3 || mode == 4 || (mode >= 5 && mode <= 7),
-          "mode must be -1, 0, 1, 3, 4, 5, 6 or 7");
+  FDE_ARG(mode == -1 || mode == 0 || mode == 1 || mode == 3 || mode == 4 || (mode >= 5 && mode <= 11),
+          "mode must be -1, 0, 1, 3, 4 or 5 .. 11");
   FDE_ARG(kblk >= 0 && (kblk == 0 || kstr >= 0), "bad kblk / kstr");
   FDE_ARG(ldc >= (m > 1 ? m : 1), "ldc < m");
   FDE_ARG(lda >= 1 && ldb >= 1, "bad lda / ldb");
@@ -944,9 +1029,11 @@ extern "C" fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float al
     set_tc_mode(mode >= 4 ? 3 : mode);
     set_skinny_force(mode == 4 ? 1 : 0);
   }
-  if (mode >= 5) {
+  if (mode >= 8) gb.kind = (mode == 8 || mode == 11) ? kTcBF16 : kTcBF16x3;
+  if ((mode >= 5 && mode <= 7) || mode >= 10) {
     size_t budget = (size_t)1 << 40;
-    const fde_status ps = gemm_batch_pack(scratch, &gb, mode != 6, mode != 5, &budget, st);
+    const bool pa = mode >= 10 || mode != 6, pb = mode >= 10 || mode != 5;
+    const fde_status ps = gemm_batch_pack(scratch, &gb, pa, pb, &budget, st);
     if (ps != FDE_OK) {
       set_tc_mode(saved);
       set_skinny_force(-1);

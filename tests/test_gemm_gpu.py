@@ -13,10 +13,17 @@ torch = pytest.importorskip("torch")
 # elementwise error bounds relative to (|A| |B|)_ij:
 #  SIMT / 3xTF32: FP32 accumulation over k terms plus the 2^-21 split residue
 #  TF32: operands rounded to 11 significant bits (2 * 2^-11) plus accumulation
+#  BF16 (modes 8, 11): operands rounded to 8 significant bits (2 * 2^-9)
+#  BF16 hi/lo split (modes 9, 10): remainders below 2^-18 per operand and the
+#  dropped lo*lo product, 4 * 2^-18
 def _bound(mode, k):
     u = 2.0 ** -24
     if mode == 1:
         return 2 * 2.0 ** -11 + 2 * k * u
+    if mode in (8, 11):
+        return 2 * 2.0 ** -9 + 2 * k * u
+    if mode in (9, 10):
+        return 4 * 2.0 ** -18 + 2 * k * u
     return 2.0 ** -20 + 2 * k * u  # modes 0, 4 (FP32 FMA), 3 and 5-7 (3xTF32)
 
 
@@ -42,12 +49,14 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3, 5, 6, 7])
+@pytest.mark.parametrize("mode", [0, 1, 3, 5, 6, 7, 8, 9, 10, 11])
 @pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_gemm_f32(lib, mode, ta, tb, shape):
     """Modes 5-7: 3xTF32 with A, B or both packed (pre-split tiles loaded by
-    bulk asynchronous copies), every transpose and the ragged shapes."""
+    bulk asynchronous copies); 8 / 9: BF16 operands (kind::f16), rounded or
+    split into hi + lo; 10 / 11: those with both operands packed; every
+    transpose and the ragged shapes."""
     m, n, k, pad, batch = shape
     rng = np.random.default_rng(m * 7 + n * 3 + k + 100 * ta + 10 * tb + mode)
     ar, ac = (k, m) if ta else (m, k)
@@ -82,7 +91,7 @@ def test_gemm_f32(lib, mode, ta, tb, shape):
             assert np.array_equal(Cg[i, :, m:], C0[i, :, m:])
 
 
-@pytest.mark.parametrize("mode", [1, 3, 5, 6, 7])
+@pytest.mark.parametrize("mode", [1, 3, 5, 6, 7, 8, 9, 10, 11])
 def test_gemm_two_level_k(lib, mode):
     """k runs over panels of kblk columns that sit kstr apart (non-transposed A,
     transposed B), as in the stacked low-rank update of the Sylvester solver."""
@@ -136,6 +145,28 @@ def test_gemm_split_beats_tf32(lib):
         got = dC.cpu().numpy().reshape(n, m).T
         errs[mode] = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert errs[3] < 2e-6 and errs[7] < 2e-6 and errs[1] > 100 * errs[3], errs
+
+
+def test_gemm_bf16_split_beats_bf16(lib):
+    """BF16 operands: the hi/lo split (three products) is about 2^-8 times the
+    error of plain BF16 products, packed or not, and plain BF16 sits near its
+    8-bit rounding."""
+    rng = np.random.default_rng(12)
+    m = n = 256
+    k = 512
+    A = rng.standard_normal((k, m)).astype(np.float32)
+    B = rng.standard_normal((n, k)).astype(np.float32)
+    ref = A.T.astype(np.float64) @ B.T.astype(np.float64)
+    errs = {}
+    for mode in (8, 9, 10, 11):
+        dA, dB = torch.from_numpy(A.ravel().copy()).cuda(), torch.from_numpy(B.ravel().copy()).cuda()
+        dC = torch.zeros(m * n, dtype=torch.float32, device="cuda")
+        lib.gemm_f32(0, 0, m, n, k, 1.0, dA.data_ptr(), m, 0, dB.data_ptr(), k, 0, 0.0, dC.data_ptr(), m, 0,
+                     mode=mode)
+        got = dC.cpu().numpy().reshape(n, m).T
+        errs[mode] = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert 5e-4 < errs[8] < 5e-3 and 5e-4 < errs[11] < 5e-3, errs
+    assert errs[9] < 3e-5 and errs[10] < 3e-5 and errs[8] > 30 * errs[9], errs
 
 
 SKINNY_SHAPES = [

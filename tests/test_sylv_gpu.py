@@ -91,6 +91,54 @@ def test_sylv_step_vs_oracle(lib, prec, N, leaf, alpha):
         P.close()
 
 
+@pytest.mark.parametrize("split", ["0", "1"])
+@pytest.mark.parametrize("N,leaf,alpha", [(256, 64, (1.3, 1.7)), (512, 128, (1.5, 1.5))])
+def test_bf16_refine_step_vs_oracle(lib, monkeypatch, split, N, leaf, alpha):
+    """FDE_BF16_REFINE: the level products of the inner solver on BF16 tensor
+    cores (rounded operands, or hi/lo split with FDE_BF16_SPLIT=1); the
+    unrefined inner solve is only BF16-accurate, the FP64 refinement still
+    reaches the oracle's solution within 1e-8."""
+    monkeypatch.setenv("FDE_BF16_SPLIT", split)
+    w = I.fd2d(N=N, alpha=alpha, steps=50, leaf=leaf)
+    P = Pair(lib, w, B.FDE_BF16_REFINE)
+    try:
+        C = O.fde2d_rhs(w, w.u0, 0) + I.random_matrix_fast(N, N, seed=3)
+        Xo = O.sylvester_bartels_stewart(O.fd_operator(w.ops[0]), O.fd_operator(w.ops[1]), C)
+        Xd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+        Cd = _dev(C)
+        lib.prof_reset()
+        lib.prof_enable(True)
+        lib.sylv_inner_solve(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+        torch.cuda.synchronize()
+        lib.prof_enable(False)
+        assert lib.prof_query("gemm32tc")[1] > 0
+        lib.prof_reset()
+        e_inner = _relerr(_host(Xd, N, N), Xo)
+        assert e_inner < (1e-4 if split == "1" else 5e-2), e_inner
+        Xd.zero_()
+        relres, sweeps = lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+        e = _relerr(_host(Xd, N, N), Xo)
+        # the refinement stops on its update estimate; with the coarser inner
+        # solve the last update leaves a residual near 1e-9 (error ~1e-11)
+        assert e <= 1e-8 and relres < 1e-8 and 1 <= sweeps <= 12, (e, relres, sweeps)
+    finally:
+        P.close()
+
+
+def test_bf16_refine_time_loop_vs_oracle(lib, monkeypatch):
+    """Ten steps of the 2D time loop with FDE_BF16_REFINE against the oracle's
+    loop."""
+    monkeypatch.delenv("FDE_BF16_SPLIT", raising=False)
+    w = I.fd2d(N=256, alpha=(1.3, 1.7), steps=50, leaf=64)
+    rp = lib.run_params(w, prec=B.FDE_BF16_REFINE)
+    rp.steps = 10
+    U0 = _dev(w.u0)
+    Uo = torch.zeros_like(U0)
+    st = lib.fde_run(rp, U0.data_ptr(), Uo.data_ptr())
+    assert _relerr(_host(Uo, w.N, w.N), O.fde2d_run(w, steps=10)) <= 1e-8
+    assert st.sweeps_total >= 10
+
+
 def test_sylv_warm_start_and_symmetry(lib):
     # A_x = A_y and symmetric C give a symmetric X (oracle pin); warm start from
     # the exact solution needs a single sweep.
