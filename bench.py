@@ -242,7 +242,7 @@ def family_roofline(fam, ms, launches, work, kind, peaks):
 
 
 FAMILIES = ["gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply", "fft_df", "fft_f32", "transpose",
-            "refine", "fadi_axpy"]
+            "refine", "fadi_axpy", "pack"]
 # double-float FFT: FP32 operations per algorithmic flop (5 P log2 P per
 # transform, 6 per complex product) of the radix-8 kernel with the normwise
 # double-float addition: a radix-8 butterfly costs 950 operations for 120

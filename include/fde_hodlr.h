@@ -448,7 +448,7 @@ fde_status fde_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const 
  * fde_prof_query returns the summed device time (ms) and launch count of a
  * family ("gemm32", "gemm32tc", "gemm64", "trsyl32", "trsyl64", "fft_apply",
  * "fft_df", "fft_f32", "schur", "recompress", "fadi_axpy", "transpose",
- * "refine"; an unknown name reads as no launches), synchronising the events
+ * "refine", "pack"; an unknown name reads as no launches), synchronising the events
  * it reads;
  * fde_prof_reset clears the records. */
 unsigned long long fde_launch_count(void);

@@ -47,6 +47,12 @@ struct GemmBatch {
   // product), kTcBF16x3 splits them into BF16 hi + lo (three products);
   // FP32 accumulation in every case.  Packed tiles are packed for this kind.
   int kind = 0;
+  // Repacked operands (gemm_batch_pack with repack): the pack jobs of the
+  // operand that changes between runs; gemm_batch_run refreshes its packed
+  // tiles from the current values (one pack launch) before each GEMM launch.
+  const void* rp_a_jobs = nullptr;
+  const void* rp_b_jobs = nullptr;
+  int rp_a_n = 0, rp_b_n = 0;
   T alpha = T(1), beta = T(0);
 };
 
@@ -81,8 +87,14 @@ int tc_bn_for(int max_n);
 // valid for the other paths.  Does nothing (and returns FDE_OK) when the
 // tensor cores are off or the batch would not run on them, or when the packed
 // tiles would take more than *budget bytes (decremented by what is used).
+//
+// repack_a / repack_b: the operand is not constant; its packed tiles and the
+// pack jobs are kept (in `pool`) and gemm_batch_run repacks it from the
+// current values before every launch.  Pays off where every tile of that
+// operand is read by many tiles of the product (a thin operand against a
+// tall or wide one), since the kernel then only issues bulk copies.
 fde_status gemm_batch_pack(DevPool& pool, GemmBatch<float>* b, bool pack_a, bool pack_b, size_t* budget,
-                           cudaStream_t st);
+                           cudaStream_t st, bool repack_a = false, bool repack_b = false);
 
 // In-place inverse of `batch` square matrices (sizes n_i <= nmax, leading
 // dimension ld, matrix i at A + i*stride) by Gauss–Jordan elimination with

@@ -922,13 +922,19 @@ static fde_status build_level_rational(sylv_s* S, Inner<T>& in, int l, const std
     ls.r_apply.kind = ls.r_update.kind = ls.r_update2.kind = S->level_kind;
     // the stacked resolvents and the constant update factors never change:
     // pack them for the tensor cores (operator A of the application, ZA of
-    // the first update, WB of the second)
-    FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_apply), true, false, &S->pack_budget,
-                            st));
-    FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_update), true, false, &S->pack_budget,
-                            st));
-    FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_update2), false, true,
-                            &S->pack_budget, st));
+    // the first update, WB of the second).  The other operand of each (the
+    // thin X0-dependent factors, read by every tile of the tall or wide
+    // constant one) is repacked before every launch, so that the kernel only
+    // issues bulk copies (FDE_REPACK=0: converted by the loaders instead)
+    bool rp = true;
+    if (const char* e = getenv("FDE_REPACK"))
+      if (!strcmp(e, "0")) rp = false;
+    FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_apply), true, rp, &S->pack_budget,
+                            st, false, rp));
+    FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_update), true, rp, &S->pack_budget,
+                            st, false, rp));
+    FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_update2), rp, true,
+                            &S->pack_budget, st, rp, false));
   }
   FDE_CUDA(cudaStreamSynchronize(st));
   return FDE_OK;

@@ -110,6 +110,22 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2u << 61;             // SWIZZLE_128B
   return d;
 }
+// The same with 64-byte swizzle: K-major, 64-byte rows, 8-row groups 512 bytes
+// apart (dense BF16 tiles: 32 k per row).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512u >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1u << 46;             // version
+  d |= (uint64_t)4u << 61;             // SWIZZLE_64B
+  return d;
+}
+// Byte offset of 4-byte unit u (0..15) of row r in a K-major SW64 tile (rows in
+// 8-row groups of 512 bytes, 16-byte chunks XOR-swizzled by (r / 2) mod 4).
+__host__ __device__ __forceinline__ uint32_t sw64_off(int r, int u) {
+  return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((u >> 2) ^ (r >> 1)) & 3) << 4) + ((u & 3) << 2));
+}
 // round to TF32 (nearest, ties away)
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
@@ -455,7 +471,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
   // packed operand's hi and lo tiles arrive in one bulk copy; raw stages after the slots
   const int slot_bytes = (A_BYTES + B_BYTES) * (split ? 2 : 1);
   const int a_lo_off = A_BYTES, b_hi_off = split ? 2 * A_BYTES : A_BYTES, b_lo_off = b_hi_off + B_BYTES;
-  const uint32_t a_copy = (uint32_t)A_BYTES * (split ? 2u : 1u), b_copy = (uint32_t)B_BYTES * (split ? 2u : 1u);
+  // packed BF16 operands arrive dense (64-byte rows, SW64; hi then lo), half
+  // the bytes of a TF32 or converted BF16 tile
+  const bool dense_a = bf && pk_a, dense_b = bf && pk_b;
+  const uint32_t a_copy = (uint32_t)(dense_a ? BM * 64 : A_BYTES) * (split ? 2u : 1u);
+  const uint32_t b_copy = (uint32_t)(dense_b ? BN * 64 : B_BYTES) * (split ? 2u : 1u);
   uint8_t* raw = sm + (size_t)mslots * slot_bytes;
   __shared__ __align__(8) uint64_t full_bar[kMaxSlots], empty_bar[kMaxSlots], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_base;
@@ -609,16 +629,21 @@ __global__ void __launch_bounds__(kPThreads, 1)
           const uint32_t a_lo = smem_u32(slot + a_lo_off), b_lo = smem_u32(slot + b_lo_off);
           if (bf) {
             // BF16: K = 16 per instruction, 32 bytes along the row; the tile's
-            // 32 k are the row's first 64 logical bytes
+            // 32 k are the row's first 64 logical bytes (converted tiles,
+            // SW128) or the whole 64-byte row (packed tiles, SW64)
+            const uint32_t a_lo_b = dense_a ? a_hi + BM * 64 : a_lo;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
               const uint32_t off = kk * 32;
               const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
+              const uint64_t dah = dense_a ? sw64_desc(a_hi + off) : sw128_desc(a_hi + off);
+              const uint64_t dbh = dense_b ? sw64_desc(b_hi + off) : sw128_desc(b_hi + off);
               if (split) {
-                mma_bf16(acc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_bf16_n<2 * BN>(), acc0);
-                mma_bf16(acc + BN, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc_bf16_n<BN>(), 1u);
+                const uint64_t dal = dense_a ? sw64_desc(a_lo_b + off) : sw128_desc(a_lo_b + off);
+                mma_bf16(acc, dah, dbh, idesc_bf16_n<2 * BN>(), acc0);
+                mma_bf16(acc + BN, dal, dbh, idesc_bf16_n<BN>(), 1u);
               } else {
-                mma_bf16(acc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_bf16_n<BN>(), acc0);
+                mma_bf16(acc, dah, dbh, idesc_bf16_n<BN>(), acc0);
               }
             }
             mma_commit(smem_u32(&empty_bar[s]));
@@ -811,9 +836,17 @@ static fde_status tc_prepare_once() {
 
 template <int BN>
 static fde_status launch_bn(const GemmBatch<float>& b, int split, int bf, cudaStream_t st) {
-  const int mslots = tc::mslots_for<BN>(split);
   constexpr int RAW = tc::raw_stages<BN>();
-  const size_t smem = 1024 + (size_t)mslots * tc::slot_bytes<BN>(split) + (size_t)RAW * tc::raw_bytes<BN>();
+  // both operands packed: no raw stages are used, so the whole budget goes to
+  // MMA slots (a deeper ring of bulk copies in flight)
+  const bool no_raw = b.pk_a && b.pk_b;
+  int mslots = tc::mslots_for<BN>(split);
+  if (no_raw) {
+    const int s2 = (int)(tc::kSmemBudget / tc::slot_bytes<BN>(split));
+    mslots = s2 > tc::kMaxSlots ? tc::kMaxSlots : s2;
+  }
+  const size_t smem = 1024 + (size_t)mslots * tc::slot_bytes<BN>(split) +
+                      (no_raw ? (size_t)0 : (size_t)RAW * tc::raw_bytes<BN>());
   const int which = (b.ta ? 2 : 0) + (b.tb ? 1 : 0);
   auto kern = (which == 0) ? tc::tc_gemm_kernel<BN, RAW, false, false>
               : (which == 1) ? tc::tc_gemm_kernel<BN, RAW, false, true>
@@ -836,6 +869,8 @@ static fde_status launch_bn(const GemmBatch<float>& b, int split, int bf, cudaSt
   return FDE_OK;
 }
 
+static fde_status repack_run(const GemmBatch<float>& b, int bn, cudaStream_t st);
+
 // Runs the batch on the tensor cores; returns FDE_OK without launching if the
 // batch is better left to the SIMT kernel (*used = false).
 fde_status tc_gemm_run(const GemmBatch<float>& b, cudaStream_t st, bool* used) {
@@ -851,6 +886,7 @@ fde_status tc_gemm_run(const GemmBatch<float>& b, cudaStream_t st, bool* used) {
     set_error("tensor-core GEMM: B packed for BN = %d, launch needs %d", b.pk_bn, bn);
     return FDE_ERR_ARG;
   }
+  if (b.rp_a_n || b.rp_b_n) FDE_TRY(repack_run(b, bn, st));
   if (bn == 32)
     FDE_TRY(launch_bn<32>(b, split, bf, st));
   else if (bn == 64)
@@ -897,18 +933,13 @@ __global__ void pack_tiles_kernel(const GemmDesc<float>* __restrict__ descs, con
     return X[col + row];
   };
   if (bf) {
-    // BF16: pair p of row r (k = 2p, 2p + 1) at pair position p; the second
-    // half of each row stays unused
+    // BF16: dense 64-byte rows in the SW64 layout (pair p of row r: k = 2p,
+    // 2p + 1), the hi tile (R x 64 bytes) then the lo tile
     uint32_t* hu = reinterpret_cast<uint32_t*>(hi);
-    uint32_t* lu = reinterpret_cast<uint32_t*>(lo);
-    for (int e = threadIdx.x; e < R * tc::BK; e += blockDim.x) {
-      const int r = e / tc::BK, p = e % tc::BK;
-      const uint32_t off = tc::sw_off(r, p) >> 2;
-      if (p >= tc::BK / 2) {
-        hu[off] = 0u;
-        lu[off] = 0u;
-        continue;
-      }
+    uint32_t* lu = hu + R * 16;
+    for (int e = threadIdx.x; e < R * (tc::BK / 2); e += blockDim.x) {
+      const int r = e / (tc::BK / 2), p = e % (tc::BK / 2);
+      const uint32_t off = tc::sw64_off(r, p) >> 2;
       uint32_t l;
       hu[off] = tc::bf16_pair(elem(r, 2 * p), elem(r, 2 * p + 1), &l);
       lu[off] = l;
@@ -926,8 +957,27 @@ __global__ void pack_tiles_kernel(const GemmDesc<float>* __restrict__ descs, con
 }
 }  // namespace
 
+// Refreshes the packed tiles of the batch's repacked operands from their
+// current values.
+static fde_status repack_run(const GemmBatch<float>& b, int bn, cudaStream_t st) {
+  const int bf = b.kind == kTcDefault ? 0 : 1;
+  const double bytes = 12.0 * 32.0 * ((double)b.rp_a_n * 128 + (double)b.rp_b_n * bn);  // read 4, write 8 per element
+  ProfScope ps("pack", st, bytes, 0);
+  if (b.rp_a_n) {
+    pack_tiles_kernel<false><<<(unsigned)b.rp_a_n, 256, 0, st>>>(b.d_desc, (const PackJob*)b.rp_a_jobs, 128,
+                                                                  b.ta ? 1 : 0, bf);
+    FDE_LAUNCH("pack_tiles_kernel");
+  }
+  if (b.rp_b_n) {
+    pack_tiles_kernel<true><<<(unsigned)b.rp_b_n, 256, 0, st>>>(b.d_desc, (const PackJob*)b.rp_b_jobs, bn,
+                                                                 b.tb ? 1 : 0, bf);
+    FDE_LAUNCH("pack_tiles_kernel");
+  }
+  return FDE_OK;
+}
+
 fde_status gemm_batch_pack(DevPool& pool, GemmBatch<float>* b, bool pack_a, bool pack_b, size_t* budget,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool repack_a, bool repack_b) {
   const int mode = tc_mode();
   if (b->batch == 0 || mode == 0 || (!pack_a && !pack_b)) return FDE_OK;
   if (b->max_m < 64 || b->max_n < 16 || b->max_k < 32 || b->max_ldc > (1 << 26)) return FDE_OK;
@@ -972,7 +1022,11 @@ fde_status gemm_batch_pack(DevPool& pool, GemmBatch<float>* b, bool pack_a, bool
   DevPool scratch;
   if (!ja.empty()) {
     PackJob* dj;
-    FDE_TRY(scratch.alloc(&dj, ja.size()));
+    FDE_TRY((repack_a ? pool : scratch).alloc(&dj, ja.size()));
+    if (repack_a) {
+      b->rp_a_jobs = dj;
+      b->rp_a_n = (int)ja.size();
+    }
     FDE_CUDA(cudaMemcpyAsync(dj, ja.data(), ja.size() * sizeof(PackJob), cudaMemcpyHostToDevice, st));
     pack_tiles_kernel<false><<<(unsigned)ja.size(), 256, 0, st>>>(b->d_desc, dj, 128, b->ta ? 1 : 0,
                                                                  b->kind == kTcDefault ? 0 : 1);
@@ -980,7 +1034,11 @@ fde_status gemm_batch_pack(DevPool& pool, GemmBatch<float>* b, bool pack_a, bool
   }
   if (!jbv.empty()) {
     PackJob* dj;
-    FDE_TRY(scratch.alloc(&dj, jbv.size()));
+    FDE_TRY((repack_b ? pool : scratch).alloc(&dj, jbv.size()));
+    if (repack_b) {
+      b->rp_b_jobs = dj;
+      b->rp_b_n = (int)jbv.size();
+    }
     FDE_CUDA(cudaMemcpyAsync(dj, jbv.data(), jbv.size() * sizeof(PackJob), cudaMemcpyHostToDevice, st));
     pack_tiles_kernel<true><<<(unsigned)jbv.size(), 256, 0, st>>>(b->d_desc, dj, bn, b->tb ? 1 : 0,
                                                                  b->kind == kTcDefault ? 0 : 1);

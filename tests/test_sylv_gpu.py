@@ -139,6 +139,35 @@ def test_bf16_refine_time_loop_vs_oracle(lib, monkeypatch):
     assert st.sweeps_total >= 10
 
 
+@pytest.mark.parametrize("prec", [B.FDE_FP32_REFINE, B.FDE_BF16_REFINE])
+def test_repacked_operands_match_converted(lib, monkeypatch, prec):
+    """The X0-dependent operands of the level products repacked before every
+    launch (pack kernel, bulk copies) against the same operands converted by
+    the GEMM's loaders (FDE_REPACK=0): the same hi/lo splits in the same
+    accumulation order, so the inner solves agree to rounding, on two calls
+    in a row (the packed tiles are refreshed, not stale)."""
+    N = 512
+    w = I.fd2d(N=N, alpha=(1.5, 1.5), steps=50, leaf=128)
+    sols = {}
+    for rp in ("1", "0"):
+        monkeypatch.setenv("FDE_REPACK", rp)
+        P = Pair(lib, w, prec)
+        try:
+            out = []
+            for seed in (3, 4):
+                C = I.random_matrix_fast(N, N, seed=seed)
+                Cd = _dev(C)
+                Xd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+                lib.sylv_inner_solve(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+                out.append(_host(Xd, N, N))
+            sols[rp] = out
+        finally:
+            P.close()
+    for a, b in zip(sols["1"], sols["0"]):
+        assert _relerr(a, b) <= 1e-12, _relerr(a, b)
+    assert _relerr(sols["1"][0], sols["1"][1]) > 1e-3
+
+
 def test_sylv_warm_start_and_symmetry(lib):
     # A_x = A_y and symmetric C give a symmetric X (oracle pin); warm start from
     # the exact solution needs a single sweep.
