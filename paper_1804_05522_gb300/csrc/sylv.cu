@@ -929,6 +929,18 @@ static fde_status build_level_rational(sylv_s* S, Inner<T>& in, int l, const std
     bool rp = true;
     if (const char* e = getenv("FDE_REPACK"))
       if (!strcmp(e, "0")) rp = false;
+    // the right-hand-side factors X0ᵀ V, X0 U: the thin constant factor packed,
+    // so that these long-k products run on the tensor cores instead of the
+    // skinny FP32 kernel (FDE_PACK_RHS=0 keeps them there)
+    bool prhs = true;
+    if (const char* e = getenv("FDE_PACK_RHS"))
+      if (!strcmp(e, "0")) prhs = false;
+    if (prhs) {
+      FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_rhs_h), false, true, &S->pack_budget,
+                              st));
+      FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_rhs_g), false, true, &S->pack_budget,
+                              st));
+    }
     FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_apply), true, rp, &S->pack_budget,
                             st, false, rp));
     FDE_TRY(gemm_batch_pack(pool, reinterpret_cast<GemmBatch<float>*>(&ls.r_update), true, rp, &S->pack_budget,

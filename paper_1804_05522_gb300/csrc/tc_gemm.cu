@@ -910,8 +910,13 @@ struct PackJob {
 // the exact remainder lo, written at the swizzled K-major offsets of the
 // shared-memory tile; zeros outside the problem.
 template <bool IS_B>
-__global__ void pack_tiles_kernel(const GemmDesc<float>* __restrict__ descs, const PackJob* __restrict__ jobs, int R,
-                                  int trans, int bf) {
+__global__ void __launch_bounds__(256) pack_tiles_kernel(const GemmDesc<float>* __restrict__ descs,
+                                                         const PackJob* __restrict__ jobs, int R, int trans, int bf) {
+  // the tile (R <= 128 rows x 32 k) is read into shared memory with coalesced
+  // loads (consecutive threads along the operand's contiguous dimension), then
+  // written as the MMA's shared-memory image one 16-byte chunk per thread,
+  // the 8 (4 for BF16) chunks of a row by consecutive threads
+  __shared__ float t[128][tc::BK + 1];
   const PackJob jb = jobs[blockIdx.x];
   const GemmDesc<float> d = descs[jb.z];
   const float* X = IS_B ? d.B : d.A;
@@ -919,40 +924,67 @@ __global__ void pack_tiles_kernel(const GemmDesc<float>* __restrict__ descs, con
   // k-contiguous when op(A) = Aᵀ (A: trans) or op(B) = B (B: !trans)
   const bool kcontig = IS_B ? !trans : trans;
   const bool two_level = d.kblk > 0 && !kcontig;
-  float* hi = jb.dst;
-  float* lo = jb.dst + (size_t)R * tc::BK;
-  auto elem = [&](int r, int c) -> float {
-    const int row = jb.r * R + r, k = jb.t * tc::BK + c;
-    if (row >= nrows || k >= d.k) return 0.f;
-    if (kcontig) return X[(size_t)row * ld + k];
-    long long col = (long long)k * ld;
-    if (two_level) {
-      const int q = k / d.kblk;
-      col = (long long)q * d.kstr + (long long)(k - q * d.kblk) * ld;
+  const int row0 = jb.r * R, k0 = jb.t * tc::BK;
+  for (int e = threadIdx.x; e < R * tc::BK; e += blockDim.x) {
+    int r, c;
+    if (kcontig) {
+      r = e / tc::BK;
+      c = e % tc::BK;
+    } else {
+      r = e % R;
+      c = e / R;
     }
-    return X[col + row];
-  };
+    const int row = row0 + r, k = k0 + c;
+    float v = 0.f;
+    if (row < nrows && k < d.k) {
+      if (kcontig) {
+        v = X[(size_t)row * ld + k];
+      } else {
+        long long col = (long long)k * ld;
+        if (two_level) {
+          const int q = k / d.kblk;
+          col = (long long)q * d.kstr + (long long)(k - q * d.kblk) * ld;
+        }
+        v = X[col + row];
+      }
+    }
+    t[r][c] = v;
+  }
+  __syncthreads();
+  uint8_t* hi = reinterpret_cast<uint8_t*>(jb.dst);
   if (bf) {
     // BF16: dense 64-byte rows in the SW64 layout (pair p of row r: k = 2p,
-    // 2p + 1), the hi tile (R x 64 bytes) then the lo tile
-    uint32_t* hu = reinterpret_cast<uint32_t*>(hi);
-    uint32_t* lu = hu + R * 16;
-    for (int e = threadIdx.x; e < R * (tc::BK / 2); e += blockDim.x) {
-      const int r = e / (tc::BK / 2), p = e % (tc::BK / 2);
-      const uint32_t off = tc::sw64_off(r, p) >> 2;
-      uint32_t l;
-      hu[off] = tc::bf16_pair(elem(r, 2 * p), elem(r, 2 * p + 1), &l);
-      lu[off] = l;
+    // 2p + 1), the hi tile (R x 64 bytes) then the lo tile; chunk q of a row
+    // holds pairs 4q .. 4q + 3
+    uint8_t* lo = hi + (size_t)R * 64;
+    for (int e = threadIdx.x; e < R * 4; e += blockDim.x) {
+      const int r = e >> 2, q = e & 3;
+      uint4 hv, lv;
+      hv.x = tc::bf16_pair(t[r][8 * q + 0], t[r][8 * q + 1], &lv.x);
+      hv.y = tc::bf16_pair(t[r][8 * q + 2], t[r][8 * q + 3], &lv.y);
+      hv.z = tc::bf16_pair(t[r][8 * q + 4], t[r][8 * q + 5], &lv.z);
+      hv.w = tc::bf16_pair(t[r][8 * q + 6], t[r][8 * q + 7], &lv.w);
+      const uint32_t off = tc::sw64_off(r, 4 * q);
+      *reinterpret_cast<uint4*>(hi + off) = hv;
+      *reinterpret_cast<uint4*>(lo + off) = lv;
     }
     return;
   }
-  for (int e = threadIdx.x; e < R * tc::BK; e += blockDim.x) {
-    const int r = e / tc::BK, c = e % tc::BK;
-    const float v = elem(r, c);
-    const uint32_t off = tc::sw_off(r, c) >> 2;
-    const float h = tc::to_tf32(v);
-    hi[off] = h;
-    lo[off] = v - h;
+  uint8_t* lo = hi + (size_t)R * tc::BK * 4;
+  for (int e = threadIdx.x; e < R * 8; e += blockDim.x) {
+    const int r = e >> 3, q = e & 7;
+    float4 h, l;
+    h.x = tc::to_tf32(t[r][4 * q + 0]);
+    h.y = tc::to_tf32(t[r][4 * q + 1]);
+    h.z = tc::to_tf32(t[r][4 * q + 2]);
+    h.w = tc::to_tf32(t[r][4 * q + 3]);
+    l.x = t[r][4 * q + 0] - h.x;
+    l.y = t[r][4 * q + 1] - h.y;
+    l.z = t[r][4 * q + 2] - h.z;
+    l.w = t[r][4 * q + 3] - h.w;
+    const uint32_t off = tc::sw_off(r, 4 * q);
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) = l;
   }
 }
 }  // namespace
