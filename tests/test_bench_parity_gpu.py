@@ -126,6 +126,52 @@ def test_fd2d_n4096_default_run_vs_oracle(lib):
         lib.runner_free(r)
 
 
+def test_fd2d_n16384_default_run_vs_oracle(lib):
+    """The N = 16384 workload (α = 1.2, 1.8; leaf 256, block-Toeplitz FFT
+    residual): its first two steps with every default switch against the
+    oracle's Bartels–Stewart trajectory (tests/golden/fd2d_n16384_oracle.txt,
+    46 minutes of oracle time).
+
+    At this size ||A_y|| is near 1e7, and the FP64 Bartels–Stewart solution
+    itself has a residual of about 3.5e-7 ||C|| (backward stable: ~ε ||A||
+    ||X||), while the refined GPU solution's exact FP64 residual is below
+    2e-9 ||C||.  So the GPU state is certified (summed Frobenius bound below
+    the tolerance) and must agree with the oracle's within the tolerance plus
+    the oracle's own bound; their smooth components (bilinear functionals
+    with the seeded unit vectors) must agree to 1e-10."""
+    name = "fd2d_n16384"
+    w = I.WORKLOADS[name]()
+    N = w.N
+    gold = _golden(name)
+    Uv, Vv = I.projection_vectors(N, 8, seed=0)
+    assert all(O.sym_part_exceeds(op, 0.5) for op in w.ops)
+    U0 = torch.from_numpy(np.asarray(w.u0).ravel(order="F").copy()).to("cuda")
+    r = lib.runner_create(lib.run_params(w, prec=B.FDE_FP32_REFINE), U0.data_ptr())
+    try:
+        bound_fro = 0.0
+        for m in range(1, max(gold) + 1):
+            lib.runner_advance(r, 1)
+            rel, mx, fro = lib.runner_residual(r)
+            bound_fro += O.sylvester_error_bound_fro(fro, 0.5, 0.5)
+            if m not in gold:
+                continue
+            X = _state(lib, r, N)
+            e = gold[m]
+            # the GPU state against the exact loop: certified within the tolerance
+            assert bound_fro <= TOL * e["fro"], (m, bound_fro / e["fro"])
+            ii = np.array([p[0] for p in e["ij"]])
+            jj = np.array([p[1] for p in e["ij"]])
+            err = X[ii, jj] - np.array(e["val"])
+            rel_fro = np.sqrt(N * N * np.mean(err ** 2)) / e["fro"]
+            # ... and the oracle's state within its own (larger) bound of it
+            assert rel_fro <= TOL + e["obound_fro"] / e["fro"], (m, rel_fro, e["obound_fro"] / e["fro"])
+            assert abs(np.linalg.norm(X) - e["fro"]) <= TOL * e["fro"] + e["obound_fro"]
+            for k, v in e["proj"].items():
+                assert abs(Uv[:, k] @ X @ Vv[:, k] - v) <= 1e-10 * e["fro"], (m, k)
+    finally:
+        lib.runner_free(r)
+
+
 def _certified_step(lib, N, steps, monkeypatch, resid=None):
     if resid:
         monkeypatch.setenv("FDE_RESID", resid)
