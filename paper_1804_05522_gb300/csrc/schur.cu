@@ -709,6 +709,170 @@ __global__ void __launch_bounds__(kMaxRowWarps * 32) __maxnreg__(sizeof(T) == 4 
 #undef RV
 }
 
+// Blocks of at most 32 x 32 (FP32): an anti-diagonal wavefront over the
+// block's entries instead of a column-by-column back substitution.  Lane =
+// row i.  Rows are grouped into units (1 row, or the 2 rows of a 2 x 2 block
+// of S) and columns into units from the right (1 column, or the 2 of a 2 x 2
+// block of R); the unit of row i solves column unit u at step base_i + u,
+// base_i = the number of row units below it.  At that step every entry it
+// needs is solved: the rows below in the same columns (earlier steps of the
+// lanes below) and its own row to the right (its earlier steps).  So each
+// step is one pull: rhs = F(i, c) - Σ_{k below} S(i, k) Y(k, c)
+// - Σ_{l right} Y(i, l) R(c, l), independent loads and products, then the
+// unit's 1, 2 or 4-unknown solve.  Y (holding F until solved) and R sit in
+// shared memory, row i of S in registers.
+__global__ void __launch_bounds__(32, 16) trsyl_wave_kernel(const float* __restrict__ Sall, const float* __restrict__ Rall,
+                                                        int ld, const __grid_constant__ TrsylSets sets,
+                                                        float* __restrict__ W, int ldw) {
+  __shared__ float Ys[32][33];    // Ys[i][c]: F(i, c), then Y(i, c)
+  __shared__ float Rs[32][33];    // Rs[c][l] = R(c, l)
+  __shared__ __align__(16) float stg[32 * kStg];  // staging tile of the coupling prologue
+  __shared__ int cu_c0[32], cu_w[32];  // column unit u (from the right): first column, width
+  __shared__ int s_ncu, s_nru;
+  int b = (int)blockIdx.x, si = 0;
+  while (si + 1 < sets.n && b >= sets.s[si].count) {
+    b -= sets.s[si].count;
+    ++si;
+  }
+  const TrsylSet& ps = sets.s[si];
+  const int p = b % ps.nx, q = b / ps.nx;
+  const int n1 = ps.n_x[p], n2 = ps.n_y[q];
+  if (n1 <= 0 || n2 <= 0) return;
+  float* Y = W + ps.lo_x[p] + (size_t)ps.lo_y[q] * ldw;
+  const float* S = Sall + ps.soff_x[p];
+  const float* R = Rall + ps.soff_y[q];
+  const int lane = threadIdx.x;
+  {
+    const int rx = ps.rest_x ? ps.rest_x[p] : 0, ry = ps.rest_y ? ps.rest_y[q] : 0;
+    if (rx > 0 || ry > 0) trsyl_couple<float>(S, R, ld, Y, ldw, n1, n2, rx, ry, 0, n1, stg);
+  }
+  // F (after the coupling) and R into shared memory, zeros outside the block
+  // (every entry the steps read is finite); coalesced along rows
+  for (int c = 0; c < 32; ++c) {
+    Ys[lane][c] = (lane < n1 && c < n2) ? Y[lane + (size_t)c * ldw] : 0.f;
+    Rs[lane][c] = (lane < n2 && c < n2) ? R[lane + (size_t)c * ld] : 0.f;
+  }
+  // this lane's row of S beyond its own row unit, and its unit's 2 x 2 block
+  const bool act = lane < n1;
+  const bool bottom = act && lane > 0 && S[lane + (size_t)(lane - 1) * ld] != 0.f;
+  const bool top = lane + 1 < n1 && S[(lane + 1) + (size_t)lane * ld] != 0.f;
+  const int own_hi = top ? lane + 1 : lane;  // last row of this lane's unit
+  float srow[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) srow[k] = (act && k > own_hi && k < n1) ? S[lane + (size_t)k * ld] : 0.f;
+  const float sii = act ? S[lane + (size_t)lane * ld] : 1.f;
+  float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;  // the unit's 2 x 2 block (both lanes)
+  if (bottom) {
+    s00 = S[(lane - 1) + (size_t)(lane - 1) * ld];
+    s01 = S[(lane - 1) + (size_t)lane * ld];
+    s10 = S[lane + (size_t)(lane - 1) * ld];
+    s11 = sii;
+  } else if (top) {
+    s00 = sii;
+    s01 = S[lane + (size_t)(lane + 1) * ld];
+    s10 = S[(lane + 1) + (size_t)lane * ld];
+    s11 = S[(lane + 1) + (size_t)(lane + 1) * ld];
+  }
+  // row units below each row (ballot over the unit starts), column units
+  const unsigned unit_start = __ballot_sync(0xffffffffu, act && !bottom);  // a unit's top row
+  const int base = __popc(unit_start & ~((2u << own_hi) - 1u));              // units strictly below
+  if (lane == 0) {
+    int u = 0;
+    for (int c = n2 - 1; c >= 0; ++u) {
+      const bool pair = c > 0 && R[c + (size_t)(c - 1) * ld] != 0.f;
+      cu_c0[u] = pair ? c - 1 : c;
+      cu_w[u] = pair ? 2 : 1;
+      c -= pair ? 2 : 1;
+    }
+    s_ncu = u;
+    s_nru = __popc(unit_start);
+  }
+  __syncwarp();
+  const int ncu = s_ncu, nsteps = s_nru + ncu - 1;
+  for (int t = 0; t < nsteps; ++t) {
+    const int u = t - base;
+    const bool go = act && u >= 0 && u < ncu;
+    const int c0 = go ? cu_c0[u] : 0, cw = go ? cu_w[u] : 1;
+    float r0 = go ? Ys[lane][c0] : 0.f, r1 = (go && cw == 2) ? Ys[lane][c0 + 1] : 0.f;
+    // rows below the unit in the unit's columns (solved at earlier steps)
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; k += 2) {
+      a0 += srow[k] * Ys[k][c0];
+      a1 += srow[k + 1] * Ys[k + 1][c0];
+      if (cw == 2) {
+        b0 += srow[k] * Ys[k][c0 + 1];
+        b1 += srow[k + 1] * Ys[k + 1][c0 + 1];
+      }
+    }
+    r0 -= a0 + a1;
+    r1 -= b0 + b1;
+    // this row right of the unit (solved at earlier steps of this lane)
+    const int l0 = c0 + cw;
+    a0 = a1 = b0 = b1 = 0.f;
+#pragma unroll
+    for (int l = 0; l < 32; l += 2) {
+      const bool v0 = l >= l0 && l < n2, v1 = l + 1 >= l0 && l + 1 < n2;
+      const float y0 = v0 ? Ys[lane][l] : 0.f, y1 = v1 ? Ys[lane][l + 1] : 0.f;
+      a0 += y0 * Rs[c0][l];
+      a1 += y1 * Rs[c0][l + 1];
+      if (cw == 2) {
+        b0 += y0 * Rs[c0 + 1][l];
+        b1 += y1 * Rs[c0 + 1][l + 1];
+      }
+    }
+    r0 -= a0 + a1;
+    r1 -= b0 + b1;
+    // the unit's solve; pairs of rows exchange their right-hand sides
+    const bool prow = bottom || top;
+    const int partner = bottom ? lane - 1 : lane + 1;
+    const float pr0 = __shfl_sync(0xffffffffu, r0, prow ? partner : lane);
+    const float pr1 = __shfl_sync(0xffffffffu, r1, prow ? partner : lane);
+    if (go) {
+      const float ra = Rs[c0][c0];
+      float y0, y1 = 0.f;
+      if (!prow && cw == 1) {
+        y0 = r0 / (sii + ra);
+      } else if (!prow) {
+        // [[s + a, b], [c, s + d]] (y(i, c0), y(i, c0 + 1))ᵀ = (r0, r1)ᵀ
+        const float bb = Rs[c0][c0 + 1], cc = Rs[c0 + 1][c0], dd = Rs[c0 + 1][c0 + 1];
+        const float det = (sii + ra) * (sii + dd) - bb * cc;
+        y0 = ((sii + dd) * r0 - bb * r1) / det;
+        y1 = ((sii + ra) * r1 - cc * r0) / det;
+      } else {
+        // top / bottom right-hand sides of the unit
+        const float ft0 = bottom ? pr0 : r0, fb0 = bottom ? r0 : pr0;
+        if (cw == 1) {
+          const float d = (s00 + ra) * (s11 + ra) - s01 * s10;
+          const float yt = ((s11 + ra) * ft0 - s01 * fb0) / d;
+          const float yb = ((s00 + ra) * fb0 - s10 * ft0) / d;
+          y0 = bottom ? yb : yt;
+        } else {
+          const float ft1 = bottom ? pr1 : r1, fb1 = bottom ? r1 : pr1;
+          const float a = ra, bq = Rs[c0][c0 + 1], cq = Rs[c0 + 1][c0], dq = Rs[c0 + 1][c0 + 1];
+          // the blocks of I (x) S2 + R2 (x) I commute: Δ = (S2 + aI)(S2 + dI) - bc I
+          const float tr = s00 + s11 + a + dq, cst = a * dq - bq * cq;
+          const float D00 = s00 * s00 + s01 * s10 + (a + dq) * s00 + cst, D01 = s01 * tr;
+          const float D10 = s10 * tr, D11 = s10 * s01 + s11 * s11 + (a + dq) * s11 + cst;
+          const float dd = D00 * D11 - D01 * D10;
+          const float q00 = D11 / dd, q01 = -D01 / dd, q10 = -D10 / dd, q11 = D00 / dd;
+          const float g1t = (s00 + dq) * ft0 + s01 * fb0 - bq * ft1, g1b = s10 * ft0 + (s11 + dq) * fb0 - bq * fb1;
+          const float g2t = (s00 + a) * ft1 + s01 * fb1 - cq * ft0, g2b = s10 * ft1 + (s11 + a) * fb1 - cq * fb0;
+          const float u0 = q00 * g1t + q01 * g1b, u1 = q10 * g1t + q11 * g1b;  // column c0: top, bottom
+          const float v0 = q00 * g2t + q01 * g2b, v1 = q10 * g2t + q11 * g2b;  // column c0 + 1
+          y0 = bottom ? u1 : u0;
+          y1 = bottom ? v1 : v0;
+        }
+      }
+      Ys[lane][c0] = y0;
+      if (cw == 2) Ys[lane][c0 + 1] = y1;
+    }
+    __syncwarp();
+  }
+  if (act)
+    for (int c = 0; c < n2; ++c) Y[lane + (size_t)c * ldw] = Ys[lane][c];
+}
+
 template <typename T>
 fde_status leaf_trsyl(const T* S, const T* R, int ld, int lmax, const int* d_soff_x, const int* d_lo_x,
                       const int* d_n_x, int nx, const int* d_soff_y, const int* d_lo_y, const int* d_n_y, int ny,
@@ -717,6 +881,15 @@ fde_status leaf_trsyl(const T* S, const T* R, int ld, int lmax, const int* d_sof
   sets.s[0] = TrsylSet{d_soff_x, d_lo_x, d_n_x, nx, d_soff_y, d_lo_y, d_n_y, nx * ny};
   sets.n = 1;
   return leaf_trsyl_sets<T>(S, R, ld, lmax, sets, W, ldw, st, flops);
+}
+
+// FDE_TRSYL_WAVE=0 keeps blocks of at most 32 x 32 on trsyl_kernel.
+static bool trsyl_wave_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("FDE_TRSYL_WAVE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
 }
 
 template <typename T>
@@ -766,6 +939,13 @@ fde_status leaf_trsyl_sets(const T* S, const T* R, int ld, int lmax, const Trsyl
   long long blocks = 0;
   for (int k = 0; k < sets.n; ++k) blocks += sets.s[k].count;
   if (blocks == 0) return FDE_OK;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (lmax <= 32 && trsyl_wave_enabled()) {
+      trsyl_wave_kernel<<<(unsigned)blocks, 32, 0, st>>>(S, R, ld, sets, W, ldw);
+      FDE_LAUNCH("trsyl_wave_kernel");
+      return FDE_OK;
+    }
+  }
   if (rsm)
     trsyl_kernel<T, true><<<(unsigned)blocks, warps * 32, smem_launch, st>>>(S, R, ld, lmax, sets, W, ldw, use_panel,
                                                                              panel_elems);
