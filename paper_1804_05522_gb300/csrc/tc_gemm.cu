@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
           tc_fence_after();
           uint8_t* slot = sm + (size_t)s * slot_bytes;
           const uint32_t a_hi = smem_u32(slot), b_hi = smem_u32(slot + b_hi_off);
-          const uint32_t a_lo = smem_u32(slot + a_lo_off), b_lo = smem_u32(slot + b_lo_off);
+          const uint32_t a_lo = smem_u32(slot + a_lo_off);
           if (bf) {
             // BF16: K = 16 per instruction, 32 bytes along the row; the tile's
             // 32 k are the row's first 64 logical bytes (converted tiles,
@@ -653,10 +653,17 @@ __global__ void __launch_bounds__(kPThreads, 1)
           for (int kk = 0; kk < BK / 8; ++kk) {
             const uint32_t off = kk * 32;  // 8 TF32 = 32 bytes along k inside the swizzle atom
             const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
-            mma_tf32(acc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_tf32_n<BN>(), acc0);
             if (split) {
-              mma_tf32(acc + BN, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc_tf32_n<BN>(), acc0);
+              // B_lo follows B_hi in the slot with the same 8-row swizzle
+              // atoms, so [B_hi; B_lo] is one K-major operand of 2 BN rows:
+              // one N = 2 BN MMA gives A_hi B_hi in columns [0, BN) and the
+              // A_hi B_lo correction in [BN, 2 BN), where A_lo B_hi adds (two
+              // instructions per k-step instead of three; an MMA issues in
+              // about the same time for N = 64 .. 256)
+              mma_tf32(acc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_tf32_n<2 * BN>(), acc0);
               mma_tf32(acc + BN, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc_tf32_n<BN>(), 1u);
+            } else {
+              mma_tf32(acc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc_tf32_n<BN>(), acc0);
             }
           }
           mma_commit(smem_u32(&empty_bar[s]));
