@@ -258,7 +258,7 @@ DF_OPS_PER_FLOP = 7.7
 TRAFFIC_SOURCES = ["paper_1804_05522_gb300/csrc/tc_gemm.cu", "paper_1804_05522_gb300/csrc/dense.cu",
                    "paper_1804_05522_gb300/csrc/dense.cuh", "paper_1804_05522_gb300/csrc/sylv.cu"]
 TRAFFIC = {
-    ("fd2d_n4096", "gemm32tc"): {"bytes_per_launch": 505.2e6, "sources_sha256_16": "8e57d05d5a90975e",
+    ("fd2d_n4096", "gemm32tc"): {"bytes_per_launch": 505.4e6, "sources_sha256_16": "cb37042d6ecb323d",
                                  "profile": "profiles/tc_gemm_kernel_fd2d_n4096_traffic.md"},
 }
 
