@@ -1,5 +1,7 @@
 // Double-float FFT for the incremental FP64-grade residual (arithmetic in
 // df.cuh, transforms in fft_core.cuh).
+#include <stdlib.h>
+
 #include "df.cuh"
 #include "fft_core.cuh"
 #include "fft_df.cuh"
@@ -12,6 +14,23 @@ using namespace df;
 
 constexpr int kThreads = 512;
 
+// Block size of the double-float kernel.  At P = 8192 the transform buffer
+// and the T part take 200 KB of shared memory, so one CTA runs per SM and the
+// block size alone sets the warps that hide the shared-memory and twiddle
+// latencies: 1024 threads (at most 64 registers each, a 24-byte spill) give 32
+// warps per SM against 16 for 512 threads (92 registers, no spill), 3 % less
+// time per launch at N = 4096.  Shorter transforms keep 512 threads: their
+// passes have at most 512 butterflies.
+inline int df_block_threads(int P) {
+  static const int forced = [] {
+    const char* e = getenv("FDE_DF_THREADS");
+    const int v = e ? atoi(e) : 0;
+    return (v == 512 || v == 1024) ? v : 0;
+  }();
+  if (forced) return forced;
+  return P >= 8192 ? 1024 : 512;
+}
+
 // Columns j0 = 2b, j1 = 2b + 1 share one complex transform (x_0 + i x_1):
 //   (T x)_i  = -(g * x)[i+1],   (Tᵀx)_i = -(g ⋆ x)[i-1]   (correlation: conj(ĝ))
 // Ghat and the saved transform are in the digit-reversed order of fft_forward.
@@ -19,7 +38,8 @@ constexpr int kThreads = 512;
 // (cp, cm = c d_± / P as double-float pairs) is formed in double-float
 // arithmetic, the T part kept in shared memory until the Tᵀ part is known, so
 // R is read and written once with a few FP64 operations per element.
-__global__ void __launch_bounds__(kThreads) fd_fft_sub_df_kernel(const float* __restrict__ X, long long xs,
+template <int NT>
+__global__ void __launch_bounds__(NT) fd_fft_sub_df_kernel(const float* __restrict__ X, long long xs,
                                                                 long long xc, int ncols, double* R, long long rs,
                                                                 long long rc, const float4* __restrict__ Ghat,
                                                                 const float4* __restrict__ tw, int P, int logP,
@@ -160,16 +180,26 @@ fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols
   }
   // padded transform buffer + the T part of N rows
   const size_t smem = ((size_t)fft_padded_len(P) + (size_t)N) * sizeof(float4);
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(fd_fft_sub_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)((fft_padded_len(8192) + 4096) * sizeof(float4)));
+  static const cudaError_t attr = [] {
+    const int bytes = (int)((fft_padded_len(8192) + 4096) * sizeof(float4));
+    cudaError_t e = cudaFuncSetAttribute(fd_fft_sub_df_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fd_fft_sub_df_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+  }();
   FDE_CUDA(attr);
+  // FDE_DF_THREADS=512 or 1024 overrides the block size chosen by P
+  const int nt = df_block_threads(P);
   // shift as a double-float pair (host side: FP32 rounding of the value and the remainder)
   const float hi = (float)shift;
   const float2 shift2 = make_float2(hi, (float)(shift - (double)hi));
   ProfScope ps("fft_df", st, flops, 1);
-  fd_fft_sub_df_kernel<<<(ncols + 1) / 2, kThreads, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, cp, cm,
-                                                                shift2, N, scratch, set ? 1 : 0);
+  if (nt == 512)
+    fd_fft_sub_df_kernel<512><<<(ncols + 1) / 2, 512, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP,
+                                                                   cp, cm, shift2, N, scratch, set ? 1 : 0);
+  else
+    fd_fft_sub_df_kernel<1024><<<(ncols + 1) / 2, 1024, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP,
+                                                                     cp, cm, shift2, N, scratch, set ? 1 : 0);
   FDE_LAUNCH("fd_fft_sub_df_kernel");
   return FDE_OK;
 }
