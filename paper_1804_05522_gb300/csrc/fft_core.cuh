@@ -80,6 +80,30 @@ struct ArDF {
   }
 };
 
+// Double-float with unnormalised additions and fused complex products
+// (df::df_add_un, df::c_mul_fused): about a quarter fewer FP32 operations per
+// radix-8 butterfly for about 1.4 times the normwise error of ArDF.  For
+// transforms of updates, whose error is scaled by the update's norm; exact
+// residuals keep ArDF.  Values leave a pass unnormalised (hi + lo exact, lo a
+// few u of the operands' norm); every product renormalises.
+struct ArDFFast : ArDF {
+  __device__ static C mul(C a, C b) { return df::c_mul_fused(a, b); }
+  __device__ static C add(C a, C b) { return df::c_add_un(a, b); }
+  __device__ static C sub(C a, C b) { return df::c_sub_un(a, b); }
+  __device__ static C mul_w1(C a) {
+    const float2 re = make_float2(a.x, a.y), im = make_float2(a.z, a.w);
+    const float2 p = df::df_mul(df::df_add_un(re, im), rsqrt2());
+    const float2 q = df::df_mul(df::df_add_un(im, df::df_neg(re)), rsqrt2());
+    return make_float4(p.x, p.y, q.x, q.y);
+  }
+  __device__ static C mul_w3(C a) {
+    const float2 re = make_float2(a.x, a.y), im = make_float2(a.z, a.w);
+    const float2 p = df::df_mul(df::df_add_un(im, df::df_neg(re)), rsqrt2());
+    const float2 q = df::df_mul(df::df_add_un(re, im), rsqrt2());
+    return make_float4(p.x, p.y, -q.x, -q.y);
+  }
+};
+
 struct ArF32 {
   using C = float2;
   __device__ static C zero() { return make_float2(0.f, 0.f); }

@@ -22,12 +22,9 @@ constexpr int kThreads = 512;
 // time per launch at N = 4096.  Shorter transforms keep 512 threads: their
 // passes have at most 512 butterflies.
 inline int df_block_threads(int P) {
-  static const int forced = [] {
-    const char* e = getenv("FDE_DF_THREADS");
-    const int v = e ? atoi(e) : 0;
-    return (v == 512 || v == 1024) ? v : 0;
-  }();
-  if (forced) return forced;
+  const char* e = getenv("FDE_DF_THREADS");
+  const int forced = e ? atoi(e) : 0;
+  if (forced == 512 || forced == 1024) return forced;
   return P >= 8192 ? 1024 : 512;
 }
 
@@ -38,7 +35,7 @@ inline int df_block_threads(int P) {
 // (cp, cm = c d_± / P as double-float pairs) is formed in double-float
 // arithmetic, the T part kept in shared memory until the Tᵀ part is known, so
 // R is read and written once with a few FP64 operations per element.
-template <int NT>
+template <class Ar, int NT>
 __global__ void __launch_bounds__(NT) fd_fft_sub_df_kernel(const float* __restrict__ X, long long xs,
                                                                 long long xc, int ncols, double* R, long long rs,
                                                                 long long rc, const float4* __restrict__ Ghat,
@@ -59,15 +56,15 @@ __global__ void __launch_bounds__(NT) fd_fft_sub_df_kernel(const float* __restri
     buf[fft_pad(n)] = v;
   }
   __syncthreads();
-  fft_forward<ArDF>(buf, logP, tw);
+  fft_forward<Ar>(buf, logP, tw);
   float4* Xh = scratch + (size_t)blockIdx.x * P;
   for (int k = threadIdx.x; k < P; k += blockDim.x) {
     const float4 v = buf[fft_pad(k)];
     Xh[k] = v;
-    buf[fft_pad(k)] = ArDF::mul(v, Ghat[k]);
+    buf[fft_pad(k)] = Ar::mul(v, Ghat[k]);
   }
   __syncthreads();
-  fft_inverse<ArDF>(buf, logP, tw);
+  fft_inverse<Ar>(buf, logP, tw);
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const float4 t = buf[fft_pad(i + 1)];
     const float2 c = cp[i];
@@ -75,9 +72,9 @@ __global__ void __launch_bounds__(NT) fd_fft_sub_df_kernel(const float* __restri
     side[i] = make_float4(a0.x, a0.y, a1.x, a1.y);
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < P; k += blockDim.x) buf[fft_pad(k)] = ArDF::mul(Xh[k], c_conj(Ghat[k]));
+  for (int k = threadIdx.x; k < P; k += blockDim.x) buf[fft_pad(k)] = Ar::mul(Xh[k], c_conj(Ghat[k]));
   __syncthreads();
-  fft_inverse<ArDF>(buf, logP, tw);
+  fft_inverse<Ar>(buf, logP, tw);
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const float4 t = buf[fft_pad((i - 1 + P) & (P - 1))];
     const float4 sT = side[i];
@@ -182,24 +179,39 @@ fde_status fd_apply_sub_df(const float* X, long long xs, long long xc, int ncols
   const size_t smem = ((size_t)fft_padded_len(P) + (size_t)N) * sizeof(float4);
   static const cudaError_t attr = [] {
     const int bytes = (int)((fft_padded_len(8192) + 4096) * sizeof(float4));
-    cudaError_t e = cudaFuncSetAttribute(fd_fft_sub_df_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fd_fft_sub_df_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
+    const void* fns[] = {(const void*)fd_fft_sub_df_kernel<ArDFFast, 512>,
+                         (const void*)fd_fft_sub_df_kernel<ArDFFast, 1024>,
+                         (const void*)fd_fft_sub_df_kernel<ArDF, 512>, (const void*)fd_fft_sub_df_kernel<ArDF, 1024>};
+    for (const void* f : fns) {
+      const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }();
   FDE_CUDA(attr);
-  // FDE_DF_THREADS=512 or 1024 overrides the block size chosen by P
+  // FDE_DF_THREADS=512 or 1024 overrides the block size chosen by P;
+  // FDE_DF_FAST=0 selects the normalised arithmetic of the exact residuals
   const int nt = df_block_threads(P);
+  const char* fast_env = getenv("FDE_DF_FAST");
+  const bool fast = !(fast_env && fast_env[0] == '0');
   // shift as a double-float pair (host side: FP32 rounding of the value and the remainder)
   const float hi = (float)shift;
   const float2 shift2 = make_float2(hi, (float)(shift - (double)hi));
   ProfScope ps("fft_df", st, flops, 1);
-  if (nt == 512)
-    fd_fft_sub_df_kernel<512><<<(ncols + 1) / 2, 512, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP,
-                                                                   cp, cm, shift2, N, scratch, set ? 1 : 0);
+  const unsigned grid = (unsigned)((ncols + 1) / 2);
+  const int set_i = set ? 1 : 0;
+  if (fast && nt == 1024)
+    fd_fft_sub_df_kernel<ArDFFast, 1024><<<grid, 1024, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP,
+                                                                   cp, cm, shift2, N, scratch, set_i);
+  else if (fast)
+    fd_fft_sub_df_kernel<ArDFFast, 512><<<grid, 512, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, cp,
+                                                                 cm, shift2, N, scratch, set_i);
+  else if (nt == 1024)
+    fd_fft_sub_df_kernel<ArDF, 1024><<<grid, 1024, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, cp,
+                                                               cm, shift2, N, scratch, set_i);
   else
-    fd_fft_sub_df_kernel<1024><<<(ncols + 1) / 2, 1024, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP,
-                                                                     cp, cm, shift2, N, scratch, set ? 1 : 0);
+    fd_fft_sub_df_kernel<ArDF, 512><<<grid, 512, smem, st>>>(X, xs, xc, ncols, R, rs, rc, Ghat, tw, P, logP, cp, cm,
+                                                             shift2, N, scratch, set_i);
   FDE_LAUNCH("fd_fft_sub_df_kernel");
   return FDE_OK;
 }

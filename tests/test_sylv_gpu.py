@@ -287,6 +287,41 @@ def test_incremental_df_residual_matches_fp64(lib, monkeypatch, N, leaf, alpha):
         assert _relerr(runs[mode], Uref) <= 1e-8, mode
 
 
+@pytest.mark.parametrize("N", [1000, 4096])
+def test_df_update_arithmetic_variants_agree(lib, monkeypatch, N):
+    """The double-float update R -= A(δ) in its default arithmetic
+    (unnormalised additions, fused complex products) and in the normalised
+    arithmetic of the exact residuals, at 512 and 1024 threads per column
+    pair (transform lengths 2048 and 8192): with three fixed sweeps from zero,
+    every update double-float, each variant reaches relres < 1e-9 and agrees
+    with the normalised 512-thread run to 1e-12.  The update's rounding, a few
+    u^2 |A| |δ| (u = 2^-24), only moves the FP32 rounding of the next sweep's
+    right-hand side, whose correction is already 1e-6 of the solution."""
+    w = I.fd2d(N=N, alpha=(1.3, 1.7), steps=50, leaf=128)
+    C = I.random_matrix_fast(N, N, seed=31)
+    monkeypatch.setenv("FDE_RESID", "df")
+    sols = {}
+    for fast in ("0", "1"):
+        for threads in ("512", "1024"):
+            monkeypatch.setenv("FDE_DF_FAST", fast)
+            monkeypatch.setenv("FDE_DF_THREADS", threads)
+            P = Pair(lib, w, B.FDE_FP32_REFINE)
+            try:
+                r = lib.sylv_get_refine(P.s)
+                r.fixed_sweeps = 3
+                lib.sylv_set_refine(P.s, r)
+                Cd = _dev(C)
+                Xd = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+                relres, sweeps = lib.sylv_step(P.s, Cd.data_ptr(), Xd.data_ptr(), N)
+                assert sweeps == 3 and relres < 1e-9, (fast, threads, relres)
+                sols[(fast, threads)] = _host(Xd, N, N)
+            finally:
+                P.close()
+    base = sols[("0", "512")]
+    for key, X in sols.items():
+        assert _relerr(X, base) <= 1e-12, (key, _relerr(X, base))
+
+
 def test_time_step_predictor(lib, monkeypatch):
     """The linear predictor X = 2 X_n - X_{n-1} (residual from the stored
     history, no operator application) gives the same trajectory as plain warm
