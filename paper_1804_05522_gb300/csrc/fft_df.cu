@@ -17,10 +17,10 @@ constexpr int kThreads = 512;
 // Block size of the double-float kernel.  At P = 8192 the transform buffer
 // and the T part take 200 KB of shared memory, so one CTA runs per SM and the
 // block size alone sets the warps that hide the shared-memory and twiddle
-// latencies: 1024 threads (at most 64 registers each, a 24-byte spill) give 32
-// warps per SM against 16 for 512 threads (92 registers, no spill), 3 % less
-// time per launch at N = 4096.  Shorter transforms keep 512 threads: their
-// passes have at most 512 butterflies.
+// latencies: 1024 threads (at most 64 registers each, spilling a few dozen
+// bytes) give 32 warps per SM against 16 for 512 threads (92 registers, no
+// spill), 3 % less time per launch at N = 4096.  Shorter transforms keep 512
+// threads: their passes have at most 512 butterflies.
 inline int df_block_threads(int P) {
   const char* e = getenv("FDE_DF_THREADS");
   const int forced = e ? atoi(e) : 0;
