@@ -1,4 +1,6 @@
 // Block-Toeplitz FFT products with the shifted GL operator for N > 4096.
+#include <stdlib.h>
+
 #include "df.cuh"
 #include "fft_block.cuh"
 #include "fft_core.cuh"
@@ -193,6 +195,13 @@ fde_status block_apply(const void* X, bool x_is_float, long long xs, long long x
     return launch_block<ArF32, float>((const float*)X, xs, xc, ncols, Cm, Y, ys, yc, mode, g, Hhat_f32, tw_f32, dp,
                                       dm, c, shift, N, (float2*)scratch, pair_chunk, st);
   if (prec == kBlockDF) {
+    // FP32 input is an update δ: its transforms take the cheaper arithmetic
+    // (error scaled by |δ|) unless FDE_DF_FAST=0; FP64 input (exact residuals)
+    // keeps the normalised arithmetic
+    const char* fast_env = getenv("FDE_DF_FAST");
+    if (x_is_float && !(fast_env && fast_env[0] == '0'))
+      return launch_block<ArDFFast, float>((const float*)X, xs, xc, ncols, Cm, Y, ys, yc, mode, g, Hhat_df, tw_df, dp,
+                                           dm, c, shift, N, (float4*)scratch, pair_chunk, st);
     if (x_is_float)
       return launch_block<ArDF, float>((const float*)X, xs, xc, ncols, Cm, Y, ys, yc, mode, g, Hhat_df, tw_df, dp, dm,
                                        c, shift, N, (float4*)scratch, pair_chunk, st);

@@ -287,12 +287,13 @@ def test_incremental_df_residual_matches_fp64(lib, monkeypatch, N, leaf, alpha):
         assert _relerr(runs[mode], Uref) <= 1e-8, mode
 
 
-@pytest.mark.parametrize("N", [1000, 4096])
+@pytest.mark.parametrize("N", [1000, 4096, 6000])
 def test_df_update_arithmetic_variants_agree(lib, monkeypatch, N):
     """The double-float update R -= A(δ) in its default arithmetic
     (unnormalised additions, fused complex products) and in the normalised
     arithmetic of the exact residuals, at 512 and 1024 threads per column
-    pair (transform lengths 2048 and 8192): with three fixed sweeps from zero,
+    pair (transform lengths 2048 and 8192; N = 6000 takes the block-Toeplitz
+    form, whose block size is fixed): with three fixed sweeps from zero,
     every update double-float, each variant reaches relres < 1e-9 and agrees
     with the normalised 512-thread run to 1e-12.  The update's rounding, a few
     u^2 |A| |δ| (u = 2^-24), only moves the FP32 rounding of the next sweep's
@@ -302,7 +303,7 @@ def test_df_update_arithmetic_variants_agree(lib, monkeypatch, N):
     monkeypatch.setenv("FDE_RESID", "df")
     sols = {}
     for fast in ("0", "1"):
-        for threads in ("512", "1024"):
+        for threads in ("512", "1024") if N <= 4096 else ("512",):
             monkeypatch.setenv("FDE_DF_FAST", fast)
             monkeypatch.setenv("FDE_DF_THREADS", threads)
             P = Pair(lib, w, B.FDE_FP32_REFINE)
