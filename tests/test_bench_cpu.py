@@ -48,3 +48,42 @@ def test_reference_arm_fits_its_budget(monkeypatch, capsys):
     n = int(sample.split("by (N/")[1].split(")")[0])
     assert 256 <= n < 1024 and n % 32 == 0
     assert out["value"] > 0 and out["steps"] == 3
+
+
+def test_traffic_figure_needs_unchanged_sources(tmp_path, monkeypatch):
+    """The bench line's `traffic` comes from a stored ncu capture; it is
+    reported only while the digest of the sources it depends on is the one
+    stored with it, and is null (with the reason) once they change or when no
+    capture exists for the kernel and workload."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    src = tmp_path / "kernel.cu"
+    src.write_text("first version")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES", ["kernel.cu"])
+    digest = bench.sources_digest(["kernel.cu"])
+    monkeypatch.setattr(bench, "TRAFFIC", {("work", "fam"): {"bytes_per_launch": 123.0e6,
+                                                             "sources_sha256_16": digest,
+                                                             "profile": "profiles/k.md"}})
+    value, why = bench.traffic_for("work", "fam")
+    assert value == 123.0e6 and "profiles/k.md" in why
+    src.write_text("second version")
+    value, why = bench.traffic_for("work", "fam")
+    assert value is None and "changed" in why
+    value, why = bench.traffic_for("work", "other")
+    assert value is None and "no ncu capture" in why
+
+
+def test_stored_traffic_entries_are_well_formed():
+    """Every stored capture names an existing profile summary, a 16-hex-digit
+    digest and a positive byte count."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    for key, t in bench.TRAFFIC.items():
+        assert t["bytes_per_launch"] > 0, key
+        assert len(t["sources_sha256_16"]) == 16 and int(t["sources_sha256_16"], 16) >= 0, key
+        assert os.path.exists(os.path.join(ROOT, t["profile"])), key
+    for f in bench.TRAFFIC_SOURCES:
+        assert os.path.exists(os.path.join(ROOT, f)), f
