@@ -249,6 +249,41 @@ def _qts_coupling_sign(S, R, F, base=128):
     return np.hstack([Y1, Y2])
 
 
+def _qts_wrong_r_block(S, R, F, base=128):
+    """The recursive quasi-triangular stage with the R coupling taken from the
+    lower-left block of R (zero for a quasi-triangular R, so the coupling is
+    dropped) instead of R12 transposed."""
+    m, n = F.shape
+    if m <= base and n <= base:
+        return _orig["quasi_triangular_sylvester"](S, R, F, base)
+    if m >= n:
+        h = m // 2 + (1 if S[m // 2, m // 2 - 1] != 0.0 else 0)
+        Y2 = _qts_wrong_r_block(S[h:, h:], R, F[h:], base)
+        Y1 = _qts_wrong_r_block(S[:h, :h], R, F[:h] - S[:h, h:] @ Y2, base)
+        return np.vstack([Y1, Y2])
+    h = n // 2 + (1 if R[n // 2, n // 2 - 1] != 0.0 else 0)
+    Y2 = _qts_wrong_r_block(S, R[h:, h:], F[:, h:], base)
+    Y1 = _qts_wrong_r_block(S, R[:h, :h], F[:, :h] - Y2 @ R[h:, :h], base)
+    return np.hstack([Y1, Y2])
+
+
+def _qts_splits_2x2(S, R, F, base=128):
+    """The recursive quasi-triangular stage cutting at k // 2 even inside a
+    2 x 2 diagonal block (the subdiagonal entry is then lost from both halves)."""
+    m, n = F.shape
+    if m <= base and n <= base:
+        return _orig["quasi_triangular_sylvester"](S, R, F, base)
+    if m >= n:
+        h = m // 2
+        Y2 = _qts_splits_2x2(S[h:, h:], R, F[h:], base)
+        Y1 = _qts_splits_2x2(S[:h, :h], R, F[:h] - S[:h, h:] @ Y2, base)
+        return np.vstack([Y1, Y2])
+    h = n // 2
+    Y2 = _qts_splits_2x2(S, R[h:, h:], F[:, h:], base)
+    Y1 = _qts_splits_2x2(S, R[:h, :h], F[:, :h] - Y2 @ R[:h, h:].T, base)
+    return np.hstack([Y1, Y2])
+
+
 MUTATIONS = [
     ("gl_weights", _gl_shifted_order, lambda: P.test_gl_first_weights_exact(1.5)),
     ("gl_toeplitz", _toeplitz_transposed, lambda: P.test_toeplitz_structure(1.3)),
@@ -285,6 +320,8 @@ MUTATIONS = [
     ("fde1d_run_tv", _tv1d_old_level, P.test_time_dependent_1d_coefficients_at_new_level),
     ("solve_dense", _solve_transposed, P.test_solve_dense_residual),
     ("quasi_triangular_sylvester", _qts_coupling_sign, P.test_quasi_triangular_sylvester_recursive_vs_kronecker),
+    ("quasi_triangular_sylvester", _qts_wrong_r_block, P.test_quasi_triangular_sylvester_recursive_vs_kronecker),
+    ("quasi_triangular_sylvester", _qts_splits_2x2, P.test_quasi_triangular_sylvester_recursive_vs_kronecker),
 ]
 
 
